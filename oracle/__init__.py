@@ -1,0 +1,259 @@
+"""Oracle for the aura-exchange codec (TeraAgent, Sec. 2.1, 2.2.1, 2.3).
+
+TEST INFRASTRUCTURE ONLY.  The tests, ``__graft_entry__.smoke()`` and the
+benchmark's CPU-baseline leg may import this package; the product path
+(``paper_2509_24063_gb300``) never does.  It is a thin ctypes wrapper over the
+plain single-threaded C code in ``tera_oracle.c`` (built with gcc, no CUDA).
+
+Every array here is a host numpy array.  Record arenas are ``uint8`` arrays of
+64-byte units; pair ``p`` occupies units ``[off[p] + p, off[p+1] + p + 1)``:
+one 64-byte buffer header, then its records.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "liboracle.so")
+SOURCES = [os.path.join(HERE, "tera_oracle.c")]
+
+OK, EINVAL, ENOMEM, ECAPACITY, ECORRUPT, EDOMAIN, EREFMISMATCH = range(7)
+MODE_RAW, MODE_XOR, MODE_RESIDUAL = 0, 1, 2
+REC = 64
+HDR = 64
+
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (IEEE double, no contraction, no fast-math)."""
+    newest = max(os.path.getmtime(s) for s in SOURCES + [os.path.join(HERE, "tera_oracle.h")])
+    if force or not os.path.exists(LIB_PATH) or os.path.getmtime(LIB_PATH) < newest:
+        tmp = LIB_PATH + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
+               "-fno-fast-math", "-o", tmp] + SOURCES + ["-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, LIB_PATH)
+    return LIB_PATH
+
+
+class Grid(C.Structure):
+    _fields_ = [("lo", C.c_double * 3), ("hi", C.c_double * 3), ("n", C.c_int32 * 3),
+                ("w", C.c_double)]
+
+
+def make_grid(lo, hi, n, w) -> Grid:
+    g = Grid()
+    for a in range(3):
+        g.lo[a], g.hi[a], g.n[a] = float(lo[a]), float(hi[a]), int(n[a])
+    g.w = float(w)
+    return g
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = C.CDLL(LIB_PATH)
+            P = C.c_void_p
+            u64, i64, u32, i32 = C.c_uint64, C.c_int64, C.c_uint32, C.c_int32
+            G = C.POINTER(Grid)
+            L.or_grid_check.argtypes = [G]
+            L.or_axis_edges.argtypes = [G, C.c_int, P]
+            L.or_axis_edges.restype = None
+            L.or_classify.argtypes = [G, P, P, P, i64, P, P]
+            L.or_pair_lists.argtypes = [G, P, P, i64, P, P, P, u64]
+            L.or_pack.argtypes = [P, P, u64, P, P, u32, P]
+            L.or_pack.restype = None
+            L.or_encode_pair.argtypes = [P, u64, P, u64, u32, u32, u32, P, u64, P, P]
+            L.or_decode_pair.argtypes = [P, u64, P, u64, u32, u32, P, u64, P]
+            L.or_wire_slabs.argtypes = [u64, P, P, P]
+            L.or_wire_slabs.restype = None
+            L.or_encode_all.argtypes = [u64, u32, u32, P, P, P, P, P, P, P, P, P]
+            L.or_decode_all.argtypes = [u64, u32, P, P, P, P, P, u64, P]
+            L.or_exchange_iteration.argtypes = [G, P, P, i64, u32, u32, P, P, P, P, P, P, P,
+                                                P, P, u64, P, P, P, P, P, P, u64, P, P]
+            for f in ("or_grid_check", "or_classify", "or_pair_lists", "or_encode_pair",
+                      "or_decode_pair", "or_encode_all", "or_decode_all",
+                      "or_exchange_iteration"):
+                getattr(L, f).restype = C.c_int
+            _lib = L
+    return _lib
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def n_pairs(grid: Grid) -> int:
+    return int(grid.n[0]) * int(grid.n[1]) * int(grid.n[2]) * 27
+
+
+def grid_check(grid: Grid) -> int:
+    return lib().or_grid_check(C.byref(grid))
+
+
+def axis_edges(grid: Grid, axis: int) -> np.ndarray:
+    e = np.zeros(int(grid.n[axis]) + 1, dtype=np.float64)
+    lib().or_axis_edges(C.byref(grid), axis, _p(e))
+    return e
+
+
+def classify(grid: Grid, x, y, z):
+    x, y, z = (np.ascontiguousarray(a, dtype=np.float64) for a in (x, y, z))
+    n = x.shape[0]
+    owner = np.zeros(n, dtype=np.int32)
+    mask = np.zeros(n, dtype=np.uint32)
+    st = lib().or_classify(C.byref(grid), _p(x), _p(y), _p(z), n, _p(owner), _p(mask))
+    return st, owner, mask
+
+
+def pair_lists(grid: Grid, owner, mask, idx_capacity=None):
+    P = n_pairs(grid)
+    n = owner.shape[0]
+    cnt = np.zeros(P, dtype=np.uint64)
+    off = np.zeros(P + 1, dtype=np.uint64)
+    total = int(sum(bin(int(m)).count("1") for m in mask[owner >= 0])) if n < 4096 else \
+        int(np.unpackbits(mask[owner >= 0].view(np.uint8)).sum())
+    cap = total if idx_capacity is None else idx_capacity
+    idx = np.zeros(max(cap, 1), dtype=np.uint32)
+    st = lib().or_pair_lists(C.byref(grid), _p(np.ascontiguousarray(owner)),
+                             _p(np.ascontiguousarray(mask)), n, _p(cnt), _p(off), _p(idx), cap)
+    return st, cnt, off, idx[:int(off[-1])] if st == OK else idx
+
+
+def soa_cols(soa: dict):
+    """The seven float64 columns in record word order w1..w7."""
+    return [np.ascontiguousarray(soa[k], dtype=np.float64)
+            for k in ("x", "y", "z", "diameter", "volume", "adherence", "density")]
+
+
+def pack(soa: dict, pair_off, pair_idx, class_id: int = 1) -> np.ndarray:
+    P = pair_off.shape[0] - 1
+    units = int(pair_off[-1]) + P
+    arena = np.zeros(units * REC, dtype=np.uint8)
+    ids = np.ascontiguousarray(soa["id"], dtype=np.uint64)
+    cols = soa_cols(soa)
+    arr = (C.c_void_p * 7)(*[c.ctypes.data for c in cols])
+    idx = np.ascontiguousarray(pair_idx, dtype=np.uint32)
+    if idx.size == 0:
+        idx = np.zeros(1, dtype=np.uint32)
+    lib().or_pack(_p(ids), arr, P, _p(np.ascontiguousarray(pair_off)), _p(idx), class_id,
+                  _p(arena))
+    return arena
+
+
+def encode_pair(msg: np.ndarray, ref: np.ndarray, class_id=1, mode=MODE_XOR, pair=0):
+    """msg, ref: (m, 8) / (r, 8) uint64 records.  Returns (status, wire bytes, ref_next)."""
+    msg = np.ascontiguousarray(msg, dtype=np.uint64).reshape(-1, 8)
+    ref = np.ascontiguousarray(ref, dtype=np.uint64).reshape(-1, 8)
+    m, r = msg.shape[0], ref.shape[0]
+    cap = 64 + 4 * (r + m) + 64 * m + 16
+    wire = np.zeros(cap, dtype=np.uint8)
+    wl = np.zeros(1, dtype=np.uint64)
+    nxt = np.zeros((max(m, 1), 8), dtype=np.uint64)
+    st = lib().or_encode_pair(_p(msg), m, _p(ref), r, class_id, mode, pair, _p(wire), cap,
+                              _p(wl), _p(nxt))
+    return st, wire[:int(wl[0])].copy(), nxt[:m].copy()
+
+
+def decode_pair(wire: np.ndarray, ref: np.ndarray, class_id=1, pair=0, out_cap=None):
+    wire = np.ascontiguousarray(wire, dtype=np.uint8)
+    ref = np.ascontiguousarray(ref, dtype=np.uint64).reshape(-1, 8)
+    cap = out_cap if out_cap is not None else max(1, wire.size // 4 + ref.shape[0])
+    out = np.zeros((max(cap, 1), 8), dtype=np.uint64)
+    m = np.zeros(1, dtype=np.uint64)
+    buf = wire if wire.size else np.zeros(1, dtype=np.uint8)
+    st = lib().or_decode_pair(_p(buf), wire.size, _p(ref), ref.shape[0], class_id, pair,
+                              _p(out), cap, _p(m))
+    return st, out[:int(m[0])].copy()
+
+
+def wire_slabs(pair_off, ref_off=None) -> np.ndarray:
+    P = pair_off.shape[0] - 1
+    wo = np.zeros(P + 1, dtype=np.uint64)
+    lib().or_wire_slabs(P, _p(np.ascontiguousarray(pair_off, dtype=np.uint64)),
+                        None if ref_off is None else _p(np.ascontiguousarray(ref_off,
+                                                                             dtype=np.uint64)),
+                        _p(wo))
+    return wo
+
+
+def encode_all(rec_arena, pair_off, ref_arena=None, ref_off=None, class_id=1, mode=MODE_XOR,
+               reset=None):
+    """Returns (status, wire, wire_off, wire_len, ref_next arena)."""
+    P = pair_off.shape[0] - 1
+    wo = wire_slabs(pair_off, ref_off)
+    wire = np.zeros(max(int(wo[-1]), 1), dtype=np.uint8)
+    wl = np.zeros(P, dtype=np.uint64)
+    nxt = np.zeros((int(pair_off[-1]) + P) * REC, dtype=np.uint8)
+    rs = None if reset is None else np.ascontiguousarray(reset, dtype=np.uint8)
+    st = lib().or_encode_all(P, class_id, mode, _p(rec_arena), _p(pair_off),
+                             _p(ref_arena), _p(ref_off), _p(rs), _p(wire), _p(wo), _p(wl),
+                             _p(nxt))
+    return st, wire, wo, wl, nxt
+
+
+def decode_all(wire, wire_off, ref_arena=None, ref_off=None, class_id=1, cap_units=None):
+    """Returns (status, recv arena, recv_off)."""
+    P = wire_off.shape[0] - 1
+    if cap_units is None:
+        cap_units = P + int(wire.size // 4 + (0 if ref_off is None else int(ref_off[-1])) + 1)
+    recv = np.zeros(cap_units * REC, dtype=np.uint8)
+    ro = np.zeros(P + 1, dtype=np.uint64)
+    st = lib().or_decode_all(P, class_id, _p(wire), _p(wire_off), _p(ref_arena), _p(ref_off),
+                             _p(recv), cap_units, _p(ro))
+    used = (int(ro[-1]) + P) * REC
+    return st, recv[:used].copy(), ro
+
+
+def arena_pair(arena: np.ndarray, off: np.ndarray, p: int) -> np.ndarray:
+    """Records of pair p (excluding its header) as an (n, 8) uint64 view."""
+    a, b = int(off[p]) + p + 1, int(off[p + 1]) + p + 1
+    return arena[a * REC:b * REC].view(np.uint64).reshape(-1, 8)
+
+
+def exchange_iteration(grid: Grid, soa: dict, ref=None, recv_ref=None, class_id=1,
+                       mode=MODE_XOR):
+    """One whole iteration (classify, lists, pack, encode, decode) in one C call.
+
+    ref / recv_ref: (arena, off) of the sender / receiver reference or None.
+    Returns a dict of every output plus per-step seconds."""
+    n = int(soa["x"].shape[0])
+    P = n_pairs(grid)
+    ids = np.ascontiguousarray(soa["id"], dtype=np.uint64)
+    cols = soa_cols(soa)
+    arr = (C.c_void_p * 7)(*[c.ctypes.data for c in cols])
+    st, owner, mask = classify(grid, cols[0], cols[1], cols[2])
+    total = int(np.unpackbits(mask[owner >= 0].view(np.uint8)).sum()) if n else 0
+    cap = max(total, 1)
+    r_tot = 0 if ref is None else int(ref[1][-1])
+    owner = np.zeros(n, dtype=np.int32)
+    mask = np.zeros(n, dtype=np.uint32)
+    cnt = np.zeros(P, dtype=np.uint64)
+    off = np.zeros(P + 1, dtype=np.uint64)
+    idx = np.zeros(cap, dtype=np.uint32)
+    rec = np.zeros((total + P) * REC, dtype=np.uint8)
+    wo = np.zeros(P + 1, dtype=np.uint64)
+    wire = np.zeros(64 * P + 4 * (r_tot + total) + 64 * total + 16 * P + 16, dtype=np.uint8)
+    wl = np.zeros(P, dtype=np.uint64)
+    nxt = np.zeros((total + P) * REC, dtype=np.uint8)
+    recv = np.zeros((total + P) * REC, dtype=np.uint8)
+    ro = np.zeros(P + 1, dtype=np.uint64)
+    ts = np.zeros(4, dtype=np.float64)
+    ra, rof = (None, None) if ref is None else ref
+    va, vof = (None, None) if recv_ref is None else recv_ref
+    st = lib().or_exchange_iteration(C.byref(grid), _p(ids), arr, n, class_id, mode, _p(ra),
+                                     _p(rof), _p(va), _p(vof), _p(owner), _p(mask), _p(cnt),
+                                     _p(off), _p(idx), cap, _p(rec), _p(wire), _p(wo), _p(wl),
+                                     _p(nxt), _p(recv), total + P, _p(ro), _p(ts))
+    return dict(status=st, owner=owner, mask=mask, pair_count=cnt, pair_off=off,
+                pair_idx=idx[:total], rec=rec, wire=wire, wire_off=wo, wire_len=wl,
+                ref_next=nxt, recv=recv, recv_off=ro, t_steps=ts)

@@ -1,0 +1,580 @@
+/*
+ * Oracle for the aura-exchange codec.  TEST INFRASTRUCTURE ONLY (see
+ * tera_oracle.h): plain loops, one agent or record at a time, in the order the
+ * paper describes the steps.  No blocking, fusion or reordering.
+ *
+ * Paper sections followed:
+ *   Sec. 2.1  "Aura Update": partitioning grid, aura = agents within the
+ *             interaction distance of a neighbouring box.
+ *   Sec. 2.2.1 TeraAgent IO: serialization copies each block into one
+ *             contiguous buffer; the class identity is written once; the
+ *             receiver reinterprets the buffer in place.
+ *   Sec. 2.3  Data transfer minimization: per sender/receiver-pair reference,
+ *             matching/reorder (B), difference serialization (C), restore and
+ *             defragmentation (D).
+ *   Sec. 3.11 compression after the difference (LZ4 in the paper; here the
+ *             significant-byte packer defined below).
+ */
+#define _POSIX_C_SOURCE 199309L
+#include "tera_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#include <time.h>
+
+#define REC_WORDS 8
+#define REC_BYTES 64
+#define TAIO_MAGIC 0x4F494154u /* bytes 'T','A','I','O' */
+#define WIRE_MAGIC 0x41524554u /* bytes 'T','E','R','A' */
+#define FMT_VERSION 1u
+#define HDR_BYTES 64u
+
+/* ---------- little-endian byte helpers (explicit, no type punning) ---------- */
+
+static uint64_t get_le(const uint8_t* p, int nbytes) {
+  uint64_t v = 0;
+  for (int b = 0; b < nbytes; ++b) v |= (uint64_t)p[b] << (8 * b);
+  return v;
+}
+
+static void put_le(uint8_t* p, uint64_t v, int nbytes) {
+  for (int b = 0; b < nbytes; ++b) p[b] = (uint8_t)(v >> (8 * b));
+}
+
+static uint64_t rec_word(const uint8_t* rec, int w) { return get_le(rec + 8 * w, 8); }
+
+static uint64_t f64_bits(double d) {
+  uint64_t u;
+  memcpy(&u, &d, 8);
+  return u;
+}
+
+/* ---------- grid (Sec. 2.1; Sec. 2.4 "Partitioning Grid") ---------- */
+
+int or_grid_check(const or_grid* g) {
+  for (int a = 0; a < 3; ++a) {
+    if (g->n[a] < 1) return OR_EINVAL;
+    if (!(g->lo[a] < g->hi[a])) return OR_EINVAL;
+  }
+  /* The aura must be narrower than a partitioning box (Sec. 2.1): w is
+   * positive and below the smallest box side on every axis. */
+  if (!(g->w > 0.0)) return OR_EINVAL;
+  for (int a = 0; a < 3; ++a) {
+    int n = g->n[a];
+    double* e = (double*)malloc(sizeof(double) * (size_t)(n + 1));
+    if (!e) return OR_ENOMEM;
+    or_axis_edges(g, a, e);
+    for (int k = 0; k < n; ++k) {
+      if (!(g->w < e[k + 1] - e[k])) {
+        free(e);
+        return OR_EINVAL;
+      }
+    }
+    free(e);
+  }
+  return OR_OK;
+}
+
+/* Box edges along one axis: e[k] = lo + ((hi - lo) * k) / n, and e[n] = hi. */
+void or_axis_edges(const or_grid* g, int axis, double* e) {
+  int n = g->n[axis];
+  double lo = g->lo[axis], hi = g->hi[axis];
+  for (int k = 0; k < n; ++k) e[k] = lo + ((hi - lo) * (double)k) / (double)n;
+  e[n] = hi;
+}
+
+/* ---------- O1: classification (Sec. 2.1 "Aura Update") ----------
+ * Ownership is half-open [e[i], e[i+1]).  An agent is in the aura of the
+ * neighbour box at offset o (per axis -1, 0, +1) when it lies within w of that
+ * box in the L-infinity sense: for o = -1, x < e[i] + w; for o = +1,
+ * x >= e[i+1] - w; o = 0 always qualifies.  The neighbour must exist. */
+int or_classify(const or_grid* g, const double* x, const double* y, const double* z,
+                int64_t n, int32_t* owner, uint32_t* mask) {
+  int st = or_grid_check(g);
+  if (st != OR_OK) return st;
+  double* edges[3];
+  for (int a = 0; a < 3; ++a) {
+    edges[a] = (double*)malloc(sizeof(double) * (size_t)(g->n[a] + 1));
+    or_axis_edges(g, a, edges[a]);
+  }
+  int status = OR_OK;
+  for (int64_t i = 0; i < n; ++i) {
+    double v[3] = {x[i], y[i], z[i]};
+    int idx[3];
+    int qual[3][3]; /* qual[axis][o + 1] */
+    int inside = 1;
+    for (int a = 0; a < 3; ++a) {
+      if (!(v[a] >= g->lo[a] && v[a] < g->hi[a])) inside = 0; /* NaN fails too */
+    }
+    if (!inside) {
+      owner[i] = -1;
+      mask[i] = 0;
+      status = OR_EDOMAIN;
+      continue;
+    }
+    for (int a = 0; a < 3; ++a) {
+      const double* e = edges[a];
+      int na = g->n[a];
+      int cnt = 0;
+      for (int k = 1; k <= na - 1; ++k)
+        if (v[a] >= e[k]) ++cnt;
+      idx[a] = cnt;
+      qual[a][0] = (cnt > 0) && (v[a] < e[cnt] + g->w);
+      qual[a][1] = 1;
+      qual[a][2] = (cnt < na - 1) && (v[a] >= e[cnt + 1] - g->w);
+    }
+    owner[i] = idx[0] + g->n[0] * (idx[1] + g->n[1] * idx[2]);
+    uint32_t m = 0;
+    for (int oz = -1; oz <= 1; ++oz)
+      for (int oy = -1; oy <= 1; ++oy)
+        for (int ox = -1; ox <= 1; ++ox) {
+          if (ox == 0 && oy == 0 && oz == 0) continue;
+          if (qual[0][ox + 1] && qual[1][oy + 1] && qual[2][oz + 1]) {
+            int bit = (ox + 1) + 3 * (oy + 1) + 9 * (oz + 1);
+            m |= 1u << bit;
+          }
+        }
+    mask[i] = m;
+  }
+  for (int a = 0; a < 3; ++a) free(edges[a]);
+  return status;
+}
+
+/* Per-pair lists: for agent i in ascending order and each set bit b in
+ * ascending order, append i to the list of pair owner(i)*27 + b. */
+int or_pair_lists(const or_grid* g, const int32_t* owner, const uint32_t* mask, int64_t n,
+                  uint64_t* pair_count, uint64_t* pair_off, uint32_t* pair_idx,
+                  uint64_t idx_capacity) {
+  uint64_t n_pairs = (uint64_t)g->n[0] * (uint64_t)g->n[1] * (uint64_t)g->n[2] * 27u;
+  for (uint64_t p = 0; p < n_pairs; ++p) pair_count[p] = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    if (owner[i] < 0) continue;
+    for (int b = 0; b < 27; ++b)
+      if (mask[i] >> b & 1u) pair_count[(uint64_t)owner[i] * 27u + (uint64_t)b] += 1;
+  }
+  pair_off[0] = 0;
+  for (uint64_t p = 0; p < n_pairs; ++p) pair_off[p + 1] = pair_off[p] + pair_count[p];
+  if (pair_off[n_pairs] > idx_capacity) return OR_ECAPACITY;
+  uint64_t* fill = (uint64_t*)calloc(n_pairs ? n_pairs : 1, sizeof(uint64_t));
+  if (!fill) return OR_ENOMEM;
+  for (int64_t i = 0; i < n; ++i) {
+    if (owner[i] < 0) continue;
+    for (int b = 0; b < 27; ++b) {
+      if (!(mask[i] >> b & 1u)) continue;
+      uint64_t p = (uint64_t)owner[i] * 27u + (uint64_t)b;
+      pair_idx[pair_off[p] + fill[p]] = (uint32_t)i;
+      fill[p] += 1;
+    }
+  }
+  free(fill);
+  return OR_OK;
+}
+
+/* ---------- O2: serialization (Sec. 2.2.1 "Serialization") ----------
+ * Arena layout: pair p occupies 64-byte units [pair_off[p] + p,
+ * pair_off[p+1] + p + 1): one buffer header (class id written once, as the
+ * paper replaces the vtable pointer by a class identifier), then its records. */
+static void write_taio_header(uint8_t* h, uint32_t class_id, uint32_t pair, uint64_t n) {
+  memset(h, 0, HDR_BYTES);
+  put_le(h + 0, TAIO_MAGIC, 4);
+  put_le(h + 4, FMT_VERSION, 2);
+  put_le(h + 6, REC_BYTES, 2);
+  put_le(h + 8, class_id, 4);
+  put_le(h + 12, pair, 4);
+  put_le(h + 16, n, 8);
+}
+
+void or_pack(const uint64_t* id, const double* const cols[7], uint64_t n_pairs,
+             const uint64_t* pair_off, const uint32_t* pair_idx, uint32_t class_id,
+             uint8_t* arena) {
+  for (uint64_t p = 0; p < n_pairs; ++p) {
+    uint8_t* buf = arena + (pair_off[p] + p) * REC_BYTES;
+    uint64_t m = pair_off[p + 1] - pair_off[p];
+    write_taio_header(buf, class_id, (uint32_t)p, m);
+    for (uint64_t k = 0; k < m; ++k) {
+      uint32_t i = pair_idx[pair_off[p] + k];
+      uint8_t* rec = buf + HDR_BYTES + k * REC_BYTES;
+      put_le(rec, id[i], 8);
+      for (int c = 0; c < 7; ++c) put_le(rec + 8 * (c + 1), f64_bits(cols[c][i]), 8);
+    }
+  }
+}
+
+/* ---------- O4: significant-byte length of one word ----------
+ * L = number of low-order bytes needed to hold the value (0 for zero). */
+static int sig_bytes(uint64_t v) {
+  int L = 0;
+  while (v != 0) {
+    L += 1;
+    v >>= 8;
+  }
+  return L;
+}
+
+/* ---------- O3 + O4: encode one pair (Sec. 2.3 steps B and C) ---------- */
+
+typedef struct {
+  uint64_t id;
+  uint64_t k;
+} id_pos;
+
+static int cmp_id_pos(const void* a, const void* b) {
+  uint64_t x = ((const id_pos*)a)->id, y = ((const id_pos*)b)->id;
+  return (x > y) - (x < y);
+}
+
+/* Index of the message record with this id, or -1. */
+static int64_t find_id(const id_pos* sorted, uint64_t m, uint64_t id) {
+  uint64_t lo = 0, hi = m;
+  while (lo < hi) {
+    uint64_t mid = lo + (hi - lo) / 2;
+    if (sorted[mid].id < id) lo = mid + 1;
+    else hi = mid;
+  }
+  if (lo < m && sorted[lo].id == id) return (int64_t)sorted[lo].k;
+  return -1;
+}
+
+static uint64_t round16(uint64_t v) { return (v + 15u) & ~(uint64_t)15u; }
+
+static void write_wire_header(uint8_t* h, uint32_t class_id, uint32_t mode, uint64_t n_slots,
+                              uint64_t n_new, uint64_t n_holes, uint64_t payload,
+                              uint32_t pair, uint64_t msg_bytes) {
+  memset(h, 0, HDR_BYTES);
+  put_le(h + 0, WIRE_MAGIC, 4);
+  put_le(h + 4, FMT_VERSION, 2);
+  put_le(h + 6, REC_BYTES, 2);
+  put_le(h + 8, class_id, 4);
+  put_le(h + 12, mode, 4);
+  put_le(h + 16, n_slots, 8);
+  put_le(h + 24, n_new, 8);
+  put_le(h + 32, n_holes, 8);
+  put_le(h + 40, payload, 8);
+  put_le(h + 48, pair, 4);
+  put_le(h + 56, msg_bytes, 8);
+}
+
+enum { KIND_MATCH = 0, KIND_HOLE = 1, KIND_NEW = 2 };
+
+int or_encode_pair(const uint8_t* msg, uint64_t m, const uint8_t* ref, uint64_t r,
+                   uint32_t class_id, uint32_t mode, uint32_t pair, uint8_t* wire,
+                   uint64_t wire_cap, uint64_t* wire_len, uint8_t* ref_next) {
+  if (mode != OR_MODE_RAW && mode != OR_MODE_XOR) return OR_EINVAL;
+  if (mode == OR_MODE_RAW) r = 0; /* no reference: every record is new */
+
+  /* Step B (matching): a map from id to message position. */
+  id_pos* sorted = (id_pos*)malloc(sizeof(id_pos) * (size_t)(m ? m : 1));
+  uint8_t* matched = (uint8_t*)calloc(m ? m : 1, 1);
+  int64_t* src = (int64_t*)malloc(sizeof(int64_t) * (size_t)(r ? r : 1));
+  int status = OR_OK;
+  if (!sorted || !matched || !src) {
+    status = OR_ENOMEM;
+    goto done;
+  }
+  for (uint64_t k = 0; k < m; ++k) {
+    sorted[k].id = rec_word(msg + k * REC_BYTES, 0);
+    sorted[k].k = k;
+  }
+  qsort(sorted, (size_t)m, sizeof(id_pos), cmp_id_pos);
+  for (uint64_t k = 1; k < m; ++k)
+    if (sorted[k].id == sorted[k - 1].id) {
+      status = OR_EINVAL; /* ids must be unique within a message */
+      goto done;
+    }
+  /* Reference slot j keeps its position: it is matched with the message
+   * record carrying the same id, else it becomes a placeholder (hole). */
+  uint64_t n_holes = 0;
+  for (uint64_t j = 0; j < r; ++j) {
+    int64_t k = find_id(sorted, m, rec_word(ref + j * REC_BYTES, 0));
+    src[j] = k;
+    if (k < 0) {
+      n_holes += 1;
+    } else {
+      if (matched[k]) {
+        status = OR_EINVAL; /* duplicate id in the reference */
+        goto done;
+      }
+      matched[k] = 1;
+    }
+  }
+  /* Records absent from the reference are appended in message order. */
+  uint64_t n_new = 0;
+  for (uint64_t k = 0; k < m; ++k)
+    if (!matched[k]) n_new += 1;
+  uint64_t n_codes = r + n_new;
+
+  /* Step C (difference) + byte packing: first the sizes, then the bytes. */
+  uint64_t payload = 0;
+  for (uint64_t j = 0; j < r; ++j) {
+    if (src[j] < 0) continue; /* hole: no payload */
+    const uint8_t* cur = msg + (uint64_t)src[j] * REC_BYTES;
+    for (int w = 0; w < REC_WORDS; ++w)
+      payload += (uint64_t)sig_bytes(rec_word(cur, w) ^ rec_word(ref + j * REC_BYTES, w));
+  }
+  for (uint64_t k = 0; k < m; ++k) {
+    if (matched[k]) continue;
+    for (int w = 0; w < REC_WORDS; ++w)
+      payload += (uint64_t)sig_bytes(rec_word(msg + k * REC_BYTES, w));
+  }
+  uint64_t msg_bytes = round16(HDR_BYTES + 4u * n_codes + payload);
+  *wire_len = msg_bytes;
+  if (msg_bytes > wire_cap) {
+    status = OR_ECAPACITY;
+    goto done;
+  }
+  memset(wire, 0, (size_t)msg_bytes);
+  write_wire_header(wire, class_id, mode, r, n_new, n_holes, payload, pair, msg_bytes);
+  uint8_t* codes = wire + HDR_BYTES;
+  uint8_t* pay = wire + HDR_BYTES + 4u * n_codes;
+  uint64_t off = 0;
+  uint64_t e = 0;
+  /* Reference slots, in slot order. */
+  for (uint64_t j = 0; j < r; ++j, ++e) {
+    if (src[j] < 0) {
+      put_le(codes + 4 * e, 0xFu, 4); /* placeholder: word-0 code 0xF */
+      continue;
+    }
+    const uint8_t* cur = msg + (uint64_t)src[j] * REC_BYTES;
+    const uint8_t* base = ref + j * REC_BYTES;
+    uint32_t code = 0;
+    for (int w = 0; w < REC_WORDS; ++w) {
+      uint64_t d = rec_word(cur, w) ^ rec_word(base, w);
+      int L = sig_bytes(d);
+      code |= (uint32_t)L << (4 * w);
+      put_le(pay + off, d, L);
+      off += (uint64_t)L;
+    }
+    put_le(codes + 4 * e, code, 4);
+  }
+  /* New records, in message order, written raw. */
+  for (uint64_t k = 0; k < m; ++k) {
+    if (matched[k]) continue;
+    const uint8_t* cur = msg + k * REC_BYTES;
+    uint32_t code = 0;
+    for (int w = 0; w < REC_WORDS; ++w) {
+      uint64_t d = rec_word(cur, w);
+      int L = sig_bytes(d);
+      code |= (uint32_t)L << (4 * w);
+      put_le(pay + off, d, L);
+      off += (uint64_t)L;
+    }
+    put_le(codes + 4 * e, code, 4);
+    e += 1;
+  }
+  /* New sender reference: matched records (current values) in slot order,
+   * then the new records; the same sequence the receiver reconstructs. */
+  {
+    uint64_t q = 0;
+    for (uint64_t j = 0; j < r; ++j) {
+      if (src[j] < 0) continue;
+      memcpy(ref_next + q * REC_BYTES, msg + (uint64_t)src[j] * REC_BYTES, REC_BYTES);
+      q += 1;
+    }
+    for (uint64_t k = 0; k < m; ++k) {
+      if (matched[k]) continue;
+      memcpy(ref_next + q * REC_BYTES, msg + k * REC_BYTES, REC_BYTES);
+      q += 1;
+    }
+  }
+done:
+  free(sorted);
+  free(matched);
+  free(src);
+  return status;
+}
+
+/* ---------- O5: decode one pair (Sec. 2.3 step D) ---------- */
+int or_decode_pair(const uint8_t* wire, uint64_t wire_avail, const uint8_t* ref, uint64_t r,
+                   uint32_t class_id, uint32_t pair, uint8_t* out, uint64_t out_cap,
+                   uint64_t* m_out) {
+  *m_out = 0;
+  if (wire_avail < HDR_BYTES) return OR_ECORRUPT;
+  if (get_le(wire + 0, 4) != WIRE_MAGIC) return OR_ECORRUPT;
+  if (get_le(wire + 4, 2) != FMT_VERSION) return OR_ECORRUPT;
+  if (get_le(wire + 6, 2) != REC_BYTES) return OR_ECORRUPT;
+  if (get_le(wire + 8, 4) != class_id) return OR_ECORRUPT;
+  if (get_le(wire + 48, 4) != pair) return OR_ECORRUPT;
+  uint64_t mode = get_le(wire + 12, 4);
+  uint64_t n_slots = get_le(wire + 16, 8);
+  uint64_t n_new = get_le(wire + 24, 8);
+  uint64_t n_holes = get_le(wire + 32, 8);
+  uint64_t payload = get_le(wire + 40, 8);
+  uint64_t msg_bytes = get_le(wire + 56, 8);
+  if (mode == OR_MODE_RAW) {
+    if (n_slots != 0) return OR_ECORRUPT;
+  } else if (mode == OR_MODE_XOR) {
+    if (n_slots != r) return OR_EREFMISMATCH;
+  } else {
+    return OR_ECORRUPT;
+  }
+  if (n_slots > wire_avail || n_new > wire_avail || payload > wire_avail) return OR_ECORRUPT;
+  uint64_t n_codes = n_slots + n_new;
+  if (msg_bytes != round16(HDR_BYTES + 4u * n_codes + payload)) return OR_ECORRUPT;
+  if (msg_bytes > wire_avail) return OR_ECORRUPT;
+  const uint8_t* codes = wire + HDR_BYTES;
+  const uint8_t* pay = wire + HDR_BYTES + 4u * n_codes;
+  uint64_t off = 0, holes = 0, count = 0;
+  for (uint64_t e = 0; e < n_codes; ++e) {
+    uint32_t code = (uint32_t)get_le(codes + 4 * e, 4);
+    if ((code & 0xFu) == 0xFu) {
+      /* placeholder: only in a reference slot, and no other nibble set */
+      if (e >= n_slots || (code >> 4) != 0) return OR_ECORRUPT;
+      holes += 1;
+      continue;
+    }
+    for (int w = 0; w < REC_WORDS; ++w)
+      if (((code >> (4 * w)) & 0xFu) > 8u) return OR_ECORRUPT;
+    if (e < n_slots && (code & 0xFu) != 0) return OR_ECORRUPT; /* same id => zero delta */
+    if (count >= out_cap) return OR_ECAPACITY;
+    uint8_t* rec = out + count * REC_BYTES;
+    for (int w = 0; w < REC_WORDS; ++w) {
+      int L = (int)((code >> (4 * w)) & 0xFu);
+      if (off + (uint64_t)L > payload) return OR_ECORRUPT;
+      uint64_t d = get_le(pay + off, L); /* zero-extended */
+      off += (uint64_t)L;
+      uint64_t v = (e < n_slots) ? (d ^ rec_word(ref + e * REC_BYTES, w)) : d;
+      put_le(rec + 8 * w, v, 8);
+    }
+    count += 1;
+  }
+  if (off != payload) return OR_ECORRUPT;
+  if (holes != n_holes) return OR_ECORRUPT;
+  *m_out = count;
+  return OR_OK;
+}
+
+/* ---------- arena drivers ---------- */
+
+/* Wire slab of pair p: an upper bound on its message, so that every message
+ * has a fixed place before its size is known:
+ *   round16(64 + 4 (r_p + m_p) + 64 m_p). */
+void or_wire_slabs(uint64_t n_pairs, const uint64_t* pair_off, const uint64_t* ref_off,
+                   uint64_t* wire_off) {
+  wire_off[0] = 0;
+  for (uint64_t p = 0; p < n_pairs; ++p) {
+    uint64_t m = pair_off[p + 1] - pair_off[p];
+    uint64_t r = ref_off ? ref_off[p + 1] - ref_off[p] : 0;
+    wire_off[p + 1] = wire_off[p] + round16(HDR_BYTES + 4u * (r + m) + REC_BYTES * m);
+  }
+}
+
+static int check_taio_header(const uint8_t* h, uint32_t class_id, uint32_t pair, uint64_t n) {
+  if (get_le(h + 0, 4) != TAIO_MAGIC) return OR_ECORRUPT;
+  if (get_le(h + 4, 2) != FMT_VERSION) return OR_ECORRUPT;
+  if (get_le(h + 6, 2) != REC_BYTES) return OR_ECORRUPT;
+  if (get_le(h + 8, 4) != class_id) return OR_ECORRUPT;
+  if (get_le(h + 12, 4) != pair) return OR_ECORRUPT;
+  if (get_le(h + 16, 8) != n) return OR_ECORRUPT;
+  return OR_OK;
+}
+
+int or_encode_all(uint64_t n_pairs, uint32_t class_id, uint32_t mode, const uint8_t* rec_arena,
+                  const uint64_t* pair_off, const uint8_t* ref_arena, const uint64_t* ref_off,
+                  const uint8_t* reset, uint8_t* wire, const uint64_t* wire_off,
+                  uint64_t* wire_len, uint8_t* ref_next) {
+  int status = OR_OK;
+  for (uint64_t p = 0; p < n_pairs; ++p) {
+    uint64_t m = pair_off[p + 1] - pair_off[p];
+    uint64_t r = ref_arena ? ref_off[p + 1] - ref_off[p] : 0;
+    const uint8_t* msg_buf = rec_arena + (pair_off[p] + p) * REC_BYTES;
+    const uint8_t* ref_buf = ref_arena ? ref_arena + (ref_off[p] + p) * REC_BYTES : NULL;
+    int st = check_taio_header(msg_buf, class_id, (uint32_t)p, m);
+    if (st == OR_OK && ref_buf && mode != OR_MODE_RAW && !(reset && reset[p]))
+      st = check_taio_header(ref_buf, class_id, (uint32_t)p, r);
+    uint32_t pm = (reset && reset[p]) ? (uint32_t)OR_MODE_RAW : mode;
+    uint8_t* nxt = ref_next + (pair_off[p] + p) * REC_BYTES;
+    if (st == OR_OK) {
+      write_taio_header(nxt, class_id, (uint32_t)p, m);
+      st = or_encode_pair(msg_buf + HDR_BYTES, m, ref_buf ? ref_buf + HDR_BYTES : NULL, r,
+                          class_id, pm,
+                          (uint32_t)p, wire + wire_off[p], wire_off[p + 1] - wire_off[p],
+                          &wire_len[p], nxt + HDR_BYTES);
+    } else {
+      wire_len[p] = 0;
+    }
+    if (st != OR_OK && status == OR_OK) status = st;
+  }
+  return status;
+}
+
+int or_decode_all(uint64_t n_pairs, uint32_t class_id, const uint8_t* wire,
+                  const uint64_t* wire_off, const uint8_t* ref_arena, const uint64_t* ref_off,
+                  uint8_t* recv, uint64_t recv_cap_units, uint64_t* recv_off) {
+  /* Receive-buffer sizes come from the headers: m_p = n_slots - n_holes + n_new. */
+  int status = OR_OK;
+  recv_off[0] = 0;
+  for (uint64_t p = 0; p < n_pairs; ++p) {
+    const uint8_t* h = wire + wire_off[p];
+    uint64_t avail = wire_off[p + 1] - wire_off[p];
+    uint64_t m = 0;
+    if (avail >= HDR_BYTES && get_le(h, 4) == WIRE_MAGIC) {
+      uint64_t ns = get_le(h + 16, 8), nn = get_le(h + 24, 8), nh = get_le(h + 32, 8);
+      if (nh <= ns && ns <= avail && nn <= avail) m = ns - nh + nn;
+    }
+    recv_off[p + 1] = recv_off[p] + m;
+  }
+  if (recv_off[n_pairs] + n_pairs > recv_cap_units) return OR_ECAPACITY;
+  for (uint64_t p = 0; p < n_pairs; ++p) {
+    uint64_t r = ref_arena ? ref_off[p + 1] - ref_off[p] : 0;
+    const uint8_t* ref_buf = ref_arena ? ref_arena + (ref_off[p] + p) * REC_BYTES : NULL;
+    uint8_t* out = recv + (recv_off[p] + p) * REC_BYTES;
+    uint64_t cap = recv_off[p + 1] - recv_off[p];
+    uint64_t got = 0;
+    int st = OR_OK;
+    uint64_t avail = wire_off[p + 1] - wire_off[p];
+    int uses_ref = avail >= HDR_BYTES && get_le(wire + wire_off[p] + 12, 4) == OR_MODE_XOR;
+    if (ref_buf && uses_ref) st = check_taio_header(ref_buf, class_id, (uint32_t)p, r);
+    if (st == OR_OK)
+      st = or_decode_pair(wire + wire_off[p], avail, ref_buf ? ref_buf + HDR_BYTES : NULL, r,
+                          class_id, (uint32_t)p, out + HDR_BYTES, cap, &got);
+    if (st == OR_OK && got != cap) st = OR_ECORRUPT;
+    write_taio_header(out, class_id, (uint32_t)p, cap);
+    if (st != OR_OK && status == OR_OK) status = st;
+  }
+  return status;
+}
+
+/* ---------- whole iteration (CPU baseline) ---------- */
+
+
+static double now_s(void) {
+  struct timespec ts;
+  clock_gettime(CLOCK_MONOTONIC, &ts);
+  return (double)ts.tv_sec + 1e-9 * (double)ts.tv_nsec;
+}
+
+int or_exchange_iteration(const or_grid* g, const uint64_t* id, const double* const cols[7],
+                          int64_t n, uint32_t class_id, uint32_t mode,
+                          const uint8_t* ref_arena, const uint64_t* ref_off,
+                          const uint8_t* recv_ref_arena, const uint64_t* recv_ref_off,
+                          int32_t* owner, uint32_t* mask, uint64_t* pair_count,
+                          uint64_t* pair_off, uint32_t* pair_idx, uint64_t idx_capacity,
+                          uint8_t* rec_arena, uint8_t* wire, uint64_t* wire_off,
+                          uint64_t* wire_len, uint8_t* ref_next, uint8_t* recv,
+                          uint64_t recv_cap_units, uint64_t* recv_off, double* t_steps) {
+  uint64_t n_pairs = (uint64_t)g->n[0] * (uint64_t)g->n[1] * (uint64_t)g->n[2] * 27u;
+  double t0 = now_s();
+  int st = or_classify(g, cols[0], cols[1], cols[2], n, owner, mask);
+  if (st != OR_OK) return st;
+  st = or_pair_lists(g, owner, mask, n, pair_count, pair_off, pair_idx, idx_capacity);
+  if (st != OR_OK) return st;
+  double t1 = now_s();
+  or_pack(id, cols, n_pairs, pair_off, pair_idx, class_id, rec_arena);
+  double t2 = now_s();
+  or_wire_slabs(n_pairs, pair_off, ref_off, wire_off);
+  st = or_encode_all(n_pairs, class_id, mode, rec_arena, pair_off, ref_arena, ref_off, NULL,
+                     wire, wire_off, wire_len, ref_next);
+  if (st != OR_OK) return st;
+  double t3 = now_s();
+  st = or_decode_all(n_pairs, class_id, wire, wire_off, recv_ref_arena, recv_ref_off, recv,
+                     recv_cap_units, recv_off);
+  double t4 = now_s();
+  if (t_steps) {
+    t_steps[0] = t1 - t0;
+    t_steps[1] = t2 - t1;
+    t_steps[2] = t3 - t2;
+    t_steps[3] = t4 - t3;
+  }
+  return st;
+}

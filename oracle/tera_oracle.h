@@ -1,0 +1,92 @@
+/*
+ * Oracle for the aura-exchange codec: a plain, slow, single-threaded CPU
+ * restatement of what the TeraAgent aura update computes (paper Sec. 2.1,
+ * Sec. 2.2.1, Sec. 2.3).  TEST INFRASTRUCTURE ONLY: the tests, the smoke check
+ * and the benchmark's CPU-baseline leg may call it; the product path never does.
+ * It shares no header, helper or table with the CUDA library.
+ *
+ * Records are 64 bytes = 8 little-endian 64-bit words:
+ *   w0 id | w1 x | w2 y | w3 z | w4 diameter | w5 volume | w6 adherence | w7 density
+ */
+#ifndef TERA_ORACLE_H
+#define TERA_ORACLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  OR_OK = 0,
+  OR_EINVAL = 1,
+  OR_ENOMEM = 2,
+  OR_ECAPACITY = 3,
+  OR_ECORRUPT = 4,
+  OR_EDOMAIN = 5,
+  OR_EREFMISMATCH = 6
+};
+
+enum { OR_MODE_RAW = 0, OR_MODE_XOR = 1, OR_MODE_RESIDUAL = 2 };
+
+typedef struct {
+  double lo[3], hi[3];
+  int32_t n[3];
+  double w;
+} or_grid;
+
+/* Grid edges and parameter check (Sec. 2.1 partitioning grid; Sec. 2.4). */
+int or_grid_check(const or_grid* g);
+void or_axis_edges(const or_grid* g, int axis, double* e /* n[axis]+1 */);
+
+/* O1: owner box and 26-neighbour aura mask per agent (Sec. 2.1 "Aura Update"). */
+int or_classify(const or_grid* g, const double* x, const double* y, const double* z,
+                int64_t n, int32_t* owner, uint32_t* mask);
+
+/* Per-pair stable lists (message p = agents of box s whose mask has bit b,
+ * ascending agent index; p = s*27 + b). */
+int or_pair_lists(const or_grid* g, const int32_t* owner, const uint32_t* mask, int64_t n,
+                  uint64_t* pair_count, uint64_t* pair_off, uint32_t* pair_idx,
+                  uint64_t idx_capacity);
+
+/* O2: TeraAgent IO serialization of every pair message (Sec. 2.2.1). */
+void or_pack(const uint64_t* id, const double* const cols[7], uint64_t n_pairs,
+             const uint64_t* pair_off, const uint32_t* pair_idx, uint32_t class_id,
+             uint8_t* arena);
+
+/* O3+O4: match, XOR delta and byte packing of one pair message (Sec. 2.3). */
+int or_encode_pair(const uint8_t* msg, uint64_t m, const uint8_t* ref, uint64_t r,
+                   uint32_t class_id, uint32_t mode, uint32_t pair, uint8_t* wire,
+                   uint64_t wire_cap, uint64_t* wire_len, uint8_t* ref_next);
+
+/* O5: decode and defragment one pair message (Sec. 2.3 step D). */
+int or_decode_pair(const uint8_t* wire, uint64_t wire_avail, const uint8_t* ref, uint64_t r,
+                   uint32_t class_id, uint32_t pair, uint8_t* out, uint64_t out_cap,
+                   uint64_t* m_out);
+
+/* Arena-level drivers (every pair of one iteration). */
+void or_wire_slabs(uint64_t n_pairs, const uint64_t* pair_off, const uint64_t* ref_off,
+                   uint64_t* wire_off);
+int or_encode_all(uint64_t n_pairs, uint32_t class_id, uint32_t mode, const uint8_t* rec_arena,
+                  const uint64_t* pair_off, const uint8_t* ref_arena, const uint64_t* ref_off,
+                  const uint8_t* reset, uint8_t* wire, const uint64_t* wire_off,
+                  uint64_t* wire_len, uint8_t* ref_next);
+int or_decode_all(uint64_t n_pairs, uint32_t class_id, const uint8_t* wire,
+                  const uint64_t* wire_off, const uint8_t* ref_arena, const uint64_t* ref_off,
+                  uint8_t* recv, uint64_t recv_cap_units, uint64_t* recv_off);
+
+/* Whole iteration, for the CPU baseline timing. */
+int or_exchange_iteration(const or_grid* g, const uint64_t* id, const double* const cols[7],
+                          int64_t n, uint32_t class_id, uint32_t mode,
+                          const uint8_t* ref_arena, const uint64_t* ref_off,
+                          const uint8_t* recv_ref_arena, const uint64_t* recv_ref_off,
+                          int32_t* owner, uint32_t* mask, uint64_t* pair_count,
+                          uint64_t* pair_off, uint32_t* pair_idx, uint64_t idx_capacity,
+                          uint8_t* rec_arena, uint8_t* wire, uint64_t* wire_off,
+                          uint64_t* wire_len, uint8_t* ref_next, uint8_t* recv,
+                          uint64_t recv_cap_units, uint64_t* recv_off, double* t_steps);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
