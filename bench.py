@@ -1,0 +1,387 @@
+"""Benchmark of the GB300 aura exchange (classification, serialization,
+difference encoding, byte packing, decoding) on a synthetic agent workload.
+
+One step = one whole iteration of the exchange over every pair of one
+population state.  States are generated on the device before timing (inputs
+resident in HBM); each timed step consumes the next state of the series, so
+the references chain exactly as in a simulation.  Every state (64 B/agent)
+is far larger than L2, so no L2 flush is needed between steps.
+
+Prints ONE JSON line (rank 0).  `--impl reference` times the CPU oracle on
+the host cores instead, on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "aura-exchange agents/s and encode+decode GB/s (% HBM peak); bytes/agent"
+
+# Algorithmic bytes per launch of each kernel, from the totals of the launches
+# ("Kernels and their rooflines").  N agents, E records, R
+# reference slots, H placeholders, A new records, Y payload bytes.
+def kernel_bytes(name, t):
+    N, E, R, A, Y = t["agents"], t["records"], t["ref_slots"], t["new_records"], \
+        t["payload_bytes"]
+    M = E  # matched + new = records
+    table = {
+        "classify_kernel": 32 * N,
+        "emit_kernel": 8 * N + 8 * E,
+        "rs_hist_kernel": 4 * E,
+        "rs_scatter_kernel": 16 * E,
+        "pack_kernel": (4 + 64 + 64 + 16 + 4) * E,
+        "enc_match_kernel": (64 + 16 + 4 + 4 + 4) * R + 64 * (R - t["holes"]),
+        "enc_new_kernel": 4 * E + (64 + 16) * A,
+        "enc_emit_kernel": 4 * R + 128 * (R - t["holes"]) + 4 * E + 64 * A + 4 * A + Y + 64 * M,
+        "dec_sum_kernel": 4 * (R + A),
+        "dec_emit_kernel": 4 * (R + A) + Y + 64 * (R - t["holes"]) + 64 * M,
+    }
+    return table.get(name)
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            sel = [] if self.gpu is None else [f"--id={self.gpu}"]
+            self.proc = subprocess.Popen(
+                ["nvidia-smi"] + sel + [f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        for line in (self.out or "").splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append(dict(sm=float(f[1]), smax=float(f[2]), hw=f[5], hwt=f[6], swt=f[7],
+                                 pcap=f[8]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        reasons = set()
+        for r in rows:
+            for k, name in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"),
+                            ("swt", "sw_thermal_slowdown"), ("pcap", "sw_power_cap")):
+                if r[k].lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(r["sm"] for r in rows),
+                "sm_max_mhz": max(r["smax"] for r in rows), "reasons": sorted(reasons),
+                "samples": len(rows)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def cpu_sample_states(wl, states_gpu, n_sample):
+    """First n_sample agents of two consecutive states, on the host."""
+    from synth import to_numpy
+    out = []
+    for st in states_gpu:
+        out.append(to_numpy({k: v[:n_sample] for k, v in st.items()}))
+    return out
+
+
+def oracle_time(wl, host_states):
+    """Oracle (single thread) over a chain of host states; returns per-state seconds."""
+    import oracle
+    g = oracle.make_grid(wl.lo, wl.hi, wl.grid, wl.w)
+    ref = recv_ref = None
+    times = []
+    for s in host_states:
+        t0 = time.perf_counter()
+        res = oracle.exchange_iteration(g, s, ref=ref, recv_ref=recv_ref)
+        times.append(time.perf_counter() - t0)
+        assert res["status"] == oracle.OK, res["status"]
+        ref, recv_ref = (res["ref_next"], res["pair_off"]), (res["recv"], res["recv_off"])
+    return times
+
+
+def run_reference(args):
+    """CPU oracle arm: W warm-up + K timed iterations on a bounded sample."""
+    import torch
+    from synth import WORKLOADS, Generator, scaled, to_numpy
+    rank, world, local = dist_env()
+    if rank != 0:
+        return 0
+    wl0 = WORKLOADS[args.workload]
+    n = min(wl0.n0, args.ref_agents)
+    wl = scaled(wl0, n)
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    gen = Generator(wl, device=dev)
+    states = [to_numpy(s) for s in gen.series(args.warmup + args.steps)]
+    times = oracle_time(wl, states)
+    timed = times[args.warmup:]
+    agents = sum(int(s["x"].shape[0]) for s in states[args.warmup:])
+    total = sum(timed)
+    value = agents / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "agents/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": args.workload, "agents_per_step": n,
+                   "note": f"oracle on the first {n} agents per state of the same workload"},
+        "cpu_baseline": {"value": value, "unit": "agents/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{args.warmup}+{args.steps} iterations of {args.workload} "
+                                   f"scaled to {n} agents (same cube, grid, aura, dynamics)"},
+        "e2e": {"value": value, "unit": "agents/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="tera", choices=["tera", "reference"])
+    ap.add_argument("--workload", default="uniform_100m")
+    ap.add_argument("--path", default="all_pairs", choices=["all_pairs", "per_subdomain"])
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-sample", type=int, default=2_000_000)
+    ap.add_argument("--ref-agents", type=int, default=1_000_000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-table", action="store_true", help="print per-kernel table to stderr")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "tera":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import paper_2509_24063_gb300 as tera
+    from synth import WORKLOADS, Generator
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    wl = WORKLOADS[args.workload]
+    total_steps = args.warmup + args.steps
+    # replicas: each rank runs its own seeded population (weak scaling, no exchange between ranks)
+    gen = Generator(wl, device="cuda", seed=wl.seed + 7919 * rank)
+    states = []
+    for st in gen.series(total_steps):
+        states.append({k: v for k, v in st.items() if k in
+                       ("id", "x", "y", "z", "diameter", "volume", "adherence", "density")})
+    del gen
+    torch.cuda.synchronize()
+    nmax = max(int(s["x"].shape[0]) for s in states)
+    max_records = int(nmax * 0.35) + 4096 if wl.grid[0] >= 8 else 4 * nmax + 4096
+    ctx = tera.Context(wl.lo, wl.hi, wl.grid, wl.w, device=local)
+    ex = tera.AuraExchange(ctx, max_agents=nmax, max_records=max_records,
+                           per_subdomain=(args.path == "per_subdomain"))
+    stream = torch.cuda.current_stream()
+
+    for t in range(args.warmup):
+        ex.step(states[t])
+    ctx.status()  # raises on any device-side error
+    ctx.stats(reset=True)
+    ctx.profile_table(reset=True)
+    ctx.profile(True)
+    launches0 = ctx.launches
+
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(None if world == 1 else local) as clk:
+        ev0.record(stream)
+        for t in range(args.warmup, total_steps):
+            ex.step(states[t])
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    elapsed_ms = ev0.elapsed_time(ev1)
+    launches = ctx.launches - launches0
+    ctx.profile(False)
+    prof = ctx.profile_table(reset=True)
+    stats = ctx.stats(reset=True)
+    ctx.status()
+    agents = sum(int(states[t]["x"].shape[0]) for t in range(args.warmup, total_steps))
+    t_max = elapsed_ms
+    agents_all = agents
+    if world > 1:
+        tt = torch.tensor([elapsed_ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+        aa = torch.tensor([agents], device="cuda", dtype=torch.float64)
+        dist.all_reduce(aa)
+        agents_all = int(aa.item())
+    value = agents_all / (t_max / 1e3)
+
+    # encode+decode algorithmic bytes over the timed steps (pack .. decode)
+    codec_kernels = ("pack_kernel", "enc_match_kernel", "enc_new_kernel", "enc_emit_kernel",
+                     "dec_sum_kernel", "dec_emit_kernel")
+    H = stats["holes"]
+    R, E, A, Y = stats["ref_slots"], stats["records"], stats["new_records"], \
+        stats["payload_bytes"]
+    codec_bytes = (216 * (E) + Y) + (132 * E + Y) - 0  # per-record model (matched/new alike)
+    codec_ms = sum(prof.get(k, (0, 0.0))[1] for k in prof if k.startswith(("pack", "enc_", "dec_")))
+    peaks, peak_kind = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    codec_gbs = codec_bytes / (codec_ms / 1e3) / 1e9 if codec_ms > 0 else None
+
+    # dominant kernel
+    dname, (dn, dms) = max(prof.items(), key=lambda kv: kv[1][1]) if prof else ("", (0, 0.0))
+    dbytes = kernel_bytes(dname, stats)
+    roofline = None
+    if dbytes is not None and dn > 0:
+        per_launch_bytes = dbytes / dn
+        per_launch_s = dms / dn / 1e3
+        achieved = per_launch_bytes / per_launch_s / 1e9
+        roofline = {"bound": "hbm", "kernel": dname, "achieved": achieved, "peak": hbm,
+                    "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
+                    "peak_kind": peak_kind, "launches": dn, "avg_ms": dms / dn,
+                    "algorithmic_bytes_per_launch": per_launch_bytes}
+    if args.profile_table and rank == 0:
+        tot = sum(v[1] for v in prof.values())
+        for k, (n_, ms_) in sorted(prof.items(), key=lambda kv: -kv[1][1]):
+            b = kernel_bytes(k, stats)
+            gbs = f"{b / (ms_ / 1e3) / 1e9:8.1f} GB/s" if b and ms_ > 0 else ""
+            print(f"{k:24s} {n_:6d} launches {ms_:9.3f} ms {100 * ms_ / tot:5.1f}% {gbs}",
+                  file=sys.stderr)
+        print(json.dumps(stats), file=sys.stderr)
+
+    # end to end: host-resident state in, wire messages out, through the same API
+    e2e = None
+    if args.e2e_steps > 0:
+        e2e = run_e2e(args, tera, wl, states, nmax, max_records, local)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        from synth import scaled
+        ns = min(args.cpu_sample, int(states[0]["x"].shape[0]))
+        hs = cpu_sample_states(wl, states[args.warmup - 1:args.warmup + 1], ns)
+        tms = oracle_time(scaled(wl, ns), hs)
+        cpu = {"value": int(hs[1]["x"].shape[0]) / tms[1], "unit": "agents/s", "cores": 1,
+               "kind": "oracle",
+               "sample": f"one iteration (with reference) of the first {ns} agents of two "
+                         f"consecutive states of {args.workload}; single-threaded C oracle"}
+    clk_sum = clk.summary()
+    line = {
+        "metric": METRIC, "value": value, "unit": "agents/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "agents": int(states[args.warmup]["x"].shape[0]),
+                   "grid": list(wl.grid), "aura_width": wl.w, "path": args.path,
+                   "l2": "inputs larger than L2 (64 B/agent state per step)",
+                   "parallelism": f"replicas{world}"},
+        "encode_decode_gbs": codec_gbs,
+        "encode_decode_hbm_frac": (codec_gbs / hbm) if codec_gbs else None,
+        "bytes_per_agent": stats["wire_bytes"] / max(1, E),
+        "records_per_step": E / args.steps,
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clk_sum,
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def run_e2e(args, tera, wl, states, nmax, max_records, local):
+    """Same metric through the public API with host buffers: the state columns
+    are copied from pinned host memory and the wire slabs copied back, inside
+    the timed region."""
+    import torch
+    fields = ("id", "x", "y", "z", "diameter", "volume", "adherence", "density")
+    k = min(args.e2e_steps, args.steps)
+    host = []
+    for t in range(args.warmup - 1, args.warmup + k):
+        host.append({f: states[t][f].cpu().pin_memory() for f in fields})
+    dev = {f: torch.empty(nmax, dtype=states[0][f].dtype, device="cuda") for f in fields}
+    ctx = tera.Context(wl.lo, wl.hi, wl.grid, wl.w, device=local)
+    ex = tera.AuraExchange(ctx, max_agents=nmax, max_records=max_records)
+    out_host = torch.empty(ex.wire_cap, dtype=torch.uint8).pin_memory()
+    stream = torch.cuda.current_stream()
+
+    def one(hs):
+        n = int(hs["x"].shape[0])
+        view = {}
+        for f in fields:
+            dev[f][:n].copy_(hs[f], non_blocking=True)
+            view[f] = dev[f][:n]
+        ex.step(view)
+        used = ex.wire_off[-1:].to("cpu", non_blocking=False)  # slab bytes used
+        nb = int(used.item())
+        out_host[:nb].copy_(ex.wire[:nb], non_blocking=True)
+        return n, sum(int(hs[f].numel() * hs[f].element_size()) for f in fields), nb
+
+    one(host[0])  # warm-up (first iteration of this chain)
+    torch.cuda.synchronize()
+    h2d = d2h = agents = 0
+    t0 = time.perf_counter()
+    for hs in host[1:]:
+        n, bi, bo = one(hs)
+        agents += n
+        h2d += bi
+        d2h += bo
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    ctx.status()
+    ctx.close()
+    return {"value": agents / dt, "unit": "agents/s", "h2d_bytes_per_step": h2d // k,
+            "d2h_bytes_per_step": d2h // k, "steps": k}
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,245 @@
+/*
+ * tera.h — C ABI of the GB300 aura-exchange library (libtera.so).
+ *
+ * The library implements the per-iteration aura (halo) exchange of the
+ * TeraAgent distributed engine for spherical agents whose boxes all live in
+ * one GPU's memory:
+ *
+ *   tera_partition     grid classification: owner box + 26-neighbour aura mask
+ *                      per agent, per-pair message lists        (paper Sec. 2.1)
+ *   tera_pack          TeraAgent IO serialization into flat 64-byte records
+ *                      the receiver uses in place             (paper Sec. 2.2.1)
+ *   tera_delta_encode  matching against the pair's reference, per-word XOR
+ *                      difference and significant-byte packing  (paper Sec. 2.3,
+ *                      steps B and C; Sec. 3.11 for the compression stage)
+ *   tera_delta_decode  restore from the receiver's reference and defragment
+ *                      into the new reference / receive buffer (Sec. 2.3, step D)
+ *   tera_unpack_inplace  header check + typed view of a receive buffer, no
+ *                      other reads or writes       (Sec. 2.2.1 "Deserialization")
+ *
+ * Conventions shared by every entry point:
+ *  - Device pointers are owned by the caller (allocated e.g. by PyTorch); the
+ *    library never frees them.  The context owns its own scratch memory, the
+ *    per-iteration hash table and a device status word, all released by
+ *    tera_ctx_destroy.
+ *  - `stream` is a cudaStream_t passed as void*.  Every call that takes a
+ *    stream is asynchronous on it and never synchronizes the host (except
+ *    tera_unpack_inplace and tera_ctx_status, which read a few bytes back).
+ *    Argument errors are returned at once; errors found on the device
+ *    (capacity, corrupt message, agent outside the domain) are latched in the
+ *    context's status word (first error wins) and read with tera_ctx_status.
+ *  - All multi-byte values in buffers are little-endian (native on x86-64 and
+ *    aarch64; the paper sends native bytes without conversion, Sec. 2.2).
+ *  - No C++ exception crosses this boundary.
+ *
+ * Buffer formats (all offsets in bytes):
+ *
+ *  Record (64 B): eight 64-bit words, w0 id | w1 x | w2 y | w3 z | w4 diameter |
+ *    w5 volume | w6 adherence | w7 density; floating-point words are the raw
+ *    IEEE-754 binary64 bits.
+ *
+ *  Record arena ("TAIO" buffers): used for packed messages, sender references
+ *    and receive buffers.  An arena is an array of 64-byte units; with an
+ *    offset array off[P+1] (record counts, exclusive prefix over pairs), pair
+ *    p occupies units [off[p] + p, off[p+1] + p + 1): one 64-byte header, then
+ *    its off[p+1]-off[p] records.  Header:
+ *       0 u32 magic 0x4F494154 ("TAIO")   4 u16 version 1   6 u16 record size 64
+ *       8 u32 class id   12 u32 pair p   16 u64 record count   24..63 zero
+ *
+ *  Wire message of pair p (starts at wire + wire_off[p]):
+ *       0 u32 magic 0x41524554 ("TERA")   4 u16 version 1   6 u16 record size 64
+ *       8 u32 class id   12 u32 mode (0 raw, 1 xor)   16 u64 n_slots (r)
+ *      24 u64 n_new (a)  32 u64 n_holes   40 u64 payload bytes   48 u32 pair p
+ *      52 u32 zero       56 u64 message bytes (multiple of 16)
+ *      64: u32 code[r + a]; then the payload; then zero padding.
+ *    Entry e < r is reference slot e: placeholder (code 0xF) when the agent
+ *    of that slot is not in this message, else the XOR of the current record
+ *    and the slot's record.  Entries e >= r are the records absent from the
+ *    reference, in message order, sent raw.  Nibble w of a code (bits 4w..4w+3)
+ *    is L_w = number of significant low bytes of word w (0..8); the payload
+ *    is, entry by entry and word by word, the low L_w bytes of each word,
+ *    least significant first.
+ *    The slab of pair p is sized by an upper bound known before encoding:
+ *       wire_off[p+1] - wire_off[p] = round16(64 + 4 (r_p + m_p) + 64 m_p).
+ */
+#ifndef TERA_H
+#define TERA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  TERA_OK = 0,
+  TERA_EINVAL = 1,       /* bad argument (returned at once) */
+  TERA_ENOMEM = 2,       /* cudaMalloc of context scratch failed */
+  TERA_ECAPACITY = 3,    /* a caller buffer is too small; see required capacity */
+  TERA_ECORRUPT = 4,     /* malformed message or buffer header */
+  TERA_EDOMAIN = 5,      /* an agent lies outside [lo, hi) (or is NaN) */
+  TERA_EREFMISMATCH = 6, /* message n_slots differs from the receiver's reference */
+  TERA_ETIMEOUT = 7,     /* a bounded device-side wait gave up */
+  TERA_ECUDA = 8         /* a CUDA runtime call failed */
+} tera_status;
+
+enum { TERA_MODE_RAW = 0, TERA_MODE_XOR = 1 };
+
+typedef struct tera_ctx tera_ctx;
+
+/* Struct-of-arrays agent state; device pointers, caller-owned, n < 2^32. */
+typedef struct {
+  const uint64_t* id;
+  const double *x, *y, *z, *diameter, *volume, *adherence, *density;
+  int64_t n;
+} tera_soa;
+
+/* Partitioning grid: box edges e[k] = lo + ((hi - lo) * k) / n (k < n),
+ * e[n] = hi, per axis; aura width w with 0 < w < every box side. */
+typedef struct {
+  double lo[3], hi[3];
+  int32_t n[3];
+  double w;
+} tera_grid;
+
+/* Outputs of tera_partition; device pointers, caller-owned.
+ * P = n[0]*n[1]*n[2]*27 ordered pairs; pair p = s*27 + b with sender box s and
+ * neighbour bit b = (ox+1) + 3(oy+1) + 9(oz+1) (b = 13, the box itself, is
+ * always empty). */
+typedef struct {
+  int32_t* owner;        /* [n]  owner box (ix + nx (iy + ny iz)), -1 outside */
+  uint32_t* mask;        /* [n]  bit b set when the agent is in the aura of neighbour b */
+  uint64_t* pair_count;  /* [P]  m_p, records in message p */
+  uint64_t* pair_off;    /* [P+1] exclusive prefix of pair_count */
+  uint32_t* pair_idx;    /* [idx_capacity] agent indices of each message, ascending */
+  uint64_t idx_capacity;
+} tera_partition_out;
+
+/* Create a context on `device` for one grid (Sec. 2.1 partitioning grid).
+ * Box edges and aura thresholds are computed here once, in binary64.
+ * Returns TERA_EINVAL when a grid axis has n < 1 or n > 256, lo >= hi, or w is
+ * not strictly between 0 and every box side.  class_id is written into every
+ * buffer header (the paper replaces the vtable pointer by a class id). */
+tera_status tera_ctx_create(tera_ctx** out, const tera_grid* grid, int device,
+                            uint32_t class_id);
+tera_status tera_ctx_destroy(tera_ctx* ctx);
+
+/* Number of ordered pairs P of the context's grid. */
+uint64_t tera_n_pairs(const tera_ctx* ctx);
+
+/* Pre-allocate scratch for up to max_agents agents and max_records records
+ * per iteration (otherwise done lazily by the first call that needs it;
+ * lazy growth synchronizes the device, so call this before graph capture). */
+tera_status tera_ctx_reserve(tera_ctx* ctx, int64_t max_agents, uint64_t max_records);
+
+/* Step a1 (Sec. 2.1 "Aura Update"): owner box and aura mask of every agent,
+ * and the per-pair stable lists.  Agent i is in the aura of neighbour box at
+ * offset o when, on every axis, o = 0, or o = -1 and x < e[i] + w, or o = +1
+ * and x >= e[i+1] - w (the neighbour must exist).  Agents outside [lo, hi)
+ * get owner -1, mask 0 and latch TERA_EDOMAIN.  More than idx_capacity
+ * records latch TERA_ECAPACITY (required capacity reported) and leave every
+ * pair empty.  Also starts a new iteration for the context's hash table. */
+tera_status tera_partition(tera_ctx* ctx, const tera_soa* soa, tera_partition_out* out,
+                           void* stream);
+
+/* Step a2 (Sec. 2.2.1 "Serialization"): write the TAIO buffers of pairs
+ * [pair_begin, pair_end) into rec_arena (arena_units 64-byte units), laid out
+ * with out->pair_off.  Also indexes every packed record by (pair, id) for
+ * tera_delta_encode; call it for every pair range that will be encoded,
+ * after tera_partition of the same iteration. */
+tera_status tera_pack(tera_ctx* ctx, const tera_soa* soa, const tera_partition_out* part,
+                      uint32_t pair_begin, uint32_t pair_end, uint8_t* rec_arena,
+                      uint64_t arena_units, void* stream);
+
+/* Steps a3+a4 (Sec. 2.3 B and C): encode messages [pair_begin, pair_end)
+ * against the sender reference (ref_prev laid out with ref_off_prev; both
+ * NULL means every reference is empty, as at the first iteration).
+ *  - writes wire_off[P+1] (slab layout, all pairs), the messages of the
+ *    range at wire + wire_off[p], their lengths wire_len[p];
+ *  - writes the new sender reference ref_next, laid out with pair_off
+ *    (matched records in slot order, then new records in message order).
+ * mode TERA_MODE_XOR or TERA_MODE_RAW (raw: the reference is ignored).  A
+ * pair marked by tera_reset_reference is sent raw once.  wire_capacity is in
+ * bytes; too small latches TERA_ECAPACITY with the required size. */
+tera_status tera_delta_encode(tera_ctx* ctx, const uint8_t* rec_arena, const uint64_t* pair_off,
+                              const uint8_t* ref_prev, const uint64_t* ref_off_prev,
+                              uint32_t pair_begin, uint32_t pair_end, uint8_t* ref_next,
+                              uint8_t* wire, uint64_t wire_capacity, uint64_t* wire_off,
+                              uint64_t* wire_len, int mode, void* stream);
+
+/* Step a5 (Sec. 2.3 D): decode messages [pair_begin, pair_end) against the
+ * receiver reference (ref_prev/ref_off_prev, NULL = empty) and write the
+ * defragmented records into recv (recv_capacity_units 64-byte units), laid
+ * out with recv_off[P+1], which this call computes from ALL message headers
+ * (m_p = n_slots - n_holes + n_new).  The receive buffer is the receiver's
+ * next reference.  Malformed messages latch TERA_ECORRUPT, a slot count
+ * differing from the receiver's reference TERA_EREFMISMATCH; the output of
+ * such a pair is unspecified. */
+tera_status tera_delta_decode(tera_ctx* ctx, const uint8_t* wire, const uint64_t* wire_off,
+                              const uint8_t* ref_prev, const uint64_t* ref_off_prev,
+                              uint32_t pair_begin, uint32_t pair_end, uint8_t* recv,
+                              uint64_t recv_capacity_units, uint64_t* recv_off, void* stream);
+
+/* Sec. 2.2.1 "Deserialization": check the TAIO header of ONE pair buffer
+ * (device pointer `buf`, `len` bytes available) on the host and return a
+ * device pointer to its first record and the record count.  Reads the
+ * 64-byte header back (synchronizing `stream`); reads or writes nothing
+ * else.  TERA_ECORRUPT for a wrong magic, version, record size or class id,
+ * or a count that does not fit in len. */
+tera_status tera_unpack_inplace(const uint8_t* buf, uint64_t len, uint32_t class_id,
+                                void** view, uint64_t* count, void* stream);
+
+/* Device-side form of the same check for every pair of an arena (for use
+ * inside captured graphs): latches TERA_ECORRUPT when a header's magic,
+ * version, size, class id, pair or count (off[p+1]-off[p]) is wrong. */
+tera_status tera_unpack_validate(tera_ctx* ctx, const uint8_t* arena, const uint64_t* off,
+                                 void* stream);
+
+/* Read (and clear) the latched device status; synchronizes `stream`.
+ * *required_capacity (optional) receives the largest capacity a call asked
+ * for when the status is TERA_ECAPACITY. */
+tera_status tera_ctx_status(tera_ctx* ctx, uint64_t* required_capacity, void* stream);
+
+/* Send pair p raw (against an empty reference) at the next tera_delta_encode
+ * that covers it.  Use after mutating a received view, which invalidates the
+ * pair's reference on the receiving side. */
+tera_status tera_reset_reference(tera_ctx* ctx, uint32_t pair);
+
+/* Totals accumulated on the device by every call of the context since the
+ * last reset: iterations (tera_partition calls), agents classified, records
+ * packed into messages (sum of m_p), reference slots encoded against (sum of
+ * r_p), placeholders, new records, payload bytes and wire-message bytes
+ * (sum of message lengths) written by tera_delta_encode.  No counterpart in
+ * the paper; used for bytes-per-agent and bandwidth accounting. */
+typedef struct {
+  uint64_t iterations, agents, records, ref_slots, holes, new_records, payload_bytes,
+      wire_bytes;
+} tera_stats;
+
+/* Read the totals (synchronizes `stream`); reset != 0 zeroes them afterwards. */
+tera_status tera_ctx_stats(tera_ctx* ctx, tera_stats* out, int reset, void* stream);
+
+/* Kernels this context has launched so far (for launch accounting). */
+uint64_t tera_ctx_launches(const tera_ctx* ctx);
+
+/* Measurement support (no counterpart in the paper).  When enabled, every
+ * kernel launch of the context is bracketed by a pair of CUDA events on its
+ * stream.  tera_ctx_profile_collect waits for the recorded events and adds
+ * their durations into a per-kernel table (kernel name, launches, total ms);
+ * tera_ctx_profile_entries / tera_ctx_profile_entry read the table (names stay
+ * valid until tera_ctx_profile_reset or tera_ctx_destroy); reset collects and
+ * clears it. */
+tera_status tera_ctx_profile(tera_ctx* ctx, int enable);
+tera_status tera_ctx_profile_collect(tera_ctx* ctx);
+int tera_ctx_profile_entries(const tera_ctx* ctx);
+tera_status tera_ctx_profile_entry(const tera_ctx* ctx, int i, const char** name,
+                                   uint64_t* launches, double* total_ms);
+tera_status tera_ctx_profile_reset(tera_ctx* ctx);
+
+/* Library version string. */
+const char* tera_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,540 @@
+// Context, scratch memory, status word, generic scan and the in-place
+// deserialization check of libtera.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "tera_internal.cuh"
+
+using namespace tera;
+
+namespace {
+
+template <typename T>
+void free_dev(T*& p) {
+  if (p) cudaFree(p);
+  p = nullptr;
+}
+
+template <typename T>
+tera_status alloc_dev(T*& p, size_t count) {
+  free_dev(p);
+  if (count == 0) count = 1;
+  if (cudaMalloc(reinterpret_cast<void**>(&p), sizeof(T) * count) != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+    return TERA_ENOMEM;
+  }
+  return TERA_OK;
+}
+
+// ---- generic exclusive scan of u32 values (reduce, scan partials, down-sweep) ----
+
+__global__ void scan_reduce_kernel(const u32* __restrict__ in, u64 n, u64* __restrict__ part) {
+  __shared__ u64 sm[33];
+  const u64 base = (u64)blockIdx.x * kScanChunk;
+  u64 s = 0;
+#pragma unroll
+  for (int k = 0; k < kScanPerThread; ++k) {
+    u64 i = base + (u64)k * kScanThreads + threadIdx.x;
+    if (i < n) s += in[i];
+  }
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    u64 t = threadIdx.x < (kScanThreads / 32) ? sm[threadIdx.x] : 0;
+    t = warp_sum(t);
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
+  }
+}
+
+// Single block: exclusive scan of part[0..m) in place, total to part[m].
+__global__ void scan_partials_kernel(u64* part, u64 m) {
+  __shared__ u64 sm[33];
+  u64 carry = 0;
+  for (u64 base = 0; base < m; base += kScanThreads) {
+    u64 i = base + threadIdx.x;
+    u64 v = i < m ? part[i] : 0;
+    u64 tot;
+    u64 ex = block_excl_scan<u64>(v, sm, &tot);
+    if (i < m) part[i] = carry + ex;
+    carry += tot;
+  }
+  if (threadIdx.x == 0) part[m] = carry;
+}
+
+__global__ void scan_down_kernel(const u32* __restrict__ in, u64 n, const u64* __restrict__ part,
+                                 u64* __restrict__ out64, u32* __restrict__ out32) {
+  __shared__ u64 sm[33];
+  const u64 base = (u64)blockIdx.x * kScanChunk + (u64)threadIdx.x * kScanPerThread;
+  u32 v[kScanPerThread];
+  u64 s = 0;
+#pragma unroll
+  for (int k = 0; k < kScanPerThread; ++k) {
+    u64 i = base + k;
+    v[k] = i < n ? in[i] : 0u;
+    s += v[k];
+  }
+  u64 tot;
+  u64 ex = block_excl_scan<u64>(s, sm, &tot);
+  u64 run = part[blockIdx.x] + ex;
+#pragma unroll
+  for (int k = 0; k < kScanPerThread; ++k) {
+    u64 i = base + k;
+    if (i < n) {
+      if (out64) out64[i] = run;
+      if (out32) out32[i] = (u32)run;
+    }
+    run += v[k];
+  }
+  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) {
+    u64 total = part[gridDim.x];
+    if (out64) out64[n] = total;
+    if (out32) out32[n] = (u32)total;
+  }
+}
+
+__global__ void unit_map_kernel(const u64* __restrict__ unit_off, u64 npr, u32 p0,
+                                u32* __restrict__ unit_pair, const u64* __restrict__ units_total) {
+  if (units_total[1]) return;
+  const int lane = threadIdx.x & 31;
+  const u64 warp = ((u64)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const u64 nwarps = ((u64)gridDim.x * blockDim.x) >> 5;
+  for (u64 k = warp; k < npr; k += nwarps)
+    for (u64 u = unit_off[k] + lane; u < unit_off[k + 1]; u += 32) unit_pair[u] = p0 + (u32)k;
+}
+
+__global__ void validate_arena_kernel(const uint8_t* __restrict__ arena,
+                                      const u64* __restrict__ off, u64 n_pairs, u32 class_id,
+                                      DevStatus* st) {
+  for (u64 p = (u64)blockIdx.x * blockDim.x + threadIdx.x; p < n_pairs;
+       p += (u64)gridDim.x * blockDim.x) {
+    const u64* h = reinterpret_cast<const u64*>(arena + (off[p] + p) * kRecBytes);
+    u64 w0 = h[0], w1 = h[1], n = h[2];
+    bool ok = (u32)w0 == kTaioMagic && (u32)((w0 >> 32) & 0xFFFF) == kVersion &&
+              (u32)(w0 >> 48) == kRecBytes && (u32)w1 == class_id && (u32)(w1 >> 32) == (u32)p &&
+              n == off[p + 1] - off[p];
+    if (!ok) latch(st, TERA_ECORRUPT);
+  }
+}
+
+}  // namespace
+
+namespace tera {
+
+// Optional per-kernel timing: an event pair around every launch, resolved by
+// tera_ctx_profile_collect.  Off by default.
+struct ProfState {
+  bool on = false;
+  std::vector<cudaEvent_t> pool;
+  struct Pending {
+    const char* name;
+    cudaEvent_t a, b;
+  };
+  std::vector<Pending> pending;
+  cudaEvent_t open_a = nullptr;
+  std::vector<std::string> names;
+  std::vector<uint64_t> count;
+  std::vector<double> ms;
+  cudaEvent_t get() {
+    if (!pool.empty()) {
+      cudaEvent_t e = pool.back();
+      pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+  }
+};
+
+static ProfState* prof(tera_ctx* ctx) { return reinterpret_cast<ProfState*>(ctx->prof); }
+
+void prof_begin(tera_ctx* ctx, cudaStream_t s) {
+  ProfState* p = prof(ctx);
+  if (!p || !p->on) return;
+  p->open_a = p->get();
+  cudaEventRecord(p->open_a, s);
+}
+
+tera_status check_launch(tera_ctx* ctx, const char* name, cudaStream_t s) {
+  ctx->launches += 1;
+  ProfState* p = prof(ctx);
+  if (p && p->on && p->open_a) {
+    cudaEvent_t b = p->get();
+    cudaEventRecord(b, s);
+    p->pending.push_back({name, p->open_a, b});
+    p->open_a = nullptr;
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    fprintf(stderr, "libtera: launch of %s failed: %s\n", name, cudaGetErrorString(e));
+    return TERA_ECUDA;
+  }
+  return TERA_OK;
+}
+
+int grid_for(tera_ctx* ctx, int blocks_per_sm) { return ctx->num_sms * blocks_per_sm; }
+
+tera_status launch_unit_map(tera_ctx* ctx, u32 p0, u64 npr, cudaStream_t s) {
+  if (npr == 0) return TERA_OK;
+  prof_begin(ctx, s);
+  unit_map_kernel<<<(unsigned)((npr + 7) / 8), 256, 0, s>>>(ctx->unit_off, npr, p0, ctx->unit_pair,
+                                                            ctx->d_units_total);
+  return check_launch(ctx, "unit_map_kernel", s);
+}
+
+static tera_status ensure_scan_part(tera_ctx* ctx, u64 n) {
+  u64 need = (n + kScanChunk - 1) / kScanChunk + 2;
+  if (need <= ctx->scan_part_cap) return TERA_OK;
+  cudaDeviceSynchronize();
+  u64 cap = need * 2;
+  tera_status st = alloc_dev(ctx->scan_part, cap);
+  if (st != TERA_OK) return st;
+  ctx->scan_part_cap = cap;
+  return TERA_OK;
+}
+
+tera_status scan_u32(tera_ctx* ctx, const u32* in, u64* out64, u32* out32, u64 n,
+                     cudaStream_t s) {
+  tera_status st = ensure_scan_part(ctx, n);
+  if (st != TERA_OK) return st;
+  u64 chunks = (n + kScanChunk - 1) / kScanChunk;
+  if (chunks == 0) chunks = 1;
+  if (chunks == 1) {
+    cudaMemsetAsync(ctx->scan_part, 0, sizeof(u64), s);
+    // part[1] = total is written by the down kernel through part[gridDim.x]; compute it
+    prof_begin(ctx, s);
+    scan_reduce_kernel<<<1, kScanThreads, 0, s>>>(in, n, ctx->scan_part + 1);
+    if ((st = check_launch(ctx, "scan_reduce_kernel", s)) != TERA_OK) return st;
+  } else {
+    prof_begin(ctx, s);
+    scan_reduce_kernel<<<(unsigned)chunks, kScanThreads, 0, s>>>(in, n, ctx->scan_part);
+    if ((st = check_launch(ctx, "scan_reduce_kernel", s)) != TERA_OK) return st;
+    prof_begin(ctx, s);
+    scan_partials_kernel<<<1, kScanThreads, 0, s>>>(ctx->scan_part, chunks);
+    if ((st = check_launch(ctx, "scan_partials_kernel", s)) != TERA_OK) return st;
+  }
+  prof_begin(ctx, s);
+  scan_down_kernel<<<(unsigned)chunks, kScanThreads, 0, s>>>(in, n, ctx->scan_part, out64, out32);
+  return check_launch(ctx, "scan_down_kernel", s);
+}
+
+tera_status ensure_agents(tera_ctx* ctx, int64_t n, cudaStream_t s) {
+  (void)s;
+  if (n <= ctx->cap_agents && ctx->tile_cnt && ctx->tile_base) return TERA_OK;
+  cudaDeviceSynchronize();
+  int64_t cap = n + n / 8 + kClassifyTile;
+  u64 tiles = ((u64)cap + kClassifyTile - 1) / kClassifyTile;
+  tera_status st;
+  if ((st = alloc_dev(ctx->tile_cnt, tiles + 1)) != TERA_OK) return st;
+  if ((st = alloc_dev(ctx->tile_base, tiles + 1)) != TERA_OK) return st;
+  ctx->cap_agents = cap;
+  return TERA_OK;
+}
+
+tera_status ensure_records(tera_ctx* ctx, uint64_t cap, cudaStream_t s) {
+  (void)s;
+  if (cap <= ctx->cap_records && ctx->table) return TERA_OK;
+  cudaDeviceSynchronize();
+  u64 c = cap < 1024 ? 1024 : cap;
+  tera_status st;
+  if ((st = alloc_dev(ctx->keys_a, c)) != TERA_OK) return st;
+  if ((st = alloc_dev(ctx->keys_b, c)) != TERA_OK) return st;
+  if ((st = alloc_dev(ctx->vals_b, c)) != TERA_OK) return st;
+  u64 tiles = (c + kSortTile - 1) / kSortTile;
+  if ((st = alloc_dev(ctx->rs_hist, (u64)kRadix * tiles + 1)) != TERA_OK) return st;
+  if ((st = alloc_dev(ctx->matched, c)) != TERA_OK) return st;
+  if ((st = alloc_dev(ctx->slot_src, c)) != TERA_OK) return st;
+  u64 tc = 1024;
+  while (tc < 2 * c) tc <<= 1;
+  if ((st = alloc_dev(ctx->table, tc)) != TERA_OK) return st;
+  // epoch 0 is never current, so a zeroed table is empty
+  cudaMemset(ctx->table, 0, sizeof(HashEntry) * tc);
+  ctx->table_cap = tc;
+  ctx->cap_records = c;
+  return ensure_scan_part(ctx, (u64)kRadix * tiles + 1);
+}
+
+tera_status ensure_units(tera_ctx* ctx, uint64_t cap, cudaStream_t s) {
+  (void)s;
+  if (cap <= ctx->cap_units) return TERA_OK;
+  cudaDeviceSynchronize();
+  u64 c = cap + cap / 4 + 1024;
+  tera_status st;
+  if ((st = alloc_dev(ctx->unit_sum, c)) != TERA_OK) return st;
+  if ((st = alloc_dev(ctx->unit_base, c)) != TERA_OK) return st;
+  if ((st = alloc_dev(ctx->unit_pair, c)) != TERA_OK) return st;
+  ctx->cap_units = c;
+  return TERA_OK;
+}
+
+}  // namespace tera
+
+extern "C" {
+
+const char* tera_version(void) { return "tera-gb300 1.0 (sm_103a)"; }
+
+uint64_t tera_n_pairs(const tera_ctx* ctx) { return ctx ? ctx->n_pairs : 0; }
+
+uint64_t tera_ctx_launches(const tera_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+tera_status tera_ctx_create(tera_ctx** out, const tera_grid* grid, int device, uint32_t class_id) {
+  if (!out || !grid) return TERA_EINVAL;
+  *out = nullptr;
+  GridTables t;
+  memset(&t, 0, sizeof(t));
+  auto key = [](double d) {
+    uint64_t b;
+    memcpy(&b, &d, 8);
+    return key_of(b);
+  };
+  for (int a = 0; a < 3; ++a) {
+    int n = grid->n[a];
+    if (n < 1 || n > kMaxAxis) return TERA_EINVAL;
+    if (!(grid->lo[a] < grid->hi[a])) return TERA_EINVAL;
+    if (!std::isfinite(grid->lo[a]) || !std::isfinite(grid->hi[a])) return TERA_EINVAL;
+    double lo = grid->lo[a], hi = grid->hi[a];
+    std::vector<double> e((size_t)n + 1);
+    for (int k = 0; k < n; ++k) e[k] = lo + ((hi - lo) * (double)k) / (double)n;
+    e[n] = hi;
+    if (!(grid->w > 0.0)) return TERA_EINVAL;
+    for (int k = 0; k <= n; ++k) t.ke[a][k] = key(e[k]);
+    for (int k = 0; k < n; ++k) {
+      if (!(grid->w < e[k + 1] - e[k])) return TERA_EINVAL;
+      t.ktl[a][k] = key(e[k] + grid->w);
+      t.kth[a][k] = key(e[k + 1] - grid->w);
+    }
+    t.klo[a] = key(lo);
+    t.khi[a] = key(hi);
+    t.n[a] = n;
+  }
+  if (cudaSetDevice(device) != cudaSuccess) return TERA_ECUDA;
+  tera_ctx* c = new (std::nothrow) tera_ctx();
+  if (!c) return TERA_ENOMEM;
+  memset(c, 0, sizeof(*c));
+  c->device = device;
+  c->class_id = class_id;
+  c->grid = *grid;
+  c->n_boxes = (uint32_t)grid->n[0] * (uint32_t)grid->n[1] * (uint32_t)grid->n[2];
+  c->n_pairs = (uint64_t)c->n_boxes * 27u;
+  cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+  if (c->num_sms <= 0) c->num_sms = 148;
+  tera_status st = TERA_OK;
+  if ((st = alloc_dev(c->d_grid, 1)) != TERA_OK) goto fail;
+  if ((st = alloc_dev(c->d_status, 1)) != TERA_OK) goto fail;
+  if ((st = alloc_dev(c->d_epoch, 1)) != TERA_OK) goto fail;
+  if ((st = alloc_dev(c->d_reset, c->n_pairs)) != TERA_OK) goto fail;
+  if ((st = alloc_dev(c->unit_off, c->n_pairs + 1)) != TERA_OK) goto fail;
+  if ((st = alloc_dev(c->pair_info, c->n_pairs * 8)) != TERA_OK) goto fail;
+  if ((st = alloc_dev(c->d_total, 8)) != TERA_OK) goto fail;
+  if ((st = alloc_dev(c->d_units_total, 2)) != TERA_OK) goto fail;
+  if ((st = alloc_dev(c->d_stats, 1)) != TERA_OK) goto fail;
+  c->prof = new (std::nothrow) ProfState();
+  if (cudaMallocHost(reinterpret_cast<void**>(&c->h_status), sizeof(DevStatus)) != cudaSuccess) {
+    st = TERA_ENOMEM;
+    goto fail;
+  }
+  cudaMemcpy(c->d_grid, &t, sizeof(t), cudaMemcpyHostToDevice);
+  cudaMemset(c->d_status, 0, sizeof(DevStatus));
+  cudaMemset(c->d_epoch, 0, sizeof(uint32_t));
+  cudaMemset(c->d_reset, 0, c->n_pairs);
+  cudaMemset(c->d_total, 0, 8 * sizeof(uint64_t));
+  cudaMemset(c->d_stats, 0, sizeof(DevStats));
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    st = TERA_ECUDA;
+    goto fail;
+  }
+  *out = c;
+  return TERA_OK;
+fail:
+  tera_ctx_destroy(c);
+  return st;
+}
+
+tera_status tera_ctx_destroy(tera_ctx* c) {
+  if (!c) return TERA_OK;
+  cudaSetDevice(c->device);
+  cudaDeviceSynchronize();
+  free_dev(c->d_grid);
+  free_dev(c->d_status);
+  free_dev(c->d_epoch);
+  free_dev(c->d_reset);
+  free_dev(c->tile_cnt);
+  free_dev(c->tile_base);
+  free_dev(c->keys_a);
+  free_dev(c->keys_b);
+  free_dev(c->vals_b);
+  free_dev(c->rs_hist);
+  free_dev(c->scan_part);
+  free_dev(c->d_total);
+  free_dev(c->table);
+  free_dev(c->matched);
+  free_dev(c->slot_src);
+  free_dev(c->unit_off);
+  free_dev(c->unit_sum);
+  free_dev(c->unit_base);
+  free_dev(c->unit_pair);
+  free_dev(c->pair_info);
+  free_dev(c->d_units_total);
+  free_dev(c->d_stats);
+  if (c->h_status) cudaFreeHost(c->h_status);
+  if (ProfState* p = prof(c)) {
+    for (auto& q : p->pending) {
+      cudaEventDestroy(q.a);
+      cudaEventDestroy(q.b);
+    }
+    for (auto e : p->pool) cudaEventDestroy(e);
+    if (p->open_a) cudaEventDestroy(p->open_a);
+    delete p;
+  }
+  delete c;
+  return TERA_OK;
+}
+
+tera_status tera_ctx_reserve(tera_ctx* ctx, int64_t max_agents, uint64_t max_records) {
+  if (!ctx || max_agents < 0) return TERA_EINVAL;
+  cudaSetDevice(ctx->device);
+  tera_status st = ensure_agents(ctx, max_agents, 0);
+  if (st != TERA_OK) return st;
+  st = ensure_records(ctx, max_records, 0);
+  if (st != TERA_OK) return st;
+  return ensure_units(ctx, 2 * (max_records / kCodecTile) + 4 * ctx->n_pairs + 16, 0);
+}
+
+tera_status tera_ctx_status(tera_ctx* ctx, uint64_t* required_capacity, void* stream) {
+  if (!ctx) return TERA_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cudaMemcpyAsync(ctx->h_status, ctx->d_status, sizeof(DevStatus), cudaMemcpyDeviceToHost,
+                      s) != cudaSuccess)
+    return TERA_ECUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return TERA_ECUDA;
+  DevStatus h = *ctx->h_status;
+  if (required_capacity) *required_capacity = h.required;
+  cudaMemsetAsync(ctx->d_status, 0, sizeof(DevStatus), s);
+  return (tera_status)h.code;
+}
+
+tera_status tera_ctx_stats(tera_ctx* ctx, tera_stats* out, int reset, void* stream) {
+  if (!ctx || !out) return TERA_EINVAL;
+  static_assert(sizeof(tera_stats) == sizeof(DevStats), "stats layout");
+  cudaStream_t s = (cudaStream_t)stream;
+  DevStats h;
+  if (cudaMemcpyAsync(&h, ctx->d_stats, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return TERA_ECUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return TERA_ECUDA;
+  memcpy(out, &h, sizeof(h));
+  if (reset) cudaMemsetAsync(ctx->d_stats, 0, sizeof(DevStats), s);
+  return TERA_OK;
+}
+
+tera_status tera_ctx_profile(tera_ctx* ctx, int enable) {
+  if (!ctx || !prof(ctx)) return TERA_EINVAL;
+  prof(ctx)->on = enable != 0;
+  return TERA_OK;
+}
+
+tera_status tera_ctx_profile_collect(tera_ctx* ctx) {
+  if (!ctx || !prof(ctx)) return TERA_EINVAL;
+  ProfState* p = prof(ctx);
+  for (auto& q : p->pending) {
+    if (cudaEventSynchronize(q.b) != cudaSuccess) return TERA_ECUDA;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, q.a, q.b);
+    size_t i = 0;
+    while (i < p->names.size() && p->names[i] != q.name) ++i;
+    if (i == p->names.size()) {
+      p->names.push_back(q.name);
+      p->count.push_back(0);
+      p->ms.push_back(0.0);
+    }
+    p->count[i] += 1;
+    p->ms[i] += ms;
+    p->pool.push_back(q.a);
+    p->pool.push_back(q.b);
+  }
+  p->pending.clear();
+  return TERA_OK;
+}
+
+int tera_ctx_profile_entries(const tera_ctx* ctx) {
+  if (!ctx || !ctx->prof) return 0;
+  return (int)reinterpret_cast<const ProfState*>(ctx->prof)->names.size();
+}
+
+tera_status tera_ctx_profile_entry(const tera_ctx* ctx, int i, const char** name,
+                                   uint64_t* launches, double* total_ms) {
+  if (!ctx || !ctx->prof) return TERA_EINVAL;
+  const ProfState* p = reinterpret_cast<const ProfState*>(ctx->prof);
+  if (i < 0 || (size_t)i >= p->names.size()) return TERA_EINVAL;
+  if (name) *name = p->names[(size_t)i].c_str();
+  if (launches) *launches = p->count[(size_t)i];
+  if (total_ms) *total_ms = p->ms[(size_t)i];
+  return TERA_OK;
+}
+
+tera_status tera_ctx_profile_reset(tera_ctx* ctx) {
+  if (!ctx || !prof(ctx)) return TERA_EINVAL;
+  tera_status st = tera_ctx_profile_collect(ctx);
+  ProfState* p = prof(ctx);
+  p->names.clear();
+  p->count.clear();
+  p->ms.clear();
+  return st;
+}
+
+tera_status tera_reset_reference(tera_ctx* ctx, uint32_t pair) {
+  if (!ctx || pair >= ctx->n_pairs) return TERA_EINVAL;
+  // Rare: a blocking write keeps it ordered before any later launch.
+  cudaSetDevice(ctx->device);
+  if (cudaDeviceSynchronize() != cudaSuccess) return TERA_ECUDA;
+  if (cudaMemset(ctx->d_reset + pair, 1, 1) != cudaSuccess) return TERA_ECUDA;
+  if (cudaDeviceSynchronize() != cudaSuccess) return TERA_ECUDA;
+  return TERA_OK;
+}
+
+tera_status tera_unpack_inplace(const uint8_t* buf, uint64_t len, uint32_t class_id, void** view,
+                                uint64_t* count, void* stream) {
+  if (!buf || !view || !count) return TERA_EINVAL;
+  *view = nullptr;
+  *count = 0;
+  if (len < kHdrBytes) return TERA_ECORRUPT;
+  if ((reinterpret_cast<uintptr_t>(buf) & 15u) != 0) return TERA_EINVAL;
+  uint8_t h[kHdrBytes];
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cudaMemcpyAsync(h, buf, kHdrBytes, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return TERA_ECUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return TERA_ECUDA;
+  uint32_t magic, cls;
+  uint16_t ver, rsz;
+  uint64_t n;
+  memcpy(&magic, h + 0, 4);
+  memcpy(&ver, h + 4, 2);
+  memcpy(&rsz, h + 6, 2);
+  memcpy(&cls, h + 8, 4);
+  memcpy(&n, h + 16, 8);
+  if (magic != kTaioMagic || ver != kVersion || rsz != kRecBytes || cls != class_id)
+    return TERA_ECORRUPT;
+  if (n > (len - kHdrBytes) / kRecBytes) return TERA_ECORRUPT;
+  *view = const_cast<uint8_t*>(buf + kHdrBytes);
+  *count = n;
+  return TERA_OK;
+}
+
+tera_status tera_unpack_validate(tera_ctx* ctx, const uint8_t* arena, const uint64_t* off,
+                                 void* stream) {
+  if (!ctx || !arena || !off) return TERA_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  int blocks = (int)((ctx->n_pairs + 255) / 256);
+  prof_begin(ctx, s);
+  validate_arena_kernel<<<blocks, 256, 0, s>>>(arena, reinterpret_cast<const u64*>(off),
+                                               ctx->n_pairs, ctx->class_id, ctx->d_status);
+  return check_launch(ctx, "validate_arena_kernel", s);
+}
+
+}  // extern "C"

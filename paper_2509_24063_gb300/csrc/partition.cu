@@ -1,0 +1,388 @@
+// Step a1 — grid classification and per-pair message lists (paper Sec. 2.1,
+// "Aura Update": agents within the interaction distance of a neighbouring
+// box are sent to it every iteration; the aura is narrower than the box).
+//
+// Kernels:
+//   classify_kernel  one pass over x,y,z (coalesced 16-byte loads): owner box,
+//                    26-bit aura mask, per-tile count of (agent, pair) entries
+//   emit_kernel      stable compaction of the entries in agent order
+//                    (block scan over each tile, tile bases from a scan)
+//   rs_hist_kernel / rs_scatter_kernel
+//                    stable LSD radix sort of the entries by pair index, so
+//                    each pair's list keeps ascending agent order
+//   pair_off_kernel  per-pair counts and offsets from the sorted keys
+#include "tera_internal.cuh"
+
+using namespace tera;
+
+namespace {
+
+// Per-block copy of the grid keys that this grid uses.
+struct SmemGrid {
+  u64 ke[3][kMaxAxis + 1];
+  u64 ktl[3][kMaxAxis];
+  u64 kth[3][kMaxAxis];
+  u64 klo[3], khi[3];
+  int n[3];
+};
+
+__device__ __forceinline__ void load_grid(SmemGrid& s, const GridTables* __restrict__ g) {
+  if (threadIdx.x < 3) {
+    s.n[threadIdx.x] = g->n[threadIdx.x];
+    s.klo[threadIdx.x] = g->klo[threadIdx.x];
+    s.khi[threadIdx.x] = g->khi[threadIdx.x];
+  }
+  for (int a = 0; a < 3; ++a) {
+    const int n = g->n[a];
+    for (int k = threadIdx.x; k <= n; k += blockDim.x) s.ke[a][k] = g->ke[a][k];
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+      s.ktl[a][k] = g->ktl[a][k];
+      s.kth[a][k] = g->kth[a][k];
+    }
+  }
+  __syncthreads();
+}
+
+// One axis: box index i = #{k in 1..n-1 : v >= e[k]} (binary search over the
+// increasing edge keys) and the neighbour offsets whose aura holds v.
+// Returns opts: bit 0 offset -1 qualifies (i > 0 and v < e[i] + w), bit 1
+// offset 0, bit 2 offset +1 (i < n-1 and v >= e[i+1] - w); 0 when v is not in
+// [lo, hi).
+__device__ __forceinline__ u32 classify_axis(u64 k, int a, const SmemGrid& s, int* idx) {
+  if (!(k >= s.klo[a] && k < s.khi[a])) {
+    *idx = 0;
+    return 0u;
+  }
+  const int n = s.n[a];
+  int i = 0;
+  for (int step = kMaxAxis; step > 0; step >>= 1)
+    if (i + step <= n - 1 && k >= s.ke[a][i + step]) i += step;
+  *idx = i;
+  const u32 lowq = (i > 0) && (k < s.ktl[a][i]);
+  const u32 highq = (i < n - 1) && (k >= s.kth[a][i]);
+  return 2u | lowq | (highq << 2);
+}
+
+__device__ __forceinline__ void classify_agent(u64 bx, u64 by, u64 bz, const SmemGrid& s,
+                                               int* owner, u32* mask, bool* ok) {
+  int ix, iy, iz;
+  const u32 ox = classify_axis(key_of(bx), 0, s, &ix);
+  const u32 oy = classify_axis(key_of(by), 1, s, &iy);
+  const u32 oz = classify_axis(key_of(bz), 2, s, &iz);
+  *ok = ox && oy && oz;
+  if (!*ok) {
+    *owner = -1;
+    *mask = 0;
+    return;
+  }
+  *owner = ix + s.n[0] * (iy + s.n[1] * iz);
+  u32 m = 0;
+#pragma unroll
+  for (int dz = 0; dz < 3; ++dz) {
+#pragma unroll
+    for (int dy = 0; dy < 3; ++dy) {
+      if ((oz >> dz) & (oy >> dy) & 1u) m |= ox << (3 * dy + 9 * dz);
+    }
+  }
+  *mask = m & ~(1u << 13);
+}
+
+// Each block classifies one tile of kClassifyTile agents.  In round k thread t
+// holds agents 512k + 2t and 512k + 2t + 1 of the tile (one 16-byte load per
+// coordinate), so every warp load is fully coalesced.
+__global__ void __launch_bounds__(kClassifyThreads)
+    classify_kernel(const u64* __restrict__ x, const u64* __restrict__ y,
+                    const u64* __restrict__ z, u64 n, const GridTables* __restrict__ g,
+                    int* __restrict__ owner, u32* __restrict__ mask, u32* __restrict__ tile_cnt,
+                    DevStatus* st, u32* epoch, DevStats* stats) {
+  __shared__ u64 sm[33];
+  __shared__ SmemGrid sg;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    u32 e = *epoch + 1u;
+    *epoch = e == 0u ? 1u : e;  // a new iteration for the (pair, id) index
+    stats->iterations += 1;
+    stats->agents += n;
+  }
+  load_grid(sg, g);
+  const u64 tile0 = (u64)blockIdx.x * kClassifyTile;
+  u32 cnt = 0;
+  bool bad = false;
+#pragma unroll
+  for (int k = 0; k < kClassifyPerThread / 2; ++k) {
+    const u64 a0 = tile0 + (u64)k * (2 * kClassifyThreads) + 2u * threadIdx.x;
+    u64 vx[2], vy[2], vz[2];
+    if (a0 + 1 < n) {
+      ulonglong2 tx = *reinterpret_cast<const ulonglong2*>(x + a0);
+      ulonglong2 ty = *reinterpret_cast<const ulonglong2*>(y + a0);
+      ulonglong2 tz = *reinterpret_cast<const ulonglong2*>(z + a0);
+      vx[0] = tx.x; vx[1] = tx.y; vy[0] = ty.x; vy[1] = ty.y; vz[0] = tz.x; vz[1] = tz.y;
+    } else {
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        if (a0 + q < n) {
+          vx[q] = x[a0 + q]; vy[q] = y[a0 + q]; vz[q] = z[a0 + q];
+        } else {
+          vx[q] = vy[q] = vz[q] = 0ull;
+        }
+      }
+    }
+    int o[2];
+    u32 m[2];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      bool ok;
+      classify_agent(vx[q], vy[q], vz[q], sg, &o[q], &m[q], &ok);
+      if (a0 + q < n) {
+        bad |= !ok;
+        cnt += __popc(m[q]);
+      }
+    }
+    if (a0 + 1 < n) {
+      *reinterpret_cast<int2*>(owner + a0) = make_int2(o[0], o[1]);
+      *reinterpret_cast<uint2*>(mask + a0) = make_uint2(m[0], m[1]);
+    } else if (a0 < n) {
+      owner[a0] = o[0];
+      mask[a0] = m[0];
+    }
+  }
+  if (bad) latch(st, TERA_EDOMAIN);
+  u64 tot;
+  block_excl_scan<u64>((u64)cnt, sm, &tot);
+  if (threadIdx.x == 0) tile_cnt[blockIdx.x] = (u32)tot;
+}
+
+// Emit (pair, agent) entries in agent order: tile t writes its entries at
+// tile_base[t]; within the tile, round k and thread t as in classify_kernel.
+__global__ void __launch_bounds__(kClassifyThreads)
+    emit_kernel(const int* __restrict__ owner, const u32* __restrict__ mask, u64 n,
+                const u64* __restrict__ tile_base, u64 n_tiles, u32* __restrict__ keys,
+                u32* __restrict__ vals, u64 cap, DevStatus* st) {
+  __shared__ u64 sm[33];
+  const u64 total = tile_base[n_tiles];
+  if (total > cap) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      latch(st, TERA_ECAPACITY);
+      need(st, total);
+      atomicExch(&st->abort, 1u);
+    }
+    return;
+  }
+  const u64 tile0 = (u64)blockIdx.x * kClassifyTile;
+  u64 run = tile_base[blockIdx.x];
+  for (int k = 0; k < kClassifyPerThread / 2; ++k) {
+    const u64 a0 = tile0 + (u64)k * (2 * kClassifyThreads) + 2u * threadIdx.x;
+    u32 m[2] = {0u, 0u};
+    int o[2] = {0, 0};
+    if (a0 + 1 < n) {
+      uint2 mm = *reinterpret_cast<const uint2*>(mask + a0);
+      m[0] = mm.x; m[1] = mm.y;
+      if (m[0] | m[1]) {
+        int2 oo = *reinterpret_cast<const int2*>(owner + a0);
+        o[0] = oo.x; o[1] = oo.y;
+      }
+    } else if (a0 < n) {
+      m[0] = mask[a0];
+      if (m[0]) o[0] = owner[a0];
+    }
+    const u32 c = __popc(m[0]) + __popc(m[1]);
+    u64 tot;
+    u64 ex = block_excl_scan<u64>((u64)c, sm, &tot);
+    u64 pos = run + ex;
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      u32 mm = m[q];
+      while (mm) {
+        int b = __ffs(mm) - 1;
+        mm &= mm - 1;
+        keys[pos] = (u32)o[q] * 27u + (u32)b;
+        vals[pos] = (u32)(a0 + q);
+        ++pos;
+      }
+    }
+    run += tot;
+  }
+}
+
+__device__ __forceinline__ u64 live_entries(const u64* total_ptr, u64 cap) {
+  u64 t = *total_ptr;
+  return t > cap ? 0 : t;
+}
+
+// Digit histogram of one sort tile; hist is digit-major: hist[d * n_tiles + t].
+__global__ void __launch_bounds__(kSortThreads)
+    rs_hist_kernel(const u32* __restrict__ keys, const u64* __restrict__ total_ptr, u64 cap,
+                   u32 shift, u32 radix, u32* __restrict__ hist, u32 n_tiles) {
+  __shared__ u32 cnt[kRadix];
+  const u64 E = live_entries(total_ptr, cap);
+  for (u32 d = threadIdx.x; d < radix; d += blockDim.x) cnt[d] = 0;
+  __syncthreads();
+  const u64 t0 = (u64)blockIdx.x * kSortTile;
+  if (t0 < E) {
+#pragma unroll 4
+    for (int k = 0; k < kSortPerThread; ++k) {
+      u64 i = t0 + (u64)k * kSortThreads + threadIdx.x;
+      if (i < E) atomicAdd(&cnt[(keys[i] >> shift) & (radix - 1)], 1u);
+    }
+  }
+  __syncthreads();
+  for (u32 d = threadIdx.x; d < radix; d += blockDim.x) hist[(u64)d * n_tiles + blockIdx.x] = cnt[d];
+}
+
+// Stable scatter of one sort tile.  The tile is consumed in kSortPerThread
+// rounds of kSortThreads consecutive entries (entry r*256 + t to thread t);
+// inside a round, equal digits are ranked by warp (match_any) and warp index.
+__global__ void __launch_bounds__(kSortThreads)
+    rs_scatter_kernel(const u32* __restrict__ keys_in, const u32* __restrict__ vals_in,
+                      u32* __restrict__ keys_out, u32* __restrict__ vals_out,
+                      const u64* __restrict__ total_ptr, u64 cap, u32 shift, u32 radix,
+                      const u32* __restrict__ hist_scan, u32 n_tiles) {
+  constexpr int kWarps = kSortThreads / 32;
+  __shared__ u32 base[kRadix];
+  __shared__ u32 wcnt[kWarps][kRadix];
+  __shared__ u32 rtot[kRadix];
+  const u64 E = live_entries(total_ptr, cap);
+  const u64 t0 = (u64)blockIdx.x * kSortTile;
+  if (t0 >= E) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (u32 d = threadIdx.x; d < radix; d += blockDim.x) {
+    base[d] = hist_scan[(u64)d * n_tiles + blockIdx.x];
+    for (int w = 0; w < kWarps; ++w) wcnt[w][d] = 0;
+  }
+  __syncthreads();
+  for (int k = 0; k < kSortPerThread; ++k) {
+    const u64 i = t0 + (u64)k * kSortThreads + threadIdx.x;
+    if (t0 + (u64)k * kSortThreads >= E) break;  // block-uniform
+    const bool live = i < E;
+    u32 key = live ? keys_in[i] : 0u;
+    u32 val = live ? vals_in[i] : 0u;
+    u32 d = live ? ((key >> shift) & (radix - 1)) : radix;  // sentinel digit for padding
+    u32 peers = __match_any_sync(0xFFFFFFFFu, d);
+    u32 rank = __popc(peers & ((1u << lane) - 1u));
+    if (live && rank == 0) wcnt[warp][d] = __popc(peers);
+    __syncthreads();
+    for (u32 dd = threadIdx.x; dd < radix; dd += blockDim.x) {
+      u32 s = 0;
+      for (int w = 0; w < kWarps; ++w) {
+        u32 c = wcnt[w][dd];
+        wcnt[w][dd] = s;
+        s += c;
+      }
+      rtot[dd] = s;
+    }
+    __syncthreads();
+    if (live) {
+      u32 pos = base[d] + wcnt[warp][d] + rank;
+      keys_out[pos] = key;
+      vals_out[pos] = val;
+    }
+    __syncthreads();
+    for (u32 dd = threadIdx.x; dd < radix; dd += blockDim.x) {
+      base[dd] += rtot[dd];
+      for (int w = 0; w < kWarps; ++w) wcnt[w][dd] = 0;
+    }
+    __syncthreads();
+  }
+}
+
+__device__ __forceinline__ u64 lower_bound_u32(const u32* a, u64 n, u32 v) {
+  u64 lo = 0, hi = n;
+  while (lo < hi) {
+    u64 mid = (lo + hi) >> 1;
+    if (a[mid] < v) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+__global__ void pair_off_kernel(const u32* __restrict__ sorted_keys,
+                                const u64* __restrict__ total_ptr, u64 cap, u64 n_pairs,
+                                u64* __restrict__ pair_off, u64* __restrict__ pair_count,
+                                DevStats* stats) {
+  const u64 E = live_entries(total_ptr, cap);
+  if (blockIdx.x == 0 && threadIdx.x == 0) stats->records += E;
+  for (u64 p = (u64)blockIdx.x * blockDim.x + threadIdx.x; p <= n_pairs;
+       p += (u64)gridDim.x * blockDim.x) {
+    u64 a = lower_bound_u32(sorted_keys, E, (u32)p);
+    pair_off[p] = a;
+    if (p < n_pairs) pair_count[p] = lower_bound_u32(sorted_keys, E, (u32)(p + 1)) - a;
+  }
+}
+
+}  // namespace
+
+extern "C" tera_status tera_partition(tera_ctx* ctx, const tera_soa* soa, tera_partition_out* out,
+                                      void* stream) {
+  if (!ctx || !soa || !out) return TERA_EINVAL;
+  if (soa->n < 0 || soa->n > (int64_t)0xFFFFFFFFll) return TERA_EINVAL;
+  if (soa->n > 0 && (!soa->x || !soa->y || !soa->z)) return TERA_EINVAL;
+  if (!out->owner || !out->mask || !out->pair_count || !out->pair_off ||
+      (out->idx_capacity > 0 && !out->pair_idx))
+    return TERA_EINVAL;
+  if (out->idx_capacity > 0xFFFFFFFFull) return TERA_EINVAL;
+  // 16-byte loads of x, y, z and 8-byte stores of owner / mask
+  if (((uintptr_t)soa->x | (uintptr_t)soa->y | (uintptr_t)soa->z) & 15u) return TERA_EINVAL;
+  if (((uintptr_t)out->owner | (uintptr_t)out->mask) & 7u) return TERA_EINVAL;
+  cudaSetDevice(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  const u64 n = (u64)soa->n;
+  tera_status st;
+  if ((st = ensure_agents(ctx, soa->n, s)) != TERA_OK) return st;
+  if (!ctx->tile_cnt || !ctx->tile_base) return TERA_ENOMEM;
+  if ((st = ensure_records(ctx, out->idx_capacity, s)) != TERA_OK) return st;
+  ctx->iterations += 1;
+  cudaMemsetAsync(&ctx->d_status->abort, 0, sizeof(u32), s);
+  const u64 tiles = n == 0 ? 1 : (n + kClassifyTile - 1) / kClassifyTile;
+  if (n == 0) cudaMemsetAsync(ctx->tile_cnt, 0, sizeof(u32), s);
+  prof_begin(ctx, s);
+  classify_kernel<<<(unsigned)tiles, kClassifyThreads, 0, s>>>(
+      reinterpret_cast<const u64*>(soa->x), reinterpret_cast<const u64*>(soa->y),
+      reinterpret_cast<const u64*>(soa->z), n, ctx->d_grid, out->owner, out->mask, ctx->tile_cnt,
+      ctx->d_status, ctx->d_epoch, ctx->d_stats);
+  if ((st = check_launch(ctx, "classify_kernel", s)) != TERA_OK) return st;
+  if ((st = scan_u32(ctx, ctx->tile_cnt, ctx->tile_base, nullptr, tiles, s)) != TERA_OK) return st;
+
+  // Sort passes over ceil(bits / 8) digits of the pair index.
+  const u64 P = ctx->n_pairs;
+  int bits = 1;
+  while ((1ull << bits) < P) ++bits;
+  const int passes = (bits + kRadixBits - 1) / kRadixBits;
+  const int dbits = (bits + passes - 1) / passes;
+  const u32 radix = 1u << dbits;
+  const u64 cap = out->idx_capacity;
+  const u64* total_ptr = ctx->tile_base + tiles;
+  u32* kin = ctx->keys_a;
+  u32* vin = (passes & 1) ? ctx->vals_b : out->pair_idx;
+  u32* kout = ctx->keys_b;
+  u32* vout = (passes & 1) ? out->pair_idx : ctx->vals_b;
+  if (cap > 0 || n > 0) {
+    prof_begin(ctx, s);
+    emit_kernel<<<(unsigned)tiles, kClassifyThreads, 0, s>>>(
+        out->owner, out->mask, n, ctx->tile_base, tiles, kin, vin ? vin : ctx->vals_b, cap,
+        ctx->d_status);
+    if ((st = check_launch(ctx, "emit_kernel", s)) != TERA_OK) return st;
+  }
+  const u64 sort_tiles = cap == 0 ? 1 : (cap + kSortTile - 1) / kSortTile;
+  for (int pass = 0; pass < passes && cap > 0; ++pass) {
+    const u32 shift = (u32)(pass * dbits);
+    prof_begin(ctx, s);
+    rs_hist_kernel<<<(unsigned)sort_tiles, kSortThreads, 0, s>>>(kin, total_ptr, cap, shift, radix,
+                                                                 ctx->rs_hist, (u32)sort_tiles);
+    if ((st = check_launch(ctx, "rs_hist_kernel", s)) != TERA_OK) return st;
+    if ((st = scan_u32(ctx, ctx->rs_hist, nullptr, ctx->rs_hist, (u64)radix * sort_tiles, s)) !=
+        TERA_OK)
+      return st;
+    prof_begin(ctx, s);
+    rs_scatter_kernel<<<(unsigned)sort_tiles, kSortThreads, 0, s>>>(
+        kin, vin, kout, vout, total_ptr, cap, shift, radix, ctx->rs_hist, (u32)sort_tiles);
+    if ((st = check_launch(ctx, "rs_scatter_kernel", s)) != TERA_OK) return st;
+    u32* tk = kin; kin = kout; kout = tk;
+    u32* tv = vin; vin = vout; vout = tv;
+  }
+  // after the loop, (kin, vin) hold the sorted entries; vin == out->pair_idx
+  ctx->rec_pair = kin;
+  prof_begin(ctx, s);
+  pair_off_kernel<<<(unsigned)((P + 256) / 256), 256, 0, s>>>(
+      kin, total_ptr, cap, P, reinterpret_cast<u64*>(out->pair_off),
+      reinterpret_cast<u64*>(out->pair_count), ctx->d_stats);
+  return check_launch(ctx, "pair_off_kernel", s);
+}
