@@ -180,6 +180,34 @@ tera_status tera_delta_decode(tera_ctx* ctx, const uint8_t* wire, const uint64_t
                               uint32_t pair_begin, uint32_t pair_end, uint8_t* recv,
                               uint64_t recv_capacity_units, uint64_t* recv_off, void* stream);
 
+/* The decode step for callers that cannot allocate device memory (no
+ * counterpart in the paper).  Callers that are capturing a stream into a CUDA
+ * graph, hosts whose device memory is reserved up front by their own pool,
+ * and loops that forbid allocation after start-up cannot call cudaMalloc, and
+ * so cannot create a tera_ctx.  This variant decodes every pair [0, n_pairs)
+ * exactly as tera_delta_decode does (same arguments and outputs, same bytes),
+ * but takes all of its scratch memory from one fixed array in the library's
+ * device memory (about 16.5 MB per GPU that loads the library, held until the
+ * process exits); it calls no cudaMalloc, cudaFree or allocating routine.
+ *  - Limits: n_pairs <= 32768 (TERA_ECAPACITY beyond, returned at once) and
+ *    at most 393216 codec tiles of 256 entries (about 100M slots + new
+ *    records; TERA_ECAPACITY, latched on the device, beyond).
+ *  - n_pairs must be a multiple of 27 (the grid's box count times 27).
+ *  - The first call on a device looks up the array's device address for
+ *    that device (with it current); make that first call before any stream
+ *    capture.
+ *  - Every call shares the array, which keeps the last call's contents: calls
+ *    that overlap on the GPU (other streams, other threads) race on it; the
+ *    caller must serialize them.
+ *  - Returns the device status of this call: it synchronizes `stream` and
+ *    reads the status word back; *required_capacity (optional) is set on
+ *    TERA_ECAPACITY.  No context status is touched. */
+tera_status tera_delta_decode_noalloc(const uint8_t* wire, const uint64_t* wire_off,
+                                      const uint8_t* ref_prev, const uint64_t* ref_off_prev,
+                                      uint64_t n_pairs, uint32_t class_id, uint8_t* recv,
+                                      uint64_t recv_capacity_units, uint64_t* recv_off,
+                                      uint64_t* required_capacity, void* stream);
+
 /* Sec. 2.2.1 "Deserialization": check the TAIO header of ONE pair buffer
  * (device pointer `buf`, `len` bytes available) on the host and return a
  * device pointer to its first record and the record count.  Reads the

@@ -55,6 +55,8 @@ SIGNATURES = {
     "tera_pack": (C.c_int, [P, C.POINTER(Soa), C.POINTER(PartitionOut), u32, u32, P, u64, P]),
     "tera_delta_encode": (C.c_int, [P, P, P, P, P, u32, u32, P, P, u64, P, P, C.c_int, P]),
     "tera_delta_decode": (C.c_int, [P, P, P, P, P, u32, u32, P, u64, P, P]),
+    "tera_delta_decode_noalloc": (C.c_int, [P, P, P, P, u64, u32, P, u64, P,
+                                            C.POINTER(C.c_uint64), P]),
     "tera_unpack_inplace": (C.c_int, [P, u64, u32, C.POINTER(C.c_void_p),
                                       C.POINTER(C.c_uint64), P]),
     "tera_unpack_validate": (C.c_int, [P, P, P, P]),

@@ -276,6 +276,7 @@ __global__ void __launch_bounds__(kCodecTile) dec_emit_kernel(DecArgs A) {
 
 }  // namespace
 
+#ifndef TERA_DECODE_KERNELS_ONLY
 extern "C" tera_status tera_delta_decode(tera_ctx* ctx, const uint8_t* wire,
                                          const uint64_t* wire_off, const uint8_t* ref_prev,
                                          const uint64_t* ref_off_prev, uint32_t pair_begin,
@@ -331,3 +332,4 @@ extern "C" tera_status tera_delta_decode(tera_ctx* ctx, const uint8_t* wire,
   dec_emit_kernel<<<g, kCodecTile, 0, s>>>(A);
   return check_launch(ctx, "dec_emit_kernel", s);
 }
+#endif  // TERA_DECODE_KERNELS_ONLY
