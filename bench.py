@@ -189,6 +189,8 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=2_000_000)
     ap.add_argument("--ref-agents", type=int, default=1_000_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--agents", type=int, default=0,
+                    help="override the workload's agent count (profiling on a smaller case)")
     ap.add_argument("--profile-table", action="store_true", help="print per-kernel table to stderr")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "tera":
@@ -208,6 +210,9 @@ def main():
     if world > 1:
         dist.init_process_group("nccl")
     wl = WORKLOADS[args.workload]
+    if args.agents:
+        from synth import scaled
+        wl = scaled(wl, args.agents)
     total_steps = args.warmup + args.steps
     # replicas: each rank runs its own seeded population (weak scaling, no exchange between ranks)
     gen = Generator(wl, device="cuda", seed=wl.seed + 7919 * rank)
@@ -316,7 +321,8 @@ def main():
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
         "data": "synthetic",
-        "config": {"workload": args.workload, "agents": int(states[args.warmup]["x"].shape[0]),
+        "config": {"workload": args.workload + (f"@{args.agents}" if args.agents else ""),
+                   "agents": int(states[args.warmup]["x"].shape[0]),
                    "grid": list(wl.grid), "aura_width": wl.w, "path": args.path,
                    "l2": "inputs larger than L2 (64 B/agent state per step)",
                    "parallelism": f"replicas{world}"},

@@ -240,7 +240,7 @@ tera_status ensure_agents(tera_ctx* ctx, int64_t n, cudaStream_t s) {
 
 tera_status ensure_records(tera_ctx* ctx, uint64_t cap, cudaStream_t s) {
   (void)s;
-  if (cap <= ctx->cap_records && ctx->table) return TERA_OK;
+  if (cap <= ctx->cap_records && ctx->seg) return TERA_OK;
   cudaDeviceSynchronize();
   u64 c = cap < 1024 ? 1024 : cap;
   tera_status st;
@@ -251,12 +251,11 @@ tera_status ensure_records(tera_ctx* ctx, uint64_t cap, cudaStream_t s) {
   if ((st = alloc_dev(ctx->rs_hist, (u64)kRadix * tiles + 1)) != TERA_OK) return st;
   if ((st = alloc_dev(ctx->matched, c)) != TERA_OK) return st;
   if ((st = alloc_dev(ctx->slot_src, c)) != TERA_OK) return st;
-  u64 tc = 1024;
-  while (tc < 2 * c) tc <<= 1;
-  if ((st = alloc_dev(ctx->table, tc)) != TERA_OK) return st;
-  // epoch 0 is never current, so a zeroed table is empty
-  cudaMemset(ctx->table, 0, sizeof(HashEntry) * tc);
-  ctx->table_cap = tc;
+  if ((st = alloc_dev(ctx->msg_id, c)) != TERA_OK) return st;
+  if ((st = alloc_dev(ctx->seg, 2 * c + 2 * ctx->n_pairs)) != TERA_OK) return st;
+  // epoch 0 is never current, so zeroed segments and flags are empty
+  cudaMemset(ctx->seg, 0, sizeof(u64) * (2 * c + 2 * ctx->n_pairs));
+  cudaMemset(ctx->matched, 0, sizeof(u32) * c);
   ctx->cap_records = c;
   return ensure_scan_part(ctx, (u64)kRadix * tiles + 1);
 }
@@ -373,7 +372,8 @@ tera_status tera_ctx_destroy(tera_ctx* c) {
   free_dev(c->rs_hist);
   free_dev(c->scan_part);
   free_dev(c->d_total);
-  free_dev(c->table);
+  free_dev(c->seg);
+  free_dev(c->msg_id);
   free_dev(c->matched);
   free_dev(c->slot_src);
   free_dev(c->unit_off);

@@ -22,14 +22,18 @@ namespace {
 enum { PI_R = 0, PI_M = 1, PI_NST = 2, PI_MODE = 3, PI_MATCHED = 4, PI_NEW = 5, PI_SLOTPAY = 6,
        PI_PAY = 7 };
 
-__device__ __forceinline__ u32 hash_lookup(const HashEntry* __restrict__ table, u64 tmask,
-                                           u32 epoch, u32 pair, u64 id, u64 g_lo, u64 g_hi) {
-  u64 h = hash_key(pair, id) & tmask;
-  for (u64 probe = 0; probe <= tmask; ++probe) {
-    ulonglong2 e = *reinterpret_cast<const ulonglong2*>(table + ((h + probe) & tmask));
-    if ((u32)(e.y >> 32) != epoch) return kNoMatch;
-    u32 g = (u32)e.y;
-    if (e.x == id && g >= g_lo && g < g_hi) return g;
+// Record index (global) of the message record of pair p with this id, or
+// kNoMatch; probes pair p's hash segment, comparing ids in record order.
+__device__ __forceinline__ u32 seg_lookup(const u64* __restrict__ seg, const u64* __restrict__ msg_id,
+                                          u32 epoch, u32 p, u64 g_lo, u64 m, u64 id) {
+  const u64 base = seg_base(g_lo, p), size = seg_size(m);
+  u64 i = seg_start(id, size);
+  for (u64 probe = 0; probe < size; ++probe) {
+    const u64 e = seg[base + i];
+    if ((u32)(e >> 32) != epoch) return kNoMatch;
+    const u64 g = g_lo + (u32)e;
+    if (msg_id[g] == id) return (u32)g;
+    i = (i + 1 == size) ? 0 : i + 1;
   }
   return kNoMatch;
 }
@@ -132,8 +136,8 @@ struct EncArgs {
   u32* slot_src;
   u32* matched;
   uint8_t* reset;
-  const HashEntry* table;
-  u64 tmask;
+  u64* seg;
+  const u64* msg_id;
   const u32* epoch;
   u32 p0, p1;
   u32 class_id;
@@ -144,6 +148,42 @@ struct EncArgs {
 __device__ __forceinline__ void locate(const EncArgs& A, u64 U, u32* p, u64* local) {
   *p = A.unit_pair[U];
   *local = U - A.unit_off[*p - A.p0];
+}
+
+// Message units: index every record of the pair by id in the pair's segment.
+__global__ void __launch_bounds__(kCodecTile) enc_build_kernel(EncArgs A) {
+  const u64 units = *A.units_total;
+  const u32 epoch = *A.epoch;
+  for (u64 U = blockIdx.x; U < units; U += gridDim.x) {
+    u32 p;
+    u64 local;
+    locate(A, U, &p, &local);
+    const u64* pi = A.info + (u64)p * 8;
+    const u64 nst = pi[PI_NST];
+    if (local < nst) continue;  // slot unit
+    const u64 m = pi[PI_M];
+    const u64 k = (local - nst) * kCodecTile + threadIdx.x;
+    if (k >= m) continue;
+    const u64 g_lo = A.pair_off[p];
+    const u64 id = A.msg_id[g_lo + k];
+    const u64 base = seg_base(g_lo, p), size = seg_size(m);
+    const u64 mine = ((u64)epoch << 32) | k;
+    u64 i = seg_start(id, size);
+    for (u64 probe = 0; probe < size; ++probe) {
+      u64 cur = A.seg[base + i];
+      bool done = false;
+      while ((u32)(cur >> 32) != epoch) {  // empty for this iteration: claim it
+        const u64 prev = atomicCAS(&A.seg[base + i], cur, mine);
+        if (prev == cur) {
+          done = true;
+          break;
+        }
+        cur = prev;
+      }
+      if (done) break;
+      i = (i + 1 == size) ? 0 : i + 1;
+    }
+  }
 }
 
 __global__ void __launch_bounds__(kCodecTile) enc_match_kernel(EncArgs A) {
@@ -160,12 +200,12 @@ __global__ void __launch_bounds__(kCodecTile) enc_match_kernel(EncArgs A) {
     const u64 j = local * kCodecTile + threadIdx.x;
     U64x2 v{0, 0};
     if (j < r) {
-      const u64 g_lo = A.pair_off[p], g_hi = A.pair_off[p + 1];
+      const u64 g_lo = A.pair_off[p];
       const Rec R = load_rec(A.ref + (A.ref_off[p] + p + 1 + j) * kRecBytes);
-      u32 g = hash_lookup(A.table, A.tmask, epoch, p, R.w[0], g_lo, g_hi);
+      u32 g = seg_lookup(A.seg, A.msg_id, epoch, p, g_lo, pi[PI_M], R.w[0]);
       u32 code;
       if (g != kNoMatch) {
-        if (atomicExch(&A.matched[g], 1u) != 0u) latch(A.st, TERA_EINVAL);  // duplicate id
+        if (atomicExch(&A.matched[g], epoch) == epoch) latch(A.st, TERA_EINVAL);  // duplicate id
         const Rec M = load_rec(A.rec + ((u64)g + p + 1) * kRecBytes);
         Rec d;
 #pragma unroll
@@ -201,11 +241,10 @@ __global__ void __launch_bounds__(kCodecTile) enc_new_kernel(EncArgs A) {
     U64x2 v{0, 0};
     if (k < m) {
       const u64 g = A.pair_off[p] + k;
-      if (A.matched[g] == 0u) {
+      if (A.matched[g] != epoch) {
         const Rec M = load_rec(A.rec + (g + p + 1) * kRecBytes);
-        // a second record with the same (pair, id) would be found instead of this one
-        if (hash_lookup(A.table, A.tmask, epoch, p, M.w[0], A.pair_off[p], A.pair_off[p + 1]) !=
-            (u32)g)
+        // a second record with the same id in this pair would be found instead of this one
+        if (seg_lookup(A.seg, A.msg_id, epoch, p, A.pair_off[p], m, M.w[0]) != (u32)g)
           latch(A.st, TERA_EINVAL);
         u32 b;
         rec_code(M, &b);
@@ -312,6 +351,7 @@ __global__ void __launch_bounds__(kCodecTile) enc_emit_kernel(EncArgs A) {
   __shared__ U64x2 sm[33];
   __shared__ __align__(16) uint8_t stage[kCodecTile * kRecBytes + 32];
   const u64 units = *A.units_total;
+  const u32 epoch = *A.epoch;
   for (u64 U = blockIdx.x; U < units; U += gridDim.x) {
     u32 p;
     u64 local;
@@ -344,7 +384,7 @@ __global__ void __launch_bounds__(kCodecTile) enc_emit_kernel(EncArgs A) {
       }
     } else if (e < pi[PI_M]) {
       g = A.pair_off[p] + e;
-      if (A.matched[g] == 0u) {
+      if (A.matched[g] != epoch) {
         cur = load_rec(A.rec + (g + p + 1) * kRecBytes);
         u32 b = 0;
 #pragma unroll
@@ -426,8 +466,8 @@ extern "C" tera_status tera_delta_encode(tera_ctx* ctx, const uint8_t* rec_arena
   A.slot_src = ctx->slot_src;
   A.matched = ctx->matched;
   A.reset = ctx->d_reset;
-  A.table = ctx->table;
-  A.tmask = ctx->table_cap - 1;
+  A.seg = ctx->seg;
+  A.msg_id = ctx->msg_id;
   A.epoch = ctx->d_epoch;
   A.p0 = pair_begin;
   A.p1 = pair_end;
@@ -446,6 +486,9 @@ extern "C" tera_status tera_delta_encode(tera_ctx* ctx, const uint8_t* rec_arena
   const u64 est_units = 2 * (ctx->cap_records / kCodecTile) + 2 * (u64)(pair_end - pair_begin) + 1;
   const u64 maxg = (u64)grid_for(ctx, 8);
   const unsigned g = (unsigned)(est_units < maxg ? est_units : maxg);
+  prof_begin(ctx, s);
+  enc_build_kernel<<<g, kCodecTile, 0, s>>>(A);
+  if ((st = check_launch(ctx, "enc_build_kernel", s)) != TERA_OK) return st;
   prof_begin(ctx, s);
   enc_match_kernel<<<g, kCodecTile, 0, s>>>(A);
   if ((st = check_launch(ctx, "enc_match_kernel", s)) != TERA_OK) return st;

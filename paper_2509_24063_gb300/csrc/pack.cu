@@ -3,10 +3,10 @@
 // class identity is written once in the buffer header.  The receiver can use
 // the buffer in place.
 //
-// pack_kernel: four adjacent threads build one record (each gathers two of
-// the eight struct-of-arrays columns and writes 16 bytes), so a record leaves
-// as one 64-byte segment.  The thread holding the id also indexes the record
-// by (pair, id) in the context's hash table for the matching step.
+// pack_kernel: eight adjacent threads build one record (each gathers one of
+// the eight struct-of-arrays columns and writes one word), so a record leaves
+// as one 64-byte segment.  The ids are also written in record order for the
+// matching step.
 #include "tera_internal.cuh"
 
 using namespace tera;
@@ -16,25 +16,6 @@ namespace {
 struct SoaPtrs {
   const u64* col[8];  // id, x, y, z, diameter, volume, adherence, density (as raw 64-bit words)
 };
-
-__device__ __forceinline__ void hash_insert(HashEntry* __restrict__ table, u64 tmask, u32 epoch,
-                                            u32 pair, u64 id, u32 g, DevStatus* st) {
-  u64 h = hash_key(pair, id) & tmask;
-  const u64 meta_new = ((u64)epoch << 32) | (u64)g;
-  for (u64 probe = 0; probe <= tmask; ++probe) {
-    HashEntry* e = table + ((h + probe) & tmask);
-    u64 meta = *reinterpret_cast<volatile u64*>(&e->meta);
-    while ((u32)(meta >> 32) != epoch) {
-      u64 prev = atomicCAS(&e->meta, meta, meta_new);
-      if (prev == meta) {
-        e->id = id;
-        return;
-      }
-      meta = prev;  // someone claimed or changed it; re-examine this slot
-    }
-  }
-  latch(st, TERA_ECAPACITY);  // table full: cannot happen with capacity >= 2x records
-}
 
 __device__ __forceinline__ const u64* column(const SoaPtrs& s, u32 w) {
   // select, not an indexed load from the parameter block
@@ -55,8 +36,7 @@ __device__ __forceinline__ const u64* column(const SoaPtrs& s, u32 w) {
 __global__ void __launch_bounds__(256)
     pack_kernel(SoaPtrs soa, const u32* __restrict__ pair_idx, const u64* __restrict__ pair_off,
                 const u32* __restrict__ rec_pair, u32 p0, u32 p1, uint8_t* __restrict__ arena,
-                u64 arena_units, u32 class_id, HashEntry* __restrict__ table, u64 tmask,
-                const u32* __restrict__ epoch_ptr, u32* __restrict__ matched, DevStatus* st) {
+                u64 arena_units, u32 class_id, u64* __restrict__ msg_id, DevStatus* st) {
   const u64 g_lo = pair_off[p0], g_hi = pair_off[p1];
   if (g_hi + p1 > arena_units) {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -65,7 +45,6 @@ __global__ void __launch_bounds__(256)
     }
     return;
   }
-  const u32 epoch = *epoch_ptr;
   const u64 stride = (u64)gridDim.x * blockDim.x;
   const u64 tid = (u64)blockIdx.x * blockDim.x + threadIdx.x;
   // headers of the pair range
@@ -82,10 +61,7 @@ __global__ void __launch_bounds__(256)
     const u32 i = pair_idx[g];
     const u64 v = col[i];
     reinterpret_cast<u64*>(arena + (g + p + 1) * kRecBytes)[w] = v;
-    if (w == 0) {
-      hash_insert(table, tmask, epoch, p, v, (u32)g, st);
-      matched[g] = 0u;
-    }
+    if (w == 0) msg_id[g] = v;  // ids in record order, for the matching step
   }
 }
 
@@ -123,8 +99,6 @@ extern "C" tera_status tera_pack(tera_ctx* ctx, const tera_soa* soa, const tera_
   prof_begin(ctx, s);
   pack_kernel<<<blocks, 256, 0, s>>>(p, part->pair_idx, reinterpret_cast<const u64*>(part->pair_off),
                                      ctx->rec_pair, pair_begin, pair_end, rec_arena, arena_units,
-                                     ctx->class_id,
-                                     ctx->table, ctx->table_cap - 1, ctx->d_epoch, ctx->matched,
-                                     ctx->d_status);
+                                     ctx->class_id, ctx->msg_id, ctx->d_status);
   return check_launch(ctx, "pack_kernel", s);
 }

@@ -24,11 +24,17 @@ struct SmemGrid {
   u64 kth[3][kMaxAxis];
   u64 klo[3], khi[3];
   int n[3];
+  int top[3];  // largest power of two <= n - 1 (0 when n == 1): first binary-search step
 };
 
 __device__ __forceinline__ void load_grid(SmemGrid& s, const GridTables* __restrict__ g) {
   if (threadIdx.x < 3) {
-    s.n[threadIdx.x] = g->n[threadIdx.x];
+    const int n = g->n[threadIdx.x];
+    int top = 0;
+    while (2 * (top ? top : 1) <= n - 1) top = top ? 2 * top : 1;
+    if (top == 0 && n - 1 >= 1) top = 1;
+    s.top[threadIdx.x] = top;
+    s.n[threadIdx.x] = n;
     s.klo[threadIdx.x] = g->klo[threadIdx.x];
     s.khi[threadIdx.x] = g->khi[threadIdx.x];
   }
@@ -55,7 +61,7 @@ __device__ __forceinline__ u32 classify_axis(u64 k, int a, const SmemGrid& s, in
   }
   const int n = s.n[a];
   int i = 0;
-  for (int step = kMaxAxis; step > 0; step >>= 1)
+  for (int step = s.top[a]; step > 0; step >>= 1)
     if (i + step <= n - 1 && k >= s.ke[a][i + step]) i += step;
   *idx = i;
   const u32 lowq = (i > 0) && (k < s.ktl[a][i]);

@@ -71,10 +71,6 @@ struct DevStats {
   u64 iterations, agents, records, ref_slots, holes, new_records, payload_bytes, wire_bytes;
 };
 
-struct HashEntry {
-  u64 id;
-  u64 meta;  // (epoch << 32) | global record index
-};
 
 __device__ __forceinline__ void latch(DevStatus* s, u32 code) { atomicCAS(&s->code, 0u, code); }
 __device__ __forceinline__ void need(DevStatus* s, u64 req) { atomicMax(&s->required, req); }
@@ -89,8 +85,13 @@ __device__ __forceinline__ u64 mix64(u64 z) {
   return z;
 }
 
-__device__ __forceinline__ u64 hash_key(u32 pair, u64 id) {
-  return mix64(id * 0x9E3779B97F4A7C15ull ^ ((u64)pair << 17) ^ (u64)pair);
+// Per-pair hash segments: pair p owns 2 m_p + 2 entries starting at
+// 2 pair_off[p] + 2 p; an entry is (epoch << 32) | record index within the
+// pair, and entries of older epochs are empty, so nothing is ever cleared.
+__device__ __forceinline__ u64 seg_base(u64 pair_off_p, u32 p) { return 2 * pair_off_p + 2 * (u64)p; }
+__device__ __forceinline__ u64 seg_size(u64 m) { return 2 * m + 2; }
+__device__ __forceinline__ u64 seg_start(u64 id, u64 size) {
+  return ((mix64(id) >> 32) * size) >> 32;  // range reduction without division
 }
 
 // Significant low bytes of a word: 0 for zero, else 8 - (leading zero bits / 8).
@@ -262,10 +263,10 @@ struct tera_ctx {
   uint64_t scan_part_cap;
   tera::u64* d_total;       // [4] scalars: total records, ...
 
-  // hash table + codec scratch
-  tera::HashEntry* table;
-  uint64_t table_cap;  // power of two
-  uint32_t* matched;   // [cap_records] 1 when a reference slot took the record
+  // per-pair hash segments + codec scratch
+  tera::u64* seg;        // [2 cap_records + 2 P]
+  tera::u64* msg_id;     // [cap_records] id of every packed record, in record order
+  uint32_t* matched;     // [cap_records] epoch of the iteration in which a slot took the record
   uint32_t* slot_src;  // [cap_records]
   tera::u64* unit_off;  // [P + 1]
   uint64_t cap_units;
