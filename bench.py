@@ -43,6 +43,8 @@ def kernel_bytes(name, t):
         "enc_emit_kernel": 4 * R + 128 * (R - t["holes"]) + 4 * E + 64 * A + 4 * A + Y + 64 * M,
         "dec_sum_kernel": 4 * (R + A),
         "dec_emit_kernel": 4 * (R + A) + Y + 64 * (R - t["holes"]) + 64 * M,
+        # the persistent kernel runs every codec phase: encode + decode step model
+        "codec_persistent_kernel": 216 * E + Y + 132 * E + Y,
     }
     return table.get(name)
 
@@ -184,7 +186,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="tera", choices=["tera", "reference"])
     ap.add_argument("--workload", default="uniform_100m")
-    ap.add_argument("--path", default="all_pairs", choices=["all_pairs", "per_subdomain"])
+    ap.add_argument("--path", default="batched", choices=["batched", "all_pairs", "per_subdomain"])
+    ap.add_argument("--no-graph", action="store_true", help="batched path without CUDA graphs")
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-sample", type=int, default=2_000_000)
     ap.add_argument("--ref-agents", type=int, default=1_000_000)
@@ -225,17 +229,27 @@ def main():
     nmax = max(int(s["x"].shape[0]) for s in states)
     max_records = int(nmax * 0.35) + 4096 if wl.grid[0] >= 8 else 4 * nmax + 4096
     ctx = tera.Context(wl.lo, wl.hi, wl.grid, wl.w, device=local)
-    ex = tera.AuraExchange(ctx, max_agents=nmax, max_records=max_records,
-                           per_subdomain=(args.path == "per_subdomain"))
+    ex = tera.AuraExchange(ctx, max_agents=nmax, max_records=max_records, path=args.path)
     stream = torch.cuda.current_stream()
+    use_graph = args.path == "batched" and not args.no_graph
+    tune_info = None
 
     for t in range(args.warmup):
-        ex.step(states[t])
+        if t == 1 and args.path == "batched" and not args.no_autotune:
+            from paper_2509_24063_gb300 import autotune
+            tune, table = autotune.tune_batched(ex, states[t])
+            tune_info = {"tune": list(tune), "candidates": len(table)}
+        else:
+            ex.step(states[t])
     ctx.status()  # raises on any device-side error
     ctx.stats(reset=True)
     ctx.profile_table(reset=True)
     ctx.profile(True)
     launches0 = ctx.launches
+    graphs = None
+    if use_graph:
+        graphs = [ex.capture(states[t], t) for t in range(args.warmup, total_steps)]
+    launches_captured = ctx.launches - launches0
 
     if world > 1:
         dist.barrier()
@@ -244,13 +258,18 @@ def main():
     with ClockSampler(None if world == 1 else local) as clk:
         ev0.record(stream)
         for t in range(args.warmup, total_steps):
-            ex.step(states[t])
+            if graphs is not None:
+                graphs[t - args.warmup].replay()
+                ex.advance()
+            else:
+                ex.step(states[t])
         ev1.record(stream)
         torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     elapsed_ms = ev0.elapsed_time(ev1)
-    launches = ctx.launches - launches0
+    launches = launches_captured if graphs is not None else ctx.launches - launches0
+    del graphs
     ctx.profile(False)
     prof = ctx.profile_table(reset=True)
     stats = ctx.stats(reset=True)
@@ -274,7 +293,8 @@ def main():
     R, E, A, Y = stats["ref_slots"], stats["records"], stats["new_records"], \
         stats["payload_bytes"]
     codec_bytes = (216 * (E) + Y) + (132 * E + Y) - 0  # per-record model (matched/new alike)
-    codec_ms = sum(prof.get(k, (0, 0.0))[1] for k in prof if k.startswith(("pack", "enc_", "dec_")))
+    codec_ms = sum(prof.get(k, (0, 0.0))[1] for k in prof
+                   if k.startswith(("pack", "enc_", "dec_", "bat_", "codec_", "unit_map")))
     peaks, peak_kind = measured_peaks()
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     codec_gbs = codec_bytes / (codec_ms / 1e3) / 1e9 if codec_ms > 0 else None
@@ -303,7 +323,7 @@ def main():
     # end to end: host-resident state in, wire messages out, through the same API
     e2e = None
     if args.e2e_steps > 0:
-        e2e = run_e2e(args, tera, wl, states, nmax, max_records, local)
+        e2e = run_e2e(args, tera, wl, states, nmax, max_records, local, ex.tune)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -324,6 +344,7 @@ def main():
         "config": {"workload": args.workload + (f"@{args.agents}" if args.agents else ""),
                    "agents": int(states[args.warmup]["x"].shape[0]),
                    "grid": list(wl.grid), "aura_width": wl.w, "path": args.path,
+                   "cuda_graph": use_graph, "tune": tune_info,
                    "l2": "inputs larger than L2 (64 B/agent state per step)",
                    "parallelism": f"replicas{world}"},
         "encode_decode_gbs": codec_gbs,
@@ -344,7 +365,7 @@ def main():
     return 0
 
 
-def run_e2e(args, tera, wl, states, nmax, max_records, local):
+def run_e2e(args, tera, wl, states, nmax, max_records, local, tune=None):
     """Same metric through the public API with host buffers: the state columns
     are copied from pinned host memory and the wire slabs copied back, inside
     the timed region."""
@@ -356,7 +377,8 @@ def run_e2e(args, tera, wl, states, nmax, max_records, local):
         host.append({f: states[t][f].cpu().pin_memory() for f in fields})
     dev = {f: torch.empty(nmax, dtype=states[0][f].dtype, device="cuda") for f in fields}
     ctx = tera.Context(wl.lo, wl.hi, wl.grid, wl.w, device=local)
-    ex = tera.AuraExchange(ctx, max_agents=nmax, max_records=max_records)
+    ex = tera.AuraExchange(ctx, max_agents=nmax, max_records=max_records, path=args.path,
+                           tune=tune)
     out_host = torch.empty(ex.wire_cap, dtype=torch.uint8).pin_memory()
     stream = torch.cuda.current_stream()
 

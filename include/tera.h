@@ -138,7 +138,7 @@ tera_status tera_ctx_reserve(tera_ctx* ctx, int64_t max_agents, uint64_t max_rec
  * and x >= e[i+1] - w (the neighbour must exist).  Agents outside [lo, hi)
  * get owner -1, mask 0 and latch TERA_EDOMAIN.  More than idx_capacity
  * records latch TERA_ECAPACITY (required capacity reported) and leave every
- * pair empty.  Also starts a new iteration for the context's hash table. */
+ * pair empty. */
 tera_status tera_partition(tera_ctx* ctx, const tera_soa* soa, tera_partition_out* out,
                            void* stream);
 
@@ -207,6 +207,39 @@ tera_status tera_delta_decode_noalloc(const uint8_t* wire, const uint64_t* wire_
                                       uint64_t n_pairs, uint32_t class_id, uint8_t* recv,
                                       uint64_t recv_capacity_units, uint64_t* recv_off,
                                       uint64_t* required_capacity, void* stream);
+
+/* Schedule of the batched codec (picked by the autotuner; outputs do not
+ * depend on it): threads per block = entries per tile (128, 256 or 512),
+ * blocks per SM of the persistent launch (1..16), pairs per window of the
+ * work list (1..1024), and tiles per work item (1..64). */
+typedef struct {
+  int block;
+  int ctas_per_sm;
+  int window;
+  int tiles_per_item;
+} tera_tune;
+
+/* Steps a3-a5 for EVERY pair of one iteration in one persistent launch
+ * (batching of uneven subdomain buffers; not in the paper, which batches
+ * only large messages, Sec. 2.4 "Communication").  Produces exactly the bytes
+ * of tera_delta_encode + tera_delta_decode over all pairs: wire_off, the wire
+ * messages, wire_len, the new sender reference ref_next (laid out with
+ * pair_off) and the receive buffers recv with recv_off.  The receive layout
+ * is the iteration's pair layout (recv_off = pair_off); every message header's
+ * record count is checked against it (TERA_ECORRUPT otherwise).  The sender
+ * reference is ref_prev/ref_off_prev, the receiver's recv_prev/recv_off_prev
+ * (NULL pairs = empty references).  Must follow tera_partition and tera_pack
+ * (all pairs) of the same iteration on this context.  tune == NULL uses
+ * {256, 4, 64, 4}.  Asynchronous, no host synchronization (graph-capturable once
+ * scratch is reserved); device errors are latched in the status word, a wait
+ * that exceeds its bound latches TERA_ETIMEOUT. */
+tera_status tera_codec_batched(tera_ctx* ctx, const uint8_t* rec_arena, const uint64_t* pair_off,
+                               const uint8_t* ref_prev, const uint64_t* ref_off_prev,
+                               uint8_t* ref_next, uint8_t* wire, uint64_t wire_capacity,
+                               uint64_t* wire_off, uint64_t* wire_len, const uint8_t* recv_prev,
+                               const uint64_t* recv_off_prev, uint8_t* recv,
+                               uint64_t recv_capacity_units, uint64_t* recv_off, int mode,
+                               const tera_tune* tune, void* stream);
 
 /* Sec. 2.2.1 "Deserialization": check the TAIO header of ONE pair buffer
  * (device pointer `buf`, `len` bytes available) on the host and return a

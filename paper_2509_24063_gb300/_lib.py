@@ -44,6 +44,11 @@ class Stats(C.Structure):
                                           "new_records", "payload_bytes", "wire_bytes")]
 
 
+class Tune(C.Structure):
+    _fields_ = [("block", C.c_int), ("ctas_per_sm", C.c_int), ("window", C.c_int),
+                ("tiles_per_item", C.c_int)]
+
+
 # name -> (restype, argtypes); every symbol include/tera.h declares
 P, u32, u64, i64 = C.c_void_p, C.c_uint32, C.c_uint64, C.c_int64
 SIGNATURES = {
@@ -57,6 +62,8 @@ SIGNATURES = {
     "tera_delta_decode": (C.c_int, [P, P, P, P, P, u32, u32, P, u64, P, P]),
     "tera_delta_decode_noalloc": (C.c_int, [P, P, P, P, u64, u32, P, u64, P,
                                             C.POINTER(C.c_uint64), P]),
+    "tera_codec_batched": (C.c_int, [P, P, P, P, P, P, P, u64, P, P, P, P, P, u64, P, C.c_int,
+                                     C.POINTER(Tune), P]),
     "tera_unpack_inplace": (C.c_int, [P, u64, u32, C.POINTER(C.c_void_p),
                                       C.POINTER(C.c_uint64), P]),
     "tera_unpack_validate": (C.c_int, [P, P, P, P]),

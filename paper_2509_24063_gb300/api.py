@@ -175,6 +175,21 @@ class Context:
             pe, _ptr(recv), recv.numel() // 64, _ptr(recv_off), _stream(stream)),
             "tera_delta_decode")
 
+    def codec_batched(self, rec_arena, pair_off, ref_prev, ref_off_prev, ref_next, wire, wire_off,
+                      wire_len, recv_prev, recv_off_prev, recv, recv_off, mode=_lib.MODE_XOR,
+                      tune=None, stream=None):
+        """Encode + decode of every pair in one persistent launch (tera_codec_batched)."""
+        t = None
+        if tune is not None:
+            t = _lib.Tune(int(tune[0]), int(tune[1]), int(tune[2]),
+                          int(tune[3]) if len(tune) > 3 else 4)
+        check(self.lib.tera_codec_batched(
+            self.h, _ptr(rec_arena), _ptr(pair_off), _ptr(ref_prev), _ptr(ref_off_prev),
+            _ptr(ref_next), _ptr(wire), wire.numel(), _ptr(wire_off), _ptr(wire_len),
+            _ptr(recv_prev), _ptr(recv_off_prev), _ptr(recv), recv.numel() // 64, _ptr(recv_off),
+            int(mode), C.byref(t) if t is not None else None, _stream(stream)),
+            "tera_codec_batched")
+
     def unpack_inplace(self, arena: torch.Tensor, byte_offset: int, length: int, stream=None):
         """Header check of one TAIO buffer; returns (device address of record 0, count)."""
         view = C.c_void_p()

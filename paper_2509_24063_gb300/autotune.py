@@ -1,0 +1,104 @@
+"""Autotuner of the batched codec's schedule (tile/block size, resident blocks
+per SM, pairs per work-list window).
+
+The schedule never changes the bytes produced, only the time.  Candidates are
+timed on the real data of one iteration: after partition + pack, the batched
+codec is re-run with each candidate (it is idempotent: it reads the packed
+messages and both previous references and overwrites only its outputs), with
+CUDA events on the launching stream; the fastest is kept and cached on disk
+per (GPU, pair count, record count bucket).
+"""
+from __future__ import annotations
+
+import json
+import math
+import os
+
+import torch
+
+CANDIDATES = [(b, c, w, k) for b in (128, 256, 512) for c in (1024 // b, 2048 // b)
+              for w in (32, 256, 1024) for k in (1, 4, 16)]
+# blocks per SM above what fits 2048 threads cannot be resident
+MAX_RESIDENT = {128: 16, 256: 8, 512: 4}
+
+
+def cache_path() -> str:
+    base = os.environ.get("TERA_TUNE_CACHE") or os.path.join(
+        os.path.expanduser("~"), ".cache", "tera_gb300", "autotune.json")
+    return base
+
+
+def _key(ctx, records: int) -> str:
+    name = torch.cuda.get_device_name(ctx.device)
+    bucket = 0 if records <= 0 else int(round(math.log2(records)))
+    return f"{name}|P={ctx.n_pairs}|E~2^{bucket}"
+
+
+def load_cached(ctx, records: int):
+    try:
+        with open(cache_path()) as f:
+            v = json.load(f).get(_key(ctx, records))
+        return tuple(v["tune"]) if v else None
+    except Exception:
+        return None
+
+
+def store(ctx, records: int, tune, ms: float, table):
+    path = cache_path()
+    try:
+        os.makedirs(os.path.dirname(path), exist_ok=True)
+        try:
+            with open(path) as f:
+                data = json.load(f)
+        except Exception:
+            data = {}
+        data[_key(ctx, records)] = {"tune": list(tune), "ms": ms,
+                                    "candidates": {",".join(map(str, k)): v for k, v in table}}
+        with open(path + ".tmp", "w") as f:
+            json.dump(data, f, indent=1)
+        os.replace(path + ".tmp", path)
+    except OSError:
+        pass
+
+
+def tune_batched(ex, state: dict, reps: int = 2, candidates=None, use_cache: bool = True):
+    """Pick the batched-codec schedule for exchange `ex` on this state.
+
+    Runs one eager iteration of `ex` on `state` (advancing it), then times
+    every candidate by re-running the codec of that iteration.  Returns
+    (tune, {candidate: ms})."""
+    ctx = ex.ctx
+    stream = torch.cuda.current_stream()
+    t = ex.t
+    ex.step(state)
+    torch.cuda.synchronize()
+    records = int(ex.pair_off[t % 2][-1].item())
+    if use_cache:
+        cached = load_cached(ctx, records)
+        if cached is not None:
+            ex.tune = cached
+            return cached, {}
+    cur, prv = t % 2, (t + 1) % 2
+    first = t == 0
+    args = (ex.rec, ex.pair_off[cur], None if first else ex.ref[prv],
+            None if first else ex.pair_off[prv], ex.ref[cur], ex.wire, ex.wire_off, ex.wire_len,
+            None if first else ex.recv[prv], None if first else ex.recv_off[prv], ex.recv[cur],
+            ex.recv_off[cur])
+    results = []
+    for cand in (candidates or CANDIDATES):
+        if cand[1] > MAX_RESIDENT.get(cand[0], 8):
+            continue
+        ctx.codec_batched(*args, mode=ex.mode, tune=cand, stream=stream)  # warm
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            ctx.codec_batched(*args, mode=ex.mode, tune=cand, stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        results.append((cand, e0.elapsed_time(e1) / reps))
+    ctx.status()
+    ctx.stats(reset=True)
+    best, ms = min(results, key=lambda kv: kv[1])
+    ex.tune = best
+    store(ctx, records, best, ms, results)
+    return best, dict(results)

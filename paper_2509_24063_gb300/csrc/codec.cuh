@@ -1,0 +1,551 @@
+// Per-unit device functions of the difference codec (paper Sec. 2.3, steps B,
+// C and D, with the significant-byte packer of the compression stage), shared
+// by the per-call kernels (encode.cu, decode.cu) and the persistent batched
+// kernel (batched.cu).
+//
+// Work is cut into units of T entries (T = blockDim.x) that never cross a
+// pair.  For pair p: ceil(r/T) slot units (reference slots) then ceil(m/T)
+// message units (records of the message); decode units cover the r + a
+// entries of the received message.
+//
+// CG = true marks the persistent kernel: data that other blocks of the same
+// launch produce is read with ld.global.cg (L2), never from a stale L1 line.
+#pragma once
+
+#include "tera_internal.cuh"
+
+namespace tera {
+
+// Per-pair facts of the encode (stride 8 per pair).
+enum { PI_R = 0, PI_M = 1, PI_NST = 2, PI_MODE = 3, PI_MATCHED = 4, PI_NEW = 5, PI_SLOTPAY = 6,
+       PI_PAY = 7 };
+// Per-pair facts of the decode (stride 8 per pair).
+enum { DI_NS = 0, DI_NN = 1, DI_NH = 2, DI_PAY = 3, DI_OK = 4, DI_MODE = 5, DI_NT = 6 };
+
+template <bool CG, typename T>
+__device__ __forceinline__ T ldx(const T* p) {
+  if constexpr (CG) return __ldcg(p);
+  else return *p;
+}
+
+template <bool CG>
+__device__ __forceinline__ U64x2 ldx(const U64x2* p) {
+  if constexpr (CG) {
+    const ulonglong2 v = __ldcg(reinterpret_cast<const ulonglong2*>(p));
+    return U64x2{v.x, v.y};
+  } else {
+    return *p;
+  }
+}
+
+template <bool CG>
+__device__ __forceinline__ Rec load_rec_x(const uint8_t* p) {
+  if constexpr (!CG) return load_rec(p);
+  const ulonglong2* q = reinterpret_cast<const ulonglong2*>(p);
+  Rec r;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    ulonglong2 v = __ldcg(q + i);
+    r.w[2 * i] = v.x;
+    r.w[2 * i + 1] = v.y;
+  }
+  return r;
+}
+
+struct EncArgs {
+  const uint8_t* rec;      // packed messages (TAIO arena laid out with pair_off)
+  const u64* pair_off;
+  const uint8_t* ref;      // sender reference (may be null)
+  const u64* ref_off;
+  uint8_t* ref_next;
+  uint8_t* wire;
+  const u64* wire_off;
+  u64* wire_len;
+  const u64* unit_off;     // per-call path: units of range pair k start at unit_off[k]
+  const u64* units_total;
+  const u32* unit_pair;
+  U64x2* unit_sum;
+  U64x2* unit_base;
+  u64* info;
+  u32* slot_src;
+  u32* matched;
+  uint8_t* reset;
+  u64* seg;
+  const u64* msg_id;
+  const u32* epoch;
+  u32 p0, p1;
+  u32 class_id;
+  DevStatus* st;
+  DevStats* stats;
+};
+
+struct DecArgs {
+  const uint8_t* wire;
+  const u64* wire_off;
+  const uint8_t* ref;
+  const u64* ref_off;
+  uint8_t* recv;
+  u64* recv_off;
+  const u64* unit_off;
+  const u64* units_total;
+  const u32* unit_pair;
+  U64x2* unit_sum;
+  U64x2* unit_base;
+  u64* info;
+  u32 p0, p1;
+  u32 class_id;
+  DevStatus* st;
+};
+
+__device__ __forceinline__ u32 rec_code(const Rec& d, u32* bytes) {
+  u32 code = 0, b = 0;
+#pragma unroll
+  for (int w = 0; w < 8; ++w) {
+    u32 L = sig_bytes(d.w[w]);
+    code |= L << (4 * w);
+    b += L;
+  }
+  *bytes = b;
+  return code;
+}
+
+// Record index (global) of the message record of pair p with this id, or
+// kNoMatch; probes pair p's hash segment, comparing ids in record order.
+template <bool CG>
+__device__ __forceinline__ u32 seg_lookup(const u64* __restrict__ seg,
+                                          const u64* __restrict__ msg_id, u32 epoch, u32 p,
+                                          u64 g_lo, u64 m, u64 id) {
+  const u64 base = seg_base(g_lo, p), size = seg_size(m);
+  u64 i = seg_start(id, size);
+  for (u64 probe = 0; probe < size; ++probe) {
+    const u64 e = ldx<CG>(seg + base + i);
+    if ((u32)(e >> 32) != epoch) return kNoMatch;
+    const u64 g = g_lo + (u32)e;
+    if (msg_id[g] == id) return (u32)g;
+    i = (i + 1 == size) ? 0 : i + 1;
+  }
+  return kNoMatch;
+}
+
+// ---------------- encode ----------------
+
+// Message unit: index every record of the pair by id in the pair's segment.
+template <int T, bool CG>
+__device__ __forceinline__ void enc_build_unit(const EncArgs& A, u32 p, u64 local, u32 epoch) {
+  const u64* pi = A.info + (u64)p * 8;
+  const u64 nst = pi[PI_NST];
+  const u64 m = pi[PI_M];
+  const u64 k = (local - nst) * T + threadIdx.x;
+  if (k >= m) return;
+  const u64 g_lo = A.pair_off[p];
+  const u64 id = A.msg_id[g_lo + k];
+  const u64 base = seg_base(g_lo, p), size = seg_size(m);
+  const u64 mine = ((u64)epoch << 32) | k;
+  u64 i = seg_start(id, size);
+  for (u64 probe = 0; probe < size; ++probe) {
+    u64 cur = ldx<CG>(A.seg + base + i);
+    while ((u32)(cur >> 32) != epoch) {  // empty for this iteration: claim it
+      const u64 prev = atomicCAS(&A.seg[base + i], cur, mine);
+      if (prev == cur) return;
+      cur = prev;
+    }
+    i = (i + 1 == size) ? 0 : i + 1;
+  }
+}
+
+// Slot unit: find the message record with the slot's id, write the slot's
+// code, and return the unit's (payload bytes, non-placeholder slots).
+template <int T, bool CG>
+__device__ __forceinline__ void enc_match_unit(const EncArgs& A, u32 p, u64 local, u64 U,
+                                               u32 epoch, U64x2* sm) {
+  const u64* pi = A.info + (u64)p * 8;
+  const u64 r = pi[PI_R];
+  const u64 j = local * T + threadIdx.x;
+  U64x2 v{0, 0};
+  if (j < r) {
+    const u64 g_lo = A.pair_off[p];
+    const Rec R = load_rec(A.ref + (A.ref_off[p] + p + 1 + j) * kRecBytes);
+    u32 g = seg_lookup<CG>(A.seg, A.msg_id, epoch, p, g_lo, pi[PI_M], R.w[0]);
+    u32 code;
+    if (g != kNoMatch) {
+      if (atomicExch(&A.matched[g], epoch) == epoch) latch(A.st, TERA_EINVAL);  // duplicate id
+      const Rec M = load_rec(A.rec + ((u64)g + p + 1) * kRecBytes);
+      Rec d;
+#pragma unroll
+      for (int w = 0; w < 8; ++w) d.w[w] = M.w[w] ^ R.w[w];
+      u32 b;
+      code = rec_code(d, &b);
+      v = U64x2{b, 1};
+    } else {
+      code = 0xFu;  // placeholder
+    }
+    A.slot_src[A.ref_off[p] + j] = g;
+    reinterpret_cast<u32*>(A.wire + A.wire_off[p] + kHdrBytes)[j] = code;
+  }
+  U64x2 tot;
+  block_excl_scan2(v, sm, &tot);
+  if (threadIdx.x == 0) A.unit_sum[U] = tot;
+}
+
+// Message unit: records no slot took are new; (payload bytes, new records).
+template <int T, bool CG>
+__device__ __forceinline__ void enc_new_unit(const EncArgs& A, u32 p, u64 local, u64 U, u32 epoch,
+                                             U64x2* sm) {
+  const u64* pi = A.info + (u64)p * 8;
+  const u64 nst = pi[PI_NST];
+  const u64 m = pi[PI_M];
+  const u64 k = (local - nst) * T + threadIdx.x;
+  U64x2 v{0, 0};
+  if (k < m) {
+    const u64 g = A.pair_off[p] + k;
+    if (ldx<CG>(A.matched + g) != epoch) {
+      const Rec M = load_rec(A.rec + (g + p + 1) * kRecBytes);
+      // a second record with the same id in this pair would be found instead of this one
+      if (seg_lookup<CG>(A.seg, A.msg_id, epoch, p, A.pair_off[p], m, M.w[0]) != (u32)g)
+        latch(A.st, TERA_EINVAL);
+      u32 b;
+      rec_code(M, &b);
+      v = U64x2{b, 1};
+    }
+  }
+  U64x2 tot;
+  block_excl_scan2(v, sm, &tot);
+  if (threadIdx.x == 0) A.unit_sum[U] = tot;
+}
+
+// One warp: unit prefixes of pair p (units [u0, u0 + n_units)), header,
+// padding, the new reference's header and the iteration totals.
+template <bool CG>
+__device__ __forceinline__ void enc_scan_pair(const EncArgs& A, u32 p, u64 u0, u64 n_units) {
+  const int lane = threadIdx.x & 31;
+  u64* pi = A.info + (u64)p * 8;
+  const u64 nst = pi[PI_NST];
+  const u64 r = pi[PI_R], m = pi[PI_M];
+  U64x2 run{0, 0};
+  for (u64 b = 0; b < nst; b += 32) {
+    u64 i = b + lane;
+    U64x2 v = i < nst ? ldx<CG>(A.unit_sum + u0 + i) : U64x2{0, 0};
+    U64x2 incl = v;
+    for (int o = 1; o < 32; o <<= 1) {
+      U64x2 t = shfl_up(incl, o);
+      if (lane >= o) incl += t;
+    }
+    if (i < nst) A.unit_base[u0 + i] = run + incl - v;
+    run += U64x2{__shfl_sync(0xFFFFFFFFu, incl.a, 31), __shfl_sync(0xFFFFFFFFu, incl.b, 31)};
+  }
+  const u64 slot_pay = run.a, matched = run.b;
+  U64x2 run2{0, 0};
+  const u64 nmt = n_units - nst;
+  for (u64 b = 0; b < nmt; b += 32) {
+    u64 i = b + lane;
+    U64x2 v = i < nmt ? ldx<CG>(A.unit_sum + u0 + nst + i) : U64x2{0, 0};
+    U64x2 incl = v;
+    for (int o = 1; o < 32; o <<= 1) {
+      U64x2 t = shfl_up(incl, o);
+      if (lane >= o) incl += t;
+    }
+    if (i < nmt) {
+      U64x2 ex = run2 + incl - v;
+      A.unit_base[u0 + nst + i] = U64x2{slot_pay + ex.a, ex.b};
+    }
+    run2 += U64x2{__shfl_sync(0xFFFFFFFFu, incl.a, 31), __shfl_sync(0xFFFFFFFFu, incl.b, 31)};
+  }
+  const u64 n_new = run2.b, payload = slot_pay + run2.a;
+  const u64 body = (u64)kHdrBytes + 4 * (r + n_new) + payload;
+  const u64 msg = round16(body);
+  uint8_t* w = A.wire + A.wire_off[p];
+  if (lane == 0) {
+    if (matched + n_new != m) latch(A.st, TERA_EINVAL);
+    pi[PI_MATCHED] = matched;
+    pi[PI_NEW] = n_new;
+    pi[PI_SLOTPAY] = slot_pay;
+    pi[PI_PAY] = payload;
+    ulonglong2* h = reinterpret_cast<ulonglong2*>(w);
+    h[0] = make_ulonglong2((u64)kWireMagic | ((u64)kVersion << 32) | ((u64)kRecBytes << 48),
+                           (u64)A.class_id | (pi[PI_MODE] << 32));
+    h[1] = make_ulonglong2(r, n_new);
+    h[2] = make_ulonglong2(r - matched, payload);
+    h[3] = make_ulonglong2((u64)p, msg);
+    A.wire_len[p] = msg;
+    atomicAdd(&A.stats->ref_slots, r);
+    atomicAdd(&A.stats->holes, r - matched);
+    atomicAdd(&A.stats->new_records, n_new);
+    atomicAdd(&A.stats->payload_bytes, payload);
+    atomicAdd(&A.stats->wire_bytes, msg);
+    write_taio_header(A.ref_next + (A.pair_off[p] + p) * kRecBytes, A.class_id, p, m);
+    A.reset[p] = 0;
+  }
+  if (body + lane < msg) w[body + lane] = 0;  // zero padding (< 16 bytes)
+}
+
+__device__ __forceinline__ void stage_word(uint8_t* stage, u32& o, u64 v, u32 L) {
+  for (u32 b = 0; b < L; ++b) stage[o++] = (uint8_t)(v >> (8 * b));
+}
+
+// Store stage[s0, s0 + nbytes) to gA (s0 = gA mod 16): aligned 16-byte stores
+// inside, byte stores on the ragged edges shared with neighbouring units.
+__device__ __forceinline__ void flush_stage(const uint8_t* stage, uint8_t* gA, u64 nbytes) {
+  const u32 s0 = (u32)((uintptr_t)gA & 15u);
+  uint8_t* g16 = gA - s0;
+  const u32 end = s0 + (u32)nbytes;
+  const u32 nchunks = (end + 15u) >> 4;
+  for (u32 c = threadIdx.x; c < nchunks; c += blockDim.x) {
+    const u32 lo = c << 4, hi = lo + 16u;
+    if (lo >= s0 && hi <= end) {
+      *reinterpret_cast<uint4*>(g16 + lo) = *reinterpret_cast<const uint4*>(stage + lo);
+    } else {
+      for (u32 x = (lo > s0 ? lo : s0); x < (hi < end ? hi : end); ++x) g16[x] = stage[x];
+    }
+  }
+}
+
+// Any unit: payload bytes (staged), codes of new records, new reference.
+template <int T, bool CG>
+__device__ __forceinline__ void enc_emit_unit(const EncArgs& A, u32 p, u64 local, u64 U, u32 epoch,
+                                              U64x2* sm, uint8_t* stage) {
+  const u64* pi = A.info + (u64)p * 8;
+  const u64 nst = pi[PI_NST], r = pi[PI_R];
+  const u64 n_new = ldx<CG>(pi + PI_NEW);
+  const bool slot_unit = local < nst;
+  const u64 e = slot_unit ? local * T + threadIdx.x : (local - nst) * T + threadIdx.x;
+  Rec d, cur;
+  u32 L[8];
+  U64x2 v{0, 0};
+  u64 g = 0;
+  if (slot_unit) {
+    if (e < r) {
+      u32 gg = ldx<CG>(A.slot_src + A.ref_off[p] + e);
+      if (gg != kNoMatch) {
+        g = gg;
+        cur = load_rec(A.rec + (g + p + 1) * kRecBytes);
+        const Rec R = load_rec(A.ref + (A.ref_off[p] + p + 1 + e) * kRecBytes);
+        u32 b = 0;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) {
+          d.w[w] = cur.w[w] ^ R.w[w];
+          L[w] = sig_bytes(d.w[w]);
+          b += L[w];
+        }
+        v = U64x2{b, 1};
+      }
+    }
+  } else if (e < pi[PI_M]) {
+    g = A.pair_off[p] + e;
+    if (ldx<CG>(A.matched + g) != epoch) {
+      cur = load_rec(A.rec + (g + p + 1) * kRecBytes);
+      u32 b = 0;
+#pragma unroll
+      for (int w = 0; w < 8; ++w) {
+        d.w[w] = cur.w[w];
+        L[w] = sig_bytes(d.w[w]);
+        b += L[w];
+      }
+      v = U64x2{b, 1};
+    }
+  }
+  U64x2 tot;
+  U64x2 ex = block_excl_scan2(v, sm, &tot);
+  const U64x2 base = ldx<CG>(A.unit_base + U);
+  uint8_t* w8 = A.wire + A.wire_off[p];
+  uint8_t* gA = w8 + kHdrBytes + 4 * (r + n_new) + base.a;
+  const u32 s0 = (u32)((uintptr_t)gA & 15u);
+  if (v.b) {
+    u32 o = s0 + (u32)ex.a;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) stage_word(stage, o, d.w[w], L[w]);
+    u64 pos;
+    if (slot_unit) {
+      pos = base.b + ex.b;
+    } else {
+      const u64 rank = base.b + ex.b;
+      u32 code = 0;
+#pragma unroll
+      for (int w = 0; w < 8; ++w) code |= L[w] << (4 * w);
+      reinterpret_cast<u32*>(w8 + kHdrBytes)[r + rank] = code;
+      pos = ldx<CG>(pi + PI_MATCHED) + rank;
+    }
+    store_rec(A.ref_next + (A.pair_off[p] + p + 1 + pos) * kRecBytes, cur);
+  }
+  __syncthreads();
+  flush_stage(stage, gA, tot.a);
+  __syncthreads();
+}
+
+// ---------------- decode ----------------
+
+// Returns false when the code is malformed for entry e; nibbles summed.
+__device__ __forceinline__ bool check_code(u32 code, u64 e, u64 ns, bool* hole, u32* bytes) {
+  *bytes = 0;
+  *hole = (code & 0xFu) == 0xFu;
+  if (*hole) return e < ns && (code >> 4) == 0u;
+  u32 b = 0;
+  bool ok = true;
+#pragma unroll
+  for (int w = 0; w < 8; ++w) {
+    u32 L = (code >> (4 * w)) & 0xFu;
+    ok &= L <= 8u;
+    b += L;
+  }
+  if (e < ns) ok &= (code & 0xFu) == 0u;  // same id: the word-0 difference is zero
+  *bytes = b;
+  return ok;
+}
+
+// Full header check of pair p's message; writes the decode facts and returns
+// the error (0 when valid).  expect_m: when not ~0, the receive buffer size
+// the caller laid out for p, which the header's count must equal.
+template <bool CG>
+__device__ __forceinline__ u32 dec_check_header(const DecArgs& A, u32 p, u64 expect_m) {
+  const u64 avail = A.wire_off[p + 1] - A.wire_off[p];
+  const u64* h = reinterpret_cast<const u64*>(A.wire + A.wire_off[p]);
+  u64* pi = A.info + (u64)p * 8;
+  u32 err = 0;
+  u64 ns = 0, nn = 0, nh = 0, pay = 0, mode = 0;
+  if (avail < kHdrBytes) {
+    err = TERA_ECORRUPT;
+  } else {
+    const u64 w0 = ldx<CG>(h + 0), w1 = ldx<CG>(h + 1);
+    ns = ldx<CG>(h + 2);
+    nn = ldx<CG>(h + 3);
+    nh = ldx<CG>(h + 4);
+    pay = ldx<CG>(h + 5);
+    const u64 w6 = ldx<CG>(h + 6), msg = ldx<CG>(h + 7);
+    mode = w1 >> 32;
+    const u64 r = A.ref ? A.ref_off[p + 1] - A.ref_off[p] : 0;
+    if ((u32)w0 != kWireMagic || ((w0 >> 32) & 0xFFFF) != kVersion || (w0 >> 48) != kRecBytes ||
+        (u32)w1 != A.class_id || w6 != (u64)p) {
+      err = TERA_ECORRUPT;
+    } else if (mode == TERA_MODE_XOR) {
+      if (ns != r) err = TERA_EREFMISMATCH;
+    } else if (mode == TERA_MODE_RAW) {
+      if (ns != 0) err = TERA_ECORRUPT;
+    } else {
+      err = TERA_ECORRUPT;
+    }
+    if (!err) {
+      if (ns > avail || nn > avail || pay > avail || nh > ns) err = TERA_ECORRUPT;
+      else if (msg != round16((u64)kHdrBytes + 4 * (ns + nn) + pay) || msg > avail)
+        err = TERA_ECORRUPT;
+      else if (expect_m != ~0ull && ns - nh + nn != expect_m)
+        err = TERA_ECORRUPT;
+    }
+    if (!err && mode == TERA_MODE_XOR && A.ref) {
+      // the receiver's reference buffer must be the one this message refers to
+      const u64* rh = reinterpret_cast<const u64*>(A.ref + (A.ref_off[p] + p) * kRecBytes);
+      if ((u32)rh[0] != kTaioMagic || (u32)rh[1] != A.class_id || (u32)(rh[1] >> 32) != p ||
+          rh[2] != r)
+        err = TERA_ECORRUPT;
+    }
+  }
+  pi[DI_NS] = ns;
+  pi[DI_NN] = nn;
+  pi[DI_NH] = nh;
+  pi[DI_PAY] = pay;
+  pi[DI_OK] = err ? 0 : 1;
+  pi[DI_MODE] = mode;
+  return err;
+}
+
+template <int T, bool CG>
+__device__ __forceinline__ void dec_sum_unit(const DecArgs& A, u32 p, u64 local, u64 U,
+                                             U64x2* sm) {
+  u64* pi = A.info + (u64)p * 8;
+  const u64 ns = ldx<CG>(pi + DI_NS), n = ns + ldx<CG>(pi + DI_NN);
+  const bool ok = ldx<CG>(pi + DI_OK) != 0;
+  const u64 e = local * T + threadIdx.x;
+  U64x2 v{0, 0};
+  if (ok && e < n) {
+    const u32 code =
+        ldx<CG>(reinterpret_cast<const u32*>(A.wire + A.wire_off[p] + kHdrBytes) + e);
+    bool hole;
+    u32 b;
+    if (!check_code(code, e, ns, &hole, &b)) {
+      latch(A.st, TERA_ECORRUPT);
+      pi[DI_OK] = 0;
+    }
+    v = U64x2{b, hole ? 0ull : 1ull};
+  }
+  U64x2 tot;
+  block_excl_scan2(v, sm, &tot);
+  if (threadIdx.x == 0) A.unit_sum[U] = tot;
+}
+
+// One warp: unit prefixes, totals checked against the header, receive header.
+template <bool CG>
+__device__ __forceinline__ void dec_scan_pair(const DecArgs& A, u32 p, u64 u0, u64 n_units) {
+  const int lane = threadIdx.x & 31;
+  u64* pi = A.info + (u64)p * 8;
+  U64x2 run{0, 0};
+  for (u64 b = 0; b < n_units; b += 32) {
+    u64 i = b + lane;
+    U64x2 v = i < n_units ? ldx<CG>(A.unit_sum + u0 + i) : U64x2{0, 0};
+    U64x2 incl = v;
+    for (int o = 1; o < 32; o <<= 1) {
+      U64x2 t = shfl_up(incl, o);
+      if (lane >= o) incl += t;
+    }
+    if (i < n_units) A.unit_base[u0 + i] = run + incl - v;
+    run += U64x2{__shfl_sync(0xFFFFFFFFu, incl.a, 31), __shfl_sync(0xFFFFFFFFu, incl.b, 31)};
+  }
+  const u64 m = A.recv_off[p + 1] - A.recv_off[p];
+  if (lane == 0) {
+    if (ldx<CG>(pi + DI_OK) && (run.a != ldx<CG>(pi + DI_PAY) || run.b != m)) {
+      latch(A.st, TERA_ECORRUPT);
+      pi[DI_OK] = 0;
+    }
+    write_taio_header(A.recv + (A.recv_off[p] + p) * kRecBytes, A.class_id, p, m);
+  }
+}
+
+template <int T, bool CG>
+__device__ __forceinline__ void dec_emit_unit(const DecArgs& A, u32 p, u64 local, u64 U,
+                                              U64x2* sm, uint8_t* stage) {
+  const u64* pi = A.info + (u64)p * 8;
+  if (!ldx<CG>(pi + DI_OK)) return;  // block-uniform
+  const u64 ns = ldx<CG>(pi + DI_NS), n = ns + ldx<CG>(pi + DI_NN);
+  const u64 e = local * T + threadIdx.x;
+  const uint8_t* w8 = A.wire + A.wire_off[p];
+  u32 code = 0;
+  u32 b = 0;
+  bool hole = true;
+  if (e < n) {
+    code = ldx<CG>(reinterpret_cast<const u32*>(w8 + kHdrBytes) + e);
+    check_code(code, e, ns, &hole, &b);
+  }
+  U64x2 v{b, (e < n && !hole) ? 1ull : 0ull};
+  U64x2 tot;
+  U64x2 ex = block_excl_scan2(v, sm, &tot);
+  const U64x2 base = ldx<CG>(A.unit_base + U);
+  // stage [gA, gA + tot.a) with 16-byte loads; the slab is 16-byte aligned and
+  // padded, so the rounded range stays inside this pair's slab
+  const uint8_t* gA = w8 + kHdrBytes + 4 * n + base.a;
+  const u32 s0 = (u32)((uintptr_t)gA & 15u);
+  const uint8_t* g16 = gA - s0;
+  const u32 nchunks = (u32)((s0 + tot.a + 15u) >> 4);
+  for (u32 c = threadIdx.x; c < nchunks; c += blockDim.x)
+    *reinterpret_cast<uint4*>(stage + (c << 4)) =
+        ldx<CG>(reinterpret_cast<const uint4*>(g16 + (c << 4)));
+  __syncthreads();
+  if (v.b) {
+    u32 o = s0 + (u32)ex.a;
+    Rec rec;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) {
+      const u32 L = (code >> (4 * w)) & 0xFu;
+      u64 x = 0;
+      for (u32 q = 0; q < L; ++q) x |= (u64)stage[o + q] << (8 * q);
+      o += L;
+      rec.w[w] = x;
+    }
+    if (e < ns) {
+      const Rec R = load_rec(A.ref + (A.ref_off[p] + p + 1 + e) * kRecBytes);
+#pragma unroll
+      for (int w = 0; w < 8; ++w) rec.w[w] ^= R.w[w];
+    }
+    const u64 pos = base.b + ex.b;
+    store_rec(A.recv + (A.recv_off[p] + p + 1 + pos) * kRecBytes, rec);
+  }
+  __syncthreads();
+}
+
+}  // namespace tera

@@ -155,11 +155,21 @@ struct ProfState {
 
 static ProfState* prof(tera_ctx* ctx) { return reinterpret_cast<ProfState*>(ctx->prof); }
 
+// Inside a stream capture an event becomes a graph node only when recorded as
+// "external"; outside a capture it is recorded directly.
+static void record_event(cudaEvent_t e, cudaStream_t s) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusActive)
+    cudaEventRecordWithFlags(e, s, cudaEventRecordExternal);
+  else
+    cudaEventRecord(e, s);
+}
+
 void prof_begin(tera_ctx* ctx, cudaStream_t s) {
   ProfState* p = prof(ctx);
   if (!p || !p->on) return;
   p->open_a = p->get();
-  cudaEventRecord(p->open_a, s);
+  record_event(p->open_a, s);
 }
 
 tera_status check_launch(tera_ctx* ctx, const char* name, cudaStream_t s) {
@@ -167,7 +177,7 @@ tera_status check_launch(tera_ctx* ctx, const char* name, cudaStream_t s) {
   ProfState* p = prof(ctx);
   if (p && p->on && p->open_a) {
     cudaEvent_t b = p->get();
-    cudaEventRecord(b, s);
+    record_event(b, s);
     p->pending.push_back({name, p->open_a, b});
     p->open_a = nullptr;
   }
@@ -273,6 +283,37 @@ tera_status ensure_units(tera_ctx* ctx, uint64_t cap, cudaStream_t s) {
   return TERA_OK;
 }
 
+tera_status ensure_batched(tera_ctx* ctx, u32 T, u32 W) {
+  const u64 P = ctx->n_pairs;
+  const u64 cap = ctx->cap_records;
+  // units: slot + message tiles per pair (encode), entry tiles (decode)
+  tera_status st = ensure_units(ctx, 2 * (cap / T) + 2 * P + 16, 0);
+  if (st != TERA_OK) return st;
+  const u64 items = 9 * (cap / T) + 12 * P + 64;
+  const u64 windows = (P + W - 1) / W + 1;
+  if (ctx->b_items && items <= ctx->b_items_cap && windows <= ctx->b_windows_cap &&
+      ctx->b_unit_sum && ctx->b_units_cap >= ctx->cap_units)
+    return TERA_OK;
+  cudaDeviceSynchronize();
+  const u64 ic = items + items / 4;
+  const u64 wc = windows < (P + 1) ? (P + 1) : windows;
+  if ((st = alloc_dev(ctx->b_items, ic)) != TERA_OK) return st;
+  if ((st = alloc_dev(ctx->b_done, P * 9)) != TERA_OK) return st;
+  if ((st = alloc_dev(ctx->b_need, P * 9)) != TERA_OK) return st;
+  if ((st = alloc_dev(ctx->b_enc_uoff, P + 1)) != TERA_OK) return st;
+  if ((st = alloc_dev(ctx->b_dec_uoff, P + 1)) != TERA_OK) return st;
+  if ((st = alloc_dev(ctx->b_win_total, wc)) != TERA_OK) return st;
+  if ((st = alloc_dev(ctx->b_win_base, wc + 1)) != TERA_OK) return st;
+  if ((st = alloc_dev(ctx->b_scalars, 4)) != TERA_OK) return st;
+  if ((st = alloc_dev(ctx->b_unit_sum, ctx->cap_units)) != TERA_OK) return st;
+  if ((st = alloc_dev(ctx->b_unit_base, ctx->cap_units)) != TERA_OK) return st;
+  cudaMemset(ctx->b_scalars, 0, 4 * sizeof(u64));
+  ctx->b_items_cap = ic;
+  ctx->b_windows_cap = wc;
+  ctx->b_units_cap = ctx->cap_units;
+  return ensure_scan_part(ctx, wc);
+}
+
 }  // namespace tera
 
 extern "C" {
@@ -330,7 +371,7 @@ tera_status tera_ctx_create(tera_ctx** out, const tera_grid* grid, int device, u
   if ((st = alloc_dev(c->d_epoch, 1)) != TERA_OK) goto fail;
   if ((st = alloc_dev(c->d_reset, c->n_pairs)) != TERA_OK) goto fail;
   if ((st = alloc_dev(c->unit_off, c->n_pairs + 1)) != TERA_OK) goto fail;
-  if ((st = alloc_dev(c->pair_info, c->n_pairs * 8)) != TERA_OK) goto fail;
+  if ((st = alloc_dev(c->pair_info, c->n_pairs * 16)) != TERA_OK) goto fail;  // encode + decode
   if ((st = alloc_dev(c->d_total, 8)) != TERA_OK) goto fail;
   if ((st = alloc_dev(c->d_units_total, 2)) != TERA_OK) goto fail;
   if ((st = alloc_dev(c->d_stats, 1)) != TERA_OK) goto fail;
@@ -383,6 +424,16 @@ tera_status tera_ctx_destroy(tera_ctx* c) {
   free_dev(c->pair_info);
   free_dev(c->d_units_total);
   free_dev(c->d_stats);
+  free_dev(c->b_items);
+  free_dev(c->b_done);
+  free_dev(c->b_need);
+  free_dev(c->b_enc_uoff);
+  free_dev(c->b_dec_uoff);
+  free_dev(c->b_win_total);
+  free_dev(c->b_win_base);
+  free_dev(c->b_scalars);
+  free_dev(c->b_unit_sum);
+  free_dev(c->b_unit_base);
   if (c->h_status) cudaFreeHost(c->h_status);
   if (ProfState* p = prof(c)) {
     for (auto& q : p->pending) {
@@ -445,7 +496,10 @@ tera_status tera_ctx_profile_collect(tera_ctx* ctx) {
   for (auto& q : p->pending) {
     if (cudaEventSynchronize(q.b) != cudaSuccess) return TERA_ECUDA;
     float ms = 0.f;
-    cudaEventElapsedTime(&ms, q.a, q.b);
+    if (cudaEventElapsedTime(&ms, q.a, q.b) != cudaSuccess) {
+      cudaGetLastError();  // an event pair that was never replayed: no time
+      ms = 0.f;
+    }
     size_t i = 0;
     while (i < p->names.size() && p->names[i] != q.name) ++i;
     if (i == p->names.size()) {

@@ -100,12 +100,10 @@ __global__ void __launch_bounds__(kClassifyThreads)
     classify_kernel(const u64* __restrict__ x, const u64* __restrict__ y,
                     const u64* __restrict__ z, u64 n, const GridTables* __restrict__ g,
                     int* __restrict__ owner, u32* __restrict__ mask, u32* __restrict__ tile_cnt,
-                    DevStatus* st, u32* epoch, DevStats* stats) {
+                    DevStatus* st, DevStats* stats) {
   __shared__ u64 sm[33];
   __shared__ SmemGrid sg;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
-    u32 e = *epoch + 1u;
-    *epoch = e == 0u ? 1u : e;  // a new iteration for the (pair, id) index
     stats->iterations += 1;
     stats->agents += n;
   }
@@ -343,7 +341,7 @@ extern "C" tera_status tera_partition(tera_ctx* ctx, const tera_soa* soa, tera_p
   classify_kernel<<<(unsigned)tiles, kClassifyThreads, 0, s>>>(
       reinterpret_cast<const u64*>(soa->x), reinterpret_cast<const u64*>(soa->y),
       reinterpret_cast<const u64*>(soa->z), n, ctx->d_grid, out->owner, out->mask, ctx->tile_cnt,
-      ctx->d_status, ctx->d_epoch, ctx->d_stats);
+      ctx->d_status, ctx->d_stats);
   if ((st = check_launch(ctx, "classify_kernel", s)) != TERA_OK) return st;
   if ((st = scan_u32(ctx, ctx->tile_cnt, ctx->tile_base, nullptr, tiles, s)) != TERA_OK) return st;
 

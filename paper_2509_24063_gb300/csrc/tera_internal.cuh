@@ -277,6 +277,21 @@ struct tera_ctx {
   tera::u64* d_units_total;
   void* prof;  // per-kernel CUDA-event timing (ctx.cu)
   tera::DevStats* d_stats;
+
+  // batched codec (batched.cu)
+  uint64_t b_items_cap;
+  uint64_t b_windows_cap;
+  uint64_t b_units_cap;
+  tera::u64* b_items;
+  uint32_t* b_done;
+  uint32_t* b_need;
+  tera::u64* b_enc_uoff;
+  tera::u64* b_dec_uoff;
+  uint32_t* b_win_total;
+  tera::u64* b_win_base;
+  tera::u64* b_scalars;  // [0] items, [1] ticket, [2] abort flag
+  tera::U64x2* b_unit_sum;
+  tera::U64x2* b_unit_base;
 };
 
 namespace tera {
@@ -292,4 +307,6 @@ int grid_for(tera_ctx* ctx, int blocks_per_sm);
 // unit_pair[u] = p0 + k for every unit u of range pair k (skipped when
 // units_total[1] flags an aborted call).
 tera_status launch_unit_map(tera_ctx* ctx, u32 p0, u64 npr, cudaStream_t s);
+// Scratch of the batched codec for tiles of T entries and windows of W pairs.
+tera_status ensure_batched(tera_ctx* ctx, u32 T, u32 W);
 }  // namespace tera

@@ -2,6 +2,12 @@
 kept on both sides between iterations (paper Sec. 2.3: each sender/receiver
 pair stores the same reference and updates it every iteration here).
 
+Paths (all produce the same bytes):
+  "per_subdomain"  pack / encode / decode launched once per sending box
+  "all_pairs"      pack / encode / decode launched once for all pairs
+  "batched"        pack, then encode + decode of all pairs in one persistent
+                   launch (tera_codec_batched); capturable in a CUDA graph
+
 Buffers are allocated once for a maximum agent count and record count; the
 sender and receiver references are double-buffered (previous / next).
 """
@@ -12,13 +18,18 @@ import torch
 from ._lib import MODE_XOR
 from .api import Context, PartitionBuffers
 
+PATHS = ("per_subdomain", "all_pairs", "batched")
+
 
 class AuraExchange:
     def __init__(self, ctx: Context, max_agents: int, max_records: int, mode: int = MODE_XOR,
-                 per_subdomain: bool = False):
+                 per_subdomain: bool = False, path: str | None = None, tune=None):
         self.ctx = ctx
         self.mode = mode
-        self.per_subdomain = per_subdomain
+        self.path = path or ("per_subdomain" if per_subdomain else "all_pairs")
+        if self.path not in PATHS:
+            raise ValueError(f"path must be one of {PATHS}")
+        self.tune = tune
         P = ctx.n_pairs
         dev = torch.device("cuda", ctx.device)
         self.P = P
@@ -45,15 +56,15 @@ class AuraExchange:
         self.t = 0
 
     def ranges(self):
-        if not self.per_subdomain:
+        if self.path != "per_subdomain":
             return [(0, self.P)]
         return [(27 * s, 27 * s + 27) for s in range(self.P // 27)]
 
-    def step(self, state: dict, stream=None):
-        """Classify, pack, encode and decode every pair for one iteration."""
+    def _launch(self, state: dict, t: int, stream=None):
+        """Enqueue iteration t (reference parity t % 2) on the stream."""
         ctx = self.ctx
-        cur, prv = self.t % 2, (self.t + 1) % 2
-        first = self.t == 0
+        cur, prv = t % 2, (t + 1) % 2
+        first = t == 0
         part = self.part
         pair_off = self.pair_off[cur]
         part.pair_off = pair_off  # this iteration's offsets become the next one's reference layout
@@ -64,14 +75,37 @@ class AuraExchange:
         recv_off_prev = None if first else self.recv_off[prv]
         for (a, b) in self.ranges():
             ctx.pack(state, part, self.rec, a, b, stream)
+        if self.path == "batched":
+            ctx.codec_batched(self.rec, pair_off, ref_prev, ref_off_prev, self.ref[cur], self.wire,
+                              self.wire_off, self.wire_len, recv_prev, recv_off_prev,
+                              self.recv[cur], self.recv_off[cur], self.mode, self.tune, stream)
+            return
         for (a, b) in self.ranges():
             ctx.delta_encode(self.rec, pair_off, ref_prev, ref_off_prev, self.ref[cur],
                              self.wire, self.wire_off, self.wire_len, self.mode, a, b, stream)
         for (a, b) in self.ranges():
             ctx.delta_decode(self.wire, self.wire_off, recv_prev, recv_off_prev, self.recv[cur],
                              self.recv_off[cur], a, b, stream)
+
+    def step(self, state: dict, stream=None):
+        """Classify, pack, encode and decode every pair for one iteration."""
+        self._launch(state, self.t, stream)
         self.t += 1
-        return cur
+        return (self.t + 1) % 2
+
+    def capture(self, state: dict, t: int | None = None) -> torch.cuda.CUDAGraph:
+        """A CUDA graph of iteration t (default: the next one) on this state's buffers.
+
+        Replaying it is equivalent to step(state) at that iteration; call
+        advance() after each replay.  Scratch must already be reserved (one
+        eager step beforehand does it)."""
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self._launch(state, self.t if t is None else t, torch.cuda.current_stream())
+        return g
+
+    def advance(self):
+        self.t += 1
 
     # --- views of the last iteration's outputs ---
     @property

@@ -1,0 +1,107 @@
+"""The batched form: encode + decode of every pair in one persistent launch
+(optionally replayed from CUDA graphs), checked byte for byte against the
+oracle, and invariant under every schedule the autotuner can pick."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from synth import WORKLOADS, Generator, Workload, scaled, to_numpy
+
+from test_gpu_parity import compare_iteration, run_chain, u64, u8
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def tera():
+    import paper_2509_24063_gb300 as t
+    return t
+
+
+def test_batched_uniform_4k_all_iterations(tera):
+    wl = WORKLOADS["uniform_4k"]
+    run_chain(tera, wl, wl.iterations, path="batched")
+
+
+def test_batched_uniform_1m(tera):
+    run_chain(tera, WORKLOADS["uniform_1m"], 4, path="batched")
+
+
+def test_batched_skewed_blobs(tera):
+    run_chain(tera, scaled(WORKLOADS["blobs_16m"], 1 << 20), 3, path="batched")
+
+
+@pytest.mark.parametrize("n", [0, 1, 3, 2049, 70001])
+def test_batched_ragged_sizes(tera, n):
+    wl = Workload("t", n, (0.0,) * 3, (90.0, 60.0, 60.0), (3, 2, 2), 12.0, 3,
+                  p_divide=0.05, p_die=0.05, seed=200 + n)
+    run_chain(tera, wl, 3, path="batched")
+
+
+@pytest.mark.parametrize("tune", [(128, 1, 1, 1), (128, 16, 16, 16), (256, 2, 64, 4),
+                                  (256, 4, 1024, 1), (512, 1, 7, 3), (512, 2, 256, 64)])
+def test_batched_schedule_invariance(tera, tune):
+    # every schedule gives the oracle's bytes (and so the same bytes as each other)
+    wl = Workload("t", 60000, (0.0,) * 3, (300.0, 200.0, 200.0), (3, 2, 2), 25.0, 3,
+                  p_grow=0.1, p_divide=0.02, p_die=0.02, seed=5)
+    run_chain(tera, wl, 3, path="batched", tune=tune)
+
+
+def test_graph_replay_matches_oracle(tera):
+    wl = Workload("t", 50000, (0.0,) * 3, (200.0, 200.0, 100.0), (2, 2, 1), 20.0, 5,
+                  p_grow=0.1, p_divide=0.02, p_die=0.02, seed=6)
+    states = list(Generator(wl, device="cuda").series(5))
+    ctx = tera.Context(wl.lo, wl.hi, wl.grid, wl.w)
+    ex = tera.AuraExchange(ctx, max_agents=80000, max_records=400000, path="batched")
+    ex.step(states[0])  # eager first iteration reserves all scratch
+    ctx.status()
+    graphs = [ex.capture(states[t], t) for t in range(1, 5)]
+    g = oracle.make_grid(wl.lo, wl.hi, wl.grid, wl.w)
+    res = oracle.exchange_iteration(g, to_numpy(states[0]))
+    ref, recv_ref = (res["ref_next"], res["pair_off"]), (res["recv"], res["recv_off"])
+    for t in range(1, 5):
+        graphs[t - 1].replay()
+        ex.advance()
+        torch.cuda.synchronize()
+        ctx.status()
+        res = oracle.exchange_iteration(g, to_numpy(states[t]), ref=ref, recv_ref=recv_ref)
+        compare_iteration(ctx, ex, states[t], res, ctx.n_pairs)
+        ref, recv_ref = (res["ref_next"], res["pair_off"]), (res["recv"], res["recv_off"])
+    ctx.close()
+
+
+def test_batched_wire_capacity_reported(tera):
+    wl = Workload("t", 6000, (0.0,) * 3, (120.0, 120.0, 60.0), (2, 2, 1), 25.0, 1, seed=21)
+    st = next(Generator(wl, device="cuda").series(1))
+    ctx = tera.Context(wl.lo, wl.hi, wl.grid, wl.w)
+    ex = tera.AuraExchange(ctx, max_agents=20000, max_records=100000, path="batched")
+    ex.wire = ex.wire[:1024]
+    ex.step(st)
+    code, req = ctx.status(raise_on_error=False)
+    assert code == tera.ECAPACITY and req > 1024
+    ctx.close()
+
+
+def test_autotuner_picks_a_valid_schedule(tera, tmp_path, monkeypatch):
+    from paper_2509_24063_gb300 import autotune
+    monkeypatch.setenv("TERA_TUNE_CACHE", str(tmp_path / "tune.json"))
+    wl = scaled(WORKLOADS["uniform_1m"], 300_000)
+    states = list(Generator(wl, device="cuda").series(3))
+    ctx = tera.Context(wl.lo, wl.hi, wl.grid, wl.w)
+    ex = tera.AuraExchange(ctx, max_agents=400_000, max_records=1_500_000, path="batched")
+    ex.step(states[0])
+    tune, table = autotune.tune_batched(ex, states[1], use_cache=False)
+    assert tune in autotune.CANDIDATES and len(table) >= 12
+    assert autotune.load_cached(ctx, int(ex.pair_off[1][-1].item())) == tune
+    # the tuned schedule continues the chain with the oracle's bytes
+    g = oracle.make_grid(wl.lo, wl.hi, wl.grid, wl.w)
+    ref = recv_ref = None
+    for t in range(2):
+        res = oracle.exchange_iteration(g, to_numpy(states[t]), ref=ref, recv_ref=recv_ref)
+        ref, recv_ref = (res["ref_next"], res["pair_off"]), (res["recv"], res["recv_off"])
+    ex.step(states[2])
+    ctx.status()
+    res = oracle.exchange_iteration(g, to_numpy(states[2]), ref=ref, recv_ref=recv_ref)
+    compare_iteration(ctx, ex, states[2], res, ctx.n_pairs)
+    ctx.close()

@@ -40,7 +40,7 @@ def compare_iteration(ctx, ex, st, res, P):
     np.testing.assert_array_equal(u32(ex.part.mask[:n]), res["mask"])
     np.testing.assert_array_equal(u64(ex.part.pair_count), res["pair_count"])
     off = res["pair_off"]
-    np.testing.assert_array_equal(u64(ex.part.pair_off), off)
+    np.testing.assert_array_equal(u64(ex.pair_off[ex.last]), off)
     E = int(off[-1])
     np.testing.assert_array_equal(u32(ex.part.pair_idx[:E]), res["pair_idx"])
     units = E + P
@@ -61,13 +61,14 @@ def compare_iteration(ctx, ex, st, res, P):
     return E, int(wl.sum())
 
 
-def run_chain(tera, wl, iters, per_subdomain=False, max_records=None, device="cuda"):
+def run_chain(tera, wl, iters, per_subdomain=False, max_records=None, device="cuda",
+              path=None, tune=None):
     gen = Generator(wl, device=device)
     ctx = tera.Context(wl.lo, wl.hi, wl.grid, wl.w)
     states = list(gen.series(iters))
     nmax = max(int(s["x"].shape[0]) for s in states)
     ex = tera.AuraExchange(ctx, max_agents=nmax, max_records=max_records or 4 * nmax + 1024,
-                           per_subdomain=per_subdomain)
+                           per_subdomain=per_subdomain, path=path, tune=tune)
     g = oracle.make_grid(wl.lo, wl.hi, wl.grid, wl.w)
     ref = recv_ref = None
     stats = []
