@@ -20,10 +20,12 @@ import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "liboracle.so")
-SOURCES = [os.path.join(HERE, "tera_oracle.c")]
+SOURCES = [os.path.join(HERE, "tera_oracle.c"), os.path.join(HERE, "mlp_oracle.c")]
 
 OK, EINVAL, ENOMEM, ECAPACITY, ECORRUPT, EDOMAIN, EREFMISMATCH = range(7)
 MODE_RAW, MODE_XOR, MODE_RESIDUAL = 0, 1, 2
+NPARAM = 8 * 64 + 64 + 64 * 64 + 64 + 3 * 64 + 3
+HIST = 48
 REC = 64
 HDR = 64
 
@@ -80,9 +82,38 @@ def lib():
             L.or_decode_all.argtypes = [u64, u32, P, P, P, P, P, u64, P]
             L.or_exchange_iteration.argtypes = [G, P, P, i64, u32, u32, P, P, P, P, P, P, P,
                                                 P, P, u64, P, P, P, P, P, P, u64, P, P]
+            D3 = C.POINTER(C.c_double)
+            L.or_mlp_nparam.argtypes = []
+            L.or_mlp_infer_f32.argtypes = [P, P, P]
+            L.or_mlp_infer_f32.restype = None
+            L.or_mlp_loss_grad_f64.argtypes = [P, P, P, i64, P]
+            L.or_mlp_loss_grad_f64.restype = C.c_double
+            L.or_mlp_sgd_f64.argtypes = [P, P, C.c_double]
+            L.or_mlp_sgd_f64.restype = None
+            L.or_zigzag.argtypes = [u64]
+            L.or_zigzag.restype = u64
+            L.or_unzigzag.argtypes = [u64]
+            L.or_unzigzag.restype = u64
+            L.or_cell_counts.argtypes = [P, u64, D3, C.c_double, P]
+            L.or_cell_counts.restype = None
+            L.or_features.argtypes = [P, P, u32, P]
+            L.or_predict.argtypes = [P, P, P, u32, P]
+            L.or_hist_next.argtypes = [P, P, P]
+            L.or_hist_next.restype = None
+            L.or_sample.argtypes = [P, P, P, u32, P, P]
+            L.or_encode_pair_pred.argtypes = [P, u64, P, u64, P, P, D3, C.c_double, C.c_int, u32,
+                                              u32, P, u64, P, P, P]
+            L.or_decode_pair_pred.argtypes = [P, u64, P, u64, P, P, D3, C.c_double, u32, u32, P,
+                                              u64, P, P]
+            L.or_encode_all_pred.argtypes = [u64, u32, C.c_int, P, P, P, P, P, P, D3, C.c_double,
+                                             P, P, P, P, P]
+            L.or_decode_all_pred.argtypes = [u64, u32, P, P, P, P, P, P, D3, C.c_double, P, u64,
+                                             P, P]
             for f in ("or_grid_check", "or_classify", "or_pair_lists", "or_encode_pair",
                       "or_decode_pair", "or_encode_all", "or_decode_all",
-                      "or_exchange_iteration"):
+                      "or_exchange_iteration", "or_mlp_nparam", "or_features", "or_predict",
+                      "or_sample", "or_encode_pair_pred", "or_decode_pair_pred",
+                      "or_encode_all_pred", "or_decode_all_pred"):
                 getattr(L, f).restype = C.c_int
             _lib = L
     return _lib
@@ -257,3 +288,125 @@ def exchange_iteration(grid: Grid, soa: dict, ref=None, recv_ref=None, class_id=
     return dict(status=st, owner=owner, mask=mask, pair_count=cnt, pair_off=off,
                 pair_idx=idx[:total], rec=rec, wire=wire, wire_off=wo, wire_len=wl,
                 ref_next=nxt, recv=recv, recv_off=ro, t_steps=ts)
+
+
+# ---------------- learned predictor and residual mode ----------------
+
+def _d3(v):
+    return (C.c_double * 3)(*[float(t) for t in v])
+
+
+def mlp_infer(params, x):
+    """float32 inference (fixed fmaf order) of one feature vector."""
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    out = np.zeros(3, dtype=np.float32)
+    lib().or_mlp_infer_f32(_p(p), _p(x), _p(out))
+    return out
+
+
+def mlp_loss_grad(params64, X, Y, with_grad=True):
+    p = np.ascontiguousarray(params64, dtype=np.float64)
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    Y = np.ascontiguousarray(Y, dtype=np.float64)
+    g = np.zeros(NPARAM, dtype=np.float64) if with_grad else None
+    loss = lib().or_mlp_loss_grad_f64(_p(p), _p(X), _p(Y), X.shape[0], _p(g))
+    return loss, g
+
+
+def zigzag(d):
+    return int(lib().or_zigzag(d & (2**64 - 1)))
+
+
+def unzigzag(z):
+    return int(lib().or_unzigzag(z & (2**64 - 1)))
+
+
+def cell_counts(ref_recs, lo, w):
+    ref = np.ascontiguousarray(ref_recs, dtype=np.uint64).reshape(-1, 8)
+    cnt = np.zeros(max(ref.shape[0], 1), dtype=np.uint32)
+    lib().or_cell_counts(_p(ref), ref.shape[0], _d3(lo), float(w), _p(cnt))
+    return cnt[:ref.shape[0]]
+
+
+def features(rec, hist, ncount):
+    rec = np.ascontiguousarray(rec, dtype=np.uint64)
+    hist = np.ascontiguousarray(hist, dtype=np.uint8)
+    f = np.zeros(8, dtype=np.float32)
+    ok = lib().or_features(_p(rec), _p(hist), int(ncount), _p(f))
+    return ok, f
+
+
+def hist_next(rec=None, hist=None):
+    out = np.zeros(HIST, dtype=np.uint8)
+    lib().or_hist_next(None if rec is None else _p(np.ascontiguousarray(rec, dtype=np.uint64)),
+                       None if hist is None else _p(np.ascontiguousarray(hist, dtype=np.uint8)),
+                       _p(out))
+    return out
+
+
+def encode_pair_pred(msg, ref, hist, params, lo, w, allow_residual=True, class_id=1, pair=0):
+    msg = np.ascontiguousarray(msg, dtype=np.uint64).reshape(-1, 8)
+    ref = np.ascontiguousarray(ref, dtype=np.uint64).reshape(-1, 8)
+    m, r = msg.shape[0], ref.shape[0]
+    cap = 64 + 4 * (r + m) + 64 * m + 16
+    wire = np.zeros(cap, dtype=np.uint8)
+    wl = np.zeros(1, dtype=np.uint64)
+    nxt = np.zeros((max(m, 1), 8), dtype=np.uint64)
+    hn = np.zeros((max(m, 1), HIST), dtype=np.uint8)
+    h = None if hist is None else np.ascontiguousarray(hist, dtype=np.uint8)
+    pr = None if params is None else np.ascontiguousarray(params, dtype=np.float32)
+    st = lib().or_encode_pair_pred(_p(msg), m, _p(ref), r, _p(h), _p(pr), _d3(lo), float(w),
+                                   1 if allow_residual else 0, class_id, pair, _p(wire), cap,
+                                   _p(wl), _p(nxt), _p(hn))
+    return st, wire[:int(wl[0])].copy(), nxt[:m].copy(), hn[:m].copy()
+
+
+def decode_pair_pred(wire, ref, hist, params, lo, w, class_id=1, pair=0, out_cap=None):
+    wire = np.ascontiguousarray(wire, dtype=np.uint8)
+    ref = np.ascontiguousarray(ref, dtype=np.uint64).reshape(-1, 8)
+    cap = out_cap if out_cap is not None else max(1, wire.size // 4 + ref.shape[0])
+    out = np.zeros((max(cap, 1), 8), dtype=np.uint64)
+    hn = np.zeros((max(cap, 1), HIST), dtype=np.uint8)
+    m = np.zeros(1, dtype=np.uint64)
+    h = None if hist is None else np.ascontiguousarray(hist, dtype=np.uint8)
+    pr = None if params is None else np.ascontiguousarray(params, dtype=np.float32)
+    buf = wire if wire.size else np.zeros(1, dtype=np.uint8)
+    st = lib().or_decode_pair_pred(_p(buf), wire.size, _p(ref), ref.shape[0], _p(h), _p(pr),
+                                   _d3(lo), float(w), class_id, pair, _p(out), cap, _p(m), _p(hn))
+    k = int(m[0])
+    return st, out[:k].copy(), hn[:k].copy()
+
+
+def encode_all_pred(rec_arena, pair_off, ref_arena, ref_off, hist, params, lo, w,
+                    allow_residual=True, class_id=1):
+    """Returns (status, wire, wire_off, wire_len, ref_next, hist_next)."""
+    P = pair_off.shape[0] - 1
+    wo = wire_slabs(pair_off, ref_off)
+    wire = np.zeros(max(int(wo[-1]), 1), dtype=np.uint8)
+    wl = np.zeros(P, dtype=np.uint64)
+    E = int(pair_off[-1])
+    nxt = np.zeros((E + P) * REC, dtype=np.uint8)
+    hn = np.zeros(max(E, 1) * HIST, dtype=np.uint8)
+    pr = None if params is None else np.ascontiguousarray(params, dtype=np.float32)
+    st = lib().or_encode_all_pred(P, class_id, 1 if allow_residual else 0, _p(rec_arena),
+                                  _p(pair_off), _p(ref_arena), _p(ref_off), _p(hist), _p(pr),
+                                  _d3(lo), float(w), _p(wire), _p(wo), _p(wl), _p(nxt), _p(hn))
+    return st, wire, wo, wl, nxt, hn[:E * HIST]
+
+
+def decode_all_pred(wire, wire_off, ref_arena, ref_off, hist, params, lo, w, class_id=1,
+                    cap_units=None):
+    """Returns (status, recv arena, recv_off, hist_next)."""
+    P = wire_off.shape[0] - 1
+    if cap_units is None:
+        cap_units = P + int(wire.size // 4 + (0 if ref_off is None else int(ref_off[-1])) + 1)
+    recv = np.zeros(cap_units * REC, dtype=np.uint8)
+    ro = np.zeros(P + 1, dtype=np.uint64)
+    hn = np.zeros(max(cap_units, 1) * HIST, dtype=np.uint8)
+    pr = None if params is None else np.ascontiguousarray(params, dtype=np.float32)
+    st = lib().or_decode_all_pred(P, class_id, _p(wire), _p(wire_off), _p(ref_arena), _p(ref_off),
+                                  _p(hist), _p(pr), _d3(lo), float(w), _p(recv), cap_units,
+                                  _p(ro), _p(hn))
+    E = int(ro[-1])
+    return st, recv[:(E + P) * REC].copy(), ro, hn[:E * HIST].copy()

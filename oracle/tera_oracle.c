@@ -578,3 +578,317 @@ int or_exchange_iteration(const or_grid* g, const uint64_t* id, const double* co
   }
   return st;
 }
+
+/* ---------- residual mode with the learned predictor (not in the paper) ----------
+ * Same matching and layout as or_encode_pair.  For a message in mode
+ * RESIDUAL, the position words (w1..w3) of a matched slot whose history makes
+ * it predictable carry zigzag(bits(x_t) - bits(prediction)) (mod 2^64); every
+ * other word is the XOR difference, and new records are raw.  The encoder
+ * sends RESIDUAL only when its payload is smaller than the XOR payload
+ * (allow_residual != 0); it also writes the history of the new reference. */
+int or_predict(const float* params, const uint8_t* rec, const uint8_t* hist, uint32_t ncount,
+               uint64_t* pred_bits);
+void or_hist_next(const uint8_t* rec, const uint8_t* hist, uint8_t* out);
+void or_cell_counts(const uint8_t* ref, uint64_t r, const double lo[3], double w,
+                    uint32_t* count);
+uint64_t or_zigzag(uint64_t d);
+uint64_t or_unzigzag(uint64_t z);
+
+static const uint8_t zero_hist[48] = {0};
+
+int or_encode_pair_pred(const uint8_t* msg, uint64_t m, const uint8_t* ref, uint64_t r,
+                        const uint8_t* hist, const float* params, const double lo[3], double w,
+                        int allow_residual, uint32_t class_id, uint32_t pair, uint8_t* wire,
+                        uint64_t wire_cap, uint64_t* wire_len, uint8_t* ref_next,
+                        uint8_t* hist_next) {
+  id_pos* sorted = (id_pos*)malloc(sizeof(id_pos) * (size_t)(m ? m : 1));
+  uint8_t* matched = (uint8_t*)calloc(m ? m : 1, 1);
+  int64_t* src = (int64_t*)malloc(sizeof(int64_t) * (size_t)(r ? r : 1));
+  uint32_t* ncount = (uint32_t*)calloc(r ? r : 1, sizeof(uint32_t));
+  uint8_t* pred_ok = (uint8_t*)calloc(r ? r : 1, 1);
+  uint64_t* pred = (uint64_t*)calloc(3 * (r ? r : 1), sizeof(uint64_t));
+  int status = OR_OK;
+  if (!sorted || !matched || !src || !ncount || !pred_ok || !pred) {
+    status = OR_ENOMEM;
+    goto done;
+  }
+  for (uint64_t k = 0; k < m; ++k) {
+    sorted[k].id = rec_word(msg + k * REC_BYTES, 0);
+    sorted[k].k = k;
+  }
+  qsort(sorted, (size_t)m, sizeof(id_pos), cmp_id_pos);
+  for (uint64_t k = 1; k < m; ++k)
+    if (sorted[k].id == sorted[k - 1].id) {
+      status = OR_EINVAL;
+      goto done;
+    }
+  uint64_t n_holes = 0;
+  for (uint64_t j = 0; j < r; ++j) {
+    int64_t k = find_id(sorted, m, rec_word(ref + j * REC_BYTES, 0));
+    src[j] = k;
+    if (k < 0) {
+      n_holes += 1;
+    } else {
+      if (matched[k]) {
+        status = OR_EINVAL;
+        goto done;
+      }
+      matched[k] = 1;
+    }
+  }
+  uint64_t n_new = 0;
+  for (uint64_t k = 0; k < m; ++k)
+    if (!matched[k]) n_new += 1;
+  /* predictions of the matched slots */
+  if (params && hist) {
+    or_cell_counts(ref, r, lo, w, ncount);
+    for (uint64_t j = 0; j < r; ++j)
+      if (src[j] >= 0)
+        pred_ok[j] = (uint8_t)or_predict(params, ref + j * REC_BYTES, hist + 48 * j, ncount[j],
+                                         pred + 3 * j);
+  }
+  /* the word slot j sends for word w under each mode */
+  uint64_t pay_xor = 0, pay_res = 0;
+  for (uint64_t j = 0; j < r; ++j) {
+    if (src[j] < 0) continue;
+    const uint8_t* cur = msg + (uint64_t)src[j] * REC_BYTES;
+    for (int wd = 0; wd < REC_WORDS; ++wd) {
+      const uint64_t x = rec_word(cur, wd) ^ rec_word(ref + j * REC_BYTES, wd);
+      pay_xor += (uint64_t)sig_bytes(x);
+      uint64_t v = x;
+      if (pred_ok[j] && wd >= 1 && wd <= 3) v = or_zigzag(rec_word(cur, wd) - pred[3 * j + wd - 1]);
+      pay_res += (uint64_t)sig_bytes(v);
+    }
+  }
+  uint64_t pay_new = 0;
+  for (uint64_t k = 0; k < m; ++k) {
+    if (matched[k]) continue;
+    for (int wd = 0; wd < REC_WORDS; ++wd)
+      pay_new += (uint64_t)sig_bytes(rec_word(msg + k * REC_BYTES, wd));
+  }
+  const int residual = allow_residual && params && hist && pay_res < pay_xor;
+  const uint32_t mode = residual ? (uint32_t)OR_MODE_RESIDUAL : (uint32_t)OR_MODE_XOR;
+  const uint64_t payload = (residual ? pay_res : pay_xor) + pay_new;
+  const uint64_t n_codes = r + n_new;
+  const uint64_t msg_bytes = round16(HDR_BYTES + 4u * n_codes + payload);
+  *wire_len = msg_bytes;
+  if (msg_bytes > wire_cap) {
+    status = OR_ECAPACITY;
+    goto done;
+  }
+  memset(wire, 0, (size_t)msg_bytes);
+  write_wire_header(wire, class_id, mode, r, n_new, n_holes, payload, pair, msg_bytes);
+  uint8_t* codes = wire + HDR_BYTES;
+  uint8_t* pay = wire + HDR_BYTES + 4u * n_codes;
+  uint64_t off = 0, e = 0;
+  for (uint64_t j = 0; j < r; ++j, ++e) {
+    if (src[j] < 0) {
+      put_le(codes + 4 * e, 0xFu, 4);
+      continue;
+    }
+    const uint8_t* cur = msg + (uint64_t)src[j] * REC_BYTES;
+    uint32_t code = 0;
+    for (int wd = 0; wd < REC_WORDS; ++wd) {
+      uint64_t d = rec_word(cur, wd) ^ rec_word(ref + j * REC_BYTES, wd);
+      if (residual && pred_ok[j] && wd >= 1 && wd <= 3)
+        d = or_zigzag(rec_word(cur, wd) - pred[3 * j + wd - 1]);
+      const int L = sig_bytes(d);
+      code |= (uint32_t)L << (4 * wd);
+      put_le(pay + off, d, L);
+      off += (uint64_t)L;
+    }
+    put_le(codes + 4 * e, code, 4);
+  }
+  for (uint64_t k = 0; k < m; ++k) {
+    if (matched[k]) continue;
+    const uint8_t* cur = msg + k * REC_BYTES;
+    uint32_t code = 0;
+    for (int wd = 0; wd < REC_WORDS; ++wd) {
+      const uint64_t d = rec_word(cur, wd);
+      const int L = sig_bytes(d);
+      code |= (uint32_t)L << (4 * wd);
+      put_le(pay + off, d, L);
+      off += (uint64_t)L;
+    }
+    put_le(codes + 4 * e, code, 4);
+    e += 1;
+  }
+  {
+    uint64_t q = 0;
+    for (uint64_t j = 0; j < r; ++j) {
+      if (src[j] < 0) continue;
+      memcpy(ref_next + q * REC_BYTES, msg + (uint64_t)src[j] * REC_BYTES, REC_BYTES);
+      if (hist_next)
+        or_hist_next(ref + j * REC_BYTES, hist ? hist + 48 * j : zero_hist, hist_next + 48 * q);
+      q += 1;
+    }
+    for (uint64_t k = 0; k < m; ++k) {
+      if (matched[k]) continue;
+      memcpy(ref_next + q * REC_BYTES, msg + k * REC_BYTES, REC_BYTES);
+      if (hist_next) or_hist_next(NULL, NULL, hist_next + 48 * q);
+      q += 1;
+    }
+  }
+done:
+  free(sorted);
+  free(matched);
+  free(src);
+  free(ncount);
+  free(pred_ok);
+  free(pred);
+  return status;
+}
+
+int or_decode_pair_pred(const uint8_t* wire, uint64_t wire_avail, const uint8_t* ref, uint64_t r,
+                        const uint8_t* hist, const float* params, const double lo[3], double w,
+                        uint32_t class_id, uint32_t pair, uint8_t* out, uint64_t out_cap,
+                        uint64_t* m_out, uint8_t* hist_next) {
+  *m_out = 0;
+  if (wire_avail < HDR_BYTES) return OR_ECORRUPT;
+  if (get_le(wire + 0, 4) != WIRE_MAGIC || get_le(wire + 4, 2) != FMT_VERSION ||
+      get_le(wire + 6, 2) != REC_BYTES || get_le(wire + 8, 4) != class_id ||
+      get_le(wire + 48, 4) != pair)
+    return OR_ECORRUPT;
+  const uint64_t mode = get_le(wire + 12, 4);
+  const uint64_t n_slots = get_le(wire + 16, 8), n_new = get_le(wire + 24, 8);
+  const uint64_t n_holes = get_le(wire + 32, 8), payload = get_le(wire + 40, 8);
+  const uint64_t msg_bytes = get_le(wire + 56, 8);
+  if (mode == OR_MODE_RAW) {
+    if (n_slots != 0) return OR_ECORRUPT;
+  } else if (mode == OR_MODE_XOR || mode == OR_MODE_RESIDUAL) {
+    if (n_slots != r) return OR_EREFMISMATCH;
+    if (mode == OR_MODE_RESIDUAL && (!params || !hist)) return OR_ECORRUPT;
+  } else {
+    return OR_ECORRUPT;
+  }
+  if (n_slots > wire_avail || n_new > wire_avail || payload > wire_avail) return OR_ECORRUPT;
+  const uint64_t n_codes = n_slots + n_new;
+  if (msg_bytes != round16(HDR_BYTES + 4u * n_codes + payload) || msg_bytes > wire_avail)
+    return OR_ECORRUPT;
+  uint32_t* ncount = NULL;
+  if (mode == OR_MODE_RESIDUAL) {
+    ncount = (uint32_t*)calloc(r ? r : 1, sizeof(uint32_t));
+    or_cell_counts(ref, r, lo, w, ncount);
+  }
+  const uint8_t* codes = wire + HDR_BYTES;
+  const uint8_t* pay = wire + HDR_BYTES + 4u * n_codes;
+  uint64_t off = 0, holes = 0, count = 0;
+  int status = OR_OK;
+  for (uint64_t e = 0; e < n_codes; ++e) {
+    const uint32_t code = (uint32_t)get_le(codes + 4 * e, 4);
+    if ((code & 0xFu) == 0xFu) {
+      if (e >= n_slots || (code >> 4) != 0) {
+        status = OR_ECORRUPT;
+        break;
+      }
+      holes += 1;
+      continue;
+    }
+    int bad = 0;
+    for (int wd = 0; wd < REC_WORDS; ++wd)
+      if (((code >> (4 * wd)) & 0xFu) > 8u) bad = 1;
+    if (bad || (e < n_slots && (code & 0xFu) != 0)) {
+      status = OR_ECORRUPT;
+      break;
+    }
+    if (count >= out_cap) {
+      status = OR_ECAPACITY;
+      break;
+    }
+    uint64_t pred[3];
+    int pred_ok = 0;
+    if (mode == OR_MODE_RESIDUAL && e < n_slots)
+      pred_ok = or_predict(params, ref + e * REC_BYTES, hist + 48 * e, ncount[e], pred);
+    uint8_t* rec = out + count * REC_BYTES;
+    for (int wd = 0; wd < REC_WORDS; ++wd) {
+      const int L = (int)((code >> (4 * wd)) & 0xFu);
+      if (off + (uint64_t)L > payload) {
+        status = OR_ECORRUPT;
+        break;
+      }
+      const uint64_t d = get_le(pay + off, L);
+      off += (uint64_t)L;
+      uint64_t v;
+      if (e >= n_slots) v = d;
+      else if (pred_ok && wd >= 1 && wd <= 3) v = pred[wd - 1] + or_unzigzag(d);
+      else v = d ^ rec_word(ref + e * REC_BYTES, wd);
+      put_le(rec + 8 * wd, v, 8);
+    }
+    if (status != OR_OK) break;
+    if (hist_next) {
+      if (e < n_slots)
+        or_hist_next(ref + e * REC_BYTES, hist ? hist + 48 * e : zero_hist,
+                     hist_next + 48 * count);
+      else
+        or_hist_next(NULL, NULL, hist_next + 48 * count);
+    }
+    count += 1;
+  }
+  free(ncount);
+  if (status != OR_OK) return status;
+  if (off != payload || holes != n_holes) return OR_ECORRUPT;
+  *m_out = count;
+  return OR_OK;
+}
+
+/* Arena drivers of the residual mode.  History arenas have no headers: the
+ * entry of slot j of pair p is at index off[p] + j (48 bytes each). */
+int or_encode_all_pred(uint64_t n_pairs, uint32_t class_id, int allow_residual,
+                       const uint8_t* rec_arena, const uint64_t* pair_off,
+                       const uint8_t* ref_arena, const uint64_t* ref_off, const uint8_t* hist,
+                       const float* params, const double lo[3], double w, uint8_t* wire,
+                       const uint64_t* wire_off, uint64_t* wire_len, uint8_t* ref_next,
+                       uint8_t* hist_next) {
+  int status = OR_OK;
+  for (uint64_t p = 0; p < n_pairs; ++p) {
+    const uint64_t m = pair_off[p + 1] - pair_off[p];
+    const uint64_t r = ref_arena ? ref_off[p + 1] - ref_off[p] : 0;
+    const uint8_t* msg_buf = rec_arena + (pair_off[p] + p) * REC_BYTES;
+    const uint8_t* ref_buf = ref_arena ? ref_arena + (ref_off[p] + p) * REC_BYTES : NULL;
+    uint8_t* nxt = ref_next + (pair_off[p] + p) * REC_BYTES;
+    write_taio_header(nxt, class_id, (uint32_t)p, m);
+    int st = or_encode_pair_pred(
+        msg_buf + HDR_BYTES, m, ref_buf ? ref_buf + HDR_BYTES : NULL, r,
+        (ref_arena && hist) ? hist + 48 * ref_off[p] : NULL, params, lo, w, allow_residual,
+        class_id, (uint32_t)p, wire + wire_off[p], wire_off[p + 1] - wire_off[p], &wire_len[p],
+        nxt + HDR_BYTES, hist_next ? hist_next + 48 * pair_off[p] : NULL);
+    if (st != OR_OK && status == OR_OK) status = st;
+  }
+  return status;
+}
+
+int or_decode_all_pred(uint64_t n_pairs, uint32_t class_id, const uint8_t* wire,
+                       const uint64_t* wire_off, const uint8_t* ref_arena,
+                       const uint64_t* ref_off, const uint8_t* hist, const float* params,
+                       const double lo[3], double w, uint8_t* recv, uint64_t recv_cap_units,
+                       uint64_t* recv_off, uint8_t* hist_next) {
+  int status = OR_OK;
+  recv_off[0] = 0;
+  for (uint64_t p = 0; p < n_pairs; ++p) {
+    const uint8_t* h = wire + wire_off[p];
+    const uint64_t avail = wire_off[p + 1] - wire_off[p];
+    uint64_t m = 0;
+    if (avail >= HDR_BYTES && get_le(h, 4) == WIRE_MAGIC) {
+      const uint64_t ns = get_le(h + 16, 8), nn = get_le(h + 24, 8), nh = get_le(h + 32, 8);
+      if (nh <= ns && ns <= avail && nn <= avail) m = ns - nh + nn;
+    }
+    recv_off[p + 1] = recv_off[p] + m;
+  }
+  if (recv_off[n_pairs] + n_pairs > recv_cap_units) return OR_ECAPACITY;
+  for (uint64_t p = 0; p < n_pairs; ++p) {
+    const uint64_t r = ref_arena ? ref_off[p + 1] - ref_off[p] : 0;
+    const uint8_t* ref_buf = ref_arena ? ref_arena + (ref_off[p] + p) * REC_BYTES : NULL;
+    uint8_t* out = recv + (recv_off[p] + p) * REC_BYTES;
+    const uint64_t cap = recv_off[p + 1] - recv_off[p];
+    uint64_t got = 0;
+    int st = or_decode_pair_pred(wire + wire_off[p], wire_off[p + 1] - wire_off[p],
+                                 ref_buf ? ref_buf + HDR_BYTES : NULL, r,
+                                 (ref_arena && hist) ? hist + 48 * ref_off[p] : NULL, params, lo,
+                                 w, class_id, (uint32_t)p, out + HDR_BYTES, cap, &got,
+                                 hist_next ? hist_next + 48 * recv_off[p] : NULL);
+    if (st == OR_OK && got != cap) st = OR_ECORRUPT;
+    write_taio_header(out, class_id, (uint32_t)p, cap);
+    if (st != OR_OK && status == OR_OK) status = st;
+  }
+  return status;
+}

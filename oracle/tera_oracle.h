@@ -86,6 +86,43 @@ int or_exchange_iteration(const or_grid* g, const uint64_t* id, const double* co
                           uint64_t* wire_len, uint8_t* ref_next, uint8_t* recv,
                           uint64_t recv_cap_units, uint64_t* recv_off, double* t_steps);
 
+/* Learned predictor and residual mode (mlp_oracle.c; not in the paper). */
+int or_mlp_nparam(void);
+void or_mlp_infer_f32(const float* params, const float* in, float* out);
+double or_mlp_loss_grad_f64(const double* params, const double* X, const double* Y, int64_t n,
+                            double* grad);
+void or_mlp_sgd_f64(double* params, const double* grad, double lr);
+uint64_t or_zigzag(uint64_t d);
+uint64_t or_unzigzag(uint64_t z);
+void or_cell_counts(const uint8_t* ref, uint64_t r, const double lo[3], double w,
+                    uint32_t* count);
+int or_features(const uint8_t* rec, const uint8_t* hist, uint32_t ncount, float* f);
+int or_predict(const float* params, const uint8_t* rec, const uint8_t* hist, uint32_t ncount,
+               uint64_t* pred_bits);
+void or_hist_next(const uint8_t* rec, const uint8_t* hist, uint8_t* out);
+int or_sample(const uint8_t* cur, const uint8_t* rec, const uint8_t* hist, uint32_t ncount,
+              float* x, float* y);
+int or_encode_pair_pred(const uint8_t* msg, uint64_t m, const uint8_t* ref, uint64_t r,
+                        const uint8_t* hist, const float* params, const double lo[3], double w,
+                        int allow_residual, uint32_t class_id, uint32_t pair, uint8_t* wire,
+                        uint64_t wire_cap, uint64_t* wire_len, uint8_t* ref_next,
+                        uint8_t* hist_next);
+int or_decode_pair_pred(const uint8_t* wire, uint64_t wire_avail, const uint8_t* ref, uint64_t r,
+                        const uint8_t* hist, const float* params, const double lo[3], double w,
+                        uint32_t class_id, uint32_t pair, uint8_t* out, uint64_t out_cap,
+                        uint64_t* m_out, uint8_t* hist_next);
+int or_encode_all_pred(uint64_t n_pairs, uint32_t class_id, int allow_residual,
+                       const uint8_t* rec_arena, const uint64_t* pair_off,
+                       const uint8_t* ref_arena, const uint64_t* ref_off, const uint8_t* hist,
+                       const float* params, const double lo[3], double w, uint8_t* wire,
+                       const uint64_t* wire_off, uint64_t* wire_len, uint8_t* ref_next,
+                       uint8_t* hist_next);
+int or_decode_all_pred(uint64_t n_pairs, uint32_t class_id, const uint8_t* wire,
+                       const uint64_t* wire_off, const uint8_t* ref_arena,
+                       const uint64_t* ref_off, const uint8_t* hist, const float* params,
+                       const double lo[3], double w, uint8_t* recv, uint64_t recv_cap_units,
+                       uint64_t* recv_off, uint8_t* hist_next);
+
 #ifdef __cplusplus
 }
 #endif

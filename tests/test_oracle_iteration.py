@@ -99,3 +99,30 @@ def test_reset_pair_sends_raw(oracle):
     st, recv, rvo = oracle.decode_all(wire, wo, *o["recv_ref"])
     assert st == oracle.OK
     assert recv.tobytes() == nxt.tobytes()
+
+
+def test_chain_with_predictor_histories_stay_identical(oracle):
+    """Residual mode over chained iterations: receiver records and histories
+    equal the sender's every iteration, and the residual mode is used."""
+    from test_oracle_mlp import velocity_network
+    wl = Workload("t", 4000, (0.0,) * 3, (200.0, 200.0, 100.0), (2, 2, 1), 30.0, 6,
+                  layout="blobs", n_blobs=3, p_move=1.0, persistent=True, seed=12)
+    p = velocity_network()
+    g = oracle.make_grid(wl.lo, wl.hi, wl.grid, wl.w)
+    ref = recv = None
+    modes = []
+    for st_t in Generator(wl).series(wl.iterations):
+        s = to_numpy(st_t)
+        st, owner, mask = oracle.classify(g, s["x"], s["y"], s["z"])
+        st, cnt, off, idx = oracle.pair_lists(g, owner, mask)
+        rec = oracle.pack(s, off, idx)
+        ra, ro, rh = (None, None, None) if ref is None else ref
+        st, wire, wo, wl_, nxt, hn = oracle.encode_all_pred(rec, off, ra, ro, rh, p, wl.lo, wl.w)
+        assert st == oracle.OK
+        va, vo, vh = (None, None, None) if recv is None else recv
+        st, rcv, rvo, rhn = oracle.decode_all_pred(wire, wo, va, vo, vh, p, wl.lo, wl.w)
+        assert st == oracle.OK
+        assert rcv.tobytes() == nxt.tobytes() and rhn.tobytes() == hn.tobytes()
+        modes += [int(wire[int(wo[q]) + 12]) for q in range(wl.n_pairs) if wl_[q]]
+        ref, recv = (nxt, off, hn), (rcv, rvo, rhn)
+    assert oracle.MODE_RESIDUAL in modes
