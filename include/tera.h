@@ -83,7 +83,7 @@ typedef enum {
   TERA_ECUDA = 8         /* a CUDA runtime call failed */
 } tera_status;
 
-enum { TERA_MODE_RAW = 0, TERA_MODE_XOR = 1 };
+enum { TERA_MODE_RAW = 0, TERA_MODE_XOR = 1, TERA_MODE_RESIDUAL = 2 };
 
 typedef struct tera_ctx tera_ctx;
 
@@ -208,6 +208,70 @@ tera_status tera_delta_decode_noalloc(const uint8_t* wire, const uint64_t* wire_
                                       uint64_t recv_capacity_units, uint64_t* recv_off,
                                       uint64_t* required_capacity, void* stream);
 
+/* ---------------- learned predictor (not in the paper) ----------------
+ * A small MLP predicts each agent's next position from its recent motion;
+ * a message in mode TERA_MODE_RESIDUAL carries, for the position words
+ * (w1..w3) of every matched slot the network can predict, the zigzag of the
+ * integer difference of bit patterns, zigzag(bits(x_t) - bits(prediction))
+ * (mod 2^64); every other word is the XOR difference.  The encoder sends the
+ * residual mode only for messages it makes smaller (plain XOR otherwise).
+ *
+ * Network: 8 -> 64 -> 64 -> 3, ReLU on the hidden layers, float32.  Params
+ * (4931 floats): W1[64][8], b1[64], W2[64][64], b2[64], W3[3][64], b3[3];
+ * each neuron computes acc = b; for k ascending acc = fmaf(W[k], in[k], acc)
+ * (bit-identical on every device).  Features of reference slot j (position
+ * x1 = x_{t-1} from the reference, history xp = x_{t-2}, d2):
+ *   (float)(x1 - xp) per axis, d2 per axis, (float)(diameter / 10.0),
+ *   (float)ncount * 2^-5 where ncount = reference records of the pair in the
+ *   slot's cell floor((x1 - lo) / w) (per axis, the slot itself included).
+ * A slot is predictable when its history has two steps and every feature and
+ * output is finite; prediction = x1 + (double)output per axis.
+ *
+ * History (48 bytes per slot, one array per reference, no headers; slot j of
+ * pair p at index off[p] + j): u64 xp[3] (bits) | u32 d2[3] (bits of
+ * (float)(xp - the position before it)) | u32 n (steps, 0..2) | u64 zero.
+ * Both sides keep it; the receiver's decode writes the same histories as the
+ * sender's encode. */
+typedef struct {
+  const float* params;      /* MLP weights (device); NULL: no residual mode (history only) */
+  const uint8_t* hist_prev; /* history of the reference; must be NULL iff the reference is */
+  uint8_t* hist_next;       /* history of the new reference / receive buffer (may be NULL) */
+  float* samples;           /* encoder, may be NULL: 12 floats per reference slot j at
+                               index ref_off[p] + j: 8 features, 3 target displacements
+                               (float)(x_t - x_{t-1}), valid flag (1 or 0) */
+  int allow_residual;       /* encoder: choose the residual mode when smaller */
+} tera_predictor;
+
+/* tera_delta_encode / tera_delta_decode with the predictor's histories (and,
+ * with params, the residual mode).  Same arguments and outputs otherwise;
+ * XOR-mode messages are byte-identical to those of the plain entry points. */
+tera_status tera_delta_encode_pred(tera_ctx* ctx, const uint8_t* rec_arena,
+                                   const uint64_t* pair_off, const uint8_t* ref_prev,
+                                   const uint64_t* ref_off_prev, uint32_t pair_begin,
+                                   uint32_t pair_end, uint8_t* ref_next, uint8_t* wire,
+                                   uint64_t wire_capacity, uint64_t* wire_off, uint64_t* wire_len,
+                                   int mode, const tera_predictor* pred, void* stream);
+tera_status tera_delta_decode_pred(tera_ctx* ctx, const uint8_t* wire, const uint64_t* wire_off,
+                                   const uint8_t* ref_prev, const uint64_t* ref_off_prev,
+                                   uint32_t pair_begin, uint32_t pair_end, uint8_t* recv,
+                                   uint64_t recv_capacity_units, uint64_t* recv_off,
+                                   const tera_predictor* pred, void* stream);
+
+/* Training of the predictor on the GPU (float32, deterministic).
+ * samples: n records of 12 floats as written by the encoder (records with a
+ * zero valid flag are skipped; the valid ones are compacted in order).
+ * tera_mlp_grad: gradient (4931 floats) of the mean squared error
+ *   (1/v) sum_i sum_a (o_ia - y_ia)^2 over all v valid samples.
+ * tera_mlp_train: `steps` steps of SGD, params -= lr * c * gradient with
+ *   c = min(1, clip / |gradient|) (no clipping when clip <= 0), each on the
+ *   next `batch` valid samples (cyclically); *n_valid receives v.
+ * Both synchronize `stream` (they read v back). */
+tera_status tera_mlp_grad(tera_ctx* ctx, const float* samples, uint64_t n, const float* params,
+                          float* grad, uint64_t* n_valid, void* stream);
+tera_status tera_mlp_train(tera_ctx* ctx, const float* samples, uint64_t n, float* params,
+                           int steps, int batch, float lr, float clip, uint64_t* n_valid,
+                           void* stream);
+
 /* Schedule of the batched codec (picked by the autotuner; outputs do not
  * depend on it): threads per block = entries per tile (128, 256 or 512),
  * blocks per SM of the persistent launch (1..16), pairs per window of the
@@ -240,6 +304,17 @@ tera_status tera_codec_batched(tera_ctx* ctx, const uint8_t* rec_arena, const ui
                                const uint64_t* recv_off_prev, uint8_t* recv,
                                uint64_t recv_capacity_units, uint64_t* recv_off, int mode,
                                const tera_tune* tune, void* stream);
+
+/* tera_codec_batched with the predictor: enc_pred for the sender side (its
+ * hist_prev / hist_next travel with ref_prev / ref_next), dec_pred for the
+ * receiver (recv_prev / recv).  Either may be NULL (no history on that side). */
+tera_status tera_codec_batched_pred(
+    tera_ctx* ctx, const uint8_t* rec_arena, const uint64_t* pair_off, const uint8_t* ref_prev,
+    const uint64_t* ref_off_prev, uint8_t* ref_next, uint8_t* wire, uint64_t wire_capacity,
+    uint64_t* wire_off, uint64_t* wire_len, const uint8_t* recv_prev,
+    const uint64_t* recv_off_prev, uint8_t* recv, uint64_t recv_capacity_units,
+    uint64_t* recv_off, int mode, const tera_tune* tune, const tera_predictor* enc_pred,
+    const tera_predictor* dec_pred, void* stream);
 
 /* Sec. 2.2.1 "Deserialization": check the TAIO header of ONE pair buffer
  * (device pointer `buf`, `len` bytes available) on the host and return a

@@ -11,7 +11,10 @@ LIB_PATH = os.path.join(HERE, "libtera.so")
 OK, EINVAL, ENOMEM, ECAPACITY, ECORRUPT, EDOMAIN, EREFMISMATCH, ETIMEOUT, ECUDA = range(9)
 STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECAPACITY", "ECORRUPT", "EDOMAIN", "EREFMISMATCH",
                 "ETIMEOUT", "ECUDA"]
-MODE_RAW, MODE_XOR = 0, 1
+MODE_RAW, MODE_XOR, MODE_RESIDUAL = 0, 1, 2
+MLP_PARAMS = 4931
+HIST_BYTES = 48
+SAMPLE_FLOATS = 12
 
 
 class TeraError(RuntimeError):
@@ -49,6 +52,11 @@ class Tune(C.Structure):
                 ("tiles_per_item", C.c_int)]
 
 
+class Predictor(C.Structure):
+    _fields_ = [("params", C.c_void_p), ("hist_prev", C.c_void_p), ("hist_next", C.c_void_p),
+                ("samples", C.c_void_p), ("allow_residual", C.c_int)]
+
+
 # name -> (restype, argtypes); every symbol include/tera.h declares
 P, u32, u64, i64 = C.c_void_p, C.c_uint32, C.c_uint64, C.c_int64
 SIGNATURES = {
@@ -64,6 +72,16 @@ SIGNATURES = {
                                             C.POINTER(C.c_uint64), P]),
     "tera_codec_batched": (C.c_int, [P, P, P, P, P, P, P, u64, P, P, P, P, P, u64, P, C.c_int,
                                      C.POINTER(Tune), P]),
+    "tera_delta_encode_pred": (C.c_int, [P, P, P, P, P, u32, u32, P, P, u64, P, P, C.c_int,
+                                         C.POINTER(Predictor), P]),
+    "tera_delta_decode_pred": (C.c_int, [P, P, P, P, P, u32, u32, P, u64, P,
+                                         C.POINTER(Predictor), P]),
+    "tera_codec_batched_pred": (C.c_int, [P, P, P, P, P, P, P, u64, P, P, P, P, P, u64, P,
+                                          C.c_int, C.POINTER(Tune), C.POINTER(Predictor),
+                                          C.POINTER(Predictor), P]),
+    "tera_mlp_grad": (C.c_int, [P, P, u64, P, P, C.POINTER(C.c_uint64), P]),
+    "tera_mlp_train": (C.c_int, [P, P, u64, P, C.c_int, C.c_int, C.c_float, C.c_float,
+                                 C.POINTER(C.c_uint64), P]),
     "tera_unpack_inplace": (C.c_int, [P, u64, u32, C.POINTER(C.c_void_p),
                                       C.POINTER(C.c_uint64), P]),
     "tera_unpack_validate": (C.c_int, [P, P, P, P]),

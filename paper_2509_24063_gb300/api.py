@@ -190,6 +190,67 @@ class Context:
             int(mode), C.byref(t) if t is not None else None, _stream(stream)),
             "tera_codec_batched")
 
+    @staticmethod
+    def _pred(pred):
+        """tera_predictor from a dict(params, hist_prev, hist_next, samples, allow_residual)."""
+        if pred is None:
+            return None
+        p = _lib.Predictor()
+        for k in ("params", "hist_prev", "hist_next", "samples"):
+            t = pred.get(k)
+            setattr(p, k, None if t is None else _ptr(t).value)
+        p.allow_residual = 1 if pred.get("allow_residual") else 0
+        return p
+
+    def delta_encode_pred(self, rec_arena, pair_off, ref_prev, ref_off_prev, ref_next, wire,
+                          wire_off, wire_len, pred: dict, mode=_lib.MODE_XOR, pair_begin=0,
+                          pair_end=None, stream=None):
+        pe = self.n_pairs if pair_end is None else pair_end
+        p = self._pred(pred)
+        check(self.lib.tera_delta_encode_pred(
+            self.h, _ptr(rec_arena), _ptr(pair_off), _ptr(ref_prev), _ptr(ref_off_prev),
+            pair_begin, pe, _ptr(ref_next), _ptr(wire), wire.numel(), _ptr(wire_off),
+            _ptr(wire_len), int(mode), C.byref(p), _stream(stream)), "tera_delta_encode_pred")
+
+    def delta_decode_pred(self, wire, wire_off, ref_prev, ref_off_prev, recv, recv_off,
+                          pred: dict, pair_begin=0, pair_end=None, stream=None):
+        pe = self.n_pairs if pair_end is None else pair_end
+        p = self._pred(pred)
+        check(self.lib.tera_delta_decode_pred(
+            self.h, _ptr(wire), _ptr(wire_off), _ptr(ref_prev), _ptr(ref_off_prev), pair_begin,
+            pe, _ptr(recv), recv.numel() // 64, _ptr(recv_off), C.byref(p), _stream(stream)),
+            "tera_delta_decode_pred")
+
+    def codec_batched_pred(self, rec_arena, pair_off, ref_prev, ref_off_prev, ref_next, wire,
+                           wire_off, wire_len, recv_prev, recv_off_prev, recv, recv_off,
+                           enc_pred: dict, dec_pred: dict, mode=_lib.MODE_XOR, tune=None,
+                           stream=None):
+        t = None
+        if tune is not None:
+            t = _lib.Tune(int(tune[0]), int(tune[1]), int(tune[2]),
+                          int(tune[3]) if len(tune) > 3 else 4)
+        pe, pd = self._pred(enc_pred), self._pred(dec_pred)
+        check(self.lib.tera_codec_batched_pred(
+            self.h, _ptr(rec_arena), _ptr(pair_off), _ptr(ref_prev), _ptr(ref_off_prev),
+            _ptr(ref_next), _ptr(wire), wire.numel(), _ptr(wire_off), _ptr(wire_len),
+            _ptr(recv_prev), _ptr(recv_off_prev), _ptr(recv), recv.numel() // 64, _ptr(recv_off),
+            int(mode), C.byref(t) if t is not None else None,
+            C.byref(pe) if pe is not None else None, C.byref(pd) if pd is not None else None,
+            _stream(stream)), "tera_codec_batched_pred")
+
+    def mlp_grad(self, samples, params, grad, stream=None) -> int:
+        nv = C.c_uint64()
+        check(self.lib.tera_mlp_grad(self.h, _ptr(samples), samples.numel() // 12, _ptr(params),
+                                     _ptr(grad), C.byref(nv), _stream(stream)), "tera_mlp_grad")
+        return int(nv.value)
+
+    def mlp_train(self, samples, params, steps, batch, lr, clip=1.0, stream=None) -> int:
+        nv = C.c_uint64()
+        check(self.lib.tera_mlp_train(self.h, _ptr(samples), samples.numel() // 12, _ptr(params),
+                                      int(steps), int(batch), float(lr), float(clip), C.byref(nv),
+                                      _stream(stream)), "tera_mlp_train")
+        return int(nv.value)
+
     def unpack_inplace(self, arena: torch.Tensor, byte_offset: int, length: int, stream=None):
         """Header check of one TAIO buffer; returns (device address of record 0, count)."""
         view = C.c_void_p()

@@ -22,20 +22,21 @@ using namespace tera;
 
 namespace {
 
-enum { PH_BUILD = 0, PH_MATCH, PH_NEW, PH_SCAN, PH_EMIT, PH_DSETUP, PH_DSUM, PH_DSCAN, PH_DEMIT,
-       PH_COUNT };
+enum { PH_BUILD = 0, PH_CELLS, PH_MATCH, PH_NEW, PH_SCAN, PH_EMIT, PH_DSETUP, PH_DSUM, PH_DSCAN,
+       PH_DCELLS, PH_DEMIT, PH_COUNT };
+static_assert(PH_COUNT == kBatchPhases, "phase count");
 
 // phases an item of phase `ph` waits for (bit mask over phases of the same pair)
 __device__ __forceinline__ u32 deps(int ph) {
   switch (ph) {
-    case PH_MATCH: return 1u << PH_BUILD;
+    case PH_MATCH: return (1u << PH_BUILD) | (1u << PH_CELLS);
     case PH_NEW: return (1u << PH_BUILD) | (1u << PH_MATCH);
     case PH_SCAN: return (1u << PH_MATCH) | (1u << PH_NEW);
     case PH_EMIT: return 1u << PH_SCAN;
     case PH_DSETUP: return (1u << PH_SCAN) | (1u << PH_EMIT);
     case PH_DSUM: return 1u << PH_DSETUP;
     case PH_DSCAN: return (1u << PH_DSETUP) | (1u << PH_DSUM);
-    case PH_DEMIT: return 1u << PH_DSCAN;
+    case PH_DEMIT: return (1u << PH_DSCAN) | (1u << PH_DCELLS);
     default: return 0u;
   }
 }
@@ -71,6 +72,7 @@ __device__ __forceinline__ u64 make_item(u32 ph, u32 p, u32 t) {
 
 __global__ void __launch_bounds__(1024)
     bat_setup_kernel(EncArgs E, DecArgs D, BatchArgs B, u64 P, int mode, u32 T, u32 K,
+                     int enc_cells, int dec_cells,
                      u64* __restrict__ wire_off, u64 wire_cap, u64 rec_cap, u64 recv_cap,
                      u64 units_cap, u32* __restrict__ need_out, u64* __restrict__ enc_uoff,
                      u64* __restrict__ dec_uoff, u32* epoch) {
@@ -97,6 +99,9 @@ __global__ void __launch_bounds__(1024)
       // items per phase: K tiles per item (one item for the per-pair phases)
       u32* nd = need_out + p * PH_COUNT;
       nd[PH_BUILD] = (u32)((tm + K - 1) / K);
+      nd[PH_CELLS] = enc_cells ? (u32)((ts + K - 1) / K) : 0u;
+      const u64 rr = D.ref_off ? D.ref_off[p + 1] - D.ref_off[p] : 0;
+      nd[PH_DCELLS] = dec_cells ? (u32)(((rr + T - 1) / T + K - 1) / K) : 0u;
       nd[PH_MATCH] = (u32)((ts + K - 1) / K);
       nd[PH_NEW] = (u32)((tm + K - 1) / K);
       nd[PH_SCAN] = 1;
@@ -212,13 +217,18 @@ __device__ __forceinline__ bool wait_deps(const BatchArgs& B, u32 p, int ph, Dev
 }
 
 // At least 1024 resident threads per SM: the codec is latency-bound.
-template <int T>
+template <int T, bool PR>
 __global__ void __launch_bounds__(T, 1024 / T)
     codec_persistent_kernel(EncArgs E, DecArgs D, BatchArgs B, u32 K) {
   extern __shared__ __align__(16) uint8_t stage[];
   __shared__ U64x2 sm[33];
   __shared__ u64 s_item;
   __shared__ int s_go;
+  float* sW = reinterpret_cast<float*>(stage + ((size_t)T * kRecBytes + 48));
+  if (PR) {
+    const float* params = E.pr.params ? E.pr.params : D.pr.params;
+    if (params) load_mlp(sW, params);
+  }
   const u64 n_items = __ldcg(B.n_items);
   const u32 epoch = __ldcg(E.epoch);
   for (;;) {
@@ -247,9 +257,14 @@ __global__ void __launch_bounds__(T, 1024 / T)
       case PH_BUILD:
         for (u64 t = k0; t < k0 + K && t < ntm; ++t) enc_build_unit<T, true>(E, p, nst + t, epoch);
         break;
+      case PH_CELLS:
+        if constexpr (PR)
+          for (u64 t = k0; t < k0 + K && t < nst; ++t)
+            cells_unit(E.pr, E.ref, E.ref_off, p, t, pi[PI_R], T);
+        break;
       case PH_MATCH:
         for (u64 t = k0; t < k0 + K && t < nst; ++t)
-          enc_match_unit<T, true>(E, p, t, B.enc_uoff[p] + t, epoch, sm);
+          enc_match_unit<T, true, PR>(E, p, t, B.enc_uoff[p] + t, epoch, sm, sW);
         break;
       case PH_NEW:
         for (u64 t = k0; t < k0 + K && t < ntm; ++t)
@@ -257,15 +272,15 @@ __global__ void __launch_bounds__(T, 1024 / T)
         break;
       case PH_SCAN:
         if (threadIdx.x < 32)
-          enc_scan_pair<true>(E, p, B.enc_uoff[p], B.enc_uoff[p + 1] - B.enc_uoff[p]);
+          enc_scan_pair<true, PR>(E, p, B.enc_uoff[p], B.enc_uoff[p + 1] - B.enc_uoff[p]);
         break;
       case PH_EMIT:
         for (u64 t = k0; t < k0 + K && t < nst + ntm; ++t)
-          enc_emit_unit<T, true>(E, p, t, B.enc_uoff[p] + t, epoch, sm, stage);
+          enc_emit_unit<T, true, PR>(E, p, t, B.enc_uoff[p] + t, epoch, sm, stage);
         break;
       case PH_DSETUP:
         if (threadIdx.x == 0) {
-          const u32 err = dec_check_header<true>(D, p, E.pair_off[p + 1] - E.pair_off[p]);
+          const u32 err = dec_check_header<true, PR>(D, p, E.pair_off[p + 1] - E.pair_off[p]);
           if (err) latch(D.st, err);
         }
         break;
@@ -276,9 +291,16 @@ __global__ void __launch_bounds__(T, 1024 / T)
       case PH_DSCAN:
         if (threadIdx.x < 32) dec_scan_pair<true>(D, p, B.dec_uoff[p], ntd);
         break;
+      case PH_DCELLS:
+        if constexpr (PR) {
+          const u64 rr = D.ref_off[p + 1] - D.ref_off[p];
+          const u64 ntr = (rr + T - 1) / T;
+          for (u64 t = k0; t < k0 + K && t < ntr; ++t) cells_unit(D.pr, D.ref, D.ref_off, p, t, rr, T);
+        }
+        break;
       case PH_DEMIT:
         for (u64 t = k0; t < k0 + K && t < ntd; ++t)
-          dec_emit_unit<T, true>(D, p, t, B.dec_uoff[p] + t, sm, stage);
+          dec_emit_unit<T, true, PR>(D, p, t, B.dec_uoff[p] + t, sm, stage, sW);
         break;
       default: break;
     }
@@ -289,24 +311,26 @@ __global__ void __launch_bounds__(T, 1024 / T)
   }
 }
 
-template <int T>
+template <int T, bool PR>
 tera_status launch_persistent(tera_ctx* ctx, const EncArgs& E, const DecArgs& D,
                               const BatchArgs& B, int ctas_per_sm, u32 K, cudaStream_t s) {
-  const size_t smem = (size_t)T * kRecBytes + 48;  // <= 32.8 KB: no opt-in needed
+  // stage (+ MLP weights): at most 36 KB, no opt-in needed
+  const size_t smem = (size_t)T * kRecBytes + 48 + (PR ? sizeof(float) * kMlpParams : 0);
   const unsigned grid = (unsigned)(ctx->num_sms * (ctas_per_sm > 0 ? ctas_per_sm : 1));
   prof_begin(ctx, s);
-  codec_persistent_kernel<T><<<grid, T, smem, s>>>(E, D, B, K);
+  codec_persistent_kernel<T, PR><<<grid, T, smem, s>>>(E, D, B, K);
   return check_launch(ctx, "codec_persistent_kernel", s);
 }
 
 }  // namespace
 
-extern "C" tera_status tera_codec_batched(
+static tera_status batched_impl(
     tera_ctx* ctx, const uint8_t* rec_arena, const uint64_t* pair_off, const uint8_t* ref_prev,
     const uint64_t* ref_off_prev, uint8_t* ref_next, uint8_t* wire, uint64_t wire_capacity,
     uint64_t* wire_off, uint64_t* wire_len, const uint8_t* recv_prev,
     const uint64_t* recv_off_prev, uint8_t* recv, uint64_t recv_capacity_units,
-    uint64_t* recv_off, int mode, const tera_tune* tune, void* stream) {
+    uint64_t* recv_off, int mode, const tera_tune* tune, const tera_predictor* enc_pred,
+    const tera_predictor* dec_pred, void* stream) {
   if (!ctx || !rec_arena || !pair_off || !ref_next || !wire || !wire_off || !wire_len || !recv ||
       !recv_off)
     return TERA_EINVAL;
@@ -317,6 +341,7 @@ extern "C" tera_status tera_codec_batched(
        (uintptr_t)(ref_prev ? ref_prev : wire) | (uintptr_t)(recv_prev ? recv_prev : wire)) & 15u)
     return TERA_EINVAL;
   tera_tune tn = tune ? *tune : tera_tune{256, 4, 64, 4};
+  if (enc_pred && enc_pred->params && ((uintptr_t)enc_pred->params & 3u)) return TERA_EINVAL;
   if (tn.block != 128 && tn.block != 256 && tn.block != 512) return TERA_EINVAL;
   if (tn.ctas_per_sm < 1 || tn.ctas_per_sm > 16) return TERA_EINVAL;
   if (tn.window < 1 || tn.window > 1024) return TERA_EINVAL;
@@ -324,6 +349,8 @@ extern "C" tera_status tera_codec_batched(
   cudaSetDevice(ctx->device);
   cudaStream_t s = (cudaStream_t)stream;
   const u64 P = ctx->n_pairs;
+  const bool PR = enc_pred != nullptr || dec_pred != nullptr;
+  if (PR && tn.block > 256) tn.block = 256;  // stage + weights stay within 48 KB
   const u32 T = (u32)tn.block, W = (u32)tn.window, K = (u32)tn.tiles_per_item;
   tera_status st = ensure_records(ctx, ctx->cap_records, s);
   if (st != TERA_OK) return st;
@@ -384,10 +411,35 @@ extern "C" tera_status tera_codec_batched(
   B.dec_uoff = ctx->b_dec_uoff;
   B.abort = reinterpret_cast<u32*>(ctx->b_scalars + 2);
 
+  int enc_cells = 0, dec_cells = 0;
+  if (PR) {
+    if ((st = ensure_pred(ctx)) != TERA_OK) return st;
+    E.pr.unit_res = ctx->unit_res;
+    const u64 cwords = 2 * (2 * ctx->cap_records + 2 * P);
+    if (enc_pred) {
+      if ((enc_pred->hist_prev != nullptr) != (ref_prev != nullptr)) return TERA_EINVAL;
+      fill_pred(ctx, &E.pr, enc_pred, ctx->cseg_enc);
+      E.pr.samples = enc_pred->samples;
+      E.pr.allow_residual = enc_pred->allow_residual;
+      if (E.pr.hist) {
+        enc_cells = 1;
+        cudaMemsetAsync(ctx->cseg_enc, 0, sizeof(u64) * cwords, s);
+      }
+    }
+    if (dec_pred) {
+      if ((dec_pred->hist_prev != nullptr) != (recv_prev != nullptr)) return TERA_EINVAL;
+      fill_pred(ctx, &D.pr, dec_pred, ctx->cseg_dec);
+      if (D.pr.hist) {
+        dec_cells = 1;
+        cudaMemsetAsync(ctx->cseg_dec, 0, sizeof(u64) * cwords, s);
+      }
+    }
+  }
   const u64 n_windows = (P + W - 1) / W;
   cudaMemsetAsync(ctx->b_done, 0, sizeof(u32) * P * PH_COUNT, s);
   prof_begin(ctx, s);
-  bat_setup_kernel<<<1, 1024, 0, s>>>(E, D, B, P, mode, T, K, reinterpret_cast<u64*>(wire_off),
+  bat_setup_kernel<<<1, 1024, 0, s>>>(E, D, B, P, mode, T, K, enc_cells, dec_cells,
+                                      reinterpret_cast<u64*>(wire_off),
                                       wire_capacity, ctx->cap_records, recv_capacity_units,
                                       ctx->b_units_cap < ctx->cap_units ? ctx->b_units_cap
                                                                         : ctx->cap_units,
@@ -406,9 +458,36 @@ extern "C" tera_status tera_codec_batched(
       ctx->b_need, P, W, ctx->b_win_base, n_windows, ctx->b_items, ctx->b_scalars + 0,
       reinterpret_cast<const u32*>(ctx->b_scalars + 2));
   if ((st = check_launch(ctx, "bat_window_fill_kernel", s)) != TERA_OK) return st;
-  switch (T) {
-    case 128: return launch_persistent<128>(ctx, E, D, B, tn.ctas_per_sm, K, s);
-    case 512: return launch_persistent<512>(ctx, E, D, B, tn.ctas_per_sm, K, s);
-    default: return launch_persistent<256>(ctx, E, D, B, tn.ctas_per_sm, K, s);
+  if (PR) {
+    if (T == 128) return launch_persistent<128, true>(ctx, E, D, B, tn.ctas_per_sm, K, s);
+    return launch_persistent<256, true>(ctx, E, D, B, tn.ctas_per_sm, K, s);
   }
+  switch (T) {
+    case 128: return launch_persistent<128, false>(ctx, E, D, B, tn.ctas_per_sm, K, s);
+    case 512: return launch_persistent<512, false>(ctx, E, D, B, tn.ctas_per_sm, K, s);
+    default: return launch_persistent<256, false>(ctx, E, D, B, tn.ctas_per_sm, K, s);
+  }
+}
+
+extern "C" tera_status tera_codec_batched(
+    tera_ctx* ctx, const uint8_t* rec_arena, const uint64_t* pair_off, const uint8_t* ref_prev,
+    const uint64_t* ref_off_prev, uint8_t* ref_next, uint8_t* wire, uint64_t wire_capacity,
+    uint64_t* wire_off, uint64_t* wire_len, const uint8_t* recv_prev,
+    const uint64_t* recv_off_prev, uint8_t* recv, uint64_t recv_capacity_units,
+    uint64_t* recv_off, int mode, const tera_tune* tune, void* stream) {
+  return batched_impl(ctx, rec_arena, pair_off, ref_prev, ref_off_prev, ref_next, wire,
+                      wire_capacity, wire_off, wire_len, recv_prev, recv_off_prev, recv,
+                      recv_capacity_units, recv_off, mode, tune, nullptr, nullptr, stream);
+}
+
+extern "C" tera_status tera_codec_batched_pred(
+    tera_ctx* ctx, const uint8_t* rec_arena, const uint64_t* pair_off, const uint8_t* ref_prev,
+    const uint64_t* ref_off_prev, uint8_t* ref_next, uint8_t* wire, uint64_t wire_capacity,
+    uint64_t* wire_off, uint64_t* wire_len, const uint8_t* recv_prev,
+    const uint64_t* recv_off_prev, uint8_t* recv, uint64_t recv_capacity_units,
+    uint64_t* recv_off, int mode, const tera_tune* tune, const tera_predictor* enc_pred,
+    const tera_predictor* dec_pred, void* stream) {
+  return batched_impl(ctx, rec_arena, pair_off, ref_prev, ref_off_prev, ref_next, wire,
+                      wire_capacity, wire_off, wire_len, recv_prev, recv_off_prev, recv,
+                      recv_capacity_units, recv_off, mode, tune, enc_pred, dec_pred, stream);
 }

@@ -52,6 +52,34 @@ __device__ __forceinline__ Rec load_rec_x(const uint8_t* p) {
   return r;
 }
 
+// ---------------- learned predictor (not in the paper) ----------------
+// MLP 8 -> 64 -> 64 -> 3 (ReLU hidden), float32, weights W1[64][8] b1[64]
+// W2[64][64] b2[64] W3[3][64] b3[3]; each neuron: acc = b; for k ascending
+// acc = fmaf(W[k], in[k], acc).  Per-slot history (48 bytes): u64 xp[3] (bits
+// of the position one iteration before the reference's), u32 d2[3] (bits of
+// (float)(xp - position before it)), u32 n (steps known, 0..2), u64 zero.
+constexpr int kMlpIn = 8, kMlpH = 64, kMlpOut = 3;
+constexpr int kMlpW1 = 0, kMlpB1 = kMlpW1 + kMlpH * kMlpIn, kMlpW2 = kMlpB1 + kMlpH;
+constexpr int kMlpB2 = kMlpW2 + kMlpH * kMlpH, kMlpW3 = kMlpB2 + kMlpH;
+constexpr int kMlpB3 = kMlpW3 + kMlpOut * kMlpH, kMlpParams = kMlpB3 + kMlpOut;  // 4931
+constexpr u32 kHistBytes = 48;
+constexpr u32 kModeResidual = 2;
+constexpr int kSampleFloats = 12;  // 8 features, 3 target displacements, valid flag
+
+struct PredArgs {
+  const float* params;     // MLP weights (device); null: the residual mode is off
+  const uint8_t* hist;     // history of the reference (slot j of pair p at index off[p] + j)
+  uint8_t* hist_next;      // history of the new reference / receive buffer
+  u64* cseg;               // neighbour-count segments: 2 words per entry (key + 1, count)
+  u64* pscr;               // per-slot prediction scratch: pred bits x3, ok
+  float* samples;          // per-slot training samples (encoder), may be null
+  u64* unit_res;           // per-unit residual payload bytes (encoder)
+  double lo[3];
+  double w;
+  u64 ncell[3];
+  int allow_residual;
+};
+
 struct EncArgs {
   const uint8_t* rec;      // packed messages (TAIO arena laid out with pair_off)
   const u64* pair_off;
@@ -77,6 +105,7 @@ struct EncArgs {
   u32 class_id;
   DevStatus* st;
   DevStats* stats;
+  PredArgs pr{};
 };
 
 struct DecArgs {
@@ -95,6 +124,7 @@ struct DecArgs {
   u32 p0, p1;
   u32 class_id;
   DevStatus* st;
+  PredArgs pr{};
 };
 
 __device__ __forceinline__ u32 rec_code(const Rec& d, u32* bytes) {
@@ -107,6 +137,185 @@ __device__ __forceinline__ u32 rec_code(const Rec& d, u32* bytes) {
   }
   *bytes = b;
   return code;
+}
+
+
+// Cell of a reference record: floor((v - lo) / w) per axis, in binary64.
+__device__ __forceinline__ u64 cell_key(const Rec& R, const PredArgs& pr) {
+  u64 c[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const double q = floor(__ddiv_rn(__dsub_rn(__longlong_as_double((long long)R.w[1 + a]), pr.lo[a]),
+                                     pr.w));
+    c[a] = (u64)(long long)q;
+  }
+  return c[0] + pr.ncell[0] * (c[1] + pr.ncell[1] * c[2]);
+}
+
+// Count one reference record in its cell (segment of pair p, zeroed before).
+__device__ __forceinline__ void cell_insert(u64* cseg, u64 base, u64 size, u64 key) {
+  u64 i = seg_start(key, size);
+  for (u64 probe = 0; probe < size; ++probe) {
+    u64* e = cseg + 2 * (base + i);
+    const u64 k0 = __ldcg(e);
+    if (k0 == 0) {
+      const u64 prev = atomicCAS(e, 0ull, key + 1);
+      if (prev == 0 || prev == key + 1) {
+        atomicAdd(e + 1, 1ull);
+        return;
+      }
+    } else if (k0 == key + 1) {
+      atomicAdd(e + 1, 1ull);
+      return;
+    }
+    i = (i + 1 == size) ? 0 : i + 1;
+  }
+}
+
+__device__ __forceinline__ u32 cell_count(const u64* cseg, u64 base, u64 size, u64 key) {
+  u64 i = seg_start(key, size);
+  for (u64 probe = 0; probe < size; ++probe) {
+    const u64* e = cseg + 2 * (base + i);
+    const u64 k0 = __ldcg(e);
+    if (k0 == key + 1) return (u32)__ldcg(e + 1);
+    if (k0 == 0) return 0;
+    i = (i + 1 == size) ? 0 : i + 1;
+  }
+  return 0;
+}
+
+// The network on one feature vector; W in shared memory.
+__device__ __forceinline__ void mlp_infer(const float* __restrict__ W, const float* f, float* o) {
+  float h1[kMlpH];
+#pragma unroll
+  for (int j = 0; j < kMlpH; ++j) {
+    float acc = W[kMlpB1 + j];
+#pragma unroll
+    for (int k = 0; k < kMlpIn; ++k) acc = __fmaf_rn(W[kMlpW1 + j * kMlpIn + k], f[k], acc);
+    h1[j] = acc > 0.0f ? acc : 0.0f;
+  }
+  o[0] = W[kMlpB3 + 0];
+  o[1] = W[kMlpB3 + 1];
+  o[2] = W[kMlpB3 + 2];
+  for (int j = 0; j < kMlpH; ++j) {
+    float acc = W[kMlpB2 + j];
+#pragma unroll
+    for (int k = 0; k < kMlpH; ++k) acc = __fmaf_rn(W[kMlpW2 + j * kMlpH + k], h1[k], acc);
+    const float h2 = acc > 0.0f ? acc : 0.0f;
+    // output neuron a accumulates its inputs in ascending order, like every layer
+#pragma unroll
+    for (int a = 0; a < kMlpOut; ++a) o[a] = __fmaf_rn(W[kMlpW3 + a * kMlpH + j], h2, o[a]);
+  }
+}
+
+struct Hist {
+  u64 xp[3];
+  u32 d2[3];
+  u32 n;
+};
+
+__device__ __forceinline__ Hist load_hist(const uint8_t* h) {
+  const ulonglong2* q = reinterpret_cast<const ulonglong2*>(h);
+  const ulonglong2 a = q[0], b = q[1], c = q[2];
+  Hist r;
+  r.xp[0] = a.x;
+  r.xp[1] = a.y;
+  r.xp[2] = b.x;
+  r.d2[0] = (u32)b.y;
+  r.d2[1] = (u32)(b.y >> 32);
+  r.d2[2] = (u32)c.x;
+  r.n = (u32)(c.x >> 32);
+  return r;
+}
+
+// History of a new reference entry made from reference record R with history
+// H (hn = nullptr: a new record, no history).
+__device__ __forceinline__ void store_hist_next(uint8_t* out, const Rec* R, const Hist* H) {
+  ulonglong2* q = reinterpret_cast<ulonglong2*>(out);
+  if (!R) {
+    q[0] = make_ulonglong2(0, 0);
+    q[1] = make_ulonglong2(0, 0);
+    q[2] = make_ulonglong2(0, 0);
+    return;
+  }
+  const u32 n = H ? H->n : 0u;
+  u32 d2[3] = {0u, 0u, 0u};
+  if (n >= 1) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+      d2[a] = __float_as_uint(__double2float_rn(
+          __dsub_rn(__longlong_as_double((long long)R->w[1 + a]),
+                    __longlong_as_double((long long)H->xp[a]))));
+  }
+  const u32 n2 = n + 1 > 2 ? 2u : n + 1;
+  q[0] = make_ulonglong2(R->w[1], R->w[2]);
+  q[1] = make_ulonglong2(R->w[3], (u64)d2[0] | ((u64)d2[1] << 32));
+  q[2] = make_ulonglong2((u64)d2[2] | ((u64)n2 << 32), 0);
+}
+
+// Features of a reference slot; false when it is not predictable.
+__device__ __forceinline__ bool features(const Rec& R, const Hist& H, u32 ncount, float* f) {
+  if (H.n < 2) return false;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    f[a] = __double2float_rn(__dsub_rn(__longlong_as_double((long long)R.w[1 + a]),
+                                       __longlong_as_double((long long)H.xp[a])));
+    f[3 + a] = __uint_as_float(H.d2[a]);
+  }
+  f[6] = __double2float_rn(__ddiv_rn(__longlong_as_double((long long)R.w[4]), 10.0));
+  f[7] = __fmul_rn(__uint2float_rn(ncount), 0.03125f);
+  bool ok = true;
+#pragma unroll
+  for (int i = 0; i < kMlpIn; ++i) ok &= isfinite(f[i]);
+  return ok;
+}
+
+// Predicted position bits from features; false when an output is not finite.
+__device__ __forceinline__ bool predict_from(const float* W, const Rec& R, const float* f,
+                                             u64* pred) {
+  float o[kMlpOut];
+  mlp_infer(W, f, o);
+  bool ok = isfinite(o[0]) && isfinite(o[1]) && isfinite(o[2]);
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+    pred[a] = (u64)__double_as_longlong(
+        __dadd_rn(__longlong_as_double((long long)R.w[1 + a]), (double)o[a]));
+  return ok;
+}
+
+__device__ __forceinline__ u64 zigzag(u64 d) { return (d << 1) ^ (u64)((long long)d >> 63); }
+__device__ __forceinline__ u64 unzigzag(u64 z) { return (z >> 1) ^ (0ull - (z & 1ull)); }
+
+// Predictor arguments from the caller's tera_predictor and the context.
+inline void fill_pred(const tera_ctx* ctx, PredArgs* pr, const tera_predictor* pred, u64* cseg) {
+  pr->params = pred->params;
+  pr->hist = pred->hist_prev;
+  pr->hist_next = pred->hist_next;
+  pr->cseg = cseg;
+  pr->pscr = ctx->pscr;
+  pr->samples = nullptr;
+  pr->unit_res = ctx->unit_res;
+  for (int a = 0; a < 3; ++a) {
+    pr->lo[a] = ctx->grid.lo[a];
+    pr->ncell[a] = ctx->ncell[a];
+  }
+  pr->w = ctx->grid.w;
+  pr->allow_residual = 0;
+}
+
+// Slot units of either side: count every reference record in its cell.
+__device__ __forceinline__ void cells_unit(const PredArgs& pr, const uint8_t* ref,
+                                           const u64* ref_off, u32 p, u64 local, u64 r, int T) {
+  const u64 j = local * (u64)T + threadIdx.x;
+  if (j >= r) return;
+  const Rec R = load_rec(ref + (ref_off[p] + p + 1 + j) * kRecBytes);
+  cell_insert(pr.cseg, seg_base(ref_off[p], p), seg_size(r), cell_key(R, pr));
+}
+
+// Load the MLP weights into shared memory (all threads).
+__device__ __forceinline__ void load_mlp(float* sW, const float* params) {
+  for (int i = threadIdx.x; i < kMlpParams; i += blockDim.x) sW[i] = params[i];
+  __syncthreads();
 }
 
 // Record index (global) of the message record of pair p with this id, or
@@ -155,14 +364,18 @@ __device__ __forceinline__ void enc_build_unit(const EncArgs& A, u32 p, u64 loca
 
 // Slot unit: find the message record with the slot's id, write the slot's
 // code, and return the unit's (payload bytes, non-placeholder slots).
-template <int T, bool CG>
+template <int T, bool CG, bool PR = false>
 __device__ __forceinline__ void enc_match_unit(const EncArgs& A, u32 p, u64 local, u64 U,
-                                               u32 epoch, U64x2* sm) {
+                                               u32 epoch, U64x2* sm, const float* sW = nullptr) {
   const u64* pi = A.info + (u64)p * 8;
   const u64 r = pi[PI_R];
   const u64 j = local * T + threadIdx.x;
   U64x2 v{0, 0};
+  u64 vres = 0;
   if (j < r) {
+    if constexpr (PR) {
+      if (A.pr.samples) A.pr.samples[(u64)kSampleFloats * (A.ref_off[p] + j) + 11] = 0.0f;
+    }
     const u64 g_lo = A.pair_off[p];
     const Rec R = load_rec(A.ref + (A.ref_off[p] + p + 1 + j) * kRecBytes);
     u32 g = seg_lookup<CG>(A.seg, A.msg_id, epoch, p, g_lo, pi[PI_M], R.w[0]);
@@ -176,15 +389,61 @@ __device__ __forceinline__ void enc_match_unit(const EncArgs& A, u32 p, u64 loca
       u32 b;
       code = rec_code(d, &b);
       v = U64x2{b, 1};
+      if constexpr (PR) {
+        // the slot's prediction, its residual payload, and a training sample
+        vres = b;
+        u64* ps = A.pr.pscr + 4 * (A.ref_off[p] + j);
+        bool ok = false;
+        float f[kMlpIn];
+        if (A.pr.hist && pi[PI_MODE] == TERA_MODE_XOR) {
+          const Hist H = load_hist(A.pr.hist + kHistBytes * (A.ref_off[p] + j));
+          const u32 nc = cell_count(A.pr.cseg, seg_base(A.ref_off[p], p), seg_size(r),
+                                    cell_key(R, A.pr));
+          if (features(R, H, nc, f)) {
+            if (A.pr.samples) {
+              float* s = A.pr.samples + (u64)kSampleFloats * (A.ref_off[p] + j);
+#pragma unroll
+              for (int i = 0; i < kMlpIn; ++i) s[i] = f[i];
+#pragma unroll
+              for (int a = 0; a < 3; ++a)
+                s[kMlpIn + a] = __double2float_rn(
+                    __dsub_rn(__longlong_as_double((long long)M.w[1 + a]),
+                              __longlong_as_double((long long)R.w[1 + a])));
+              s[11] = 1.0f;
+            }
+            if (A.pr.params) {
+              u64 pred[3];
+              ok = predict_from(sW, R, f, pred);
+              if (ok) {
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                  vres += sig_bytes(zigzag(M.w[1 + a] - pred[a]));
+                  vres -= sig_bytes(d.w[1 + a]);
+                  ps[a] = pred[a];
+                }
+              }
+            }
+          }
+        }
+        ps[3] = ok ? 1ull : 0ull;
+      }
     } else {
       code = 0xFu;  // placeholder
+      if constexpr (PR) A.pr.pscr[4 * (A.ref_off[p] + j) + 3] = 0;
     }
     A.slot_src[A.ref_off[p] + j] = g;
-    reinterpret_cast<u32*>(A.wire + A.wire_off[p] + kHdrBytes)[j] = code;
+    // with the predictor the message mode is chosen later: the slot codes
+    // are written when the payload is
+    if constexpr (!PR) reinterpret_cast<u32*>(A.wire + A.wire_off[p] + kHdrBytes)[j] = code;
   }
   U64x2 tot;
   block_excl_scan2(v, sm, &tot);
   if (threadIdx.x == 0) A.unit_sum[U] = tot;
+  if constexpr (PR) {
+    U64x2 tr;
+    block_excl_scan2(U64x2{vres, 0}, sm, &tr);
+    if (threadIdx.x == 0) A.pr.unit_res[U] = tr.a;
+  }
 }
 
 // Message unit: records no slot took are new; (payload bytes, new records).
@@ -215,16 +474,35 @@ __device__ __forceinline__ void enc_new_unit(const EncArgs& A, u32 p, u64 local,
 
 // One warp: unit prefixes of pair p (units [u0, u0 + n_units)), header,
 // padding, the new reference's header and the iteration totals.
-template <bool CG>
+template <bool CG, bool PR = false>
 __device__ __forceinline__ void enc_scan_pair(const EncArgs& A, u32 p, u64 u0, u64 n_units) {
   const int lane = threadIdx.x & 31;
   u64* pi = A.info + (u64)p * 8;
   const u64 nst = pi[PI_NST];
   const u64 r = pi[PI_R], m = pi[PI_M];
+  u64 mode = pi[PI_MODE];
+  if constexpr (PR) {
+    // residual mode when the predictor makes the slots' payload smaller
+    u64 bx = 0, br = 0;
+    for (u64 b = 0; b < nst; b += 32) {
+      u64 i = b + lane;
+      if (i < nst) {
+        bx += ldx<CG>(A.unit_sum + u0 + i).a;
+        br += ldx<CG>(A.pr.unit_res + u0 + i);
+      }
+    }
+    bx = warp_sum(bx);
+    br = warp_sum(br);
+    if (A.pr.params && A.pr.allow_residual && mode == TERA_MODE_XOR && br < bx) mode = kModeResidual;
+  }
+  const bool res = PR && mode == kModeResidual;
   U64x2 run{0, 0};
   for (u64 b = 0; b < nst; b += 32) {
     u64 i = b + lane;
     U64x2 v = i < nst ? ldx<CG>(A.unit_sum + u0 + i) : U64x2{0, 0};
+    if constexpr (PR) {
+      if (res && i < nst) v.a = ldx<CG>(A.pr.unit_res + u0 + i);
+    }
     U64x2 incl = v;
     for (int o = 1; o < 32; o <<= 1) {
       U64x2 t = shfl_up(incl, o);
@@ -256,13 +534,14 @@ __device__ __forceinline__ void enc_scan_pair(const EncArgs& A, u32 p, u64 u0, u
   uint8_t* w = A.wire + A.wire_off[p];
   if (lane == 0) {
     if (matched + n_new != m) latch(A.st, TERA_EINVAL);
+    pi[PI_MODE] = mode;
     pi[PI_MATCHED] = matched;
     pi[PI_NEW] = n_new;
     pi[PI_SLOTPAY] = slot_pay;
     pi[PI_PAY] = payload;
     ulonglong2* h = reinterpret_cast<ulonglong2*>(w);
     h[0] = make_ulonglong2((u64)kWireMagic | ((u64)kVersion << 32) | ((u64)kRecBytes << 48),
-                           (u64)A.class_id | (pi[PI_MODE] << 32));
+                           (u64)A.class_id | (mode << 32));
     h[1] = make_ulonglong2(r, n_new);
     h[2] = make_ulonglong2(r - matched, payload);
     h[3] = make_ulonglong2((u64)p, msg);
@@ -299,8 +578,9 @@ __device__ __forceinline__ void flush_stage(const uint8_t* stage, uint8_t* gA, u
   }
 }
 
-// Any unit: payload bytes (staged), codes of new records, new reference.
-template <int T, bool CG>
+// Any unit: payload bytes (staged), codes of new records, new reference
+// (with the predictor: also the slot codes, residual words and histories).
+template <int T, bool CG, bool PR = false>
 __device__ __forceinline__ void enc_emit_unit(const EncArgs& A, u32 p, u64 local, u64 U, u32 epoch,
                                               U64x2* sm, uint8_t* stage) {
   const u64* pi = A.info + (u64)p * 8;
@@ -308,7 +588,7 @@ __device__ __forceinline__ void enc_emit_unit(const EncArgs& A, u32 p, u64 local
   const u64 n_new = ldx<CG>(pi + PI_NEW);
   const bool slot_unit = local < nst;
   const u64 e = slot_unit ? local * T + threadIdx.x : (local - nst) * T + threadIdx.x;
-  Rec d, cur;
+  Rec d, cur, R;
   u32 L[8];
   U64x2 v{0, 0};
   u64 g = 0;
@@ -318,15 +598,34 @@ __device__ __forceinline__ void enc_emit_unit(const EncArgs& A, u32 p, u64 local
       if (gg != kNoMatch) {
         g = gg;
         cur = load_rec(A.rec + (g + p + 1) * kRecBytes);
-        const Rec R = load_rec(A.ref + (A.ref_off[p] + p + 1 + e) * kRecBytes);
+        R = load_rec(A.ref + (A.ref_off[p] + p + 1 + e) * kRecBytes);
+#pragma unroll
+        for (int w = 0; w < 8; ++w) d.w[w] = cur.w[w] ^ R.w[w];
+        if constexpr (PR) {
+          if (ldx<CG>(pi + PI_MODE) == kModeResidual) {
+            const u64* ps = A.pr.pscr + 4 * (A.ref_off[p] + e);
+            if (ldx<CG>(ps + 3)) {
+#pragma unroll
+              for (int a = 0; a < 3; ++a) d.w[1 + a] = zigzag(cur.w[1 + a] - ldx<CG>(ps + a));
+            }
+          }
+        }
         u32 b = 0;
 #pragma unroll
         for (int w = 0; w < 8; ++w) {
-          d.w[w] = cur.w[w] ^ R.w[w];
           L[w] = sig_bytes(d.w[w]);
           b += L[w];
         }
         v = U64x2{b, 1};
+      }
+      if constexpr (PR) {
+        u32 code = 0xFu;
+        if (gg != kNoMatch) {
+          code = 0;
+#pragma unroll
+          for (int w = 0; w < 8; ++w) code |= L[w] << (4 * w);
+        }
+        reinterpret_cast<u32*>(A.wire + A.wire_off[p] + kHdrBytes)[e] = code;
       }
     }
   } else if (e < pi[PI_M]) {
@@ -365,6 +664,21 @@ __device__ __forceinline__ void enc_emit_unit(const EncArgs& A, u32 p, u64 local
       pos = ldx<CG>(pi + PI_MATCHED) + rank;
     }
     store_rec(A.ref_next + (A.pair_off[p] + p + 1 + pos) * kRecBytes, cur);
+    if constexpr (PR) {
+      if (A.pr.hist_next) {
+        uint8_t* hn = A.pr.hist_next + kHistBytes * (A.pair_off[p] + pos);
+        if (slot_unit) {
+          if (A.pr.hist) {
+            const Hist H = load_hist(A.pr.hist + kHistBytes * (A.ref_off[p] + e));
+            store_hist_next(hn, &R, &H);
+          } else {
+            store_hist_next(hn, &R, nullptr);
+          }
+        } else {
+          store_hist_next(hn, nullptr, nullptr);
+        }
+      }
+    }
   }
   __syncthreads();
   flush_stage(stage, gA, tot.a);
@@ -394,7 +708,7 @@ __device__ __forceinline__ bool check_code(u32 code, u64 e, u64 ns, bool* hole, 
 // Full header check of pair p's message; writes the decode facts and returns
 // the error (0 when valid).  expect_m: when not ~0, the receive buffer size
 // the caller laid out for p, which the header's count must equal.
-template <bool CG>
+template <bool CG, bool PR = false>
 __device__ __forceinline__ u32 dec_check_header(const DecArgs& A, u32 p, u64 expect_m) {
   const u64 avail = A.wire_off[p + 1] - A.wire_off[p];
   const u64* h = reinterpret_cast<const u64*>(A.wire + A.wire_off[p]);
@@ -415,7 +729,7 @@ __device__ __forceinline__ u32 dec_check_header(const DecArgs& A, u32 p, u64 exp
     if ((u32)w0 != kWireMagic || ((w0 >> 32) & 0xFFFF) != kVersion || (w0 >> 48) != kRecBytes ||
         (u32)w1 != A.class_id || w6 != (u64)p) {
       err = TERA_ECORRUPT;
-    } else if (mode == TERA_MODE_XOR) {
+    } else if (mode == TERA_MODE_XOR || (PR && A.pr.params && mode == kModeResidual)) {
       if (ns != r) err = TERA_EREFMISMATCH;
     } else if (mode == TERA_MODE_RAW) {
       if (ns != 0) err = TERA_ECORRUPT;
@@ -429,7 +743,7 @@ __device__ __forceinline__ u32 dec_check_header(const DecArgs& A, u32 p, u64 exp
       else if (expect_m != ~0ull && ns - nh + nn != expect_m)
         err = TERA_ECORRUPT;
     }
-    if (!err && mode == TERA_MODE_XOR && A.ref) {
+    if (!err && mode != TERA_MODE_RAW && A.ref) {
       // the receiver's reference buffer must be the one this message refers to
       const u64* rh = reinterpret_cast<const u64*>(A.ref + (A.ref_off[p] + p) * kRecBytes);
       if ((u32)rh[0] != kTaioMagic || (u32)rh[1] != A.class_id || (u32)(rh[1] >> 32) != p ||
@@ -497,9 +811,10 @@ __device__ __forceinline__ void dec_scan_pair(const DecArgs& A, u32 p, u64 u0, u
   }
 }
 
-template <int T, bool CG>
+template <int T, bool CG, bool PR = false>
 __device__ __forceinline__ void dec_emit_unit(const DecArgs& A, u32 p, u64 local, u64 U,
-                                              U64x2* sm, uint8_t* stage) {
+                                              U64x2* sm, uint8_t* stage,
+                                              const float* sW = nullptr) {
   const u64* pi = A.info + (u64)p * 8;
   if (!ldx<CG>(pi + DI_OK)) return;  // block-uniform
   const u64 ns = ldx<CG>(pi + DI_NS), n = ns + ldx<CG>(pi + DI_NN);
@@ -537,12 +852,36 @@ __device__ __forceinline__ void dec_emit_unit(const DecArgs& A, u32 p, u64 local
       o += L;
       rec.w[w] = x;
     }
+    const u64 pos = base.b + ex.b;
     if (e < ns) {
       const Rec R = load_rec(A.ref + (A.ref_off[p] + p + 1 + e) * kRecBytes);
+      bool pred_ok = false;
+      u64 pred[3];
+      if constexpr (PR) {
+        Hist H;
+        if (A.pr.hist) H = load_hist(A.pr.hist + kHistBytes * (A.ref_off[p] + e));
+        if (A.pr.hist && ldx<CG>(pi + DI_MODE) == kModeResidual) {
+          const u64 r = A.ref_off[p + 1] - A.ref_off[p];
+          const u32 nc = cell_count(A.pr.cseg, seg_base(A.ref_off[p], p), seg_size(r),
+                                    cell_key(R, A.pr));
+          float f[kMlpIn];
+          if (features(R, H, nc, f)) pred_ok = predict_from(sW, R, f, pred);
+        }
+        if (A.pr.hist_next)
+          store_hist_next(A.pr.hist_next + kHistBytes * (A.recv_off[p] + pos), &R,
+                          A.pr.hist ? &H : nullptr);
+      }
 #pragma unroll
-      for (int w = 0; w < 8; ++w) rec.w[w] ^= R.w[w];
+      for (int w = 0; w < 8; ++w) {
+        if (pred_ok && w >= 1 && w <= 3) rec.w[w] = pred[w - 1] + unzigzag(rec.w[w]);
+        else rec.w[w] ^= R.w[w];
+      }
+    } else {
+      if constexpr (PR) {
+        if (A.pr.hist_next)
+          store_hist_next(A.pr.hist_next + kHistBytes * (A.recv_off[p] + pos), nullptr, nullptr);
+      }
     }
-    const u64 pos = base.b + ex.b;
     store_rec(A.recv + (A.recv_off[p] + p + 1 + pos) * kRecBytes, rec);
   }
   __syncthreads();

@@ -289,7 +289,7 @@ tera_status ensure_batched(tera_ctx* ctx, u32 T, u32 W) {
   // units: slot + message tiles per pair (encode), entry tiles (decode)
   tera_status st = ensure_units(ctx, 2 * (cap / T) + 2 * P + 16, 0);
   if (st != TERA_OK) return st;
-  const u64 items = 9 * (cap / T) + 12 * P + 64;
+  const u64 items = 11 * (cap / T) + 16 * P + 64;
   const u64 windows = (P + W - 1) / W + 1;
   if (ctx->b_items && items <= ctx->b_items_cap && windows <= ctx->b_windows_cap &&
       ctx->b_unit_sum && ctx->b_units_cap >= ctx->cap_units)
@@ -298,8 +298,8 @@ tera_status ensure_batched(tera_ctx* ctx, u32 T, u32 W) {
   const u64 ic = items + items / 4;
   const u64 wc = windows < (P + 1) ? (P + 1) : windows;
   if ((st = alloc_dev(ctx->b_items, ic)) != TERA_OK) return st;
-  if ((st = alloc_dev(ctx->b_done, P * 9)) != TERA_OK) return st;
-  if ((st = alloc_dev(ctx->b_need, P * 9)) != TERA_OK) return st;
+  if ((st = alloc_dev(ctx->b_done, P * kBatchPhases)) != TERA_OK) return st;
+  if ((st = alloc_dev(ctx->b_need, P * kBatchPhases)) != TERA_OK) return st;
   if ((st = alloc_dev(ctx->b_enc_uoff, P + 1)) != TERA_OK) return st;
   if ((st = alloc_dev(ctx->b_dec_uoff, P + 1)) != TERA_OK) return st;
   if ((st = alloc_dev(ctx->b_win_total, wc)) != TERA_OK) return st;
@@ -312,6 +312,21 @@ tera_status ensure_batched(tera_ctx* ctx, u32 T, u32 W) {
   ctx->b_windows_cap = wc;
   ctx->b_units_cap = ctx->cap_units;
   return ensure_scan_part(ctx, wc);
+}
+
+tera_status ensure_pred(tera_ctx* ctx) {
+  const u64 cap = ctx->cap_records, P = ctx->n_pairs;
+  if (ctx->cseg_enc && ctx->pred_cap >= cap && ctx->unit_res && ctx->unit_res_cap >= ctx->cap_units)
+    return TERA_OK;
+  cudaDeviceSynchronize();
+  tera_status st;
+  if ((st = alloc_dev(ctx->cseg_enc, 2 * (2 * cap + 2 * P))) != TERA_OK) return st;
+  if ((st = alloc_dev(ctx->cseg_dec, 2 * (2 * cap + 2 * P))) != TERA_OK) return st;
+  if ((st = alloc_dev(ctx->pscr, 4 * cap)) != TERA_OK) return st;
+  if ((st = alloc_dev(ctx->unit_res, ctx->cap_units)) != TERA_OK) return st;
+  ctx->pred_cap = cap;
+  ctx->unit_res_cap = ctx->cap_units;
+  return TERA_OK;
 }
 
 }  // namespace tera
@@ -329,6 +344,7 @@ tera_status tera_ctx_create(tera_ctx** out, const tera_grid* grid, int device, u
   *out = nullptr;
   GridTables t;
   memset(&t, 0, sizeof(t));
+  uint64_t ncell_tmp[3] = {1, 1, 1};
   auto key = [](double d) {
     uint64_t b;
     memcpy(&b, &d, 8);
@@ -353,6 +369,7 @@ tera_status tera_ctx_create(tera_ctx** out, const tera_grid* grid, int device, u
     t.klo[a] = key(lo);
     t.khi[a] = key(hi);
     t.n[a] = n;
+    ncell_tmp[a] = (uint64_t)std::floor((hi - lo) / grid->w) + 1;
   }
   if (cudaSetDevice(device) != cudaSuccess) return TERA_ECUDA;
   tera_ctx* c = new (std::nothrow) tera_ctx();
@@ -363,6 +380,7 @@ tera_status tera_ctx_create(tera_ctx** out, const tera_grid* grid, int device, u
   c->grid = *grid;
   c->n_boxes = (uint32_t)grid->n[0] * (uint32_t)grid->n[1] * (uint32_t)grid->n[2];
   c->n_pairs = (uint64_t)c->n_boxes * 27u;
+  for (int a = 0; a < 3; ++a) c->ncell[a] = ncell_tmp[a];
   cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
   if (c->num_sms <= 0) c->num_sms = 148;
   tera_status st = TERA_OK;
@@ -434,6 +452,11 @@ tera_status tera_ctx_destroy(tera_ctx* c) {
   free_dev(c->b_scalars);
   free_dev(c->b_unit_sum);
   free_dev(c->b_unit_base);
+  free_dev(c->cseg_enc);
+  free_dev(c->cseg_dec);
+  free_dev(c->pscr);
+  free_dev(c->unit_res);
+  free_dev(c->mlp_scratch);
   if (c->h_status) cudaFreeHost(c->h_status);
   if (ProfState* p = prof(c)) {
     for (auto& q : p->pending) {

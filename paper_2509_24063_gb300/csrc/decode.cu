@@ -23,6 +23,7 @@ __device__ __forceinline__ void locate(const DecArgs& A, u64 U, u32* p, u64* loc
   *local = U - A.unit_off[*p - A.p0];
 }
 
+template <bool PR>
 __global__ void __launch_bounds__(1024) dec_setup_kernel(DecArgs A, u64 P, u64 recv_cap,
                                                          u64* __restrict__ units_total,
                                                          u64 units_cap) {
@@ -59,7 +60,7 @@ __global__ void __launch_bounds__(1024) dec_setup_kernel(DecArgs A, u64 P, u64 r
     u64 v = 0;
     if (k < npr && !abort) {
       const u32 p = A.p0 + (u32)k;
-      const u32 err = dec_check_header<false>(A, p, ~0ull);
+      const u32 err = dec_check_header<false, PR>(A, p, ~0ull);
       if (err) latch(A.st, err);
       u64* pi = A.info + (u64)p * 8;
       const u64 nt = err ? 0 : (pi[DI_NS] + pi[DI_NN] + kCodecTile - 1) / kCodecTile;
@@ -99,27 +100,41 @@ __global__ void dec_scan_kernel(DecArgs A) {
     dec_scan_pair<false>(A, A.p0 + (u32)k, A.unit_off[k], A.unit_off[k + 1] - A.unit_off[k]);
 }
 
+template <bool PR>
 __global__ void __launch_bounds__(kCodecTile) dec_emit_kernel(DecArgs A) {
   __shared__ U64x2 sm[33];
   __shared__ __align__(16) uint8_t stage[kCodecTile * kRecBytes + 48];
+  __shared__ float sW[PR ? kMlpParams : 1];
+  if (PR && A.pr.params) load_mlp(sW, A.pr.params);
   const u64 units = A.units_total[0];
   for (u64 U = blockIdx.x; U < units; U += gridDim.x) {
     u32 p;
     u64 local;
     locate(A, U, &p, &local);
-    dec_emit_unit<kCodecTile, false>(A, p, local, U, sm, stage);
+    dec_emit_unit<kCodecTile, false, PR>(A, p, local, U, sm, stage, sW);
+  }
+}
+
+// Every record of the receiver's reference: count it in its cell (predictor).
+__global__ void dec_cells_kernel(DecArgs A) {
+  const u64 g0 = A.ref_off[A.p0], g1 = A.ref_off[A.p1];
+  for (u64 g = g0 + (u64)blockIdx.x * blockDim.x + threadIdx.x; g < g1;
+       g += (u64)gridDim.x * blockDim.x) {
+    const u32 p = upper_pair(A.ref_off, A.p0, A.p1, g);
+    const u64 r = A.ref_off[p + 1] - A.ref_off[p];
+    const Rec R = load_rec(A.ref + (g + p + 1) * kRecBytes);
+    cell_insert(A.pr.cseg, seg_base(A.ref_off[p], p), seg_size(r), cell_key(R, A.pr));
   }
 }
 
 }  // namespace
 
 #ifndef TERA_DECODE_KERNELS_ONLY
-extern "C" tera_status tera_delta_decode(tera_ctx* ctx, const uint8_t* wire,
-                                         const uint64_t* wire_off, const uint8_t* ref_prev,
-                                         const uint64_t* ref_off_prev, uint32_t pair_begin,
-                                         uint32_t pair_end, uint8_t* recv,
-                                         uint64_t recv_capacity_units, uint64_t* recv_off,
-                                         void* stream) {
+static tera_status decode_impl(tera_ctx* ctx, const uint8_t* wire, const uint64_t* wire_off,
+                               const uint8_t* ref_prev, const uint64_t* ref_off_prev,
+                               uint32_t pair_begin, uint32_t pair_end, uint8_t* recv,
+                               uint64_t recv_capacity_units, uint64_t* recv_off,
+                               const tera_predictor* pred, void* stream) {
   if (!ctx || !wire || !wire_off || !recv || !recv_off) return TERA_EINVAL;
   if ((ref_prev == nullptr) != (ref_off_prev == nullptr)) return TERA_EINVAL;
   if (pair_begin > pair_end || pair_end > ctx->n_pairs) return TERA_EINVAL;
@@ -149,9 +164,26 @@ extern "C" tera_status tera_delta_decode(tera_ctx* ctx, const uint8_t* wire,
   A.p1 = pair_end;
   A.class_id = ctx->class_id;
   A.st = ctx->d_status;
+  const bool PR = pred != nullptr;
+  if (PR) {
+    if ((st = ensure_pred(ctx)) != TERA_OK) return st;
+    if (pred->params && ((uintptr_t)pred->params & 3u)) return TERA_EINVAL;
+    if (((uintptr_t)pred->hist_prev | (uintptr_t)pred->hist_next) & 15u) return TERA_EINVAL;
+    if (pred->hist_prev && !ref_prev) return TERA_EINVAL;
+    fill_pred(ctx, &A.pr, pred, ctx->cseg_dec);
+    A.pr.hist = ref_prev ? pred->hist_prev : nullptr;
+    if (A.pr.hist) {
+      const u64 cwords = 2 * (2 * ctx->cap_records + 2 * P);
+      cudaMemsetAsync(ctx->cseg_dec, 0, sizeof(u64) * cwords, s);
+    }
+  }
   prof_begin(ctx, s);
-  dec_setup_kernel<<<1, 1024, 0, s>>>(A, P, recv_capacity_units, ctx->d_units_total,
-                                      ctx->cap_units);
+  if (PR)
+    dec_setup_kernel<true><<<1, 1024, 0, s>>>(A, P, recv_capacity_units, ctx->d_units_total,
+                                              ctx->cap_units);
+  else
+    dec_setup_kernel<false><<<1, 1024, 0, s>>>(A, P, recv_capacity_units, ctx->d_units_total,
+                                               ctx->cap_units);
   if ((st = check_launch(ctx, "dec_setup_kernel", s)) != TERA_OK) return st;
   if (pair_begin == pair_end) return TERA_OK;
   if ((st = launch_unit_map(ctx, pair_begin, pair_end - pair_begin, s)) != TERA_OK) return st;
@@ -165,8 +197,35 @@ extern "C" tera_status tera_delta_decode(tera_ctx* ctx, const uint8_t* wire,
   prof_begin(ctx, s);
   dec_scan_kernel<<<(unsigned)((npr + 7) / 8), 256, 0, s>>>(A);
   if ((st = check_launch(ctx, "dec_scan_kernel", s)) != TERA_OK) return st;
+  if (PR && A.pr.hist) {
+    prof_begin(ctx, s);
+    dec_cells_kernel<<<g, 256, 0, s>>>(A);
+    if ((st = check_launch(ctx, "dec_cells_kernel", s)) != TERA_OK) return st;
+  }
   prof_begin(ctx, s);
-  dec_emit_kernel<<<g, kCodecTile, 0, s>>>(A);
+  if (PR) dec_emit_kernel<true><<<g, kCodecTile, 0, s>>>(A);
+  else dec_emit_kernel<false><<<g, kCodecTile, 0, s>>>(A);
   return check_launch(ctx, "dec_emit_kernel", s);
+}
+
+extern "C" tera_status tera_delta_decode(tera_ctx* ctx, const uint8_t* wire,
+                                         const uint64_t* wire_off, const uint8_t* ref_prev,
+                                         const uint64_t* ref_off_prev, uint32_t pair_begin,
+                                         uint32_t pair_end, uint8_t* recv,
+                                         uint64_t recv_capacity_units, uint64_t* recv_off,
+                                         void* stream) {
+  return decode_impl(ctx, wire, wire_off, ref_prev, ref_off_prev, pair_begin, pair_end, recv,
+                     recv_capacity_units, recv_off, nullptr, stream);
+}
+
+extern "C" tera_status tera_delta_decode_pred(tera_ctx* ctx, const uint8_t* wire,
+                                              const uint64_t* wire_off, const uint8_t* ref_prev,
+                                              const uint64_t* ref_off_prev, uint32_t pair_begin,
+                                              uint32_t pair_end, uint8_t* recv,
+                                              uint64_t recv_capacity_units, uint64_t* recv_off,
+                                              const tera_predictor* pred, void* stream) {
+  if (!pred) return TERA_EINVAL;
+  return decode_impl(ctx, wire, wire_off, ref_prev, ref_off_prev, pair_begin, pair_end, recv,
+                     recv_capacity_units, recv_off, pred, stream);
 }
 #endif  // TERA_DECODE_KERNELS_ONLY

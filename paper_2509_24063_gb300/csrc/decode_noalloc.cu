@@ -122,14 +122,14 @@ extern "C" tera_status tera_delta_decode_noalloc(const uint8_t* wire, const uint
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
   if (sms <= 0) sms = 148;
-  dec_setup_kernel<<<1, 1024, 0, s>>>(A, n_pairs, recv_capacity_units, units_total,
-                                      kStaticMaxUnits);
+  dec_setup_kernel<false><<<1, 1024, 0, s>>>(A, n_pairs, recv_capacity_units, units_total,
+                                             kStaticMaxUnits);
   static_unit_map_kernel<<<(unsigned)((n_pairs + 7) / 8), 256, 0, s>>>(
       A.unit_off, n_pairs, reinterpret_cast<u32*>(base + kOffUnitPair), units_total);
   const unsigned g = (unsigned)sms * 8u;
   dec_sum_kernel<<<g, kCodecTile, 0, s>>>(A);
   dec_scan_kernel<<<(unsigned)((n_pairs + 7) / 8), 256, 0, s>>>(A);
-  dec_emit_kernel<<<g, kCodecTile, 0, s>>>(A);
+  dec_emit_kernel<false><<<g, kCodecTile, 0, s>>>(A);
   if (cudaGetLastError() != cudaSuccess) return TERA_ECUDA;
   DevStatus h;
   if (cudaMemcpyAsync(&h, status, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess)

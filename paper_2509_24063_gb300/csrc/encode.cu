@@ -109,8 +109,24 @@ __global__ void __launch_bounds__(kCodecTile) enc_build_kernel(EncArgs A) {
   }
 }
 
+// Slot units: count every reference record in its cell (predictor only).
+__global__ void __launch_bounds__(kCodecTile) enc_cells_kernel(EncArgs A) {
+  const u64 units = *A.units_total;
+  for (u64 U = blockIdx.x; U < units; U += gridDim.x) {
+    u32 p;
+    u64 local;
+    locate(A, U, &p, &local);
+    const u64* pi = A.info + (u64)p * 8;
+    if (local >= pi[PI_NST]) continue;  // message unit
+    cells_unit(A.pr, A.ref, A.ref_off, p, local, pi[PI_R], kCodecTile);
+  }
+}
+
+template <bool PR>
 __global__ void __launch_bounds__(kCodecTile) enc_match_kernel(EncArgs A) {
   __shared__ U64x2 sm[33];
+  __shared__ float sW[PR ? kMlpParams : 1];
+  if (PR && A.pr.params) load_mlp(sW, A.pr.params);
   const u64 units = *A.units_total;
   const u32 epoch = *A.epoch;
   for (u64 U = blockIdx.x; U < units; U += gridDim.x) {
@@ -118,7 +134,7 @@ __global__ void __launch_bounds__(kCodecTile) enc_match_kernel(EncArgs A) {
     u64 local;
     locate(A, U, &p, &local);
     if (local >= A.info[(u64)p * 8 + PI_NST]) continue;  // message unit (block-uniform)
-    enc_match_unit<kCodecTile, false>(A, p, local, U, epoch, sm);
+    enc_match_unit<kCodecTile, false, PR>(A, p, local, U, epoch, sm, sW);
   }
 }
 
@@ -136,14 +152,16 @@ __global__ void __launch_bounds__(kCodecTile) enc_new_kernel(EncArgs A) {
 }
 
 // One warp per pair of the range.
+template <bool PR>
 __global__ void enc_scan_kernel(EncArgs A) {
   const u64 warp = ((u64)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const u64 nwarps = ((u64)gridDim.x * blockDim.x) >> 5;
   if (A.units_total[1]) return;  // capacity exceeded: write nothing
   for (u64 k = warp; k < (u64)(A.p1 - A.p0); k += nwarps)
-    enc_scan_pair<false>(A, A.p0 + (u32)k, A.unit_off[k], A.unit_off[k + 1] - A.unit_off[k]);
+    enc_scan_pair<false, PR>(A, A.p0 + (u32)k, A.unit_off[k], A.unit_off[k + 1] - A.unit_off[k]);
 }
 
+template <bool PR>
 __global__ void __launch_bounds__(kCodecTile) enc_emit_kernel(EncArgs A) {
   __shared__ U64x2 sm[33];
   __shared__ __align__(16) uint8_t stage[kCodecTile * kRecBytes + 32];
@@ -153,18 +171,18 @@ __global__ void __launch_bounds__(kCodecTile) enc_emit_kernel(EncArgs A) {
     u32 p;
     u64 local;
     locate(A, U, &p, &local);
-    enc_emit_unit<kCodecTile, false>(A, p, local, U, epoch, sm, stage);
+    enc_emit_unit<kCodecTile, false, PR>(A, p, local, U, epoch, sm, stage);
   }
 }
 
 }  // namespace
 
-extern "C" tera_status tera_delta_encode(tera_ctx* ctx, const uint8_t* rec_arena,
-                                         const uint64_t* pair_off, const uint8_t* ref_prev,
-                                         const uint64_t* ref_off_prev, uint32_t pair_begin,
-                                         uint32_t pair_end, uint8_t* ref_next, uint8_t* wire,
-                                         uint64_t wire_capacity, uint64_t* wire_off,
-                                         uint64_t* wire_len, int mode, void* stream) {
+static tera_status encode_impl(tera_ctx* ctx, const uint8_t* rec_arena, const uint64_t* pair_off,
+                               const uint8_t* ref_prev, const uint64_t* ref_off_prev,
+                               uint32_t pair_begin, uint32_t pair_end, uint8_t* ref_next,
+                               uint8_t* wire, uint64_t wire_capacity, uint64_t* wire_off,
+                               uint64_t* wire_len, int mode, const tera_predictor* pred,
+                               void* stream) {
   if (!ctx || !rec_arena || !pair_off || !ref_next || !wire || !wire_off || !wire_len)
     return TERA_EINVAL;
   if ((ref_prev == nullptr) != (ref_off_prev == nullptr)) return TERA_EINVAL;
@@ -206,6 +224,21 @@ extern "C" tera_status tera_delta_encode(tera_ctx* ctx, const uint8_t* rec_arena
   A.class_id = ctx->class_id;
   A.st = ctx->d_status;
   A.stats = ctx->d_stats;
+  const bool PR = pred != nullptr;
+  if (PR) {
+    if ((st = ensure_pred(ctx)) != TERA_OK) return st;
+    if (pred->params && ((uintptr_t)pred->params & 3u)) return TERA_EINVAL;
+    if (((uintptr_t)pred->hist_prev | (uintptr_t)pred->hist_next) & 15u) return TERA_EINVAL;
+    if (pred->hist_prev && !ref_prev) return TERA_EINVAL;
+    fill_pred(ctx, &A.pr, pred, ctx->cseg_enc);
+    A.pr.hist = ref_prev ? pred->hist_prev : nullptr;
+    A.pr.samples = pred->samples;
+    A.pr.allow_residual = pred->allow_residual;
+    if (A.pr.hist) {
+      const u64 cwords = 2 * (2 * ctx->cap_records + 2 * P);
+      cudaMemsetAsync(ctx->cseg_enc, 0, sizeof(u64) * cwords, s);
+    }
+  }
   prof_begin(ctx, s);
   enc_setup_kernel<<<1, 1024, 0, s>>>(A.pair_off, A.ref_off, P, pair_begin, pair_end, mode,
                                       ctx->d_reset, reinterpret_cast<u64*>(wire_off),
@@ -221,17 +254,47 @@ extern "C" tera_status tera_delta_encode(tera_ctx* ctx, const uint8_t* rec_arena
   prof_begin(ctx, s);
   enc_build_kernel<<<g, kCodecTile, 0, s>>>(A);
   if ((st = check_launch(ctx, "enc_build_kernel", s)) != TERA_OK) return st;
+  if (PR && A.pr.hist) {
+    prof_begin(ctx, s);
+    enc_cells_kernel<<<g, kCodecTile, 0, s>>>(A);
+    if ((st = check_launch(ctx, "enc_cells_kernel", s)) != TERA_OK) return st;
+  }
   prof_begin(ctx, s);
-  enc_match_kernel<<<g, kCodecTile, 0, s>>>(A);
+  if (PR) enc_match_kernel<true><<<g, kCodecTile, 0, s>>>(A);
+  else enc_match_kernel<false><<<g, kCodecTile, 0, s>>>(A);
   if ((st = check_launch(ctx, "enc_match_kernel", s)) != TERA_OK) return st;
   prof_begin(ctx, s);
   enc_new_kernel<<<g, kCodecTile, 0, s>>>(A);
   if ((st = check_launch(ctx, "enc_new_kernel", s)) != TERA_OK) return st;
   const u64 npr = pair_end - pair_begin;
   prof_begin(ctx, s);
-  enc_scan_kernel<<<(unsigned)((npr + 7) / 8), 256, 0, s>>>(A);
+  if (PR) enc_scan_kernel<true><<<(unsigned)((npr + 7) / 8), 256, 0, s>>>(A);
+  else enc_scan_kernel<false><<<(unsigned)((npr + 7) / 8), 256, 0, s>>>(A);
   if ((st = check_launch(ctx, "enc_scan_kernel", s)) != TERA_OK) return st;
   prof_begin(ctx, s);
-  enc_emit_kernel<<<g, kCodecTile, 0, s>>>(A);
+  if (PR) enc_emit_kernel<true><<<g, kCodecTile, 0, s>>>(A);
+  else enc_emit_kernel<false><<<g, kCodecTile, 0, s>>>(A);
   return check_launch(ctx, "enc_emit_kernel", s);
+}
+
+extern "C" tera_status tera_delta_encode(tera_ctx* ctx, const uint8_t* rec_arena,
+                                         const uint64_t* pair_off, const uint8_t* ref_prev,
+                                         const uint64_t* ref_off_prev, uint32_t pair_begin,
+                                         uint32_t pair_end, uint8_t* ref_next, uint8_t* wire,
+                                         uint64_t wire_capacity, uint64_t* wire_off,
+                                         uint64_t* wire_len, int mode, void* stream) {
+  return encode_impl(ctx, rec_arena, pair_off, ref_prev, ref_off_prev, pair_begin, pair_end,
+                     ref_next, wire, wire_capacity, wire_off, wire_len, mode, nullptr, stream);
+}
+
+extern "C" tera_status tera_delta_encode_pred(tera_ctx* ctx, const uint8_t* rec_arena,
+                                              const uint64_t* pair_off, const uint8_t* ref_prev,
+                                              const uint64_t* ref_off_prev, uint32_t pair_begin,
+                                              uint32_t pair_end, uint8_t* ref_next,
+                                              uint8_t* wire, uint64_t wire_capacity,
+                                              uint64_t* wire_off, uint64_t* wire_len, int mode,
+                                              const tera_predictor* pred, void* stream) {
+  if (!pred) return TERA_EINVAL;
+  return encode_impl(ctx, rec_arena, pair_off, ref_prev, ref_off_prev, pair_begin, pair_end,
+                     ref_next, wire, wire_capacity, wire_off, wire_len, mode, pred, stream);
 }

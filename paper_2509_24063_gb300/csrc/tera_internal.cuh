@@ -18,6 +18,7 @@ constexpr u32 kRecBytes = 64u;
 constexpr u32 kHdrBytes = 64u;
 constexpr int kMaxAxis = 256;
 constexpr u32 kNoMatch = 0xFFFFFFFFu;
+constexpr int kBatchPhases = 11;  // phases of the batched codec's work list
 
 // Agents per classification tile and records per codec tile.
 constexpr int kClassifyThreads = 256;
@@ -282,6 +283,17 @@ struct tera_ctx {
   uint64_t b_items_cap;
   uint64_t b_windows_cap;
   uint64_t b_units_cap;
+
+  // learned predictor (cell counts of both sides, per-slot predictions)
+  uint64_t ncell[3];
+  uint64_t pred_cap;
+  tera::u64* cseg_enc;
+  tera::u64* cseg_dec;
+  tera::u64* pscr;
+  tera::u64* unit_res;
+  uint64_t unit_res_cap;
+  float* mlp_scratch;       // training: compacted samples + gradient partials
+  uint64_t mlp_scratch_cap;
   tera::u64* b_items;
   uint32_t* b_done;
   uint32_t* b_need;
@@ -307,6 +319,8 @@ int grid_for(tera_ctx* ctx, int blocks_per_sm);
 // unit_pair[u] = p0 + k for every unit u of range pair k (skipped when
 // units_total[1] flags an aborted call).
 tera_status launch_unit_map(tera_ctx* ctx, u32 p0, u64 npr, cudaStream_t s);
+// Scratch of the learned predictor for the current record capacity.
+tera_status ensure_pred(tera_ctx* ctx);
 // Scratch of the batched codec for tiles of T entries and windows of W pairs.
 tera_status ensure_batched(tera_ctx* ctx, u32 T, u32 W);
 }  // namespace tera

@@ -23,7 +23,8 @@ PATHS = ("per_subdomain", "all_pairs", "batched")
 
 class AuraExchange:
     def __init__(self, ctx: Context, max_agents: int, max_records: int, mode: int = MODE_XOR,
-                 per_subdomain: bool = False, path: str | None = None, tune=None):
+                 per_subdomain: bool = False, path: str | None = None, tune=None,
+                 predictor: bool = False, params=None, allow_residual: bool = True):
         self.ctx = ctx
         self.mode = mode
         self.path = path or ("per_subdomain" if per_subdomain else "all_pairs")
@@ -50,6 +51,16 @@ class AuraExchange:
         self.wire_off = torch.zeros(P + 1, **i64)
         self.wire_len = torch.zeros(P, **i64)
         self.t = 0
+        # learned predictor: per-slot histories on both sides, the network's
+        # weights, and (optionally) a buffer receiving training samples
+        self.predictor = predictor or params is not None
+        self.params = params
+        self.allow_residual = allow_residual
+        self.samples = None
+        if self.predictor:
+            hb = max(max_records, 1) * 48
+            self.hist = [torch.zeros(hb, **u8), torch.zeros(hb, **u8)]
+            self.rhist = [torch.zeros(hb, **u8), torch.zeros(hb, **u8)]
 
     def reset(self):
         """Forget both references: the next iteration is sent without a reference."""
@@ -75,6 +86,26 @@ class AuraExchange:
         recv_off_prev = None if first else self.recv_off[prv]
         for (a, b) in self.ranges():
             ctx.pack(state, part, self.rec, a, b, stream)
+        if self.predictor:
+            enc = dict(params=self.params, hist_prev=None if first else self.hist[prv],
+                       hist_next=self.hist[cur], samples=self.samples,
+                       allow_residual=self.allow_residual)
+            dec = dict(params=self.params, hist_prev=None if first else self.rhist[prv],
+                       hist_next=self.rhist[cur])
+            if self.path == "batched":
+                ctx.codec_batched_pred(self.rec, pair_off, ref_prev, ref_off_prev, self.ref[cur],
+                                       self.wire, self.wire_off, self.wire_len, recv_prev,
+                                       recv_off_prev, self.recv[cur], self.recv_off[cur], enc,
+                                       dec, self.mode, self.tune, stream)
+                return
+            for (a, b) in self.ranges():
+                ctx.delta_encode_pred(self.rec, pair_off, ref_prev, ref_off_prev, self.ref[cur],
+                                      self.wire, self.wire_off, self.wire_len, enc, self.mode, a,
+                                      b, stream)
+            for (a, b) in self.ranges():
+                ctx.delta_decode_pred(self.wire, self.wire_off, recv_prev, recv_off_prev,
+                                      self.recv[cur], self.recv_off[cur], dec, a, b, stream)
+            return
         if self.path == "batched":
             ctx.codec_batched(self.rec, pair_off, ref_prev, ref_off_prev, self.ref[cur], self.wire,
                               self.wire_off, self.wire_len, recv_prev, recv_off_prev,
@@ -114,6 +145,12 @@ class AuraExchange:
 
     def sender_ref(self):
         return self.ref[self.last], self.pair_off[self.last]
+
+    def sender_hist(self):
+        return self.hist[self.last]
+
+    def receiver_hist(self):
+        return self.rhist[self.last]
 
     def receiver_ref(self):
         return self.recv[self.last], self.recv_off[self.last]
