@@ -113,6 +113,20 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
+def job_totals(elapsed_ms: float, agents: int, world: int, device) -> tuple:
+    """Whole-job numbers of a replicated run: the slowest rank's time and the
+    agents processed by all ranks."""
+    if world <= 1:
+        return elapsed_ms, agents
+    import torch
+    import torch.distributed as dist
+    tt = torch.tensor([elapsed_ms], device=device, dtype=torch.float64)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    aa = torch.tensor([agents], device=device, dtype=torch.float64)
+    dist.all_reduce(aa)
+    return float(tt.item()), int(aa.item())
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -196,11 +210,18 @@ def main():
     ap.add_argument("--agents", type=int, default=0,
                     help="override the workload's agent count (profiling on a smaller case)")
     ap.add_argument("--profile-table", action="store_true", help="print per-kernel table to stderr")
+    ap.add_argument("--predictor", action="store_true",
+                    help="learned predictor: train on the workload's generated iterations, then "
+                         "time and compare bytes/agent against plain XOR on fresh iterations")
+    ap.add_argument("--train-iters", type=int, default=200)
+    ap.add_argument("--eval-iters", type=int, default=20)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "tera":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
         return run_reference(args)
+    if args.predictor:
+        return run_predictor(args)
 
     import numpy as np
     import torch
@@ -275,15 +296,7 @@ def main():
     stats = ctx.stats(reset=True)
     ctx.status()
     agents = sum(int(states[t]["x"].shape[0]) for t in range(args.warmup, total_steps))
-    t_max = elapsed_ms
-    agents_all = agents
-    if world > 1:
-        tt = torch.tensor([elapsed_ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
-        aa = torch.tensor([agents], device="cuda", dtype=torch.float64)
-        dist.all_reduce(aa)
-        agents_all = int(aa.item())
+    t_max, agents_all = job_totals(elapsed_ms, agents, world, "cuda")
     value = agents_all / (t_max / 1e3)
 
     # encode+decode algorithmic bytes over the timed steps (pack .. decode)
@@ -362,6 +375,89 @@ def main():
     ctx.close()
     if world > 1:
         dist.destroy_process_group()
+    return 0
+
+
+def run_predictor(args):
+    """Train the predictor on the workload's generated iterations (seed A),
+    then run fresh iterations (seed B) with and without it: agents/s of the
+    predictor path (timed, states resident) and wire bytes per record of both."""
+    import torch
+    import paper_2509_24063_gb300 as tera
+    from paper_2509_24063_gb300 import predictor
+    from synth import WORKLOADS, Generator, scaled
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    wl = WORKLOADS["drift_16m" if args.workload == "uniform_100m" else args.workload]
+    if args.agents:
+        wl = scaled(wl, args.agents)
+    t0 = time.time()
+    gen = Generator(wl, device="cuda")
+    nmax = int(wl.n0 * 1.05) + 4096
+    max_records = 2 * nmax
+    ctx = tera.Context(wl.lo, wl.hi, wl.grid, wl.w, device=local)
+    ex = tera.AuraExchange(ctx, nmax, max_records, path="all_pairs", predictor=True)
+    every = max(1, args.train_iters // 20)
+    picks = set(range(2, args.train_iters, every))
+    per = max_records * 12
+    samples = torch.zeros(len(picks) * per, dtype=torch.float32, device="cuda")
+    k = 0
+    for t, st in enumerate(gen.series(args.train_iters)):
+        if t in picks:
+            ex.samples = samples[k * per:(k + 1) * per]
+            k += 1
+        else:
+            ex.samples = None
+        ex.step({f: st[f] for f in ("id", "x", "y", "z", "diameter", "volume", "adherence",
+                                     "density")})
+    ctx.status()
+    del ex
+    params = predictor.init_params(5)
+    t1 = time.time()
+    nv = predictor.train(ctx, samples, params)
+    torch.cuda.synchronize()
+    t2 = time.time()
+    del samples
+    evals = [{f: st[f] for f in ("id", "x", "y", "z", "diameter", "volume", "adherence",
+                                   "density")}
+             for st in Generator(wl, device="cuda", seed=wl.seed + 1).series(args.eval_iters)]
+    skip = min(3, len(evals) - 1)
+    bx, rx = predictor.wire_bytes(ctx, evals, nmax, max_records, skip=skip)
+    ex = tera.AuraExchange(ctx, nmax, max_records, path="batched", params=params)
+    for t in range(skip):
+        ex.step(evals[t])
+    ctx.status()
+    ctx.stats(reset=True)
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(None) as clk:
+        e0.record(stream)
+        for t in range(skip, len(evals)):
+            ex.step(evals[t])
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    st = ctx.stats(reset=True)
+    ctx.status()
+    steps = len(evals) - skip
+    agents = sum(int(evals[t]["x"].shape[0]) for t in range(skip, len(evals)))
+    line = {
+        "metric": METRIC, "value": agents / (ms / 1e3), "unit": "agents/s", "n_gpus": 1,
+        "steps": steps, "warmup": skip, "ms_per_step": ms / steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64+f32", "data": "synthetic",
+        "config": {"workload": wl.name + (f"@{args.agents}" if args.agents else ""),
+                   "agents": int(evals[-1]["x"].shape[0]), "train_iterations": args.train_iters,
+                   "eval_iterations": args.eval_iters, "path": "batched+predictor"},
+        "bytes_per_agent_xor": bx / max(1, rx),
+        "bytes_per_agent_residual": st["wire_bytes"] / max(1, st["records"]),
+        "residual_vs_xor": (st["wire_bytes"] / max(1, st["records"])) / (bx / max(1, rx)),
+        "training": {"samples": nv, "steps": 4000, "batch": 8192, "lr": 0.02, "clip": 1.0,
+                     "seconds": t2 - t1, "collect_seconds": t1 - t0},
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line))
+    ctx.close()
     return 0
 
 
