@@ -43,8 +43,10 @@ def kernel_bytes(name, t):
         "enc_emit_kernel": 4 * R + 128 * (R - t["holes"]) + 4 * E + 64 * A + 4 * A + Y + 64 * M,
         "dec_sum_kernel": 4 * (R + A),
         "dec_emit_kernel": 4 * (R + A) + Y + 64 * (R - t["holes"]) + 64 * M,
-        # the persistent kernel runs every codec phase: encode + decode step model
-        "codec_persistent_kernel": 216 * E + Y + 132 * E + Y,
+        # the persistent kernel runs encode + decode: compulsory traffic only
+        # (message, reference, new reference and wire on the sender; wire,
+        # reference and receive buffers on the receiver)
+        "codec_persistent_kernel": 64 * (3 * E + 2 * R) + 2 * t["wire_bytes"],
     }
     return table.get(name)
 
@@ -203,6 +205,8 @@ def main():
     ap.add_argument("--path", default="batched", choices=["batched", "all_pairs", "per_subdomain"])
     ap.add_argument("--no-graph", action="store_true", help="batched path without CUDA graphs")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--tune", default="",
+                    help="fixed batched schedule block,ctas_per_sm[,table_records] (skips the tuner)")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-sample", type=int, default=2_000_000)
     ap.add_argument("--ref-agents", type=int, default=1_000_000)
@@ -250,13 +254,15 @@ def main():
     nmax = max(int(s["x"].shape[0]) for s in states)
     max_records = int(nmax * 0.35) + 4096 if wl.grid[0] >= 8 else 4 * nmax + 4096
     ctx = tera.Context(wl.lo, wl.hi, wl.grid, wl.w, device=local)
-    ex = tera.AuraExchange(ctx, max_agents=nmax, max_records=max_records, path=args.path)
+    fixed = tuple(int(v) for v in args.tune.split(",")) if args.tune else None
+    ex = tera.AuraExchange(ctx, max_agents=nmax, max_records=max_records, path=args.path,
+                           tune=fixed)
     stream = torch.cuda.current_stream()
     use_graph = args.path == "batched" and not args.no_graph
-    tune_info = None
+    tune_info = {"tune": list(fixed), "candidates": 0} if fixed else None
 
     for t in range(args.warmup):
-        if t == 1 and args.path == "batched" and not args.no_autotune:
+        if t == 1 and args.path == "batched" and not args.no_autotune and fixed is None:
             from paper_2509_24063_gb300 import autotune
             tune, table = autotune.tune_batched(ex, states[t])
             tune_info = {"tune": list(tune), "candidates": len(table)}
@@ -305,7 +311,7 @@ def main():
     H = stats["holes"]
     R, E, A, Y = stats["ref_slots"], stats["records"], stats["new_records"], \
         stats["payload_bytes"]
-    codec_bytes = (216 * (E) + Y) + (132 * E + Y) - 0  # per-record model (matched/new alike)
+    codec_bytes = kernel_bytes("pack_kernel", stats) + kernel_bytes("codec_persistent_kernel", stats)
     codec_ms = sum(prof.get(k, (0, 0.0))[1] for k in prof
                    if k.startswith(("pack", "enc_", "dec_", "bat_", "codec_", "unit_map")))
     peaks, peak_kind = measured_peaks()

@@ -273,19 +273,23 @@ tera_status tera_mlp_train(tera_ctx* ctx, const float* samples, uint64_t n, floa
                            void* stream);
 
 /* Schedule of the batched codec (picked by the autotuner; outputs do not
- * depend on it): threads per block = entries per tile (128, 256 or 512),
- * blocks per SM of the persistent launch (1..16), pairs per window of the
- * work list (1..1024), and tiles per work item (1..64). */
+ * depend on it): threads per block = entries per tile (128, 256, 512 or
+ * 1024), blocks per SM of the persistent launch (1..16, block x blocks <=
+ * 2048), and the largest message (records) matched in a block's shared-memory
+ * hash table: 0 = as large as the shared memory left to the block allows, else
+ * a power of two >= 32 (smaller when it does not fit); larger messages use the
+ * pair's hash segment in global memory.  reserved must be 0. */
 typedef struct {
   int block;
   int ctas_per_sm;
-  int window;
-  int tiles_per_item;
+  int table_records;
+  int reserved;
 } tera_tune;
 
 /* Steps a3-a5 for EVERY pair of one iteration in one persistent launch
  * (batching of uneven subdomain buffers; not in the paper, which batches
- * only large messages, Sec. 2.4 "Communication").  Produces exactly the bytes
+ * only large messages, Sec. 2.4 "Communication").  Each block carries whole
+ * pairs, one at a time, through encode and decode.  Produces exactly the bytes
  * of tera_delta_encode + tera_delta_decode over all pairs: wire_off, the wire
  * messages, wire_len, the new sender reference ref_next (laid out with
  * pair_off) and the receive buffers recv with recv_off.  The receive layout
@@ -294,9 +298,8 @@ typedef struct {
  * reference is ref_prev/ref_off_prev, the receiver's recv_prev/recv_off_prev
  * (NULL pairs = empty references).  Must follow tera_partition and tera_pack
  * (all pairs) of the same iteration on this context.  tune == NULL uses
- * {256, 4, 64, 4}.  Asynchronous, no host synchronization (graph-capturable once
- * scratch is reserved); device errors are latched in the status word, a wait
- * that exceeds its bound latches TERA_ETIMEOUT. */
+ * {512, 2, 0, 0}.  Asynchronous, no host synchronization (graph-capturable once
+ * scratch is reserved); device errors are latched in the status word. */
 tera_status tera_codec_batched(tera_ctx* ctx, const uint8_t* rec_arena, const uint64_t* pair_off,
                                const uint8_t* ref_prev, const uint64_t* ref_off_prev,
                                uint8_t* ref_next, uint8_t* wire, uint64_t wire_capacity,

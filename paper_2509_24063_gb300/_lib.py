@@ -48,8 +48,8 @@ class Stats(C.Structure):
 
 
 class Tune(C.Structure):
-    _fields_ = [("block", C.c_int), ("ctas_per_sm", C.c_int), ("window", C.c_int),
-                ("tiles_per_item", C.c_int)]
+    _fields_ = [("block", C.c_int), ("ctas_per_sm", C.c_int), ("table_records", C.c_int),
+                ("reserved", C.c_int)]
 
 
 class Predictor(C.Structure):

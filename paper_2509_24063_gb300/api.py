@@ -181,8 +181,8 @@ class Context:
         """Encode + decode of every pair in one persistent launch (tera_codec_batched)."""
         t = None
         if tune is not None:
-            t = _lib.Tune(int(tune[0]), int(tune[1]), int(tune[2]),
-                          int(tune[3]) if len(tune) > 3 else 4)
+            t = _lib.Tune(int(tune[0]), int(tune[1]), int(tune[2]) if len(tune) > 2 else 0,
+                          int(tune[3]) if len(tune) > 3 else 0)
         check(self.lib.tera_codec_batched(
             self.h, _ptr(rec_arena), _ptr(pair_off), _ptr(ref_prev), _ptr(ref_off_prev),
             _ptr(ref_next), _ptr(wire), wire.numel(), _ptr(wire_off), _ptr(wire_len),
@@ -227,8 +227,8 @@ class Context:
                            stream=None):
         t = None
         if tune is not None:
-            t = _lib.Tune(int(tune[0]), int(tune[1]), int(tune[2]),
-                          int(tune[3]) if len(tune) > 3 else 4)
+            t = _lib.Tune(int(tune[0]), int(tune[1]), int(tune[2]) if len(tune) > 2 else 0,
+                          int(tune[3]) if len(tune) > 3 else 0)
         pe, pd = self._pred(enc_pred), self._pred(dec_pred)
         check(self.lib.tera_codec_batched_pred(
             self.h, _ptr(rec_arena), _ptr(pair_off), _ptr(ref_prev), _ptr(ref_off_prev),

@@ -1,5 +1,6 @@
-"""Autotuner of the batched codec's schedule (tile/block size, resident blocks
-per SM, pairs per work-list window).
+"""Autotuner of the batched codec's schedule (tile/block size and resident
+blocks per SM; each block's shared-memory match table takes what its share of
+the SM's shared memory allows).
 
 The schedule never changes the bytes produced, only the time.  Candidates are
 timed on the real data of one iteration: after partition + pack, the batched
@@ -16,10 +17,9 @@ import os
 
 import torch
 
-CANDIDATES = [(b, c, w, k) for b in (128, 256, 512) for c in (1024 // b, 2048 // b)
-              for w in (32, 256, 1024) for k in (1, 4, 16)]
-# blocks per SM above what fits 2048 threads cannot be resident
-MAX_RESIDENT = {128: 16, 256: 8, 512: 4}
+# (threads per block, blocks per SM, table records (0: what fits), reserved)
+CANDIDATES = [(b, c, 0, 0) for b in (128, 256, 512, 1024) for c in (1, 2, 4, 8, 16)
+              if b * c <= 2048]
 
 
 def cache_path() -> str:
@@ -86,8 +86,6 @@ def tune_batched(ex, state: dict, reps: int = 2, candidates=None, use_cache: boo
             ex.recv_off[cur])
     results = []
     for cand in (candidates or CANDIDATES):
-        if cand[1] > MAX_RESIDENT.get(cand[0], 8):
-            continue
         ctx.codec_batched(*args, mode=ex.mode, tune=cand, stream=stream)  # warm
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)

@@ -1,147 +1,129 @@
 // Batched codec: steps a3-a5 (paper Sec. 2.3, steps B, C and D) for every
-// pair of one iteration in ONE persistent launch over a work list.
+// pair of one iteration in ONE persistent launch.
 //
-// The work list holds (phase, pair, tile) items.  Pairs are taken in windows
-// of W pairs; inside a window the items are ordered phase by phase, so a
-// window's pairs move through build -> match -> new -> scan -> emit ->
-// decode-setup -> decode-sum -> decode-scan -> decode-emit while their data
-// is still in L2.  Persistent blocks claim items in list order with one
-// atomic ticket; an item first waits (bounded, with __nanosleep) until the
-// items of the earlier phases of ITS pair are done.  Those items have lower
-// tickets, so they were claimed by blocks that are running or finished: the
-// waits always end, and a wait that exceeds its bound latches TERA_ETIMEOUT
-// and stops every block instead of hanging.
+// Each block takes whole pairs (an atomic ticket over the pair index; the
+// next ticket is claimed while the current pair runs) and carries a pair
+// through every step on its own, so no block ever waits for another:
 //
-// Tile size T (block size), blocks per SM and W come from the caller
-// (tera_tune, picked by the autotuner); the bytes produced do not depend on
-// them.  The receive layout is the pair layout of the iteration (every
-// header's record count is checked against it).
+//   match   index the message ids, look every reference slot's id up, mark
+//           the message records the slots take.  A pair with at most
+//           table_records records does this in a shared-memory hash table
+//           (u32 entries: (record + 1) << 8 | 8-bit fingerprint, ids compared
+//           against the message's id array); larger pairs (and the predictor
+//           path) use the pair's global hash segment.
+//   slots   difference, code, payload and new-reference record of every slot
+//           (tiles of T slots; payload positions from a running prefix kept
+//           on chip; the wire puts the slot payload after all r + n_new codes,
+//           and n_new = m - matched is known once the match is done)
+//   new     records no slot took, in message order; the last tile writes the
+//           header, the padding and the iteration totals
+//   decode  the receiver's side from the wire and its own reference: codes,
+//           payload and receive buffer, again with an on-chip running prefix
+//
+// Tile size T (block size) and blocks per SM come from the caller (tera_tune,
+// picked by the autotuner); the bytes produced do not depend on them.  The
+// receive layout is the pair layout of the iteration (every header's record
+// count is checked against it).
 #include "codec.cuh"
 
 using namespace tera;
 
 namespace {
 
-enum { PH_BUILD = 0, PH_CELLS, PH_MATCH, PH_NEW, PH_SCAN, PH_EMIT, PH_DSETUP, PH_DSUM, PH_DSCAN,
-       PH_DCELLS, PH_DEMIT, PH_COUNT };
-static_assert(PH_COUNT == kBatchPhases, "phase count");
-
-// phases an item of phase `ph` waits for (bit mask over phases of the same pair)
-__device__ __forceinline__ u32 deps(int ph) {
-  switch (ph) {
-    case PH_MATCH: return (1u << PH_BUILD) | (1u << PH_CELLS);
-    case PH_NEW: return (1u << PH_BUILD) | (1u << PH_MATCH);
-    case PH_SCAN: return (1u << PH_MATCH) | (1u << PH_NEW);
-    case PH_EMIT: return 1u << PH_SCAN;
-    case PH_DSETUP: return (1u << PH_SCAN) | (1u << PH_EMIT);
-    case PH_DSUM: return 1u << PH_DSETUP;
-    case PH_DSCAN: return (1u << PH_DSETUP) | (1u << PH_DSUM);
-    case PH_DEMIT: return (1u << PH_DSCAN) | (1u << PH_DCELLS);
-    default: return 0u;
-  }
-}
+enum { PT_MATCHED = 0, PT_XOR = 1, PT_RES = 2, PT_COUNT = 4 };
+// message entries per thread of a new-record tile (XOR mode: few are new)
+constexpr u32 kNewPerThread = 8;
+// hash phases take kIlp entries per thread (entry i*T + thread of the tile),
+// so several independent probes / atomics are in flight per thread
+constexpr u32 kIlp = 4;
 
 struct BatchArgs {
-  const u64* items;
-  const u64* n_items;
+  u64 n_pairs;
   u64* ticket;
-  u32* done;        // [P * PH_COUNT]
-  const u32* need;  // [P * PH_COUNT]
-  const u64* enc_uoff;
-  const u64* dec_uoff;
+  u64* ptot;  // [P * PT_COUNT] per-pair totals of the match step
   u32* abort;
 };
 
-constexpr u64 kSpinLimit = 1ull << 25;  // x ~100 ns sleeps: several seconds
+__device__ __forceinline__ u64 ceil_div(u64 a, u64 b) { return (a + b - 1) / b; }
 
-__device__ __forceinline__ u32 ld_acquire(const u32* p) {
-  u32 v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
+// Entries per thread of pair p's new-record tiles.
+__device__ __forceinline__ u32 new_per_thread(u64 mode) {
+  return mode == TERA_MODE_RAW ? 1u : kNewPerThread;
 }
 
-__device__ __forceinline__ void red_release_add(u32* p, u32 v) {
-  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" : : "l"(p), "r"(v) : "memory");
-}
+// Shared-memory matching state of the block's current pair.
+struct SmemTable {
+  u32* tbl;   // hash table, or nullptr: the pair uses its global hash segment
+  u32 mask;   // table entries - 1
+  u32* bits;  // bit k: message record k was taken by a slot
+};
 
-__device__ __forceinline__ u64 make_item(u32 ph, u32 p, u32 t) {
-  return ((u64)ph << 60) | ((u64)p << 32) | (u64)t;
+__device__ __forceinline__ u32 fp_of(u64 h) { return (u32)h & 0xFFu; }
+__device__ __forceinline__ u32 tbl_start(u64 h, u32 mask) { return (u32)(h >> 32) & mask; }
+
+// Block scan of two per-thread counts packed in one word (payload bytes in
+// the low half, records in the high half; a tile's totals fit in 32 bits).
+__device__ __forceinline__ U64x2 tile_scan(u32 bytes, u32 recs, U64x2* sm, U64x2* total) {
+  u64 tot;
+  const u64 ex = block_excl_scan<u64>((u64)bytes | ((u64)recs << 32), reinterpret_cast<u64*>(sm),
+                                      &tot);
+  *total = U64x2{tot & 0xFFFFFFFFull, tot >> 32};
+  return U64x2{ex & 0xFFFFFFFFull, ex >> 32};
 }
 
 // ---------------- setup: per-pair facts, layouts, capacity checks ----------------
 
+// One block; thread t owns a contiguous run of pairs (one pass of loads, one scan).
 __global__ void __launch_bounds__(1024)
-    bat_setup_kernel(EncArgs E, DecArgs D, BatchArgs B, u64 P, int mode, u32 T, u32 K,
-                     int enc_cells, int dec_cells,
+    bat_setup_kernel(EncArgs E, DecArgs D, BatchArgs B, u64 P, int mode,
                      u64* __restrict__ wire_off, u64 wire_cap, u64 rec_cap, u64 recv_cap,
-                     u64 units_cap, u32* __restrict__ need_out, u64* __restrict__ enc_uoff,
-                     u64* __restrict__ dec_uoff, u32* epoch) {
+                     u32* epoch) {
   __shared__ u64 sm[33];
   if (threadIdx.x == 0) {
     const u32 ep = *epoch + 1u;
     *epoch = ep == 0u ? 1u : ep;
   }
-  u64 cw = 0, ce = 0, cd = 0;
-  for (u64 b0 = 0; b0 < P; b0 += blockDim.x) {
-    const u64 p = b0 + threadIdx.x;
-    u64 vw = 0, ve = 0, vd = 0;
-    if (p < P) {
-      const u64 m = E.pair_off[p + 1] - E.pair_off[p];
-      const u64 r_full = E.ref_off ? E.ref_off[p + 1] - E.ref_off[p] : 0;
-      const bool raw = mode == TERA_MODE_RAW || E.reset[p];
-      const u64 r = (raw || E.ref_off == nullptr) ? 0 : r_full;
-      const u64 ts = (r + T - 1) / T, tm = (m + T - 1) / T, td = (r + m + T - 1) / T;
-      u64* pi = E.info + p * 8;
-      pi[PI_R] = r;
-      pi[PI_M] = m;
-      pi[PI_NST] = ts;
-      pi[PI_MODE] = raw ? TERA_MODE_RAW : TERA_MODE_XOR;
-      // items per phase: K tiles per item (one item for the per-pair phases)
-      u32* nd = need_out + p * PH_COUNT;
-      nd[PH_BUILD] = (u32)((tm + K - 1) / K);
-      nd[PH_CELLS] = enc_cells ? (u32)((ts + K - 1) / K) : 0u;
-      const u64 rr = D.ref_off ? D.ref_off[p + 1] - D.ref_off[p] : 0;
-      nd[PH_DCELLS] = dec_cells ? (u32)(((rr + T - 1) / T + K - 1) / K) : 0u;
-      nd[PH_MATCH] = (u32)((ts + K - 1) / K);
-      nd[PH_NEW] = (u32)((tm + K - 1) / K);
-      nd[PH_SCAN] = 1;
-      nd[PH_EMIT] = (u32)((ts + tm + K - 1) / K);
-      nd[PH_DSETUP] = 1;
-      nd[PH_DSUM] = (u32)((td + K - 1) / K);
-      nd[PH_DSCAN] = 1;
-      nd[PH_DEMIT] = (u32)((td + K - 1) / K);
-      vw = round16((u64)kHdrBytes + 4 * (r_full + m) + (u64)kRecBytes * m);
-      ve = ts + tm;
-      vd = td;
-      D.recv_off[p] = E.pair_off[p];  // receive buffers sized by the record counts
-    }
-    u64 tw, te, td;
-    const u64 xw = block_excl_scan<u64>(vw, sm, &tw);
-    const u64 xe = block_excl_scan<u64>(ve, sm, &te);
-    const u64 xd = block_excl_scan<u64>(vd, sm, &td);
-    if (p < P) {
-      wire_off[p] = cw + xw;
-      enc_uoff[p] = ce + xe;
-      dec_uoff[p] = cd + xd;
-    }
-    cw += tw;
-    ce += te;
-    cd += td;
+  const u64 per = (P + blockDim.x - 1) / blockDim.x;
+  const u64 q0 = (u64)threadIdx.x * per;
+  const u64 q1 = q0 + per < P ? q0 + per : P;
+  u64 sw = 0;
+  for (u64 p = q0; p < q1; ++p) {
+    const u64 m = E.pair_off[p + 1] - E.pair_off[p];
+    const u64 r_full = E.ref_off ? E.ref_off[p + 1] - E.ref_off[p] : 0;
+    const bool raw = mode == TERA_MODE_RAW || E.reset[p];
+    const u64 r = (raw || E.ref_off == nullptr) ? 0 : r_full;
+    u64* pi = E.info + p * 8;
+    pi[PI_R] = r;
+    pi[PI_M] = m;
+    pi[PI_MODE] = raw ? TERA_MODE_RAW : TERA_MODE_XOR;
+    const u64 slab = round16((u64)kHdrBytes + 4 * (r_full + m) + (u64)kRecBytes * m);
+    wire_off[p] = slab;
+    sw += slab;
+    D.recv_off[p] = E.pair_off[p];  // receive buffers sized by the record counts
+  }
+  u64 tw;
+  u64 run = block_excl_scan<u64>(sw, sm, &tw);
+  for (u64 p = q0; p < q1; ++p) {
+    const u64 slab = wire_off[p];
+    wire_off[p] = run;
+    run += slab;
   }
   if (threadIdx.x == 0) {
-    wire_off[P] = cw;
-    enc_uoff[P] = ce;
-    dec_uoff[P] = cd;
+    wire_off[P] = tw;
     D.recv_off[P] = E.pair_off[P];
     bool abort = false;
-    if (cw > wire_cap) {
+    if (tw > wire_cap) {
       latch(E.st, TERA_ECAPACITY);
-      need(E.st, cw);
+      need(E.st, tw);
       abort = true;
     }
-    if (E.ref_off && E.ref_off[P] > rec_cap) {
+    // record scratch is sized for rec_cap records per side
+    const u64 rmax = E.ref_off ? E.ref_off[P] : 0, dmax = D.ref_off ? D.ref_off[P] : 0;
+    const u64 big = E.pair_off[P] > rmax ? (E.pair_off[P] > dmax ? E.pair_off[P] : dmax)
+                                          : (rmax > dmax ? rmax : dmax);
+    if (big > rec_cap) {
       latch(E.st, TERA_ECAPACITY);
-      need(E.st, E.ref_off[P]);
+      need(E.st, big);
       abort = true;
     }
     if (E.pair_off[P] + P > recv_cap) {
@@ -149,176 +131,853 @@ __global__ void __launch_bounds__(1024)
       need(E.st, E.pair_off[P] + P);
       abort = true;
     }
-    if (ce > units_cap || cd > units_cap) {  // cannot happen: scratch is sized for it
-      latch(E.st, TERA_ECAPACITY);
-      abort = true;
-    }
     *B.abort = abort ? 1u : 0u;
     *B.ticket = 0;
   }
 }
 
-// items of a window: total per window (one block of W threads per window)
-__global__ void bat_window_count_kernel(const u32* __restrict__ need, u64 P, u32 W,
-                                        u32* __restrict__ win_total) {
-  __shared__ u64 sm[33];
-  const u64 p = (u64)blockIdx.x * W + threadIdx.x;
-  u64 c = 0;
-  if (threadIdx.x < W && p < P)
-    for (int ph = 0; ph < PH_COUNT; ++ph) c += need[p * PH_COUNT + ph];
-  u64 tot;
-  block_excl_scan<u64>(c, sm, &tot);
-  if (threadIdx.x == 0) win_total[blockIdx.x] = (u32)tot;
+// ---------------- match in shared memory ----------------
+
+// Index message records [0, m) of pair p.  A second record with an id already
+// present is an invalid message (TERA_EINVAL) and is not indexed.
+template <int T>
+__device__ __forceinline__ void smem_build(const EncArgs& A, u32 p, u64 m, const SmemTable& tb) {
+  const u64 g_lo = A.pair_off[p];
+  for (u32 i = threadIdx.x; i <= tb.mask; i += T) tb.tbl[i] = 0u;
+  for (u32 i = threadIdx.x; i < (u32)((m + 31) / 32); i += T) tb.bits[i] = 0u;
+  __syncthreads();
+  for (u64 k0 = 0; k0 < m; k0 += (u64)T * kIlp) {
+    u64 id[kIlp];
+#pragma unroll
+    for (u32 i = 0; i < kIlp; ++i) {
+      const u64 k = k0 + (u64)i * T + threadIdx.x;
+      id[i] = k < m ? A.msg_id[g_lo + k] : 0;
+    }
+#pragma unroll
+    for (u32 i = 0; i < kIlp; ++i) {
+      const u64 k = k0 + (u64)i * T + threadIdx.x;
+      if (k >= m) continue;
+      const u64 h = mix64(id[i]);
+      const u32 fp = fp_of(h), e = ((u32)(k + 1) << 8) | fp;
+      u32 at = tbl_start(h, tb.mask);
+      for (u32 probe = 0; probe <= tb.mask; ++probe) {
+        const u32 old = atomicCAS(&tb.tbl[at], 0u, e);
+        if (old == 0u) break;
+        if ((old & 0xFFu) == fp && A.msg_id[g_lo + (old >> 8) - 1] == id[i]) {
+          latch(A.st, TERA_EINVAL);  // ids must be unique within a message
+          break;
+        }
+        at = (at + 1) & tb.mask;
+      }
+    }
+  }
 }
 
-// items of a window, phase by phase, pair by pair, tile by tile
-__global__ void bat_window_fill_kernel(const u32* __restrict__ need, u64 P, u32 W,
-                                       const u64* __restrict__ win_base, u64 n_windows,
-                                       u64* __restrict__ items, u64* __restrict__ n_items,
-                                       const u32* __restrict__ abort) {
-  __shared__ u64 sm[33];
-  if (*abort) {  // capacities exceeded: no work list (and no write past its end)
-    if (blockIdx.x == 0 && threadIdx.x == 0) *n_items = 0;
-    return;
+// Message record (index in the pair) with this id, probing from `at`; kNoMatch if none.
+__device__ __forceinline__ u32 smem_find(const EncArgs& A, const SmemTable& tb, u64 g_lo, u64 id,
+                                         u32 fp, u32 at) {
+  for (u32 probe = 0; probe <= tb.mask; ++probe) {
+    const u32 e = tb.tbl[at];
+    if (e == 0u) return kNoMatch;
+    if ((e & 0xFFu) == fp && A.msg_id[g_lo + (e >> 8) - 1] == id) return (e >> 8) - 1;
+    at = (at + 1) & tb.mask;
   }
-  const u64 p = (u64)blockIdx.x * W + threadIdx.x;
-  const bool live = threadIdx.x < W && p < P;
-  u64 pos = win_base[blockIdx.x];
-  for (int ph = 0; ph < PH_COUNT; ++ph) {
-    const u64 c = live ? need[p * PH_COUNT + ph] : 0;
-    u64 tot;
-    const u64 ex = block_excl_scan<u64>(c, sm, &tot);
-    for (u64 t = 0; t < c; ++t) items[pos + ex + t] = make_item((u32)ph, (u32)p, (u32)t);
-    pos += tot;
+  return kNoMatch;
+}
+
+// Look every slot of pair p up; slot_src[slot] = global record index or
+// kNoMatch; bits mark the taken records.  Returns this thread's match count.
+template <int T>
+__device__ __forceinline__ u32 smem_match(const EncArgs& A, u32 p, u64 r, const SmemTable& tb) {
+  const u64 ro = A.ref_off[p], g_lo = A.pair_off[p];
+  u32 found = 0;
+  for (u64 j0 = 0; j0 < r; j0 += (u64)T * kIlp) {
+    u64 id[kIlp];
+#pragma unroll
+    for (u32 i = 0; i < kIlp; ++i) {
+      const u64 j = j0 + (u64)i * T + threadIdx.x;
+      id[i] = j < r ? *reinterpret_cast<const u64*>(A.ref + (ro + p + 1 + j) * kRecBytes) : 0;
+    }
+    // first fingerprint hit of every slot (shared memory only), then the
+    // id checks of all of them in flight together
+    u32 cand[kIlp], at[kIlp], fp[kIlp];
+#pragma unroll
+    for (u32 i = 0; i < kIlp; ++i) {
+      const u64 j = j0 + (u64)i * T + threadIdx.x;
+      cand[i] = kNoMatch;
+      const u64 h = mix64(id[i]);
+      fp[i] = fp_of(h);
+      at[i] = tbl_start(h, tb.mask);
+      if (j >= r) continue;
+      for (u32 probe = 0; probe <= tb.mask; ++probe) {
+        const u32 e = tb.tbl[at[i]];
+        if (e == 0u) break;
+        if ((e & 0xFFu) == fp[i]) {
+          cand[i] = (e >> 8) - 1;
+          break;
+        }
+        at[i] = (at[i] + 1) & tb.mask;
+      }
+    }
+    u64 cid[kIlp];
+#pragma unroll
+    for (u32 i = 0; i < kIlp; ++i) cid[i] = cand[i] != kNoMatch ? A.msg_id[g_lo + cand[i]] : 0;
+#pragma unroll
+    for (u32 i = 0; i < kIlp; ++i) {
+      const u64 j = j0 + (u64)i * T + threadIdx.x;
+      if (j >= r) continue;
+      u32 k = cand[i];
+      if (k != kNoMatch && cid[i] != id[i])  // fingerprint collision: keep probing
+        k = smem_find(A, tb, g_lo, id[i], fp[i], (at[i] + 1) & tb.mask);
+      if (k != kNoMatch) {
+        const u32 bit = 1u << (k & 31u);
+        if (atomicOr(&tb.bits[k >> 5], bit) & bit) {
+          latch(A.st, TERA_EINVAL);  // a second slot with the same id: that slot is a hole
+          k = kNoMatch;
+        }
+      }
+      found += k != kNoMatch;
+      A.slot_src[ro + j] = k != kNoMatch ? (u32)(g_lo + k) : kNoMatch;
+    }
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) *n_items = win_base[n_windows];
+  return found;
+}
+
+// ---------------- match in the global hash segments ----------------
+
+template <int T>
+__device__ __forceinline__ void bat_build(const EncArgs& A, u32 p, u64 tile, u32 epoch) {
+  const u64* pi = A.info + (u64)p * 8;
+  const u64 m = pi[PI_M];
+  const u64 g_lo = A.pair_off[p];
+  const u64 base = seg_base(g_lo, p), size = seg_size(m);
+  u64 id[kIlp], at[kIlp], cur[kIlp];
+  bool live[kIlp];
+#pragma unroll
+  for (u32 i = 0; i < kIlp; ++i) {
+    const u64 k = tile * T * kIlp + (u64)i * T + threadIdx.x;
+    live[i] = k < m;
+    id[i] = live[i] ? A.msg_id[g_lo + k] : 0;
+  }
+  // first probe of every entry: one load each, then one CAS each
+#pragma unroll
+  for (u32 i = 0; i < kIlp; ++i) {
+    at[i] = seg_start(id[i], size);
+    cur[i] = live[i] ? __ldcg(&A.seg[base + at[i]].a) : 0;
+  }
+  // the CASes of all entries in flight together, then the stragglers
+  u64 prev[kIlp];
+#pragma unroll
+  for (u32 i = 0; i < kIlp; ++i) {
+    const u64 k = tile * T * kIlp + (u64)i * T + threadIdx.x;
+    const bool empty = live[i] && (u32)(cur[i] >> 32) != epoch;
+    prev[i] = empty ? atomicCAS(&A.seg[base + at[i]].a, cur[i], ((u64)epoch << 32) | k) : ~0ull;
+  }
+#pragma unroll
+  for (u32 i = 0; i < kIlp; ++i) {
+    if (!live[i]) continue;
+    const u64 k = tile * T * kIlp + (u64)i * T + threadIdx.x;
+    if ((u32)(cur[i] >> 32) != epoch && prev[i] == cur[i]) {
+      A.seg[base + at[i]].b = id[i];
+    } else {  // taken in this iteration: continue along the probe sequence
+      seg_insert_from<true>(A.seg, base, size, id[i], ((u64)epoch << 32) | k, epoch,
+                            at[i] + 1 == size ? 0 : at[i] + 1);
+    }
+  }
+}
+
+// Predictor work of a matched slot (as in the per-call encoder): training
+// sample, prediction and the slot's residual payload size.
+template <bool PR>
+__device__ __forceinline__ u64 pred_slot(const EncArgs& A, u32 p, u64 j, u64 r, u64 mode,
+                                         const Rec& R, const Rec& M, u32 bxor, const float* sW) {
+  u64 vres = bxor;
+  u64* ps = A.pr.pscr + 4 * (A.ref_off[p] + j);
+  bool ok = false;
+  float f[kMlpIn];
+  if (A.pr.hist && mode == TERA_MODE_XOR) {
+    const Hist H = load_hist(A.pr.hist + kHistBytes * (A.ref_off[p] + j));
+    const u32 nc = cell_count(A.pr.cseg, seg_base(A.ref_off[p], p), seg_size(r), cell_key(R, A.pr));
+    if (features(R, H, nc, f)) {
+      if (A.pr.samples) {
+        float* s = A.pr.samples + (u64)kSampleFloats * (A.ref_off[p] + j);
+#pragma unroll
+        for (int i = 0; i < kMlpIn; ++i) s[i] = f[i];
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+          s[kMlpIn + a] = __double2float_rn(__dsub_rn(__longlong_as_double((long long)M.w[1 + a]),
+                                                      __longlong_as_double((long long)R.w[1 + a])));
+        s[11] = 1.0f;
+      }
+      if (A.pr.params) {
+        u64 pred[3];
+        ok = predict_from(sW, R, f, pred);
+        if (ok) {
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            vres += sig_bytes(zigzag(M.w[1 + a] - pred[a]));
+            vres -= sig_bytes(M.w[1 + a] ^ R.w[1 + a]);
+            ps[a] = pred[a];
+          }
+        }
+      }
+    }
+  }
+  ps[3] = ok ? 1ull : 0ull;
+  return vres;
+}
+
+template <int T>
+__device__ __forceinline__ void bat_match_ilp(const EncArgs& A, const BatchArgs& B, u32 p,
+                                              u64 tile, u32 epoch) {
+  const u64* pi = A.info + (u64)p * 8;
+  const u64 r = pi[PI_R], m = pi[PI_M];
+  const u64 ro = A.ref_off[p], g_lo = A.pair_off[p];
+  const u64 base = seg_base(g_lo, p), size = seg_size(m);
+  u64 id[kIlp], at[kIlp];
+  U64x2 e[kIlp];
+  bool live[kIlp];
+#pragma unroll
+  for (u32 i = 0; i < kIlp; ++i) {
+    const u64 j = tile * T * kIlp + (u64)i * T + threadIdx.x;
+    live[i] = j < r;
+    id[i] = live[i] ? *reinterpret_cast<const u64*>(A.ref + (ro + p + 1 + j) * kRecBytes) : 0;
+  }
+#pragma unroll
+  for (u32 i = 0; i < kIlp; ++i) {
+    at[i] = seg_start(id[i], size);
+    e[i] = live[i] ? ldx<true>(A.seg + base + at[i]) : U64x2{0, 0};
+  }
+  u32 g[kIlp];
+#pragma unroll
+  for (u32 i = 0; i < kIlp; ++i) {
+    g[i] = kNoMatch;
+    if (!live[i] || (u32)(e[i].a >> 32) != epoch) continue;
+    if (e[i].b == id[i]) g[i] = (u32)(g_lo + (u32)e[i].a);
+    else g[i] = seg_lookup_from<true>(A.seg, epoch, base, size, g_lo, id[i],
+                                      at[i] + 1 == size ? 0 : at[i] + 1);
+  }
+  u32 old[kIlp];
+#pragma unroll
+  for (u32 i = 0; i < kIlp; ++i) old[i] = g[i] != kNoMatch ? atomicExch(&A.matched[g[i]], epoch) : 0u;
+  int found = 0;
+#pragma unroll
+  for (u32 i = 0; i < kIlp; ++i) {
+    if (!live[i]) continue;
+    // a second slot with the same id: invalid reference; that slot is a hole
+    if (g[i] != kNoMatch && old[i] == epoch) {
+      latch(A.st, TERA_EINVAL);
+      g[i] = kNoMatch;
+    }
+    found += g[i] != kNoMatch;
+    A.slot_src[ro + tile * T * kIlp + (u64)i * T + threadIdx.x] = g[i];
+  }
+  // block total of matches: warp sums, one atomic per warp
+  int wsum = found;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) wsum += __shfl_xor_sync(0xFFFFFFFFu, wsum, o);
+  if ((threadIdx.x & 31) == 0 && wsum)
+    atomicAdd(B.ptot + (u64)p * PT_COUNT + PT_MATCHED, (u64)wsum);
+}
+
+template <int T, bool PR>
+__device__ __forceinline__ void bat_match(const EncArgs& A, const BatchArgs& B, u32 p, u64 tile,
+                                          u32 epoch, U64x2* sm, const float* sW) {
+  const u64* pi = A.info + (u64)p * 8;
+  const u64 r = pi[PI_R], m = pi[PI_M];
+  const u64 j = tile * T + threadIdx.x;
+  int found = 0;
+  u64 bx = 0, br = 0;
+  if (j < r) {
+    const u64 ro = A.ref_off[p];
+    const uint8_t* rp = A.ref + (ro + p + 1 + j) * kRecBytes;
+    if constexpr (PR) {
+      if (A.pr.samples) A.pr.samples[(u64)kSampleFloats * (ro + j) + 11] = 0.0f;
+    }
+    Rec R;
+    u64 id;
+    if constexpr (PR) {
+      R = load_rec(rp);
+      id = R.w[0];
+    } else {
+      id = *reinterpret_cast<const u64*>(rp);
+    }
+    u32 g = seg_lookup<true>(A.seg, epoch, p, A.pair_off[p], m, id);
+    // a second slot with the same id: invalid reference; that slot is a hole
+    if (g != kNoMatch && atomicExch(&A.matched[g], epoch) == epoch) {
+      latch(A.st, TERA_EINVAL);
+      g = kNoMatch;
+    }
+    if (g != kNoMatch) {
+      found = 1;
+      if constexpr (PR) {
+        const Rec M = load_rec(A.rec + ((u64)g + p + 1) * kRecBytes);
+        u32 b = 0;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) b += sig_bytes(M.w[w] ^ R.w[w]);
+        bx = b;
+        br = pred_slot<PR>(A, p, j, r, pi[PI_MODE], R, M, b, sW);
+      }
+    } else if constexpr (PR) {
+      A.pr.pscr[4 * (ro + j) + 3] = 0;
+    }
+    A.slot_src[ro + j] = g;
+  }
+  if constexpr (PR) {
+    U64x2 tot;
+    block_excl_scan2(U64x2{bx, br}, sm, &tot);
+    const int c = __syncthreads_count(found);
+    if (threadIdx.x == 0) {
+      u64* pt = B.ptot + (u64)p * PT_COUNT;
+      if (c) atomicAdd(pt + PT_MATCHED, (u64)c);
+      if (tot.a) atomicAdd(pt + PT_XOR, tot.a);
+      if (tot.b) atomicAdd(pt + PT_RES, tot.b);
+    }
+  } else {
+    const int c = __syncthreads_count(found);
+    if (threadIdx.x == 0 && c) atomicAdd(B.ptot + (u64)p * PT_COUNT + PT_MATCHED, (u64)c);
+  }
+}
+
+// Message mode of pair p once MATCH is complete.
+template <bool PR>
+__device__ __forceinline__ u64 pair_mode(const EncArgs& A, const BatchArgs& B, u32 p) {
+  u64 mode = A.info[(u64)p * 8 + PI_MODE];
+  if constexpr (PR) {
+    const u64* pt = B.ptot + (u64)p * PT_COUNT;
+    if (A.pr.params && A.pr.allow_residual && mode == TERA_MODE_XOR &&
+        __ldcg(pt + PT_RES) < __ldcg(pt + PT_XOR))
+      mode = kModeResidual;
+  }
+  return mode;
+}
+
+// One tile of slots; g = this thread's slot source (read one tile ahead).
+// Registers: the difference d is formed in place of the reference record, and
+// the byte counts are recomputed from d when staging.
+template <int T, bool PR>
+__device__ __forceinline__ void bat_slot(const EncArgs& A, const BatchArgs& B, u32 p, u64 tile,
+                                         u32 g, U64x2* sm, uint8_t* stage, U64x2& run) {
+  const u64* pi = A.info + (u64)p * 8;
+  const u64 r = pi[PI_R], m = pi[PI_M];
+  const u64 ro = A.ref_off[p];
+  const u64 j = tile * T + threadIdx.x;
+  Rec cur, d;
+  u32 vb = 0, vn = 0;
+  if (j < r) {
+    // both records in flight at once
+    d = load_rec(A.ref + (ro + p + 1 + j) * kRecBytes);
+    u32 code = 0xFu;  // placeholder
+    if (g != kNoMatch) {
+      cur = load_rec(A.rec + ((u64)g + p + 1) * kRecBytes);
+#pragma unroll
+      for (int w = 0; w < 8; ++w) d.w[w] ^= cur.w[w];
+      if constexpr (PR) {
+        if (pair_mode<PR>(A, B, p) == kModeResidual) {
+          const u64* ps = A.pr.pscr + 4 * (ro + j);
+          if (__ldcg(ps + 3)) {
+#pragma unroll
+            for (int a = 0; a < 3; ++a) d.w[1 + a] = zigzag(cur.w[1 + a] - __ldcg(ps + a));
+          }
+        }
+      }
+      u32 b = 0;
+      code = 0;
+#pragma unroll
+      for (int w = 0; w < 8; ++w) {
+        const u32 L = sig_bytes(d.w[w]);
+        b += L;
+        code |= L << (4 * w);
+      }
+      vb = b;
+      vn = 1;
+    }
+    reinterpret_cast<u32*>(A.wire + A.wire_off[p] + kHdrBytes)[j] = code;
+  }
+  U64x2 tot;
+  const U64x2 ex = tile_scan(vb, vn, sm, &tot);
+  const U64x2 pre = run;
+  run = pre + tot;
+  const u64 n_new = m - __ldcg(B.ptot + (u64)p * PT_COUNT + PT_MATCHED);
+  uint8_t* gA = A.wire + A.wire_off[p] + kHdrBytes + 4 * (r + n_new) + pre.a;
+  if (vn) {
+    u32 o = (u32)((uintptr_t)gA & 15u) + (u32)ex.a;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) stage_word(stage, o, d.w[w], sig_bytes(d.w[w]));
+    const u64 pos = pre.b + ex.b;
+    store_rec(A.ref_next + (A.pair_off[p] + p + 1 + pos) * kRecBytes, cur);
+    if constexpr (PR) {
+      if (A.pr.hist_next) {
+        const Rec R = load_rec(A.ref + (ro + p + 1 + j) * kRecBytes);
+        uint8_t* hn = A.pr.hist_next + kHistBytes * (A.pair_off[p] + pos);
+        if (A.pr.hist) {
+          const Hist H = load_hist(A.pr.hist + kHistBytes * (ro + j));
+          store_hist_next(hn, &R, &H);
+        } else {
+          store_hist_next(hn, &R, nullptr);
+        }
+      }
+    }
+  }
+  __syncthreads();
+  flush_stage(stage, gA, tot.a);
+  __syncthreads();
+}
+
+// Header, padding, iteration totals and the new reference's header of pair p
+// once every slot and new record is written (warp 0).  slot_tot / new_tot:
+// (payload bytes, records) of the slots and of the new records.
+template <bool PR>
+__device__ __forceinline__ void finish_pair(const EncArgs& A, const BatchArgs& B, u32 p, u64 r,
+                                            u64 m, u64 matched, U64x2 slot_tot, U64x2 new_tot) {
+  if (threadIdx.x >= 32) return;
+  const int lane = threadIdx.x;
+  const u64 n_new = m - matched;
+  const u64 payload = slot_tot.a + new_tot.a;
+  const u64 body = (u64)kHdrBytes + 4 * (r + n_new) + payload;
+  const u64 msg = round16(body);
+  const u64 mode = pair_mode<PR>(A, B, p);
+  uint8_t* w8 = A.wire + A.wire_off[p];
+  if (lane == 0) {
+    if (new_tot.b != n_new || slot_tot.b != matched) latch(A.st, TERA_EINVAL);
+    ulonglong2* h = reinterpret_cast<ulonglong2*>(w8);
+    h[0] = make_ulonglong2((u64)kWireMagic | ((u64)kVersion << 32) | ((u64)kRecBytes << 48),
+                           (u64)A.class_id | (mode << 32));
+    h[1] = make_ulonglong2(r, n_new);
+    h[2] = make_ulonglong2(r - matched, payload);
+    h[3] = make_ulonglong2((u64)p, msg);
+    A.wire_len[p] = msg;
+    atomicAdd(&A.stats->ref_slots, r);
+    atomicAdd(&A.stats->holes, r - matched);
+    atomicAdd(&A.stats->new_records, n_new);
+    atomicAdd(&A.stats->payload_bytes, payload);
+    atomicAdd(&A.stats->wire_bytes, msg);
+    write_taio_header(A.ref_next + (A.pair_off[p] + p) * kRecBytes, A.class_id, p, m);
+    A.reset[p] = 0;
+  }
+  if (body + lane < msg) w8[body + lane] = 0;  // zero padding (< 16 bytes)
+}
+
+// Payload bytes of one word: staged, or stored directly when the tile's
+// payload does not fit the stage.
+__device__ __forceinline__ void put_word(uint8_t* dst, u32& o, u64 v, u32 L) {
+  for (u32 b = 0; b < L; ++b) dst[o++] = (uint8_t)(v >> (8 * b));
+}
+
+template <int T, bool PR>
+__device__ __forceinline__ void bat_new(const EncArgs& A, const BatchArgs& B, u32 p, u64 tile,
+                                        u32 epoch, U64x2* sm, uint8_t* stage, u32 stage_cap,
+                                        U64x2& run, U64x2 slot_tot, const SmemTable& tb) {
+  u64* pi = A.info + (u64)p * 8;
+  const u64 r = pi[PI_R], m = pi[PI_M];
+  const u64 matched = __ldcg(B.ptot + (u64)p * PT_COUNT + PT_MATCHED);
+  const u64 n_new = m - matched;
+  const u64 slot_pay = slot_tot.a;
+  const u32 V = new_per_thread(pi[PI_MODE]);
+  const u64 g_lo = A.pair_off[p];
+  const u64 kb = tile * T * V + (u64)threadIdx.x * V;
+  u32 nmask = 0;
+  for (u32 i = 0; i < V; ++i) {
+    const u64 k = kb + i;
+    if (k >= m) continue;
+    const bool taken = tb.tbl ? ((tb.bits[k >> 5] >> (k & 31u)) & 1u) != 0u
+                              : __ldcg(A.matched + g_lo + k) == epoch;
+    if (!taken) nmask |= 1u << i;
+  }
+  u64 bytes = 0, cnt = 0;
+  for (u32 mm = nmask; mm; mm &= mm - 1) {
+    const u64 g = g_lo + kb + (u64)(__ffs(mm) - 1);
+    const Rec M = load_rec(A.rec + (g + p + 1) * kRecBytes);
+    // a second record with the same id in this pair would be found instead of
+    // this one (the shared-memory index rejected such records when it was built)
+    if (!tb.tbl && seg_lookup<true>(A.seg, epoch, p, g_lo, m, M.w[0]) != (u32)g)
+      latch(A.st, TERA_EINVAL);
+#pragma unroll
+    for (int w = 0; w < 8; ++w) bytes += sig_bytes(M.w[w]);
+    ++cnt;
+  }
+  U64x2 tot;
+  const U64x2 ex = tile_scan((u32)bytes, (u32)cnt, sm, &tot);
+  const U64x2 pre = run;
+  run = pre + tot;
+  uint8_t* w8 = A.wire + A.wire_off[p];
+  uint8_t* gA = w8 + kHdrBytes + 4 * (r + n_new) + slot_pay + pre.a;
+  const u32 s0 = (u32)((uintptr_t)gA & 15u);
+  const bool staged = s0 + tot.a <= stage_cap;  // block-uniform
+  if (nmask) {
+    u32 o = staged ? s0 + (u32)ex.a : 0u;
+    uint8_t* dst = staged ? stage : gA + ex.a;
+    u64 rank = pre.b + ex.b;
+    for (u32 mm = nmask; mm; mm &= mm - 1) {
+      const u64 g = g_lo + kb + (u64)(__ffs(mm) - 1);
+      const Rec M = load_rec(A.rec + (g + p + 1) * kRecBytes);
+      u32 code = 0;
+#pragma unroll
+      for (int w = 0; w < 8; ++w) {
+        const u32 L = sig_bytes(M.w[w]);
+        code |= L << (4 * w);
+        put_word(dst, o, M.w[w], L);
+      }
+      reinterpret_cast<u32*>(w8 + kHdrBytes)[r + rank] = code;
+      store_rec(A.ref_next + (g_lo + p + 1 + matched + rank) * kRecBytes, M);
+      if constexpr (PR) {
+        if (A.pr.hist_next)
+          store_hist_next(A.pr.hist_next + kHistBytes * (g_lo + matched + rank), nullptr, nullptr);
+      }
+      ++rank;
+    }
+  }
+  __syncthreads();
+  if (staged) flush_stage(stage, gA, tot.a);
+  __syncthreads();
+  // the last tile: header, padding and the iteration totals
+  const u64 ntiles = ceil_div(m, (u64)T * V);
+  if (tile + 1 < (ntiles ? ntiles : 1)) return;
+  finish_pair<PR>(A, B, p, r, m, matched, slot_tot, run);
+}
+
+// Shared-memory path: the message records no slot took, in message order,
+// into list[0, n) (the hash table's memory, free once matching is done).
+// Returns n (block-uniform).
+template <int T>
+__device__ __forceinline__ u32 smem_new_list(const SmemTable& tb, u64 m, u32* list, u32* sm32) {
+  const u32 words = (u32)((m + 31) / 32);
+  const u32 per = (words + T - 1) / T;
+  const u32 w0 = threadIdx.x * per, w1 = w0 + per < words ? w0 + per : words;
+  u32 cnt = 0;
+  for (u32 w = w0; w < w1; ++w) {
+    const u32 valid = (w + 1) * 32 <= m ? 0xFFFFFFFFu : ((1u << (m & 31u)) - 1u);
+    cnt += __popc(~tb.bits[w] & valid);
+  }
+  u32 tot;
+  u32 pos = block_excl_scan<u32>(cnt, sm32, &tot);
+  for (u32 w = w0; w < w1; ++w) {
+    const u32 valid = (w + 1) * 32 <= m ? 0xFFFFFFFFu : ((1u << (m & 31u)) - 1u);
+    for (u32 x = ~tb.bits[w] & valid; x; x &= x - 1) list[pos++] = w * 32 + (u32)(__ffs(x) - 1);
+  }
+  __syncthreads();
+  return tot;
+}
+
+// One tile of T new records (list entries tile*T + thread): codes, payload
+// and new-reference records; the running prefix is carried in `run`.
+template <int T, bool PR>
+__device__ __forceinline__ void bat_new_list(const EncArgs& A, u32 p, u64 r, u64 m, u64 matched,
+                                             U64x2 slot_tot, const u32* list, u32 n_list,
+                                             u64 tile, U64x2* sm, uint8_t* stage, u32 stage_cap,
+                                             U64x2& run) {
+  const u64 n_new = m - matched;
+  const u64 g_lo = A.pair_off[p];
+  const u64 i = tile * T + threadIdx.x;
+  Rec M;
+  u32 vb = 0, vn = 0;
+  if (i < n_list) {
+    M = load_rec(A.rec + (g_lo + list[i] + p + 1) * kRecBytes);
+#pragma unroll
+    for (int w = 0; w < 8; ++w) vb += sig_bytes(M.w[w]);
+    vn = 1;
+  }
+  U64x2 tot;
+  const U64x2 ex = tile_scan(vb, vn, sm, &tot);
+  const U64x2 pre = run;
+  run = pre + tot;
+  uint8_t* w8 = A.wire + A.wire_off[p];
+  uint8_t* gA = w8 + kHdrBytes + 4 * (r + n_new) + slot_tot.a + pre.a;
+  const u32 s0 = (u32)((uintptr_t)gA & 15u);
+  const bool staged = s0 + tot.a <= stage_cap;  // block-uniform
+  if (vn) {
+    u32 o = staged ? s0 + (u32)ex.a : 0u;
+    uint8_t* dst = staged ? stage : gA + ex.a;
+    u32 code = 0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) {
+      const u32 L = sig_bytes(M.w[w]);
+      code |= L << (4 * w);
+      put_word(dst, o, M.w[w], L);
+    }
+    const u64 rank = pre.b + ex.b;
+    reinterpret_cast<u32*>(w8 + kHdrBytes)[r + rank] = code;
+    store_rec(A.ref_next + (g_lo + p + 1 + matched + rank) * kRecBytes, M);
+    if constexpr (PR) {
+      if (A.pr.hist_next)
+        store_hist_next(A.pr.hist_next + kHistBytes * (g_lo + matched + rank), nullptr, nullptr);
+    }
+  }
+  __syncthreads();
+  if (staged) flush_stage(stage, gA, tot.a);
+  __syncthreads();
+}
+
+// ---------------- decode phase ----------------
+
+struct DecShared {
+  u64 ns, nn, pay, mode;
+  int ok;
+};
+
+// One tile of entries; code = this thread's entry code (read one tile ahead).
+template <int T, bool PR>
+__device__ __forceinline__ void bat_dec_tile(const DecArgs& A, const BatchArgs& B, u32 p,
+                                             u64 tile, u32 code, const DecShared& h, u64 m,
+                                             U64x2* sm, uint8_t* stage, U64x2& run,
+                                             const float* sW) {
+  const u64 ns = h.ns, n = h.ns + h.nn;
+  const uint8_t* w8 = A.wire + A.wire_off[p];
+  const u64 e = tile * T + threadIdx.x;
+  u32 b = 0;
+  bool hole = true;
+  int bad = 0;
+  // the slot's reference record is read before (and while) the prefix is found
+  Rec R;
+  if (e < ns) R = load_rec(A.ref + (A.ref_off[p] + p + 1 + e) * kRecBytes);
+  if (e < n && !check_code(code, e, ns, &hole, &b)) bad = 1;
+  const u32 vn = (e < n && !hole) ? 1u : 0u;
+  U64x2 tot;
+  const U64x2 ex = tile_scan(b, vn, sm, &tot);
+  const U64x2 pre = run;
+  run = pre + tot;
+  // malformed codes, or more payload / records than the header announces
+  const bool corrupt = __syncthreads_or(bad) || pre.a + tot.a > h.pay || pre.b + tot.b > m;
+  if (corrupt && threadIdx.x == 0) latch(A.st, TERA_ECORRUPT);
+  const bool ok = !corrupt;
+  // stage [gA, gA + tot.a) with 16-byte loads; the slab is 16-byte aligned
+  // and padded, and the range was checked, so it stays inside the message
+  const uint8_t* gA = w8 + kHdrBytes + 4 * n + pre.a;
+  const u32 s0 = (u32)((uintptr_t)gA & 15u);
+  if (ok) {
+    const uint8_t* g16 = gA - s0;
+    const u32 nchunks = (u32)((s0 + tot.a + 15u) >> 4);
+    for (u32 c = threadIdx.x; c < nchunks; c += T)
+      *reinterpret_cast<uint4*>(stage + (c << 4)) =
+          __ldcg(reinterpret_cast<const uint4*>(g16 + (c << 4)));
+  }
+  __syncthreads();
+  if (ok && vn) {
+    u32 o = s0 + (u32)ex.a;
+    Rec rec;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) {
+      const u32 L = (code >> (4 * w)) & 0xFu;
+      u64 x = 0;
+      for (u32 q = 0; q < L; ++q) x |= (u64)stage[o + q] << (8 * q);
+      o += L;
+      rec.w[w] = x;
+    }
+    const u64 pos = pre.b + ex.b;
+    if (e < ns) {
+      bool pred_ok = false;
+      u64 pred[3];
+      if constexpr (PR) {
+        Hist H;
+        if (A.pr.hist) H = load_hist(A.pr.hist + kHistBytes * (A.ref_off[p] + e));
+        if (A.pr.hist && h.mode == kModeResidual) {
+          const u64 r = A.ref_off[p + 1] - A.ref_off[p];
+          const u32 nc = cell_count(A.pr.cseg, seg_base(A.ref_off[p], p), seg_size(r),
+                                    cell_key(R, A.pr));
+          float f[kMlpIn];
+          if (features(R, H, nc, f)) pred_ok = predict_from(sW, R, f, pred);
+        }
+        if (A.pr.hist_next)
+          store_hist_next(A.pr.hist_next + kHistBytes * (A.recv_off[p] + pos), &R,
+                          A.pr.hist ? &H : nullptr);
+      }
+#pragma unroll
+      for (int w = 0; w < 8; ++w) {
+        if (pred_ok && w >= 1 && w <= 3) rec.w[w] = pred[w - 1] + unzigzag(rec.w[w]);
+        else rec.w[w] ^= R.w[w];
+      }
+    } else {
+      if constexpr (PR) {
+        if (A.pr.hist_next)
+          store_hist_next(A.pr.hist_next + kHistBytes * (A.recv_off[p] + pos), nullptr, nullptr);
+      }
+    }
+    store_rec(A.recv + (A.recv_off[p] + p + 1 + pos) * kRecBytes, rec);
+  }
+  __syncthreads();
+  // the last tile: every byte and record the header announced was decoded
+  if (ok && threadIdx.x == 0 && tile + 1 == (n ? ceil_div(n, T) : 1) &&
+      (pre.a + tot.a != h.pay || pre.b + tot.b != m))
+    latch(A.st, TERA_ECORRUPT);
+}
+
+template <int T, bool PR>
+__device__ __forceinline__ void bat_dec(const DecArgs& A, const BatchArgs& B, u32 p,
+                                        DecShared* hs, U64x2* sm, uint8_t* stage,
+                                        const float* sW) {
+  const u64 m = A.recv_off[p + 1] - A.recv_off[p];
+  if (threadIdx.x == 0) {
+    DecHdr H;
+    const u32 err = dec_read_header<true, PR>(A, p, m, &H);
+    hs->ns = H.ns;
+    hs->nn = H.nn;
+    hs->pay = H.pay;
+    hs->mode = H.mode;
+    hs->ok = err ? 0 : 1;
+    if (err) latch(A.st, err);
+    write_taio_header(A.recv + (A.recv_off[p] + p) * kRecBytes, A.class_id, p, m);
+  }
+  __syncthreads();
+  const DecShared h = *hs;
+  if (!h.ok) return;  // block-uniform
+  const u64 n = h.ns + h.nn;
+  const u64 ntiles = n ? ceil_div(n, T) : 1;
+  U64x2 run{0, 0};
+  const u32* codes = reinterpret_cast<const u32*>(A.wire + A.wire_off[p] + kHdrBytes);
+  u32 c_next = threadIdx.x < n ? __ldcg(codes + threadIdx.x) : 0u;
+  for (u64 t = 0; t < ntiles; ++t) {
+    const u32 c = c_next;
+    const u64 en = (t + 1) * T + threadIdx.x;
+    c_next = en < n ? __ldcg(codes + en) : 0u;
+    bat_dec_tile<T, PR>(A, B, p, t, c, h, m, sm, stage, run, sW);
+  }
 }
 
 // ---------------- the persistent kernel ----------------
 
-__device__ __forceinline__ bool wait_deps(const BatchArgs& B, u32 p, int ph, DevStatus* st) {
-  const u32 mask = deps(ph);
-  for (int q = 0; q < PH_COUNT; ++q) {
-    if (!((mask >> q) & 1u)) continue;
-    const u32 want = B.need[(u64)p * PH_COUNT + q];
-    const u32* ctr = B.done + (u64)p * PH_COUNT + q;
-    u64 spin = 0;
-    while (ld_acquire(ctr) < want) {
-      if (*(volatile u32*)B.abort) return false;
-      if (++spin > kSpinLimit) {
-        latch(st, TERA_ETIMEOUT);
-        atomicExch(B.abort, 1u);
-        return false;
-      }
-      __nanosleep(100);
-    }
-  }
-  return true;
-}
-
-// At least 1024 resident threads per SM: the codec is latency-bound.
+// Shared memory: stage (T records + 48 bytes) | MLP weights (predictor) |
+// hash table (2 table_records u32) | taken bits (table_records / 32 u32).
 template <int T, bool PR>
-__global__ void __launch_bounds__(T, 1024 / T)
-    codec_persistent_kernel(EncArgs E, DecArgs D, BatchArgs B, u32 K) {
-  extern __shared__ __align__(16) uint8_t stage[];
+__global__ void __launch_bounds__(T, (1024 / T) > 0 ? (1024 / T) : 1)
+    codec_persistent_kernel(EncArgs E, DecArgs D, BatchArgs B, u32 table_records) {
+  extern __shared__ __align__(16) uint8_t dyn[];
+  constexpr u32 kStageCap = (u32)T * kRecBytes + 48;
+  uint8_t* stage = dyn;
+  float* sW = reinterpret_cast<float*>(dyn + kStageCap);
+  u32* tbl = reinterpret_cast<u32*>(dyn + kStageCap + (PR ? sizeof(float) * kMlpParams : 0));
+  u32* bits = tbl + 2 * table_records;
   __shared__ U64x2 sm[33];
-  __shared__ u64 s_item;
-  __shared__ int s_go;
-  float* sW = reinterpret_cast<float*>(stage + ((size_t)T * kRecBytes + 48));
+  __shared__ u64 s_pair;
+  __shared__ u32 s_cnt;
+  __shared__ DecShared hs;
   if (PR) {
     const float* params = E.pr.params ? E.pr.params : D.pr.params;
     if (params) load_mlp(sW, params);
   }
-  const u64 n_items = __ldcg(B.n_items);
   const u32 epoch = __ldcg(E.epoch);
+  u64 next = 0;
+  if (threadIdx.x == 0) {
+    next = atomicAdd(B.ticket, 1ull);
+    s_cnt = 0;
+  }
   for (;;) {
-    if (threadIdx.x == 0) {
-      s_go = 0;
-      if (!*(volatile u32*)B.abort) {
-        const u64 t = atomicAdd(B.ticket, 1ull);
-        if (t < n_items) {
-          const u64 it = B.items[t];
-          s_item = it;
-          s_go = wait_deps(B, (u32)(it >> 32) & 0x0FFFFFFFu, (int)(it >> 60), E.st) ? 1 : 0;
+    if (threadIdx.x == 0)
+      s_pair = (next < B.n_pairs && !*(volatile u32*)B.abort) ? next : ~0ull;
+    __syncthreads();
+    if (s_pair == ~0ull) break;
+    const u32 p = (u32)s_pair;
+    // claim the next pair now; no pair waits for another
+    if (threadIdx.x == 0) next = atomicAdd(B.ticket, 1ull);
+    const u64* pi = E.info + (u64)p * 8;
+    const u64 r = pi[PI_R], m = pi[PI_M];
+    SmemTable tb{nullptr, 0u, bits};
+    if (!PR && table_records > 0 && m <= table_records) {
+      u32 size = 32;
+      while (size < 2 * m) size <<= 1;
+      tb.tbl = tbl;
+      tb.mask = size - 1;
+      smem_build<T>(E, p, m, tb);
+      __syncthreads();
+      u32 c = smem_match<T>(E, p, r, tb);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xFFFFFFFFu, c, o);
+      if ((threadIdx.x & 31) == 0 && c) atomicAdd(&s_cnt, c);
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        B.ptot[(u64)p * PT_COUNT + PT_MATCHED] = s_cnt;
+        s_cnt = 0;
+      }
+    } else {
+      const u64 ntb = ceil_div(m, (u64)T * kIlp);
+      for (u64 t = 0; t < ntb; ++t) bat_build<T>(E, p, t, epoch);
+      __syncthreads();
+      if constexpr (PR) {
+        const u64 nst = ceil_div(r, T);
+        if (E.pr.hist) {
+          for (u64 t = 0; t < nst; ++t) cells_unit(E.pr, E.ref, E.ref_off, p, t, r, T);
+          __syncthreads();
         }
+        for (u64 t = 0; t < nst; ++t) bat_match<T, PR>(E, B, p, t, epoch, sm, sW);
+      } else {
+        const u64 ntm = ceil_div(r, (u64)T * kIlp);
+        for (u64 t = 0; t < ntm; ++t) bat_match_ilp<T>(E, B, p, t, epoch);
       }
     }
     __syncthreads();
-    if (!s_go) break;
-    const u64 it = s_item;
-    const int ph = (int)(it >> 60);
-    const u32 p = (u32)(it >> 32) & 0x0FFFFFFFu;
-    const u64 k0 = (u64)(u32)it * K;  // first tile of this item
-    const u64* pi = E.info + (u64)p * 8;
-    const u64 nst = pi[PI_NST];
-    const u64 ntm = (pi[PI_M] + T - 1) / T;
-    const u64 ntd = B.dec_uoff[p + 1] - B.dec_uoff[p];
-    switch (ph) {
-      case PH_BUILD:
-        for (u64 t = k0; t < k0 + K && t < ntm; ++t) enc_build_unit<T, true>(E, p, nst + t, epoch);
-        break;
-      case PH_CELLS:
-        if constexpr (PR)
-          for (u64 t = k0; t < k0 + K && t < nst; ++t)
-            cells_unit(E.pr, E.ref, E.ref_off, p, t, pi[PI_R], T);
-        break;
-      case PH_MATCH:
-        for (u64 t = k0; t < k0 + K && t < nst; ++t)
-          enc_match_unit<T, true, PR>(E, p, t, B.enc_uoff[p] + t, epoch, sm, sW);
-        break;
-      case PH_NEW:
-        for (u64 t = k0; t < k0 + K && t < ntm; ++t)
-          enc_new_unit<T, true>(E, p, nst + t, B.enc_uoff[p] + nst + t, epoch, sm);
-        break;
-      case PH_SCAN:
-        if (threadIdx.x < 32)
-          enc_scan_pair<true, PR>(E, p, B.enc_uoff[p], B.enc_uoff[p + 1] - B.enc_uoff[p]);
-        break;
-      case PH_EMIT:
-        for (u64 t = k0; t < k0 + K && t < nst + ntm; ++t)
-          enc_emit_unit<T, true, PR>(E, p, t, B.enc_uoff[p] + t, epoch, sm, stage);
-        break;
-      case PH_DSETUP:
-        if (threadIdx.x == 0) {
-          const u32 err = dec_check_header<true, PR>(D, p, E.pair_off[p + 1] - E.pair_off[p]);
-          if (err) latch(D.st, err);
-        }
-        break;
-      case PH_DSUM:
-        for (u64 t = k0; t < k0 + K && t < ntd; ++t)
-          dec_sum_unit<T, true>(D, p, t, B.dec_uoff[p] + t, sm);
-        break;
-      case PH_DSCAN:
-        if (threadIdx.x < 32) dec_scan_pair<true>(D, p, B.dec_uoff[p], ntd);
-        break;
-      case PH_DCELLS:
-        if constexpr (PR) {
-          const u64 rr = D.ref_off[p + 1] - D.ref_off[p];
-          const u64 ntr = (rr + T - 1) / T;
-          for (u64 t = k0; t < k0 + K && t < ntr; ++t) cells_unit(D.pr, D.ref, D.ref_off, p, t, rr, T);
-        }
-        break;
-      case PH_DEMIT:
-        for (u64 t = k0; t < k0 + K && t < ntd; ++t)
-          dec_emit_unit<T, true, PR>(D, p, t, B.dec_uoff[p] + t, sm, stage, sW);
-        break;
-      default: break;
+    U64x2 run{0, 0};
+    const u64 nst = ceil_div(r, T);
+    {
+      const u64 ro = E.ref_off ? E.ref_off[p] : 0;
+      u32 g_next = threadIdx.x < r ? __ldcg(E.slot_src + ro + threadIdx.x) : kNoMatch;
+      for (u64 t = 0; t < nst; ++t) {
+        const u32 g = g_next;
+        const u64 jn = (t + 1) * T + threadIdx.x;
+        g_next = jn < r ? __ldcg(E.slot_src + ro + jn) : kNoMatch;
+        bat_slot<T, PR>(E, B, p, t, g, sm, stage, run);
+      }
     }
-    // release: the barrier orders every thread's writes before thread 0's
-    // release, which publishes them (with this item's count) at GPU scope
+    const U64x2 slot_tot = run;
+    run = U64x2{0, 0};
+    if (tb.tbl) {
+      const u64 matched = slot_tot.b;
+      const u32 n_list = smem_new_list<T>(tb, m, tb.tbl, reinterpret_cast<u32*>(sm));
+      const u64 tl = ceil_div(n_list, T);
+      for (u64 t = 0; t < tl; ++t)
+        bat_new_list<T, PR>(E, p, r, m, matched, slot_tot, tb.tbl, n_list, t, sm, stage,
+                            kStageCap, run);
+      finish_pair<PR>(E, B, p, r, m, matched, slot_tot, run);
+    } else {
+      const u64 tn = ceil_div(m, (u64)T * new_per_thread(pi[PI_MODE]));
+      for (u64 t = 0; t < (tn ? tn : 1); ++t)
+        bat_new<T, PR>(E, B, p, t, epoch, sm, stage, kStageCap, run, slot_tot, tb);
+    }
     __syncthreads();
-    if (threadIdx.x == 0) red_release_add(B.done + (u64)p * PH_COUNT + ph, 1u);
+    if constexpr (PR) {
+      if (D.pr.hist) {
+        const u64 rr = D.ref_off[p + 1] - D.ref_off[p];
+        const u64 ntr = ceil_div(rr, T);
+        for (u64 t = 0; t < ntr; ++t) cells_unit(D.pr, D.ref, D.ref_off, p, t, rr, T);
+        __syncthreads();
+      }
+    }
+    bat_dec<T, PR>(D, B, p, &hs, sm, stage, sW);
+    __syncthreads();
   }
+}
+
+// Shared memory of one block for tile size T: (bytes, table_records).
+inline void persistent_smem(u32 T, bool PR, int ctas_per_sm, u32 want_records, size_t* bytes,
+                            u32* records) {
+  const size_t base = (size_t)T * kRecBytes + 48 + (PR ? sizeof(float) * kMlpParams : 0);
+  // per-SM shared memory (228 KB) split over the blocks, minus the static
+  // shared memory and the 1 KB the runtime reserves per block
+  const size_t per_block = (size_t)228 * 1024 / (size_t)(ctas_per_sm > 0 ? ctas_per_sm : 1);
+  size_t cap = per_block > 2048 ? per_block - 2048 : 0;
+  if (cap > (size_t)227 * 1024) cap = (size_t)227 * 1024;
+  u32 rec = 0;
+  if (!PR) {
+    // 2 table entries (u32) + 1 bit per record
+    for (u32 c = 32; c <= (1u << 20); c <<= 1)
+      if (base + 8 * (size_t)c + c / 8 <= cap && (want_records == 0 || c <= want_records)) rec = c;
+  }
+  *records = rec;
+  *bytes = base + 8 * (size_t)rec + rec / 8;
 }
 
 template <int T, bool PR>
 tera_status launch_persistent(tera_ctx* ctx, const EncArgs& E, const DecArgs& D,
-                              const BatchArgs& B, int ctas_per_sm, u32 K, cudaStream_t s) {
-  // stage (+ MLP weights): at most 36 KB, no opt-in needed
-  const size_t smem = (size_t)T * kRecBytes + 48 + (PR ? sizeof(float) * kMlpParams : 0);
+                              const BatchArgs& B, int ctas_per_sm, u32 want_records,
+                              cudaStream_t s) {
+  size_t smem;
+  u32 records;
+  persistent_smem(T, PR, ctas_per_sm, want_records, &smem, &records);
+  if (smem > 48 * 1024 &&
+      cudaFuncSetAttribute(codec_persistent_kernel<T, PR>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return TERA_ECUDA;
   const unsigned grid = (unsigned)(ctx->num_sms * (ctas_per_sm > 0 ? ctas_per_sm : 1));
   prof_begin(ctx, s);
-  codec_persistent_kernel<T, PR><<<grid, T, smem, s>>>(E, D, B, K);
+  codec_persistent_kernel<T, PR><<<grid, T, smem, s>>>(E, D, B, records);
   return check_launch(ctx, "codec_persistent_kernel", s);
 }
 
@@ -340,21 +999,25 @@ static tera_status batched_impl(
   if (((uintptr_t)rec_arena | (uintptr_t)ref_next | (uintptr_t)wire | (uintptr_t)recv |
        (uintptr_t)(ref_prev ? ref_prev : wire) | (uintptr_t)(recv_prev ? recv_prev : wire)) & 15u)
     return TERA_EINVAL;
-  tera_tune tn = tune ? *tune : tera_tune{256, 4, 64, 4};
+  tera_tune tn = tune ? *tune : tera_tune{512, 2, 0, 0};
   if (enc_pred && enc_pred->params && ((uintptr_t)enc_pred->params & 3u)) return TERA_EINVAL;
-  if (tn.block != 128 && tn.block != 256 && tn.block != 512) return TERA_EINVAL;
-  if (tn.ctas_per_sm < 1 || tn.ctas_per_sm > 16) return TERA_EINVAL;
-  if (tn.window < 1 || tn.window > 1024) return TERA_EINVAL;
-  if (tn.tiles_per_item < 1 || tn.tiles_per_item > 64) return TERA_EINVAL;
+  if (tn.block != 128 && tn.block != 256 && tn.block != 512 && tn.block != 1024) return TERA_EINVAL;
+  if (tn.ctas_per_sm < 1 || tn.ctas_per_sm > 16 || tn.block * tn.ctas_per_sm > 2048)
+    return TERA_EINVAL;
+  if (tn.table_records < 0 || (tn.table_records > 0 && (tn.table_records < 32 ||
+                                                        (tn.table_records & (tn.table_records - 1)))))
+    return TERA_EINVAL;
+  if (tn.reserved != 0) return TERA_EINVAL;
   cudaSetDevice(ctx->device);
   cudaStream_t s = (cudaStream_t)stream;
   const u64 P = ctx->n_pairs;
   const bool PR = enc_pred != nullptr || dec_pred != nullptr;
   if (PR && tn.block > 256) tn.block = 256;  // stage + weights stay within 48 KB
-  const u32 T = (u32)tn.block, W = (u32)tn.window, K = (u32)tn.tiles_per_item;
+  const u32 T = (u32)tn.block;
   tera_status st = ensure_records(ctx, ctx->cap_records, s);
   if (st != TERA_OK) return st;
-  if ((st = ensure_batched(ctx, T, W)) != TERA_OK) return st;
+  if ((st = ensure_batched(ctx)) != TERA_OK) return st;
+  if (!ctx->pair_info) return TERA_EINVAL;  // allocated with the context
 
   EncArgs E;
   E.rec = rec_arena;
@@ -368,8 +1031,8 @@ static tera_status batched_impl(
   E.unit_off = nullptr;
   E.units_total = nullptr;
   E.unit_pair = nullptr;
-  E.unit_sum = ctx->unit_sum;
-  E.unit_base = ctx->unit_base;
+  E.unit_sum = nullptr;
+  E.unit_base = nullptr;
   E.info = ctx->pair_info;
   E.slot_src = ctx->slot_src;
   E.matched = ctx->matched;
@@ -393,8 +1056,8 @@ static tera_status batched_impl(
   D.unit_off = nullptr;
   D.units_total = nullptr;
   D.unit_pair = nullptr;
-  D.unit_sum = ctx->b_unit_sum;
-  D.unit_base = ctx->b_unit_base;
+  D.unit_sum = nullptr;
+  D.unit_base = nullptr;
   D.info = ctx->pair_info + 8 * P;
   D.p0 = 0;
   D.p1 = (u32)P;
@@ -402,70 +1065,44 @@ static tera_status batched_impl(
   D.st = ctx->d_status;
 
   BatchArgs B;
-  B.items = ctx->b_items;
-  B.n_items = ctx->b_scalars + 0;
+  B.n_pairs = P;
   B.ticket = ctx->b_scalars + 1;
-  B.done = ctx->b_done;
-  B.need = ctx->b_need;
-  B.enc_uoff = ctx->b_enc_uoff;
-  B.dec_uoff = ctx->b_dec_uoff;
+  B.ptot = ctx->b_ptot;
   B.abort = reinterpret_cast<u32*>(ctx->b_scalars + 2);
 
-  int enc_cells = 0, dec_cells = 0;
   if (PR) {
     if ((st = ensure_pred(ctx)) != TERA_OK) return st;
-    E.pr.unit_res = ctx->unit_res;
     const u64 cwords = 2 * (2 * ctx->cap_records + 2 * P);
     if (enc_pred) {
       if ((enc_pred->hist_prev != nullptr) != (ref_prev != nullptr)) return TERA_EINVAL;
       fill_pred(ctx, &E.pr, enc_pred, ctx->cseg_enc);
       E.pr.samples = enc_pred->samples;
       E.pr.allow_residual = enc_pred->allow_residual;
-      if (E.pr.hist) {
-        enc_cells = 1;
-        cudaMemsetAsync(ctx->cseg_enc, 0, sizeof(u64) * cwords, s);
-      }
+      if (E.pr.hist) cudaMemsetAsync(ctx->cseg_enc, 0, sizeof(u64) * cwords, s);
     }
     if (dec_pred) {
       if ((dec_pred->hist_prev != nullptr) != (recv_prev != nullptr)) return TERA_EINVAL;
       fill_pred(ctx, &D.pr, dec_pred, ctx->cseg_dec);
-      if (D.pr.hist) {
-        dec_cells = 1;
-        cudaMemsetAsync(ctx->cseg_dec, 0, sizeof(u64) * cwords, s);
-      }
+      if (D.pr.hist) cudaMemsetAsync(ctx->cseg_dec, 0, sizeof(u64) * cwords, s);
     }
   }
-  const u64 n_windows = (P + W - 1) / W;
-  cudaMemsetAsync(ctx->b_done, 0, sizeof(u32) * P * PH_COUNT, s);
+  cudaMemsetAsync(ctx->b_ptot, 0, sizeof(u64) * P * PT_COUNT, s);
   prof_begin(ctx, s);
-  bat_setup_kernel<<<1, 1024, 0, s>>>(E, D, B, P, mode, T, K, enc_cells, dec_cells,
-                                      reinterpret_cast<u64*>(wire_off),
+  bat_setup_kernel<<<1, 1024, 0, s>>>(E, D, B, P, mode, reinterpret_cast<u64*>(wire_off),
                                       wire_capacity, ctx->cap_records, recv_capacity_units,
-                                      ctx->b_units_cap < ctx->cap_units ? ctx->b_units_cap
-                                                                        : ctx->cap_units,
-                                      ctx->b_need, ctx->b_enc_uoff,
-                                      ctx->b_dec_uoff, ctx->d_epoch);
+                                      ctx->d_epoch);
   if ((st = check_launch(ctx, "bat_setup_kernel", s)) != TERA_OK) return st;
-  const unsigned wthreads = W < 32 ? 32u : ((W + 31) / 32) * 32;
-  prof_begin(ctx, s);
-  bat_window_count_kernel<<<(unsigned)n_windows, wthreads, 0, s>>>(ctx->b_need, P, W,
-                                                                    ctx->b_win_total);
-  if ((st = check_launch(ctx, "bat_window_count_kernel", s)) != TERA_OK) return st;
-  if ((st = scan_u32(ctx, ctx->b_win_total, ctx->b_win_base, nullptr, n_windows, s)) != TERA_OK)
-    return st;
-  prof_begin(ctx, s);
-  bat_window_fill_kernel<<<(unsigned)n_windows, wthreads, 0, s>>>(
-      ctx->b_need, P, W, ctx->b_win_base, n_windows, ctx->b_items, ctx->b_scalars + 0,
-      reinterpret_cast<const u32*>(ctx->b_scalars + 2));
-  if ((st = check_launch(ctx, "bat_window_fill_kernel", s)) != TERA_OK) return st;
+  const int c = tn.ctas_per_sm;
+  const u32 want = (u32)tn.table_records;
   if (PR) {
-    if (T == 128) return launch_persistent<128, true>(ctx, E, D, B, tn.ctas_per_sm, K, s);
-    return launch_persistent<256, true>(ctx, E, D, B, tn.ctas_per_sm, K, s);
+    if (T == 128) return launch_persistent<128, true>(ctx, E, D, B, c, want, s);
+    return launch_persistent<256, true>(ctx, E, D, B, c, want, s);
   }
   switch (T) {
-    case 128: return launch_persistent<128, false>(ctx, E, D, B, tn.ctas_per_sm, K, s);
-    case 512: return launch_persistent<512, false>(ctx, E, D, B, tn.ctas_per_sm, K, s);
-    default: return launch_persistent<256, false>(ctx, E, D, B, tn.ctas_per_sm, K, s);
+    case 128: return launch_persistent<128, false>(ctx, E, D, B, c, want, s);
+    case 256: return launch_persistent<256, false>(ctx, E, D, B, c, want, s);
+    case 512: return launch_persistent<512, false>(ctx, E, D, B, c, want, s);
+    default: return launch_persistent<1024, false>(ctx, E, D, B, c, want, s);
   }
 }
 

@@ -98,7 +98,7 @@ struct EncArgs {
   u32* slot_src;
   u32* matched;
   uint8_t* reset;
-  u64* seg;
+  U64x2* seg;              // per-pair hash segments of the message ids
   const u64* msg_id;
   const u32* epoch;
   u32 p0, p1;
@@ -318,22 +318,57 @@ __device__ __forceinline__ void load_mlp(float* sW, const float* params) {
   __syncthreads();
 }
 
-// Record index (global) of the message record of pair p with this id, or
-// kNoMatch; probes pair p's hash segment, comparing ids in record order.
+// Hash entry of a pair's segment: a = tag (epoch << 32 | record index in the
+// pair), b = the record's id.  An entry whose tag carries another epoch is
+// empty for this iteration, so the segments never need clearing.
+//
+// Insert: claim the first empty entry on the probe sequence with a CAS of the
+// tag, then store the id.  Lookups run only after every insert of the pair
+// has finished (a later kernel, or a later phase of the batched kernel).
 template <bool CG>
-__device__ __forceinline__ u32 seg_lookup(const u64* __restrict__ seg,
-                                          const u64* __restrict__ msg_id, u32 epoch, u32 p,
-                                          u64 g_lo, u64 m, u64 id) {
-  const u64 base = seg_base(g_lo, p), size = seg_size(m);
-  u64 i = seg_start(id, size);
+__device__ __forceinline__ void seg_insert_from(U64x2* seg, u64 base, u64 size, u64 id, u64 tag,
+                                                u32 epoch, u64 i) {
   for (u64 probe = 0; probe < size; ++probe) {
-    const u64 e = ldx<CG>(seg + base + i);
-    if ((u32)(e >> 32) != epoch) return kNoMatch;
-    const u64 g = g_lo + (u32)e;
-    if (msg_id[g] == id) return (u32)g;
+    U64x2* e = seg + base + i;
+    u64 cur = ldx<CG>(&e->a);
+    while ((u32)(cur >> 32) != epoch) {  // empty for this iteration: claim it
+      const u64 prev = atomicCAS(&e->a, cur, tag);
+      if (prev == cur) {
+        e->b = id;
+        return;
+      }
+      cur = prev;
+    }
+    i = (i + 1 == size) ? 0 : i + 1;
+  }
+}
+
+template <bool CG>
+__device__ __forceinline__ void seg_insert(U64x2* seg, u64 base, u64 size, u64 id, u64 tag,
+                                           u32 epoch) {
+  seg_insert_from<CG>(seg, base, size, id, tag, epoch, seg_start(id, size));
+}
+
+// Record index (global) of the message record with this id, probing from
+// entry i of the segment [base, base + size), or kNoMatch.
+template <bool CG>
+__device__ __forceinline__ u32 seg_lookup_from(const U64x2* __restrict__ seg, u32 epoch, u64 base,
+                                               u64 size, u64 g_lo, u64 id, u64 i) {
+  for (u64 probe = 0; probe < size; ++probe) {
+    const U64x2 e = ldx<CG>(seg + base + i);
+    if ((u32)(e.a >> 32) != epoch) return kNoMatch;
+    if (e.b == id) return (u32)(g_lo + (u32)e.a);
     i = (i + 1 == size) ? 0 : i + 1;
   }
   return kNoMatch;
+}
+
+// The same for pair p (one 16-byte load per probe compares the stored id).
+template <bool CG>
+__device__ __forceinline__ u32 seg_lookup(const U64x2* __restrict__ seg, u32 epoch, u32 p,
+                                          u64 g_lo, u64 m, u64 id) {
+  const u64 size = seg_size(m);
+  return seg_lookup_from<CG>(seg, epoch, seg_base(g_lo, p), size, g_lo, id, seg_start(id, size));
 }
 
 // ---------------- encode ----------------
@@ -348,18 +383,7 @@ __device__ __forceinline__ void enc_build_unit(const EncArgs& A, u32 p, u64 loca
   if (k >= m) return;
   const u64 g_lo = A.pair_off[p];
   const u64 id = A.msg_id[g_lo + k];
-  const u64 base = seg_base(g_lo, p), size = seg_size(m);
-  const u64 mine = ((u64)epoch << 32) | k;
-  u64 i = seg_start(id, size);
-  for (u64 probe = 0; probe < size; ++probe) {
-    u64 cur = ldx<CG>(A.seg + base + i);
-    while ((u32)(cur >> 32) != epoch) {  // empty for this iteration: claim it
-      const u64 prev = atomicCAS(&A.seg[base + i], cur, mine);
-      if (prev == cur) return;
-      cur = prev;
-    }
-    i = (i + 1 == size) ? 0 : i + 1;
-  }
+  seg_insert<CG>(A.seg, seg_base(g_lo, p), seg_size(m), id, ((u64)epoch << 32) | k, epoch);
 }
 
 // Slot unit: find the message record with the slot's id, write the slot's
@@ -378,7 +402,7 @@ __device__ __forceinline__ void enc_match_unit(const EncArgs& A, u32 p, u64 loca
     }
     const u64 g_lo = A.pair_off[p];
     const Rec R = load_rec(A.ref + (A.ref_off[p] + p + 1 + j) * kRecBytes);
-    u32 g = seg_lookup<CG>(A.seg, A.msg_id, epoch, p, g_lo, pi[PI_M], R.w[0]);
+    u32 g = seg_lookup<CG>(A.seg, epoch, p, g_lo, pi[PI_M], R.w[0]);
     u32 code;
     if (g != kNoMatch) {
       if (atomicExch(&A.matched[g], epoch) == epoch) latch(A.st, TERA_EINVAL);  // duplicate id
@@ -460,7 +484,7 @@ __device__ __forceinline__ void enc_new_unit(const EncArgs& A, u32 p, u64 local,
     if (ldx<CG>(A.matched + g) != epoch) {
       const Rec M = load_rec(A.rec + (g + p + 1) * kRecBytes);
       // a second record with the same id in this pair would be found instead of this one
-      if (seg_lookup<CG>(A.seg, A.msg_id, epoch, p, A.pair_off[p], m, M.w[0]) != (u32)g)
+      if (seg_lookup<CG>(A.seg, epoch, p, A.pair_off[p], m, M.w[0]) != (u32)g)
         latch(A.st, TERA_EINVAL);
       u32 b;
       rec_code(M, &b);
@@ -705,14 +729,18 @@ __device__ __forceinline__ bool check_code(u32 code, u64 e, u64 ns, bool* hole, 
   return ok;
 }
 
-// Full header check of pair p's message; writes the decode facts and returns
-// the error (0 when valid).  expect_m: when not ~0, the receive buffer size
-// the caller laid out for p, which the header's count must equal.
+// Header facts of a received message.
+struct DecHdr {
+  u64 ns, nn, nh, pay, mode;
+};
+
+// Full header check of pair p's message; fills *H and returns the error (0
+// when valid).  expect_m: when not ~0, the receive buffer size the caller
+// laid out for p, which the header's count must equal.
 template <bool CG, bool PR = false>
-__device__ __forceinline__ u32 dec_check_header(const DecArgs& A, u32 p, u64 expect_m) {
+__device__ __forceinline__ u32 dec_read_header(const DecArgs& A, u32 p, u64 expect_m, DecHdr* H) {
   const u64 avail = A.wire_off[p + 1] - A.wire_off[p];
   const u64* h = reinterpret_cast<const u64*>(A.wire + A.wire_off[p]);
-  u64* pi = A.info + (u64)p * 8;
   u32 err = 0;
   u64 ns = 0, nn = 0, nh = 0, pay = 0, mode = 0;
   if (avail < kHdrBytes) {
@@ -751,12 +779,26 @@ __device__ __forceinline__ u32 dec_check_header(const DecArgs& A, u32 p, u64 exp
         err = TERA_ECORRUPT;
     }
   }
-  pi[DI_NS] = ns;
-  pi[DI_NN] = nn;
-  pi[DI_NH] = nh;
-  pi[DI_PAY] = pay;
+  H->ns = ns;
+  H->nn = nn;
+  H->nh = nh;
+  H->pay = pay;
+  H->mode = mode;
+  return err;
+}
+
+// dec_read_header, with the facts stored in the pair's decode info.
+template <bool CG, bool PR = false>
+__device__ __forceinline__ u32 dec_check_header(const DecArgs& A, u32 p, u64 expect_m) {
+  DecHdr H;
+  const u32 err = dec_read_header<CG, PR>(A, p, expect_m, &H);
+  u64* pi = A.info + (u64)p * 8;
+  pi[DI_NS] = H.ns;
+  pi[DI_NN] = H.nn;
+  pi[DI_NH] = H.nh;
+  pi[DI_PAY] = H.pay;
   pi[DI_OK] = err ? 0 : 1;
-  pi[DI_MODE] = mode;
+  pi[DI_MODE] = H.mode;
   return err;
 }
 

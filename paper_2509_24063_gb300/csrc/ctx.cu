@@ -264,7 +264,7 @@ tera_status ensure_records(tera_ctx* ctx, uint64_t cap, cudaStream_t s) {
   if ((st = alloc_dev(ctx->msg_id, c)) != TERA_OK) return st;
   if ((st = alloc_dev(ctx->seg, 2 * c + 2 * ctx->n_pairs)) != TERA_OK) return st;
   // epoch 0 is never current, so zeroed segments and flags are empty
-  cudaMemset(ctx->seg, 0, sizeof(u64) * (2 * c + 2 * ctx->n_pairs));
+  cudaMemset(ctx->seg, 0, sizeof(U64x2) * (2 * c + 2 * ctx->n_pairs));
   cudaMemset(ctx->matched, 0, sizeof(u32) * c);
   ctx->cap_records = c;
   return ensure_scan_part(ctx, (u64)kRadix * tiles + 1);
@@ -283,35 +283,14 @@ tera_status ensure_units(tera_ctx* ctx, uint64_t cap, cudaStream_t s) {
   return TERA_OK;
 }
 
-tera_status ensure_batched(tera_ctx* ctx, u32 T, u32 W) {
-  const u64 P = ctx->n_pairs;
-  const u64 cap = ctx->cap_records;
-  // units: slot + message tiles per pair (encode), entry tiles (decode)
-  tera_status st = ensure_units(ctx, 2 * (cap / T) + 2 * P + 16, 0);
-  if (st != TERA_OK) return st;
-  const u64 items = 11 * (cap / T) + 16 * P + 64;
-  const u64 windows = (P + W - 1) / W + 1;
-  if (ctx->b_items && items <= ctx->b_items_cap && windows <= ctx->b_windows_cap &&
-      ctx->b_unit_sum && ctx->b_units_cap >= ctx->cap_units)
-    return TERA_OK;
+tera_status ensure_batched(tera_ctx* ctx) {
+  if (ctx->b_ptot) return TERA_OK;
   cudaDeviceSynchronize();
-  const u64 ic = items + items / 4;
-  const u64 wc = windows < (P + 1) ? (P + 1) : windows;
-  if ((st = alloc_dev(ctx->b_items, ic)) != TERA_OK) return st;
-  if ((st = alloc_dev(ctx->b_done, P * kBatchPhases)) != TERA_OK) return st;
-  if ((st = alloc_dev(ctx->b_need, P * kBatchPhases)) != TERA_OK) return st;
-  if ((st = alloc_dev(ctx->b_enc_uoff, P + 1)) != TERA_OK) return st;
-  if ((st = alloc_dev(ctx->b_dec_uoff, P + 1)) != TERA_OK) return st;
-  if ((st = alloc_dev(ctx->b_win_total, wc)) != TERA_OK) return st;
-  if ((st = alloc_dev(ctx->b_win_base, wc + 1)) != TERA_OK) return st;
+  tera_status st;
+  if ((st = alloc_dev(ctx->b_ptot, ctx->n_pairs * 4)) != TERA_OK) return st;
   if ((st = alloc_dev(ctx->b_scalars, 4)) != TERA_OK) return st;
-  if ((st = alloc_dev(ctx->b_unit_sum, ctx->cap_units)) != TERA_OK) return st;
-  if ((st = alloc_dev(ctx->b_unit_base, ctx->cap_units)) != TERA_OK) return st;
   cudaMemset(ctx->b_scalars, 0, 4 * sizeof(u64));
-  ctx->b_items_cap = ic;
-  ctx->b_windows_cap = wc;
-  ctx->b_units_cap = ctx->cap_units;
-  return ensure_scan_part(ctx, wc);
+  return TERA_OK;
 }
 
 tera_status ensure_pred(tera_ctx* ctx) {
@@ -442,16 +421,8 @@ tera_status tera_ctx_destroy(tera_ctx* c) {
   free_dev(c->pair_info);
   free_dev(c->d_units_total);
   free_dev(c->d_stats);
-  free_dev(c->b_items);
-  free_dev(c->b_done);
-  free_dev(c->b_need);
-  free_dev(c->b_enc_uoff);
-  free_dev(c->b_dec_uoff);
-  free_dev(c->b_win_total);
-  free_dev(c->b_win_base);
   free_dev(c->b_scalars);
-  free_dev(c->b_unit_sum);
-  free_dev(c->b_unit_base);
+  free_dev(c->b_ptot);
   free_dev(c->cseg_enc);
   free_dev(c->cseg_dec);
   free_dev(c->pscr);

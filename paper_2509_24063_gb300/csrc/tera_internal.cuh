@@ -18,7 +18,6 @@ constexpr u32 kRecBytes = 64u;
 constexpr u32 kHdrBytes = 64u;
 constexpr int kMaxAxis = 256;
 constexpr u32 kNoMatch = 0xFFFFFFFFu;
-constexpr int kBatchPhases = 11;  // phases of the batched codec's work list
 
 // Agents per classification tile and records per codec tile.
 constexpr int kClassifyThreads = 256;
@@ -265,7 +264,7 @@ struct tera_ctx {
   tera::u64* d_total;       // [4] scalars: total records, ...
 
   // per-pair hash segments + codec scratch
-  tera::u64* seg;        // [2 cap_records + 2 P]
+  tera::U64x2* seg;      // [2 cap_records + 2 P] hash entries {tag, id}
   tera::u64* msg_id;     // [cap_records] id of every packed record, in record order
   uint32_t* matched;     // [cap_records] epoch of the iteration in which a slot took the record
   uint32_t* slot_src;  // [cap_records]
@@ -279,10 +278,6 @@ struct tera_ctx {
   void* prof;  // per-kernel CUDA-event timing (ctx.cu)
   tera::DevStats* d_stats;
 
-  // batched codec (batched.cu)
-  uint64_t b_items_cap;
-  uint64_t b_windows_cap;
-  uint64_t b_units_cap;
 
   // learned predictor (cell counts of both sides, per-slot predictions)
   uint64_t ncell[3];
@@ -294,16 +289,9 @@ struct tera_ctx {
   uint64_t unit_res_cap;
   float* mlp_scratch;       // training: compacted samples + gradient partials
   uint64_t mlp_scratch_cap;
-  tera::u64* b_items;
-  uint32_t* b_done;
-  uint32_t* b_need;
-  tera::u64* b_enc_uoff;
-  tera::u64* b_dec_uoff;
-  uint32_t* b_win_total;
-  tera::u64* b_win_base;
-  tera::u64* b_scalars;  // [0] items, [1] ticket, [2] abort flag
-  tera::U64x2* b_unit_sum;
-  tera::U64x2* b_unit_base;
+  // batched codec (batched.cu)
+  tera::u64* b_scalars;  // [1] pair ticket, [2] abort flag
+  tera::u64* b_ptot;     // [P * 4] per-pair totals of the match step
 };
 
 namespace tera {
@@ -321,6 +309,6 @@ int grid_for(tera_ctx* ctx, int blocks_per_sm);
 tera_status launch_unit_map(tera_ctx* ctx, u32 p0, u64 npr, cudaStream_t s);
 // Scratch of the learned predictor for the current record capacity.
 tera_status ensure_pred(tera_ctx* ctx);
-// Scratch of the batched codec for tiles of T entries and windows of W pairs.
-tera_status ensure_batched(tera_ctx* ctx, u32 T, u32 W);
+// Scratch of the batched codec.
+tera_status ensure_batched(tera_ctx* ctx);
 }  // namespace tera
