@@ -144,9 +144,9 @@ tera_status tera_partition(tera_ctx* ctx, const tera_soa* soa, tera_partition_ou
 
 /* Step a2 (Sec. 2.2.1 "Serialization"): write the TAIO buffers of pairs
  * [pair_begin, pair_end) into rec_arena (arena_units 64-byte units), laid out
- * with out->pair_off.  Also indexes every packed record by (pair, id) for
- * tera_delta_encode; call it for every pair range that will be encoded,
- * after tera_partition of the same iteration. */
+ * with out->pair_off.  Call it after tera_partition of the same iteration on
+ * this context (the whole pair range is packed in agent order from the
+ * partition's entry list). */
 tera_status tera_pack(tera_ctx* ctx, const tera_soa* soa, const tera_partition_out* part,
                       uint32_t pair_begin, uint32_t pair_end, uint8_t* rec_arena,
                       uint64_t arena_units, void* stream);
@@ -296,8 +296,8 @@ typedef struct {
  * is the iteration's pair layout (recv_off = pair_off); every message header's
  * record count is checked against it (TERA_ECORRUPT otherwise).  The sender
  * reference is ref_prev/ref_off_prev, the receiver's recv_prev/recv_off_prev
- * (NULL pairs = empty references).  Must follow tera_partition and tera_pack
- * (all pairs) of the same iteration on this context.  tune == NULL uses
+ * (NULL pairs = empty references).  rec_arena is any packed arena laid out
+ * with pair_off (record ids are read from the records).  tune == NULL uses
  * {512, 2, 0, 0}.  Asynchronous, no host synchronization (graph-capturable once
  * scratch is reserved); device errors are latched in the status word. */
 tera_status tera_codec_batched(tera_ctx* ctx, const uint8_t* rec_arena, const uint64_t* pair_off,

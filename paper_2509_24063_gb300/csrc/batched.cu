@@ -9,7 +9,7 @@
 //           the message records the slots take.  A pair with at most
 //           table_records records does this in a shared-memory hash table
 //           (u32 entries: (record + 1) << 8 | 8-bit fingerprint, ids compared
-//           against the message's id array); larger pairs (and the predictor
+//           against word 0 of the message's records); larger pairs (and the predictor
 //           path) use the pair's global hash segment.
 //   slots   difference, code, payload and new-reference record of every slot
 //           (tiles of T slots; payload positions from a running prefix kept
@@ -151,7 +151,7 @@ __device__ __forceinline__ void smem_build(const EncArgs& A, u32 p, u64 m, const
 #pragma unroll
     for (u32 i = 0; i < kIlp; ++i) {
       const u64 k = k0 + (u64)i * T + threadIdx.x;
-      id[i] = k < m ? A.msg_id[g_lo + k] : 0;
+      id[i] = k < m ? msg_id(A, p, g_lo + k) : 0;
     }
 #pragma unroll
     for (u32 i = 0; i < kIlp; ++i) {
@@ -163,7 +163,7 @@ __device__ __forceinline__ void smem_build(const EncArgs& A, u32 p, u64 m, const
       for (u32 probe = 0; probe <= tb.mask; ++probe) {
         const u32 old = atomicCAS(&tb.tbl[at], 0u, e);
         if (old == 0u) break;
-        if ((old & 0xFFu) == fp && A.msg_id[g_lo + (old >> 8) - 1] == id[i]) {
+        if ((old & 0xFFu) == fp && msg_id(A, p, g_lo + (old >> 8) - 1) == id[i]) {
           latch(A.st, TERA_EINVAL);  // ids must be unique within a message
           break;
         }
@@ -174,12 +174,12 @@ __device__ __forceinline__ void smem_build(const EncArgs& A, u32 p, u64 m, const
 }
 
 // Message record (index in the pair) with this id, probing from `at`; kNoMatch if none.
-__device__ __forceinline__ u32 smem_find(const EncArgs& A, const SmemTable& tb, u64 g_lo, u64 id,
-                                         u32 fp, u32 at) {
+__device__ __forceinline__ u32 smem_find(const EncArgs& A, u32 p, const SmemTable& tb, u64 g_lo,
+                                         u64 id, u32 fp, u32 at) {
   for (u32 probe = 0; probe <= tb.mask; ++probe) {
     const u32 e = tb.tbl[at];
     if (e == 0u) return kNoMatch;
-    if ((e & 0xFFu) == fp && A.msg_id[g_lo + (e >> 8) - 1] == id) return (e >> 8) - 1;
+    if ((e & 0xFFu) == fp && msg_id(A, p, g_lo + (e >> 8) - 1) == id) return (e >> 8) - 1;
     at = (at + 1) & tb.mask;
   }
   return kNoMatch;
@@ -221,14 +221,14 @@ __device__ __forceinline__ u32 smem_match(const EncArgs& A, u32 p, u64 r, const 
     }
     u64 cid[kIlp];
 #pragma unroll
-    for (u32 i = 0; i < kIlp; ++i) cid[i] = cand[i] != kNoMatch ? A.msg_id[g_lo + cand[i]] : 0;
+    for (u32 i = 0; i < kIlp; ++i) cid[i] = cand[i] != kNoMatch ? msg_id(A, p, g_lo + cand[i]) : 0;
 #pragma unroll
     for (u32 i = 0; i < kIlp; ++i) {
       const u64 j = j0 + (u64)i * T + threadIdx.x;
       if (j >= r) continue;
       u32 k = cand[i];
       if (k != kNoMatch && cid[i] != id[i])  // fingerprint collision: keep probing
-        k = smem_find(A, tb, g_lo, id[i], fp[i], (at[i] + 1) & tb.mask);
+        k = smem_find(A, p, tb, g_lo, id[i], fp[i], (at[i] + 1) & tb.mask);
       if (k != kNoMatch) {
         const u32 bit = 1u << (k & 31u);
         if (atomicOr(&tb.bits[k >> 5], bit) & bit) {
@@ -257,7 +257,7 @@ __device__ __forceinline__ void bat_build(const EncArgs& A, u32 p, u64 tile, u32
   for (u32 i = 0; i < kIlp; ++i) {
     const u64 k = tile * T * kIlp + (u64)i * T + threadIdx.x;
     live[i] = k < m;
-    id[i] = live[i] ? A.msg_id[g_lo + k] : 0;
+    id[i] = live[i] ? msg_id(A, p, g_lo + k) : 0;
   }
   // first probe of every entry: one load each, then one CAS each
 #pragma unroll
@@ -1038,7 +1038,6 @@ static tera_status batched_impl(
   E.matched = ctx->matched;
   E.reset = ctx->d_reset;
   E.seg = ctx->seg;
-  E.msg_id = ctx->msg_id;
   E.epoch = ctx->d_epoch;
   E.p0 = 0;
   E.p1 = (u32)P;

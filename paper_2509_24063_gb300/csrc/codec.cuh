@@ -99,7 +99,6 @@ struct EncArgs {
   u32* matched;
   uint8_t* reset;
   U64x2* seg;              // per-pair hash segments of the message ids
-  const u64* msg_id;
   const u32* epoch;
   u32 p0, p1;
   u32 class_id;
@@ -371,6 +370,12 @@ __device__ __forceinline__ u32 seg_lookup(const U64x2* __restrict__ seg, u32 epo
   return seg_lookup_from<CG>(seg, epoch, seg_base(g_lo, p), size, g_lo, id, seg_start(id, size));
 }
 
+// Id of message record g (global record index) of pair p: word 0 of the
+// record in the packed arena.
+__device__ __forceinline__ u64 msg_id(const EncArgs& A, u32 p, u64 g) {
+  return *reinterpret_cast<const u64*>(A.rec + (g + p + 1) * kRecBytes);
+}
+
 // ---------------- encode ----------------
 
 // Message unit: index every record of the pair by id in the pair's segment.
@@ -382,7 +387,7 @@ __device__ __forceinline__ void enc_build_unit(const EncArgs& A, u32 p, u64 loca
   const u64 k = (local - nst) * T + threadIdx.x;
   if (k >= m) return;
   const u64 g_lo = A.pair_off[p];
-  const u64 id = A.msg_id[g_lo + k];
+  const u64 id = msg_id(A, p, g_lo + k);
   seg_insert<CG>(A.seg, seg_base(g_lo, p), seg_size(m), id, ((u64)epoch << 32) | k, epoch);
 }
 

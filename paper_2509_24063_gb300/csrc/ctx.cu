@@ -255,13 +255,16 @@ tera_status ensure_records(tera_ctx* ctx, uint64_t cap, cudaStream_t s) {
   u64 c = cap < 1024 ? 1024 : cap;
   tera_status st;
   if ((st = alloc_dev(ctx->keys_a, c)) != TERA_OK) return st;
+  if ((st = alloc_dev(ctx->ent_agent, c)) != TERA_OK) return st;
+  if ((st = alloc_dev(ctx->ent_dest, c)) != TERA_OK) return st;
   if ((st = alloc_dev(ctx->keys_b, c)) != TERA_OK) return st;
+  if ((st = alloc_dev(ctx->keys_c, c)) != TERA_OK) return st;
   if ((st = alloc_dev(ctx->vals_b, c)) != TERA_OK) return st;
+  if ((st = alloc_dev(ctx->vals_c, c)) != TERA_OK) return st;
   u64 tiles = (c + kSortTile - 1) / kSortTile;
   if ((st = alloc_dev(ctx->rs_hist, (u64)kRadix * tiles + 1)) != TERA_OK) return st;
   if ((st = alloc_dev(ctx->matched, c)) != TERA_OK) return st;
   if ((st = alloc_dev(ctx->slot_src, c)) != TERA_OK) return st;
-  if ((st = alloc_dev(ctx->msg_id, c)) != TERA_OK) return st;
   if ((st = alloc_dev(ctx->seg, 2 * c + 2 * ctx->n_pairs)) != TERA_OK) return st;
   // epoch 0 is never current, so zeroed segments and flags are empty
   cudaMemset(ctx->seg, 0, sizeof(U64x2) * (2 * c + 2 * ctx->n_pairs));
@@ -405,13 +408,16 @@ tera_status tera_ctx_destroy(tera_ctx* c) {
   free_dev(c->tile_cnt);
   free_dev(c->tile_base);
   free_dev(c->keys_a);
+  free_dev(c->ent_agent);
+  free_dev(c->ent_dest);
   free_dev(c->keys_b);
+  free_dev(c->keys_c);
   free_dev(c->vals_b);
+  free_dev(c->vals_c);
   free_dev(c->rs_hist);
   free_dev(c->scan_part);
   free_dev(c->d_total);
   free_dev(c->seg);
-  free_dev(c->msg_id);
   free_dev(c->matched);
   free_dev(c->slot_src);
   free_dev(c->unit_off);

@@ -217,7 +217,6 @@ static tera_status encode_impl(tera_ctx* ctx, const uint8_t* rec_arena, const ui
   A.matched = ctx->matched;
   A.reset = ctx->d_reset;
   A.seg = ctx->seg;
-  A.msg_id = ctx->msg_id;
   A.epoch = ctx->d_epoch;
   A.p0 = pair_begin;
   A.p1 = pair_end;

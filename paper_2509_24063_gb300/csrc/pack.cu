@@ -3,10 +3,16 @@
 // class identity is written once in the buffer header.  The receiver can use
 // the buffer in place.
 //
-// pack_kernel: eight adjacent threads build one record (each gathers one of
-// the eight struct-of-arrays columns and writes one word), so a record leaves
-// as one 64-byte segment.  The ids are also written in record order for the
-// matching step.
+// pack_entries_kernel (all pairs): one thread per (agent, pair) entry, in
+// agent order, as tera_partition emitted them: consecutive threads read
+// nearby agents, so the column reads sweep the state arrays instead of
+// jumping, and each record leaves as one 64-byte store to its place
+// (entry -> record index from the partition's sort).
+//
+// pack_kernel (a range of pairs): eight adjacent threads build one record
+// (each gathers one of the eight struct-of-arrays columns and writes one
+// word), so a record leaves as one 64-byte segment.
+
 #include "tera_internal.cuh"
 
 using namespace tera;
@@ -36,7 +42,7 @@ __device__ __forceinline__ const u64* column(const SoaPtrs& s, u32 w) {
 __global__ void __launch_bounds__(256)
     pack_kernel(SoaPtrs soa, const u32* __restrict__ pair_idx, const u64* __restrict__ pair_off,
                 const u32* __restrict__ rec_pair, u32 p0, u32 p1, uint8_t* __restrict__ arena,
-                u64 arena_units, u32 class_id, u64* __restrict__ msg_id, DevStatus* st) {
+                u64 arena_units, u32 class_id, DevStatus* st) {
   const u64 g_lo = pair_off[p0], g_hi = pair_off[p1];
   if (g_hi + p1 > arena_units) {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -61,7 +67,38 @@ __global__ void __launch_bounds__(256)
     const u32 i = pair_idx[g];
     const u64 v = col[i];
     reinterpret_cast<u64*>(arena + (g + p + 1) * kRecBytes)[w] = v;
-    if (w == 0) msg_id[g] = v;  // ids in record order, for the matching step
+  }
+}
+
+
+// One thread per entry e of the last partition (agent order).
+__global__ void __launch_bounds__(256)
+    pack_entries_kernel(SoaPtrs soa, const u32* __restrict__ ent_key,
+                        const u32* __restrict__ ent_agent, const u32* __restrict__ ent_dest,
+                        const u64* __restrict__ pair_off, u64 P, uint8_t* __restrict__ arena,
+                        u64 arena_units, u32 class_id, DevStatus* st) {
+  const u64 E = pair_off[P];
+  if (E + P > arena_units) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      latch(st, TERA_ECAPACITY);
+      need(st, E + P);
+    }
+    return;
+  }
+  const u64 stride = (u64)gridDim.x * blockDim.x;
+  const u64 tid = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+  for (u64 p = tid; p < P; p += stride) {
+    const u64 m = pair_off[p + 1] - pair_off[p];
+    write_taio_header(arena + (pair_off[p] + p) * kRecBytes, class_id, (u32)p, m);
+  }
+  for (u64 e = tid; e < E; e += stride) {
+    const u32 a = ent_agent[e];
+    const u64 g = ent_dest[e];
+    const u64 p = ent_key[e];
+    Rec R;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) R.w[w] = soa.col[w][a];
+    store_rec(arena + (g + p + 1) * kRecBytes, R);
   }
 }
 
@@ -96,9 +133,17 @@ extern "C" tera_status tera_pack(tera_ctx* ctx, const tera_soa* soa, const tera_
   u64 maxg = (u64)grid_for(ctx, 8);
   unsigned blocks = (unsigned)(est < maxg ? est : maxg);
   if (!ctx->rec_pair) return TERA_EINVAL;  // tera_partition has not run on this context
+  if (pair_begin == 0 && pair_end == ctx->n_pairs) {
+    prof_begin(ctx, s);
+    pack_entries_kernel<<<(unsigned)grid_for(ctx, 8), 256, 0, s>>>(
+        p, ctx->keys_a, ctx->ent_agent, ctx->ent_dest,
+        reinterpret_cast<const u64*>(part->pair_off), ctx->n_pairs, rec_arena, arena_units,
+        ctx->class_id, ctx->d_status);
+    return check_launch(ctx, "pack_entries_kernel", s);
+  }
   prof_begin(ctx, s);
   pack_kernel<<<blocks, 256, 0, s>>>(p, part->pair_idx, reinterpret_cast<const u64*>(part->pair_off),
                                      ctx->rec_pair, pair_begin, pair_end, rec_arena, arena_units,
-                                     ctx->class_id, ctx->msg_id, ctx->d_status);
+                                     ctx->class_id, ctx->d_status);
   return check_launch(ctx, "pack_kernel", s);
 }

@@ -8,8 +8,10 @@
 //   emit_kernel      stable compaction of the entries in agent order
 //                    (block scan over each tile, tile bases from a scan)
 //   rs_hist_kernel / rs_scatter_kernel
-//                    stable LSD radix sort of the entries by pair index, so
-//                    each pair's list keeps ascending agent order
+//                    stable LSD radix sort of the entry indices by pair
+//                    index, so each pair's list keeps ascending agent order;
+//                    the last pass writes the agent of every record and the
+//                    record index of every entry (pack reads in agent order)
 //   pair_off_kernel  per-pair counts and offsets from the sorted keys
 #include "tera_internal.cuh"
 
@@ -199,7 +201,7 @@ __global__ void __launch_bounds__(kClassifyThreads)
         int b = __ffs(mm) - 1;
         mm &= mm - 1;
         keys[pos] = (u32)o[q] * 27u + (u32)b;
-        vals[pos] = (u32)(a0 + q);
+        vals[pos] = (u32)(a0 + q);  // the entry's agent
         ++pos;
       }
     }
@@ -235,9 +237,14 @@ __global__ void __launch_bounds__(kSortThreads)
 // Stable scatter of one sort tile.  The tile is consumed in kSortPerThread
 // rounds of kSortThreads consecutive entries (entry r*256 + t to thread t);
 // inside a round, equal digits are ranked by warp (match_any) and warp index.
+// The values are entry indices: vals_in == nullptr on the first pass (entry i
+// is at position i).  On the last pass (agent != nullptr) the outputs are the
+// record's agent (vals_out[pos] = agent[e]) and the entry's record index
+// (dest[e] = pos).
 __global__ void __launch_bounds__(kSortThreads)
     rs_scatter_kernel(const u32* __restrict__ keys_in, const u32* __restrict__ vals_in,
                       u32* __restrict__ keys_out, u32* __restrict__ vals_out,
+                      const u32* __restrict__ agent, u32* __restrict__ dest,
                       const u64* __restrict__ total_ptr, u64 cap, u32 shift, u32 radix,
                       const u32* __restrict__ hist_scan, u32 n_tiles) {
   constexpr int kWarps = kSortThreads / 32;
@@ -258,7 +265,7 @@ __global__ void __launch_bounds__(kSortThreads)
     if (t0 + (u64)k * kSortThreads >= E) break;  // block-uniform
     const bool live = i < E;
     u32 key = live ? keys_in[i] : 0u;
-    u32 val = live ? vals_in[i] : 0u;
+    u32 val = live ? (vals_in ? vals_in[i] : (u32)i) : 0u;
     u32 d = live ? ((key >> shift) & (radix - 1)) : radix;  // sentinel digit for padding
     u32 peers = __match_any_sync(0xFFFFFFFFu, d);
     u32 rank = __popc(peers & ((1u << lane) - 1u));
@@ -277,7 +284,12 @@ __global__ void __launch_bounds__(kSortThreads)
     if (live) {
       u32 pos = base[d] + wcnt[warp][d] + rank;
       keys_out[pos] = key;
-      vals_out[pos] = val;
+      if (agent) {
+        vals_out[pos] = agent[val];
+        dest[val] = pos;
+      } else {
+        vals_out[pos] = val;
+      }
     }
     __syncthreads();
     for (u32 dd = threadIdx.x; dd < radix; dd += blockDim.x) {
@@ -354,20 +366,24 @@ extern "C" tera_status tera_partition(tera_ctx* ctx, const tera_soa* soa, tera_p
   const u32 radix = 1u << dbits;
   const u64 cap = out->idx_capacity;
   const u64* total_ptr = ctx->tile_base + tiles;
-  u32* kin = ctx->keys_a;
-  u32* vin = (passes & 1) ? ctx->vals_b : out->pair_idx;
-  u32* kout = ctx->keys_b;
-  u32* vout = (passes & 1) ? out->pair_idx : ctx->vals_b;
   if (cap > 0 || n > 0) {
     prof_begin(ctx, s);
     emit_kernel<<<(unsigned)tiles, kClassifyThreads, 0, s>>>(
-        out->owner, out->mask, n, ctx->tile_base, tiles, kin, vin ? vin : ctx->vals_b, cap,
+        out->owner, out->mask, n, ctx->tile_base, tiles, ctx->keys_a, ctx->ent_agent, cap,
         ctx->d_status);
     if ((st = check_launch(ctx, "emit_kernel", s)) != TERA_OK) return st;
   }
+  // pass k reads (kin, vin) and writes the b buffers (k even) or the c buffers;
+  // the last pass writes the sorted keys to the buffer it does not read
   const u64 sort_tiles = cap == 0 ? 1 : (cap + kSortTile - 1) / kSortTile;
+  const u32* kin = ctx->keys_a;
+  const u32* vin = nullptr;
+  u32* kfinal = passes == 1 ? ctx->keys_b : ((passes & 1) ? ctx->keys_b : ctx->keys_c);
   for (int pass = 0; pass < passes && cap > 0; ++pass) {
     const u32 shift = (u32)(pass * dbits);
+    const bool last = pass + 1 == passes;
+    u32* kout = last ? kfinal : ((pass & 1) ? ctx->keys_c : ctx->keys_b);
+    u32* vout = last ? out->pair_idx : ((pass & 1) ? ctx->vals_c : ctx->vals_b);
     prof_begin(ctx, s);
     rs_hist_kernel<<<(unsigned)sort_tiles, kSortThreads, 0, s>>>(kin, total_ptr, cap, shift, radix,
                                                                  ctx->rs_hist, (u32)sort_tiles);
@@ -377,13 +393,14 @@ extern "C" tera_status tera_partition(tera_ctx* ctx, const tera_soa* soa, tera_p
       return st;
     prof_begin(ctx, s);
     rs_scatter_kernel<<<(unsigned)sort_tiles, kSortThreads, 0, s>>>(
-        kin, vin, kout, vout, total_ptr, cap, shift, radix, ctx->rs_hist, (u32)sort_tiles);
+        kin, vin, kout, vout, last ? ctx->ent_agent : nullptr, last ? ctx->ent_dest : nullptr,
+        total_ptr, cap, shift, radix, ctx->rs_hist, (u32)sort_tiles);
     if ((st = check_launch(ctx, "rs_scatter_kernel", s)) != TERA_OK) return st;
-    u32* tk = kin; kin = kout; kout = tk;
-    u32* tv = vin; vin = vout; vout = tv;
+    kin = kout;
+    vin = vout;
   }
-  // after the loop, (kin, vin) hold the sorted entries; vin == out->pair_idx
-  ctx->rec_pair = kin;
+  // after the loop, kin holds the sorted keys and out->pair_idx the agents
+  ctx->rec_pair = const_cast<u32*>(kin);
   prof_begin(ctx, s);
   pair_off_kernel<<<(unsigned)((P + 256) / 256), 256, 0, s>>>(
       kin, total_ptr, cap, P, reinterpret_cast<u64*>(out->pair_off),

@@ -254,9 +254,15 @@ struct tera_ctx {
   uint64_t cap_records;
   uint32_t* tile_cnt;      // [tiles + 1]
   tera::u64* tile_base;     // [tiles + 1]
-  uint32_t* keys_a;        // [cap_records]
-  uint32_t* keys_b;
+  // entries (agent, pair) of the last partition in agent order, and where
+  // each went in the pair-sorted order (pack reads them in agent order)
+  uint32_t* keys_a;        // [cap_records] pair of entry e
+  uint32_t* ent_agent;     // [cap_records] agent of entry e
+  uint32_t* ent_dest;      // [cap_records] record index of entry e
+  uint32_t* keys_b;        // sort passes
+  uint32_t* keys_c;
   uint32_t* vals_b;
+  uint32_t* vals_c;
   uint32_t* rec_pair;      // pair of each record of the last partition (sorted keys)
   uint32_t* rs_hist;       // [kRadix * sort tiles]
   tera::u64* scan_part;     // partials of the generic scan
@@ -265,7 +271,6 @@ struct tera_ctx {
 
   // per-pair hash segments + codec scratch
   tera::U64x2* seg;      // [2 cap_records + 2 P] hash entries {tag, id}
-  tera::u64* msg_id;     // [cap_records] id of every packed record, in record order
   uint32_t* matched;     // [cap_records] epoch of the iteration in which a slot took the record
   uint32_t* slot_src;  // [cap_records]
   tera::u64* unit_off;  // [P + 1]
