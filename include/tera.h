@@ -298,7 +298,7 @@ typedef struct {
  * reference is ref_prev/ref_off_prev, the receiver's recv_prev/recv_off_prev
  * (NULL pairs = empty references).  rec_arena is any packed arena laid out
  * with pair_off (record ids are read from the records).  tune == NULL uses
- * {512, 2, 0, 0}.  Asynchronous, no host synchronization (graph-capturable once
+ * {256, 4, 0, 0}.  Asynchronous, no host synchronization (graph-capturable once
  * scratch is reserved); device errors are latched in the status word. */
 tera_status tera_codec_batched(tera_ctx* ctx, const uint8_t* rec_arena, const uint64_t* pair_off,
                                const uint8_t* ref_prev, const uint64_t* ref_off_prev,

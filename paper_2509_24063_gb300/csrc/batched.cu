@@ -7,10 +7,10 @@
 //
 //   match   index the message ids, look every reference slot's id up, mark
 //           the message records the slots take.  A pair with at most
-//           table_records records does this in a shared-memory hash table
-//           (u32 entries: (record + 1) << 8 | 8-bit fingerprint, ids compared
-//           against word 0 of the message's records); larger pairs (and the predictor
-//           path) use the pair's global hash segment.
+//           table_records (<= 8191) records does this in a shared-memory hash
+//           table (u16 entries: (record + 1) << 3 | 3-bit fingerprint, ids
+//           compared against word 0 of the message's records); larger pairs
+//           (and the predictor path) use the pair's global hash segment.
 //   slots   difference, code, payload and new-reference record of every slot
 //           (tiles of T slots; payload positions from a running prefix kept
 //           on chip; the wire puts the slot payload after all r + n_new codes,
@@ -53,12 +53,14 @@ __device__ __forceinline__ u32 new_per_thread(u64 mode) {
 
 // Shared-memory matching state of the block's current pair.
 struct SmemTable {
-  u32* tbl;   // hash table, or nullptr: the pair uses its global hash segment
-  u32 mask;   // table entries - 1
-  u32* bits;  // bit k: message record k was taken by a slot
+  unsigned short* tbl;  // hash table, or nullptr: the pair uses its global hash segment
+  u32 mask;             // table entries - 1
+  u32* bits;            // bit k: message record k was taken by a slot
 };
 
-__device__ __forceinline__ u32 fp_of(u64 h) { return (u32)h & 0xFFu; }
+constexpr u32 kFpBits = 3, kFpMask = (1u << kFpBits) - 1u;
+constexpr u32 kTableMax = (1u << (16 - kFpBits)) - 1u;  // records of a u16 entry
+__device__ __forceinline__ u32 fp_of(u64 h) { return (u32)h & kFpMask; }
 __device__ __forceinline__ u32 tbl_start(u64 h, u32 mask) { return (u32)(h >> 32) & mask; }
 
 // Block scan of two per-thread counts packed in one word (payload bytes in
@@ -143,7 +145,7 @@ __global__ void __launch_bounds__(1024)
 template <int T>
 __device__ __forceinline__ void smem_build(const EncArgs& A, u32 p, u64 m, const SmemTable& tb) {
   const u64 g_lo = A.pair_off[p];
-  for (u32 i = threadIdx.x; i <= tb.mask; i += T) tb.tbl[i] = 0u;
+  for (u32 i = threadIdx.x; i <= tb.mask; i += T) tb.tbl[i] = 0;
   for (u32 i = threadIdx.x; i < (u32)((m + 31) / 32); i += T) tb.bits[i] = 0u;
   __syncthreads();
   for (u64 k0 = 0; k0 < m; k0 += (u64)T * kIlp) {
@@ -158,12 +160,13 @@ __device__ __forceinline__ void smem_build(const EncArgs& A, u32 p, u64 m, const
       const u64 k = k0 + (u64)i * T + threadIdx.x;
       if (k >= m) continue;
       const u64 h = mix64(id[i]);
-      const u32 fp = fp_of(h), e = ((u32)(k + 1) << 8) | fp;
+      const u32 fp = fp_of(h);
+      const unsigned short e = (unsigned short)(((u32)(k + 1) << kFpBits) | fp);
       u32 at = tbl_start(h, tb.mask);
       for (u32 probe = 0; probe <= tb.mask; ++probe) {
-        const u32 old = atomicCAS(&tb.tbl[at], 0u, e);
+        const u32 old = atomicCAS(&tb.tbl[at], (unsigned short)0, e);
         if (old == 0u) break;
-        if ((old & 0xFFu) == fp && msg_id(A, p, g_lo + (old >> 8) - 1) == id[i]) {
+        if ((old & kFpMask) == fp && msg_id(A, p, g_lo + (old >> kFpBits) - 1) == id[i]) {
           latch(A.st, TERA_EINVAL);  // ids must be unique within a message
           break;
         }
@@ -179,7 +182,8 @@ __device__ __forceinline__ u32 smem_find(const EncArgs& A, u32 p, const SmemTabl
   for (u32 probe = 0; probe <= tb.mask; ++probe) {
     const u32 e = tb.tbl[at];
     if (e == 0u) return kNoMatch;
-    if ((e & 0xFFu) == fp && msg_id(A, p, g_lo + (e >> 8) - 1) == id) return (e >> 8) - 1;
+    if ((e & kFpMask) == fp && msg_id(A, p, g_lo + (e >> kFpBits) - 1) == id)
+      return (e >> kFpBits) - 1;
     at = (at + 1) & tb.mask;
   }
   return kNoMatch;
@@ -212,8 +216,8 @@ __device__ __forceinline__ u32 smem_match(const EncArgs& A, u32 p, u64 r, const 
       for (u32 probe = 0; probe <= tb.mask; ++probe) {
         const u32 e = tb.tbl[at[i]];
         if (e == 0u) break;
-        if ((e & 0xFFu) == fp[i]) {
-          cand[i] = (e >> 8) - 1;
+        if ((e & kFpMask) == fp[i]) {
+          cand[i] = (e >> kFpBits) - 1;
           break;
         }
         at[i] = (at[i] + 1) & tb.mask;
@@ -640,7 +644,8 @@ __device__ __forceinline__ void bat_new(const EncArgs& A, const BatchArgs& B, u3
 // into list[0, n) (the hash table's memory, free once matching is done).
 // Returns n (block-uniform).
 template <int T>
-__device__ __forceinline__ u32 smem_new_list(const SmemTable& tb, u64 m, u32* list, u32* sm32) {
+__device__ __forceinline__ u32 smem_new_list(const SmemTable& tb, u64 m, unsigned short* list,
+                                             u32* sm32) {
   const u32 words = (u32)((m + 31) / 32);
   const u32 per = (words + T - 1) / T;
   const u32 w0 = threadIdx.x * per, w1 = w0 + per < words ? w0 + per : words;
@@ -653,7 +658,8 @@ __device__ __forceinline__ u32 smem_new_list(const SmemTable& tb, u64 m, u32* li
   u32 pos = block_excl_scan<u32>(cnt, sm32, &tot);
   for (u32 w = w0; w < w1; ++w) {
     const u32 valid = (w + 1) * 32 <= m ? 0xFFFFFFFFu : ((1u << (m & 31u)) - 1u);
-    for (u32 x = ~tb.bits[w] & valid; x; x &= x - 1) list[pos++] = w * 32 + (u32)(__ffs(x) - 1);
+    for (u32 x = ~tb.bits[w] & valid; x; x &= x - 1)
+      list[pos++] = (unsigned short)(w * 32 + (u32)(__ffs(x) - 1));
   }
   __syncthreads();
   return tot;
@@ -663,7 +669,7 @@ __device__ __forceinline__ u32 smem_new_list(const SmemTable& tb, u64 m, u32* li
 // and new-reference records; the running prefix is carried in `run`.
 template <int T, bool PR>
 __device__ __forceinline__ void bat_new_list(const EncArgs& A, u32 p, u64 r, u64 m, u64 matched,
-                                             U64x2 slot_tot, const u32* list, u32 n_list,
+                                             U64x2 slot_tot, const unsigned short* list, u32 n_list,
                                              u64 tile, U64x2* sm, uint8_t* stage, u32 stage_cap,
                                              U64x2& run) {
   const u64 n_new = m - matched;
@@ -835,17 +841,27 @@ __device__ __forceinline__ void bat_dec(const DecArgs& A, const BatchArgs& B, u3
 
 // ---------------- the persistent kernel ----------------
 
-// Shared memory: stage (T records + 48 bytes) | MLP weights (predictor) |
-// hash table (2 table_records u32) | taken bits (table_records / 32 u32).
+// Shared memory, for c = table_records: one region of max(4c, 2c + stage)
+// bytes that holds the hash table (2c u16, match step), then the list of new
+// records (c u16, new step) followed by the stage (T records + 48 bytes,
+// slot / new / decode steps) | MLP weights (predictor) | taken bits (c / 8).
+__host__ __device__ constexpr size_t region_bytes(u32 T, u32 c) {
+  return (4 * (size_t)c > 2 * (size_t)c + (size_t)T * kRecBytes + 48)
+             ? 4 * (size_t)c
+             : 2 * (size_t)c + (size_t)T * kRecBytes + 48;
+}
+
 template <int T, bool PR>
 __global__ void __launch_bounds__(T, (1024 / T) > 0 ? (1024 / T) : 1)
     codec_persistent_kernel(EncArgs E, DecArgs D, BatchArgs B, u32 table_records) {
   extern __shared__ __align__(16) uint8_t dyn[];
   constexpr u32 kStageCap = (u32)T * kRecBytes + 48;
-  uint8_t* stage = dyn;
-  float* sW = reinterpret_cast<float*>(dyn + kStageCap);
-  u32* tbl = reinterpret_cast<u32*>(dyn + kStageCap + (PR ? sizeof(float) * kMlpParams : 0));
-  u32* bits = tbl + 2 * table_records;
+  const size_t region = region_bytes(T, table_records);
+  unsigned short* tbl = reinterpret_cast<unsigned short*>(dyn);
+  unsigned short* list = tbl;
+  uint8_t* stage = dyn + 2 * (size_t)table_records;
+  float* sW = reinterpret_cast<float*>(dyn + region);
+  u32* bits = reinterpret_cast<u32*>(dyn + region + (PR ? sizeof(float) * kMlpParams : 0));
   __shared__ U64x2 sm[33];
   __shared__ u64 s_pair;
   __shared__ u32 s_cnt;
@@ -871,7 +887,7 @@ __global__ void __launch_bounds__(T, (1024 / T) > 0 ? (1024 / T) : 1)
     const u64* pi = E.info + (u64)p * 8;
     const u64 r = pi[PI_R], m = pi[PI_M];
     SmemTable tb{nullptr, 0u, bits};
-    if (!PR && table_records > 0 && m <= table_records) {
+    if (!PR && table_records > 0 && m <= table_records && m <= kTableMax) {
       u32 size = 32;
       while (size < 2 * m) size <<= 1;
       tb.tbl = tbl;
@@ -920,10 +936,10 @@ __global__ void __launch_bounds__(T, (1024 / T) > 0 ? (1024 / T) : 1)
     run = U64x2{0, 0};
     if (tb.tbl) {
       const u64 matched = slot_tot.b;
-      const u32 n_list = smem_new_list<T>(tb, m, tb.tbl, reinterpret_cast<u32*>(sm));
+      const u32 n_list = smem_new_list<T>(tb, m, list, reinterpret_cast<u32*>(sm));
       const u64 tl = ceil_div(n_list, T);
       for (u64 t = 0; t < tl; ++t)
-        bat_new_list<T, PR>(E, p, r, m, matched, slot_tot, tb.tbl, n_list, t, sm, stage,
+        bat_new_list<T, PR>(E, p, r, m, matched, slot_tot, list, n_list, t, sm, stage,
                             kStageCap, run);
       finish_pair<PR>(E, B, p, r, m, matched, slot_tot, run);
     } else {
@@ -948,7 +964,7 @@ __global__ void __launch_bounds__(T, (1024 / T) > 0 ? (1024 / T) : 1)
 // Shared memory of one block for tile size T: (bytes, table_records).
 inline void persistent_smem(u32 T, bool PR, int ctas_per_sm, u32 want_records, size_t* bytes,
                             u32* records) {
-  const size_t base = (size_t)T * kRecBytes + 48 + (PR ? sizeof(float) * kMlpParams : 0);
+  const size_t weights = PR ? sizeof(float) * kMlpParams : 0;
   // per-SM shared memory (228 KB) split over the blocks, minus the static
   // shared memory and the 1 KB the runtime reserves per block
   const size_t per_block = (size_t)228 * 1024 / (size_t)(ctas_per_sm > 0 ? ctas_per_sm : 1);
@@ -956,12 +972,11 @@ inline void persistent_smem(u32 T, bool PR, int ctas_per_sm, u32 want_records, s
   if (cap > (size_t)227 * 1024) cap = (size_t)227 * 1024;
   u32 rec = 0;
   if (!PR) {
-    // 2 table entries (u32) + 1 bit per record
-    for (u32 c = 32; c <= (1u << 20); c <<= 1)
-      if (base + 8 * (size_t)c + c / 8 <= cap && (want_records == 0 || c <= want_records)) rec = c;
+    for (u32 c = 32; c <= 8192; c <<= 1)
+      if (region_bytes(T, c) + c / 8 <= cap && (want_records == 0 || c <= want_records)) rec = c;
   }
   *records = rec;
-  *bytes = base + 8 * (size_t)rec + rec / 8;
+  *bytes = region_bytes(T, rec) + weights + rec / 8;
 }
 
 template <int T, bool PR>
@@ -999,7 +1014,7 @@ static tera_status batched_impl(
   if (((uintptr_t)rec_arena | (uintptr_t)ref_next | (uintptr_t)wire | (uintptr_t)recv |
        (uintptr_t)(ref_prev ? ref_prev : wire) | (uintptr_t)(recv_prev ? recv_prev : wire)) & 15u)
     return TERA_EINVAL;
-  tera_tune tn = tune ? *tune : tera_tune{512, 2, 0, 0};
+  tera_tune tn = tune ? *tune : tera_tune{256, 4, 0, 0};
   if (enc_pred && enc_pred->params && ((uintptr_t)enc_pred->params & 3u)) return TERA_EINVAL;
   if (tn.block != 128 && tn.block != 256 && tn.block != 512 && tn.block != 1024) return TERA_EINVAL;
   if (tn.ctas_per_sm < 1 || tn.ctas_per_sm > 16 || tn.block * tn.ctas_per_sm > 2048)
