@@ -468,49 +468,34 @@ def run_predictor(args):
 
 
 def run_e2e(args, tera, wl, states, nmax, max_records, local, tune=None):
-    """Same metric through the public API with host buffers: the state columns
-    are copied from pinned host memory and the wire slabs copied back, inside
-    the timed region."""
+    """Same metric through the public API on host-resident state
+    (paper_2509_24063_gb300.host.HostExchange): every step copies the eight
+    state columns from pinned host memory and writes the used wire bytes back
+    into pinned host memory; the next step's inputs are copied while a step
+    computes (double-buffered device inputs)."""
     import torch
-    fields = ("id", "x", "y", "z", "diameter", "volume", "adherence", "density")
+    from paper_2509_24063_gb300.host import FIELDS, HostExchange
     k = min(args.e2e_steps, args.steps)
     host = []
     for t in range(args.warmup - 1, args.warmup + k):
-        host.append({f: states[t][f].cpu().pin_memory() for f in fields})
-    dev = {f: torch.empty(nmax, dtype=states[0][f].dtype, device="cuda") for f in fields}
+        host.append({f: states[t][f].cpu().pin_memory() for f in FIELDS})
     ctx = tera.Context(wl.lo, wl.hi, wl.grid, wl.w, device=local)
-    ex = tera.AuraExchange(ctx, max_agents=nmax, max_records=max_records, path=args.path,
-                           tune=tune)
-    out_host = torch.empty(ex.wire_cap, dtype=torch.uint8).pin_memory()
-    stream = torch.cuda.current_stream()
-
-    def one(hs):
-        n = int(hs["x"].shape[0])
-        view = {}
-        for f in fields:
-            dev[f][:n].copy_(hs[f], non_blocking=True)
-            view[f] = dev[f][:n]
-        ex.step(view)
-        used = ex.wire_off[-1:].to("cpu", non_blocking=False)  # slab bytes used
-        nb = int(used.item())
-        out_host[:nb].copy_(ex.wire[:nb], non_blocking=True)
-        return n, sum(int(hs[f].numel() * hs[f].element_size()) for f in fields), nb
-
-    one(host[0])  # warm-up (first iteration of this chain)
+    hx = HostExchange(ctx, nmax, max_records, path=args.path, tune=tune)
+    outs = [torch.empty(hx.wire_capacity, dtype=torch.uint8).pin_memory() for _ in range(2)]
+    hx.step(host[0], outs[0]).wait()  # first iteration of this chain (allocates scratch)
     torch.cuda.synchronize()
-    h2d = d2h = agents = 0
     t0 = time.perf_counter()
-    for hs in host[1:]:
-        n, bi, bo = one(hs)
-        agents += n
-        h2d += bi
-        d2h += bo
+    pend = [hx.step(hs, outs[(i + 1) % 2]) for i, hs in enumerate(host[1:])]
+    nbytes = [p.wait() for p in pend]
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
+    agents = sum(int(hs["x"].shape[0]) for hs in host[1:])
+    h2d = sum(int(hs[f].numel() * hs[f].element_size()) for hs in host[1:] for f in FIELDS)
     ctx.status()
     ctx.close()
     return {"value": agents / dt, "unit": "agents/s", "h2d_bytes_per_step": h2d // k,
-            "d2h_bytes_per_step": d2h // k, "steps": k}
+            "d2h_bytes_per_step": sum(nbytes) // k, "steps": k,
+            "overlap": "inputs of step t+1 copied while step t computes"}
 
 
 if __name__ == "__main__":

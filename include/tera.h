@@ -16,6 +16,8 @@
  *                      into the new reference / receive buffer (Sec. 2.3, step D)
  *   tera_unpack_inplace  header check + typed view of a receive buffer, no
  *                      other reads or writes       (Sec. 2.2.1 "Deserialization")
+ *   tera_wire_to_host  the wire messages of an iteration into host memory, with
+ *                      the length known only on the device (no host wait)
  *
  * Conventions shared by every entry point:
  *  - Device pointers are owned by the caller (allocated e.g. by PyTorch); the
@@ -318,6 +320,22 @@ tera_status tera_codec_batched_pred(
     const uint64_t* recv_off_prev, uint8_t* recv, uint64_t recv_capacity_units,
     uint64_t* recv_off, int mode, const tera_tune* tune, const tera_predictor* enc_pred,
     const tera_predictor* dec_pred, void* stream);
+
+/* Copy the wire messages of one iteration, wire[0, wire_off[P]) with P the
+ * context's pair count, into host memory host_dst, and the byte count into
+ * *host_count.  The paper sends the buffers over MPI (Sec. 2.4); here a
+ * kernel writes them into host memory the device can address (pinned memory
+ * from cudaHostAlloc / cudaHostRegister, or memory the system lets the device
+ * access), so the length never has to be read back before the copy is issued.
+ * host_dst must be 16-byte aligned; wire_off[P] is a multiple of 16.  A
+ * length above host_capacity latches TERA_ECAPACITY (required = the length)
+ * and copies nothing; *host_count is written in every case.  Asynchronous on
+ * `stream`: host_dst and *host_count are valid once the stream has reached
+ * this point (e.g. after an event recorded behind it completes).  The paper
+ * has no counterpart (it sends from host memory). */
+tera_status tera_wire_to_host(tera_ctx* ctx, const uint8_t* wire, const uint64_t* wire_off,
+                              uint8_t* host_dst, uint64_t host_capacity, uint64_t* host_count,
+                              void* stream);
 
 /* Sec. 2.2.1 "Deserialization": check the TAIO header of ONE pair buffer
  * (device pointer `buf`, `len` bytes available) on the host and return a

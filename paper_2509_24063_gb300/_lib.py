@@ -85,6 +85,7 @@ SIGNATURES = {
     "tera_unpack_inplace": (C.c_int, [P, u64, u32, C.POINTER(C.c_void_p),
                                       C.POINTER(C.c_uint64), P]),
     "tera_unpack_validate": (C.c_int, [P, P, P, P]),
+    "tera_wire_to_host": (C.c_int, [P, P, P, P, u64, P, P]),
     "tera_ctx_status": (C.c_int, [P, C.POINTER(C.c_uint64), P]),
     "tera_reset_reference": (C.c_int, [P, u32]),
     "tera_ctx_launches": (u64, [P]),

@@ -22,6 +22,15 @@ def _ptr(t):
     return C.c_void_p(t.data_ptr())
 
 
+def _host_ptr(t):
+    """Address of a pinned host tensor (the device writes it directly)."""
+    if not isinstance(t, torch.Tensor) or t.device.type != "cpu" or not t.is_pinned():
+        raise TypeError("expected a pinned host tensor")
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return C.c_void_p(t.data_ptr())
+
+
 def _stream(stream):
     s = torch.cuda.current_stream() if stream is None else stream
     return C.c_void_p(s.cuda_stream)
@@ -263,6 +272,15 @@ class Context:
     def unpack_validate(self, arena, off, stream=None):
         check(self.lib.tera_unpack_validate(self.h, _ptr(arena), _ptr(off), _stream(stream)),
               "tera_unpack_validate")
+
+    def wire_to_host(self, wire, wire_off, host_out, host_count, stream=None):
+        """Wire messages wire[0, wire_off[-1]) into pinned host memory host_out
+        (uint8) and the byte count into host_count (pinned int64, 1 element),
+        with the length read on the device (tera_wire_to_host)."""
+        check(self.lib.tera_wire_to_host(self.h, _ptr(wire), _ptr(wire_off), _host_ptr(host_out),
+                                         host_out.numel(), _host_ptr(host_count),
+                                         _stream(stream)),
+              "tera_wire_to_host")
 
     def reset_reference(self, pair: int):
         check(self.lib.tera_reset_reference(self.h, int(pair)), "tera_reset_reference")

@@ -592,3 +592,46 @@ tera_status tera_unpack_validate(tera_ctx* ctx, const uint8_t* arena, const uint
 }
 
 }  // extern "C"
+
+// ---------------- wire messages into host memory ----------------
+
+namespace {
+
+// Grid-stride 16-byte copy of wire[0, wire_off[P]) into host memory; the
+// length is read on the device.
+__global__ void __launch_bounds__(256)
+    wire_to_host_kernel(const uint4* __restrict__ wire, const u64* __restrict__ wire_off, u64 P,
+                        uint4* __restrict__ dst, u64 cap, u64* count, DevStatus* st) {
+  const u64 n = wire_off[P];
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    *count = n;
+    if (n > cap) {
+      latch(st, TERA_ECAPACITY);
+      need(st, n);
+    }
+  }
+  if (n > cap) return;
+  const u64 n16 = n / 16;
+  for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < n16;
+       i += (u64)gridDim.x * blockDim.x)
+    dst[i] = wire[i];
+}
+
+}  // namespace
+
+extern "C" tera_status tera_wire_to_host(tera_ctx* ctx, const uint8_t* wire,
+                                         const uint64_t* wire_off, uint8_t* host_dst,
+                                         uint64_t host_capacity, uint64_t* host_count,
+                                         void* stream) {
+  if (!ctx || !wire || !wire_off || !host_dst || !host_count) return TERA_EINVAL;
+  if (((uintptr_t)wire | (uintptr_t)host_dst) & 15u) return TERA_EINVAL;
+  if ((uintptr_t)host_count & 7u) return TERA_EINVAL;
+  cudaSetDevice(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  prof_begin(ctx, s);
+  wire_to_host_kernel<<<(unsigned)grid_for(ctx, 8), 256, 0, s>>>(
+      reinterpret_cast<const uint4*>(wire), reinterpret_cast<const u64*>(wire_off),
+      ctx->n_pairs, reinterpret_cast<uint4*>(host_dst), host_capacity,
+      reinterpret_cast<u64*>(host_count), ctx->d_status);
+  return check_launch(ctx, "wire_to_host_kernel", s);
+}
