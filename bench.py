@@ -51,6 +51,46 @@ def kernel_bytes(name, t):
     return table.get(name)
 
 
+# DRAM traffic of the dominant kernel per launch, from a one-pass ncu capture of
+# the full-size run recorded in profiles/; used only while the kernel's sources
+# are the ones the capture was taken with (their digest is recorded beside it).
+KERNEL_SOURCES = {"codec_persistent_kernel": ("batched.cu", "codec.cuh", "tera_internal.cuh")}
+
+
+def kernel_digest(name):
+    import hashlib
+    files = KERNEL_SOURCES.get(name)
+    if not files:
+        return None
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, "paper_2509_24063_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(name, workload):
+    """(bytes per launch, records per launch) recorded for this kernel and
+    workload, or None when absent or taken with other kernel sources."""
+    path = os.path.join(ROOT, "profiles", f"{name}_{workload}.md")
+    try:
+        with open(path) as f:
+            text = f.read()
+    except OSError:
+        return None
+    vals = {}
+    for line in text.splitlines():
+        if ":" in line and line.startswith("- "):
+            k, v = line[2:].split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("kernel source digest") != kernel_digest(name):
+        return None
+    try:
+        return float(vals["DRAM bytes per launch"]), float(vals["records per launch"])
+    except (KeyError, ValueError):
+        return None
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -326,8 +366,13 @@ def main():
         per_launch_bytes = dbytes / dn
         per_launch_s = dms / dn / 1e3
         achieved = per_launch_bytes / per_launch_s / 1e9
+        rec = recorded_traffic(dname, wl.name) if not args.agents else None
+        traffic = None
+        if rec is not None:
+            # scaled to this run's records per launch (traffic grows with them)
+            traffic = rec[0] * (stats["records"] / dn) / rec[1]
         roofline = {"bound": "hbm", "kernel": dname, "achieved": achieved, "peak": hbm,
-                    "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
+                    "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
                     "peak_kind": peak_kind, "launches": dn, "avg_ms": dms / dn,
                     "algorithmic_bytes_per_launch": per_launch_bytes}
     if args.profile_table and rank == 0:

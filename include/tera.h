@@ -50,7 +50,7 @@
  *
  *  Wire message of pair p (starts at wire + wire_off[p]):
  *       0 u32 magic 0x41524554 ("TERA")   4 u16 version 1   6 u16 record size 64
- *       8 u32 class id   12 u32 mode (0 raw, 1 xor)   16 u64 n_slots (r)
+ *       8 u32 class id   12 u32 mode (0 raw, 1 xor, 2 residual)   16 u64 n_slots (r)
  *      24 u64 n_new (a)  32 u64 n_holes   40 u64 payload bytes   48 u32 pair p
  *      52 u32 zero       56 u64 message bytes (multiple of 16)
  *      64: u32 code[r + a]; then the payload; then zero padding.

@@ -40,9 +40,18 @@ constexpr u32 kIlp = 4;
 struct BatchArgs {
   u64 n_pairs;
   u64* ticket;
-  u64* ptot;  // [P * PT_COUNT] per-pair totals of the match step
+  u64* ptot;          // [P * PT_COUNT] per-pair totals of the match step
   u32* abort;
+  const u64* items;   // work items: pair << 32 | member << 16 | team size
+  const u64* n_items;
+  u32* team;          // [P * 8] barrier counters of the teams
+  U64x2* tsum;        // per-tile totals of team pairs (slot tiles, then decode tiles)
+  const u64* tbase;   // [P] first tile total of a team pair
 };
+
+__device__ __forceinline__ u64 make_item(u64 p, u32 member, u32 g) {
+  return (p << 32) | ((u64)member << 16) | (u64)g;
+}
 
 __device__ __forceinline__ u64 ceil_div(u64 a, u64 b) { return (a + b - 1) / b; }
 
@@ -73,22 +82,89 @@ __device__ __forceinline__ U64x2 tile_scan(u32 bytes, u32 recs, U64x2* sm, U64x2
   return U64x2{ex & 0xFFFFFFFFull, ex >> 32};
 }
 
+// Exclusive block scan of packed counts (low / high 32 bits) with two
+// barriers: the caller alternates `buf` (33 words) between consecutive scans,
+// so it is never written while another warp may still read it.  After the
+// last scan of a run, one __syncthreads() must precede other uses of buf.
+__device__ __forceinline__ u64 scan_packed(u64 v, u64* buf, u64* total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nwarps = (blockDim.x + 31) >> 5;
+  const u64 incl = warp_incl_scan<u64>(v);
+  if (lane == 31) buf[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    const u64 x = lane < nwarps ? buf[lane] : 0ull;
+    const u64 xi = warp_incl_scan<u64>(x);
+    if (lane < nwarps) buf[lane] = xi - x;
+    if (lane == nwarps - 1) buf[32] = xi;
+  }
+  __syncthreads();
+  *total = buf[32];
+  return buf[warp] + incl - v;
+}
+
+// Each warp stages its own contiguous byte range in a private region (32
+// records + 16 bytes of alignment slack) and stores it with 16-byte stores
+// inside and byte stores on the edges it shares with the neighbouring warps.
+constexpr u32 kWarpStage = 32 * kRecBytes + 16;
+
+__device__ __forceinline__ void warp_flush(const uint8_t* wst, uint8_t* gW, u32 n) {
+  const u32 s0 = (u32)((uintptr_t)gW & 15u);
+  uint8_t* g16 = gW - s0;
+  const u32 end = s0 + n;
+  const u32 nchunks = (end + 15u) >> 4;
+  for (u32 c = threadIdx.x & 31; c < nchunks; c += 32) {
+    const u32 lo = c << 4, hi = lo + 16u;
+    if (lo >= s0 && hi <= end) {
+      *reinterpret_cast<uint4*>(g16 + lo) = *reinterpret_cast<const uint4*>(wst + lo);
+    } else {
+      for (u32 x = (lo > s0 ? lo : s0); x < (hi < end ? hi : end); ++x) g16[x] = wst[x];
+    }
+  }
+}
+
+// Blocks that carry a pair of `size` entries (reference slots + message
+// records + receiver slots): 1, or a team when the pair exceeds the average
+// load of a block (so no single block holds up the end of the launch).  The
+// predictor path keeps one block per pair.
+__device__ __forceinline__ u32 team_size(u64 size, u64 thresh, u32 gmax, int pred) {
+  if (pred || size <= thresh) return 1u;
+  const u64 g = ceil_div(size, thresh);
+  return (u32)(g < gmax ? g : gmax);
+}
+
+// Tile totals a team pair keeps: slot tiles, new-record tiles (at most one per
+// T records), decode tiles (a valid message has at most rr + m entries).
+__device__ __forceinline__ u64 team_tiles(u64 r, u64 m, u64 rr, u32 T) {
+  return ceil_div(r, T) + ceil_div(m, T) + ceil_div(rr + m, T);
+}
+
 // ---------------- setup: per-pair facts, layouts, capacity checks ----------------
 
 // One block; thread t owns a contiguous run of pairs (one pass of loads, one scan).
 __global__ void __launch_bounds__(1024)
     bat_setup_kernel(EncArgs E, DecArgs D, BatchArgs B, u64 P, int mode,
                      u64* __restrict__ wire_off, u64 wire_cap, u64 rec_cap, u64 recv_cap,
-                     u32* epoch) {
+                     u32* epoch, u32 T, u32 blocks, u32 gmax, u64 min_team, int pred,
+                     u64* __restrict__ items, u64 items_cap, u64* __restrict__ tbase,
+                     u64 tsum_cap, u64* __restrict__ n_items) {
   __shared__ u64 sm[33];
+  __shared__ u64 s_thresh;
   if (threadIdx.x == 0) {
     const u32 ep = *epoch + 1u;
     *epoch = ep == 0u ? 1u : ep;
+    // a pair becomes a team when its entries exceed the average per block
+    const u64 total = E.pair_off[P] + (E.ref_off ? E.ref_off[P] : 0) +
+                      (D.ref_off ? D.ref_off[P] : 0);
+    const u64 avg = ceil_div(total, blocks);
+    s_thresh = avg > min_team ? avg : min_team;
   }
+  __syncthreads();
+  const u64 thresh = s_thresh;
   const u64 per = (P + blockDim.x - 1) / blockDim.x;
   const u64 q0 = (u64)threadIdx.x * per;
   const u64 q1 = q0 + per < P ? q0 + per : P;
-  u64 sw = 0;
+  u64 sw = 0, nbig = 0, nsmall = 0, ntiles = 0;
   for (u64 p = q0; p < q1; ++p) {
     const u64 m = E.pair_off[p + 1] - E.pair_off[p];
     const u64 r_full = E.ref_off ? E.ref_off[p + 1] - E.ref_off[p] : 0;
@@ -102,13 +178,39 @@ __global__ void __launch_bounds__(1024)
     wire_off[p] = slab;
     sw += slab;
     D.recv_off[p] = E.pair_off[p];  // receive buffers sized by the record counts
+    const u64 rr = D.ref_off ? D.ref_off[p + 1] - D.ref_off[p] : 0;
+    const u32 g = team_size(r + m + rr, thresh, gmax, pred);
+    if (g > 1) {
+      nbig += g;
+      ntiles += team_tiles(r, m, rr, T);
+    } else {
+      ++nsmall;
+    }
   }
-  u64 tw;
+  u64 tw, tbig, tsmall, ttiles;
   u64 run = block_excl_scan<u64>(sw, sm, &tw);
+  u64 pbig = block_excl_scan<u64>(nbig, sm, &tbig);
+  u64 psmall = block_excl_scan<u64>(nsmall, sm, &tsmall);
+  u64 ptile = block_excl_scan<u64>(ntiles, sm, &ttiles);
+  const bool fits = tbig + tsmall <= items_cap && ttiles <= tsum_cap;
+  psmall += tbig;  // team items first: the large pairs start early
   for (u64 p = q0; p < q1; ++p) {
     const u64 slab = wire_off[p];
     wire_off[p] = run;
     run += slab;
+    if (!fits) continue;
+    const u64 m = E.pair_off[p + 1] - E.pair_off[p];
+    const u64 r = (mode == TERA_MODE_RAW || E.reset[p] || E.ref_off == nullptr)
+                      ? 0 : E.ref_off[p + 1] - E.ref_off[p];
+    const u64 rr = D.ref_off ? D.ref_off[p + 1] - D.ref_off[p] : 0;
+    const u32 g = team_size(r + m + rr, thresh, gmax, pred);
+    if (g > 1) {
+      for (u32 i = 0; i < g; ++i) items[pbig++] = make_item(p, i, g);
+      tbase[p] = ptile;
+      ptile += team_tiles(r, m, rr, T);
+    } else {
+      items[psmall++] = make_item(p, 0, 1);
+    }
   }
   if (threadIdx.x == 0) {
     wire_off[P] = tw;
@@ -133,6 +235,11 @@ __global__ void __launch_bounds__(1024)
       need(E.st, E.pair_off[P] + P);
       abort = true;
     }
+    if (!fits) {  // cannot happen: the work list is sized for it
+      latch(E.st, TERA_ECAPACITY);
+      abort = true;
+    }
+    *n_items = abort ? 0 : tbig + tsmall;
     *B.abort = abort ? 1u : 0u;
     *B.ticket = 0;
   }
@@ -461,7 +568,7 @@ __device__ __forceinline__ u64 pair_mode(const EncArgs& A, const BatchArgs& B, u
 // the byte counts are recomputed from d when staging.
 template <int T, bool PR>
 __device__ __forceinline__ void bat_slot(const EncArgs& A, const BatchArgs& B, u32 p, u64 tile,
-                                         u32 g, U64x2* sm, uint8_t* stage, U64x2& run) {
+                                         u32 g, u64* buf, uint8_t* stage, U64x2& run) {
   const u64* pi = A.info + (u64)p * 8;
   const u64 r = pi[PI_R], m = pi[PI_M];
   const u64 ro = A.ref_off[p];
@@ -498,16 +605,21 @@ __device__ __forceinline__ void bat_slot(const EncArgs& A, const BatchArgs& B, u
     }
     reinterpret_cast<u32*>(A.wire + A.wire_off[p] + kHdrBytes)[j] = code;
   }
-  U64x2 tot;
-  const U64x2 ex = tile_scan(vb, vn, sm, &tot);
+  u64 tot64;
+  const u64 ex64 = scan_packed((u64)vb | ((u64)vn << 32), buf, &tot64);
+  const U64x2 ex{ex64 & 0xFFFFFFFFull, ex64 >> 32}, tot{tot64 & 0xFFFFFFFFull, tot64 >> 32};
   const U64x2 pre = run;
   run = pre + tot;
   const u64 n_new = m - __ldcg(B.ptot + (u64)p * PT_COUNT + PT_MATCHED);
-  uint8_t* gA = A.wire + A.wire_off[p] + kHdrBytes + 4 * (r + n_new) + pre.a;
+  // this warp's bytes: [wstart, wend) of the tile's payload
+  const u32 wstart = __shfl_sync(0xFFFFFFFFu, (u32)ex.a, 0);
+  const u32 wend = __shfl_sync(0xFFFFFFFFu, (u32)ex.a + vb, 31);
+  uint8_t* gW = A.wire + A.wire_off[p] + kHdrBytes + 4 * (r + n_new) + pre.a + wstart;
+  uint8_t* wst = stage + (threadIdx.x >> 5) * kWarpStage;
   if (vn) {
-    u32 o = (u32)((uintptr_t)gA & 15u) + (u32)ex.a;
+    u32 o = (u32)((uintptr_t)gW & 15u) + ((u32)ex.a - wstart);
 #pragma unroll
-    for (int w = 0; w < 8; ++w) stage_word(stage, o, d.w[w], sig_bytes(d.w[w]));
+    for (int w = 0; w < 8; ++w) stage_word(wst, o, d.w[w], sig_bytes(d.w[w]));
     const u64 pos = pre.b + ex.b;
     store_rec(A.ref_next + (A.pair_off[p] + p + 1 + pos) * kRecBytes, cur);
     if constexpr (PR) {
@@ -523,9 +635,9 @@ __device__ __forceinline__ void bat_slot(const EncArgs& A, const BatchArgs& B, u
       }
     }
   }
-  __syncthreads();
-  flush_stage(stage, gA, tot.a);
-  __syncthreads();
+  __syncwarp();
+  warp_flush(wst, gW, wend - wstart);
+  __syncwarp();
 }
 
 // Header, padding, iteration totals and the new reference's header of pair p
@@ -725,7 +837,7 @@ struct DecShared {
 template <int T, bool PR>
 __device__ __forceinline__ void bat_dec_tile(const DecArgs& A, const BatchArgs& B, u32 p,
                                              u64 tile, u32 code, const DecShared& h, u64 m,
-                                             U64x2* sm, uint8_t* stage, U64x2& run,
+                                             u64* buf, uint8_t* stage, U64x2& run,
                                              const float* sW) {
   const u64 ns = h.ns, n = h.ns + h.nn;
   const uint8_t* w8 = A.wire + A.wire_off[p];
@@ -736,36 +848,43 @@ __device__ __forceinline__ void bat_dec_tile(const DecArgs& A, const BatchArgs& 
   // the slot's reference record is read before (and while) the prefix is found
   Rec R;
   if (e < ns) R = load_rec(A.ref + (A.ref_off[p] + p + 1 + e) * kRecBytes);
-  if (e < n && !check_code(code, e, ns, &hole, &b)) bad = 1;
+  if (e < n && !check_code(code, e, ns, &hole, &b)) {
+    bad = 1;
+    latch(A.st, TERA_ECORRUPT);  // malformed code: its entry is not decoded
+  }
   const u32 vn = (e < n && !hole) ? 1u : 0u;
-  U64x2 tot;
-  const U64x2 ex = tile_scan(b, vn, sm, &tot);
+  u64 tot64;
+  const u64 ex64 = scan_packed((u64)b | ((u64)vn << 32), buf, &tot64);
+  const U64x2 ex{ex64 & 0xFFFFFFFFull, ex64 >> 32}, tot{tot64 & 0xFFFFFFFFull, tot64 >> 32};
   const U64x2 pre = run;
   run = pre + tot;
-  // malformed codes, or more payload / records than the header announces
-  const bool corrupt = __syncthreads_or(bad) || pre.a + tot.a > h.pay || pre.b + tot.b > m;
-  if (corrupt && threadIdx.x == 0) latch(A.st, TERA_ECORRUPT);
-  const bool ok = !corrupt;
-  // stage [gA, gA + tot.a) with 16-byte loads; the slab is 16-byte aligned
-  // and padded, and the range was checked, so it stays inside the message
-  const uint8_t* gA = w8 + kHdrBytes + 4 * n + pre.a;
-  const u32 s0 = (u32)((uintptr_t)gA & 15u);
+  // more payload / records than the header announces (block-uniform)
+  const bool ok = pre.a + tot.a <= h.pay && pre.b + tot.b <= m;
+  if (!ok && threadIdx.x == 0) latch(A.st, TERA_ECORRUPT);
+  // this warp's payload bytes [wstart, wend) of the tile, staged with 16-byte
+  // loads; the slab is 16-byte aligned and padded, and the range was checked,
+  // so the loads stay inside the message
+  const u32 wstart = __shfl_sync(0xFFFFFFFFu, (u32)ex.a, 0);
+  const u32 wend = __shfl_sync(0xFFFFFFFFu, (u32)ex.a + b, 31);
+  const uint8_t* gW = w8 + kHdrBytes + 4 * n + pre.a + wstart;
+  const u32 s0 = (u32)((uintptr_t)gW & 15u);
+  uint8_t* wst = stage + (threadIdx.x >> 5) * kWarpStage;
   if (ok) {
-    const uint8_t* g16 = gA - s0;
-    const u32 nchunks = (u32)((s0 + tot.a + 15u) >> 4);
-    for (u32 c = threadIdx.x; c < nchunks; c += T)
-      *reinterpret_cast<uint4*>(stage + (c << 4)) =
+    const uint8_t* g16 = gW - s0;
+    const u32 nchunks = (s0 + (wend - wstart) + 15u) >> 4;
+    for (u32 c = threadIdx.x & 31; c < nchunks; c += 32)
+      *reinterpret_cast<uint4*>(wst + (c << 4)) =
           __ldcg(reinterpret_cast<const uint4*>(g16 + (c << 4)));
   }
-  __syncthreads();
-  if (ok && vn) {
-    u32 o = s0 + (u32)ex.a;
+  __syncwarp();
+  if (ok && vn && !bad) {
+    u32 o = s0 + ((u32)ex.a - wstart);
     Rec rec;
 #pragma unroll
     for (int w = 0; w < 8; ++w) {
       const u32 L = (code >> (4 * w)) & 0xFu;
       u64 x = 0;
-      for (u32 q = 0; q < L; ++q) x |= (u64)stage[o + q] << (8 * q);
+      for (u32 q = 0; q < L; ++q) x |= (u64)wst[o + q] << (8 * q);
       o += L;
       rec.w[w] = x;
     }
@@ -800,18 +919,19 @@ __device__ __forceinline__ void bat_dec_tile(const DecArgs& A, const BatchArgs& 
     }
     store_rec(A.recv + (A.recv_off[p] + p + 1 + pos) * kRecBytes, rec);
   }
-  __syncthreads();
+  __syncwarp();
   // the last tile: every byte and record the header announced was decoded
   if (ok && threadIdx.x == 0 && tile + 1 == (n ? ceil_div(n, T) : 1) &&
       (pre.a + tot.a != h.pay || pre.b + tot.b != m))
     latch(A.st, TERA_ECORRUPT);
 }
 
-template <int T, bool PR>
-__device__ __forceinline__ void bat_dec(const DecArgs& A, const BatchArgs& B, u32 p,
-                                        DecShared* hs, U64x2* sm, uint8_t* stage,
-                                        const float* sW) {
-  const u64 m = A.recv_off[p + 1] - A.recv_off[p];
+// Header of pair p's received message (thread 0 reads and checks it; the
+// first caller of a pair also latches its error and writes the receive
+// buffer's TAIO header).  Returns the facts to every thread.
+template <bool PR>
+__device__ __forceinline__ DecShared dec_header(const DecArgs& A, u32 p, u64 m, DecShared* hs,
+                                                bool first) {
   if (threadIdx.x == 0) {
     DecHdr H;
     const u32 err = dec_read_header<true, PR>(A, p, m, &H);
@@ -820,11 +940,21 @@ __device__ __forceinline__ void bat_dec(const DecArgs& A, const BatchArgs& B, u3
     hs->pay = H.pay;
     hs->mode = H.mode;
     hs->ok = err ? 0 : 1;
-    if (err) latch(A.st, err);
-    write_taio_header(A.recv + (A.recv_off[p] + p) * kRecBytes, A.class_id, p, m);
+    if (first) {
+      if (err) latch(A.st, err);
+      write_taio_header(A.recv + (A.recv_off[p] + p) * kRecBytes, A.class_id, p, m);
+    }
   }
   __syncthreads();
-  const DecShared h = *hs;
+  return *hs;
+}
+
+template <int T, bool PR>
+__device__ __forceinline__ void bat_dec(const DecArgs& A, const BatchArgs& B, u32 p,
+                                        DecShared* hs, u64* bufs, uint8_t* stage,
+                                        const float* sW) {
+  const u64 m = A.recv_off[p + 1] - A.recv_off[p];
+  const DecShared h = dec_header<PR>(A, p, m, hs, true);
   if (!h.ok) return;  // block-uniform
   const u64 n = h.ns + h.nn;
   const u64 ntiles = n ? ceil_div(n, T) : 1;
@@ -835,20 +965,216 @@ __device__ __forceinline__ void bat_dec(const DecArgs& A, const BatchArgs& B, u3
     const u32 c = c_next;
     const u64 en = (t + 1) * T + threadIdx.x;
     c_next = en < n ? __ldcg(codes + en) : 0u;
-    bat_dec_tile<T, PR>(A, B, p, t, c, h, m, sm, stage, run, sW);
+    bat_dec_tile<T, PR>(A, B, p, t, c, h, m, bufs + 33 * (t & 1), stage, run, sW);
   }
+  __syncthreads();  // the scan buffers and the stage are reused next
+}
+
+// ---------------- pairs carried by a team of blocks ----------------
+
+__device__ __forceinline__ u32 ld_acquire(const u32* p) {
+  u32 v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void red_release_add(u32* p, u32 v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" : : "l"(p), "r"(v) : "memory");
+}
+
+constexpr u64 kSpinLimit = 1ull << 25;  // x ~64 ns sleeps: about two seconds
+
+// Every member of a team arrives, then waits for the others.  The members
+// were claimed, in list order, by running blocks that wait for nothing else,
+// so the wait ends; past the bound it latches TERA_ETIMEOUT and goes on.
+__device__ __forceinline__ void team_barrier(u32* ctr, u32 g, DevStatus* st) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    red_release_add(ctr, 1u);
+    u64 spin = 0;
+    while (ld_acquire(ctr) < g) {
+      if (++spin > kSpinLimit) {
+        latch(st, TERA_ETIMEOUT);
+        break;
+      }
+      __nanosleep(64);
+    }
+  }
+  __syncthreads();
+}
+
+// Block sum of two counts (red: 66 words of shared memory).
+__device__ __forceinline__ U64x2 block_sum2(u64 a, u64 b, u64* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nwarps = (blockDim.x + 31) >> 5;
+  a = warp_sum(a);
+  b = warp_sum(b);
+  if (lane == 0) {
+    red[warp] = a;
+    red[32 + warp] = b;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    u64 sa = 0, sb = 0;
+    for (int w = 0; w < nwarps; ++w) {
+      sa += red[w];
+      sb += red[32 + w];
+    }
+    red[64] = sa;
+    red[65] = sb;
+  }
+  __syncthreads();
+  const U64x2 r{red[64], red[65]};
+  __syncthreads();
+  return r;
+}
+
+// Sum of the first t tile totals.
+template <int T>
+__device__ __forceinline__ U64x2 tiles_prefix(const U64x2* ts, u64 t, u64* red) {
+  u64 a = 0, b = 0;
+  for (u64 x = threadIdx.x; x < t; x += T) {
+    const U64x2 v = ldx<true>(ts + x);
+    a += v.a;
+    b += v.b;
+  }
+  return block_sum2(a, b, red);
+}
+
+// Totals (payload bytes, matched) of one slot tile.
+template <int T>
+__device__ __forceinline__ void team_slot_sum(const EncArgs& A, u32 p, u64 r, u64 ro, u64 tile,
+                                              U64x2* ts, u64* red) {
+  const u64 j = tile * T + threadIdx.x;
+  u64 b = 0, f = 0;
+  if (j < r) {
+    const u32 g = __ldcg(A.slot_src + ro + j);
+    if (g != kNoMatch) {
+      const Rec R = load_rec(A.ref + (ro + p + 1 + j) * kRecBytes);
+      const Rec M = load_rec(A.rec + ((u64)g + p + 1) * kRecBytes);
+#pragma unroll
+      for (int w = 0; w < 8; ++w) b += sig_bytes(R.w[w] ^ M.w[w]);
+      f = 1;
+    }
+  }
+  const U64x2 t = block_sum2(b, f, red);
+  if (threadIdx.x == 0) ts[tile] = t;
+}
+
+// Totals (payload bytes, records) of the new records of one new-record tile
+// (entries as in bat_new: V per thread).
+template <int T>
+__device__ __forceinline__ void team_new_sum(const EncArgs& A, u32 p, u64 m, u32 V, u64 tile,
+                                             u32 epoch, U64x2* ns, u64* red) {
+  const u64 g_lo = A.pair_off[p];
+  const u64 kb = tile * T * V + (u64)threadIdx.x * V;
+  u64 b = 0, c = 0;
+  for (u32 i = 0; i < V; ++i) {
+    const u64 k = kb + i;
+    if (k >= m || __ldcg(A.matched + g_lo + k) == epoch) continue;
+    const Rec M = load_rec(A.rec + (g_lo + k + p + 1) * kRecBytes);
+#pragma unroll
+    for (int w = 0; w < 8; ++w) b += sig_bytes(M.w[w]);
+    ++c;
+  }
+  const U64x2 t = block_sum2(b, c, red);
+  if (threadIdx.x == 0) ns[tile] = t;
+}
+
+// Totals (payload bytes, records) of one decode tile, from the codes.
+template <int T>
+__device__ __forceinline__ void team_dec_sum(const DecArgs& A, u32 p, const DecShared& h,
+                                             u64 tile, U64x2* ds, u64* red) {
+  const u64 ns = h.ns, n = h.ns + h.nn;
+  const u64 e = tile * T + threadIdx.x;
+  u64 b = 0, f = 0;
+  if (e < n) {
+    const u32 code = __ldcg(reinterpret_cast<const u32*>(A.wire + A.wire_off[p] + kHdrBytes) + e);
+    bool hole;
+    u32 bb;
+    if (!check_code(code, e, ns, &hole, &bb)) latch(A.st, TERA_ECORRUPT);
+    b = bb;
+    f = hole ? 0 : 1;
+  }
+  const U64x2 t = block_sum2(b, f, red);
+  if (threadIdx.x == 0) ds[tile] = t;
+}
+
+// Member i of a team of g blocks carries its share of pair p's tiles through
+// every step (global hash segments; no predictor).  Team barriers separate
+// the steps; the payload positions of a member's tiles come from the sums of
+// all tile totals before them (written in a first pass over the tiles).
+template <int T>
+__device__ __noinline__ void team_pair(const EncArgs& E, const DecArgs& D, const BatchArgs& B,
+                                          u32 p, u32 i, u32 g, u32 epoch, U64x2* sm, u64* red,
+                                          uint8_t* stage, DecShared* hs) {
+  constexpr u32 kStageCap = (u32)T * kRecBytes + 48;
+  const u64* pi = E.info + (u64)p * 8;
+  const u64 r = pi[PI_R], m = pi[PI_M];
+  const u64 ro = E.ref_off ? E.ref_off[p] : 0;
+  u32* ctr = B.team + (u64)p * 8;
+  u64* bufs = reinterpret_cast<u64*>(sm);
+  for (u64 t = i; t < ceil_div(m, (u64)T * kIlp); t += g) bat_build<T>(E, p, t, epoch);
+  team_barrier(ctr + 0, g, E.st);
+  for (u64 t = i; t < ceil_div(r, (u64)T * kIlp); t += g) bat_match_ilp<T>(E, B, p, t, epoch);
+  team_barrier(ctr + 1, g, E.st);
+  const u64 nst = ceil_div(r, T);
+  const u32 V = new_per_thread(pi[PI_MODE]);
+  const u64 ntn = ceil_div(m, (u64)T * V);
+  U64x2* ts = B.tsum + B.tbase[p];
+  U64x2* nts = ts + nst;
+  for (u64 t = i; t < nst; t += g) team_slot_sum<T>(E, p, r, ro, t, ts, red);
+  for (u64 t = i; t < ntn; t += g) team_new_sum<T>(E, p, m, V, t, epoch, nts, red);
+  team_barrier(ctr + 2, g, E.st);
+  u32 k = 0;
+  for (u64 t = i; t < nst; t += g, ++k) {
+    U64x2 run = tiles_prefix<T>(ts, t, red);
+    const u64 j = t * T + threadIdx.x;
+    const u32 src = j < r ? __ldcg(E.slot_src + ro + j) : kNoMatch;
+    bat_slot<T, false>(E, B, p, t, src, bufs + 33 * (k & 1), stage, run);
+  }
+  __syncthreads();
+  // the new records (the member with the last new tile writes the header)
+  const U64x2 slot_tot = tiles_prefix<T>(ts, nst, red);
+  const SmemTable none{nullptr, 0u, nullptr};
+  for (u64 t = i; t < (ntn ? ntn : 1); t += g) {
+    U64x2 run = tiles_prefix<T>(nts, t, red);
+    bat_new<T, false>(E, B, p, t, epoch, sm, stage, kStageCap, run, slot_tot, none);
+  }
+  team_barrier(ctr + 3, g, E.st);
+  const u64 mr = D.recv_off[p + 1] - D.recv_off[p];
+  const DecShared h = dec_header<false>(D, p, mr, hs, i == 0);
+  const u64 n = h.ok ? h.ns + h.nn : 0;
+  const u64 ndt = h.ok ? (n ? ceil_div(n, T) : 1) : 0;
+  U64x2* ds = nts + ceil_div(m, T);
+  for (u64 t = i; t < ndt; t += g) team_dec_sum<T>(D, p, h, t, ds, red);
+  team_barrier(ctr + 4, g, E.st);
+  const u32* codes = reinterpret_cast<const u32*>(D.wire + D.wire_off[p] + kHdrBytes);
+  k = 0;
+  for (u64 t = i; t < ndt; t += g, ++k) {
+    U64x2 run = tiles_prefix<T>(ds, t, red);
+    const u64 e = t * T + threadIdx.x;
+    const u32 c = e < n ? __ldcg(codes + e) : 0u;
+    bat_dec_tile<T, false>(D, B, p, t, c, h, mr, bufs + 33 * (k & 1), stage, run, nullptr);
+  }
+  __syncthreads();
 }
 
 // ---------------- the persistent kernel ----------------
 
 // Shared memory, for c = table_records: one region of max(4c, 2c + stage)
 // bytes that holds the hash table (2c u16, match step), then the list of new
-// records (c u16, new step) followed by the stage (T records + 48 bytes,
-// slot / new / decode steps) | MLP weights (predictor) | taken bits (c / 8).
+// records (c u16, new step) followed by the stage (the block's T records + 48
+// bytes for the new step, or one region per warp for the slot and decode
+// steps) | MLP weights (predictor) | taken bits (c / 8).
+__host__ __device__ constexpr size_t stage_bytes(u32 T) {
+  // the block stage (T records + 48 bytes) or the warps' stages, the larger
+  return (size_t)(T / 32) * kWarpStage > (size_t)T * kRecBytes + 48 ? (size_t)(T / 32) * kWarpStage
+                                                                      : (size_t)T * kRecBytes + 48;
+}
 __host__ __device__ constexpr size_t region_bytes(u32 T, u32 c) {
-  return (4 * (size_t)c > 2 * (size_t)c + (size_t)T * kRecBytes + 48)
-             ? 4 * (size_t)c
-             : 2 * (size_t)c + (size_t)T * kRecBytes + 48;
+  return (4 * (size_t)c > 2 * (size_t)c + stage_bytes(T)) ? 4 * (size_t)c
+                                                          : 2 * (size_t)c + stage_bytes(T);
 }
 
 template <int T, bool PR>
@@ -863,7 +1189,8 @@ __global__ void __launch_bounds__(T, (1024 / T) > 0 ? (1024 / T) : 1)
   float* sW = reinterpret_cast<float*>(dyn + region);
   u32* bits = reinterpret_cast<u32*>(dyn + region + (PR ? sizeof(float) * kMlpParams : 0));
   __shared__ U64x2 sm[33];
-  __shared__ u64 s_pair;
+  __shared__ u64 red[66];
+  __shared__ u64 s_item;
   __shared__ u32 s_cnt;
   __shared__ DecShared hs;
   if (PR) {
@@ -871,19 +1198,25 @@ __global__ void __launch_bounds__(T, (1024 / T) > 0 ? (1024 / T) : 1)
     if (params) load_mlp(sW, params);
   }
   const u32 epoch = __ldcg(E.epoch);
-  u64 next = 0;
-  if (threadIdx.x == 0) {
-    next = atomicAdd(B.ticket, 1ull);
-    s_cnt = 0;
-  }
+  const u64 n_items = __ldcg(B.n_items);
+  if (threadIdx.x == 0) s_cnt = 0;
   for (;;) {
-    if (threadIdx.x == 0)
-      s_pair = (next < B.n_pairs && !*(volatile u32*)B.abort) ? next : ~0ull;
+    // claim the next item only when this block is free: a team member never
+    // waits for an item that a busy block holds
+    if (threadIdx.x == 0) {
+      const u64 t = atomicAdd(B.ticket, 1ull);
+      s_item = (t < n_items && !*(volatile u32*)B.abort) ? B.items[t] : ~0ull;
+    }
     __syncthreads();
-    if (s_pair == ~0ull) break;
-    const u32 p = (u32)s_pair;
-    // claim the next pair now; no pair waits for another
-    if (threadIdx.x == 0) next = atomicAdd(B.ticket, 1ull);
+    const u64 it = s_item;
+    if (it == ~0ull) break;
+    const u32 p = (u32)(it >> 32);
+    const u32 g = (u32)it & 0xFFFFu;
+    if (g > 1) {
+      if constexpr (!PR)
+        team_pair<T>(E, D, B, p, (u32)(it >> 16) & 0xFFFFu, g, epoch, sm, red, stage, &hs);
+      continue;
+    }
     const u64* pi = E.info + (u64)p * 8;
     const u64 r = pi[PI_R], m = pi[PI_M];
     SmemTable tb{nullptr, 0u, bits};
@@ -929,8 +1262,9 @@ __global__ void __launch_bounds__(T, (1024 / T) > 0 ? (1024 / T) : 1)
         const u32 g = g_next;
         const u64 jn = (t + 1) * T + threadIdx.x;
         g_next = jn < r ? __ldcg(E.slot_src + ro + jn) : kNoMatch;
-        bat_slot<T, PR>(E, B, p, t, g, sm, stage, run);
+        bat_slot<T, PR>(E, B, p, t, g, reinterpret_cast<u64*>(sm) + 33 * (t & 1), stage, run);
       }
+      __syncthreads();  // the scan buffers and the stage are reused next
     }
     const U64x2 slot_tot = run;
     run = U64x2{0, 0};
@@ -956,7 +1290,7 @@ __global__ void __launch_bounds__(T, (1024 / T) > 0 ? (1024 / T) : 1)
         __syncthreads();
       }
     }
-    bat_dec<T, PR>(D, B, p, &hs, sm, stage, sW);
+    bat_dec<T, PR>(D, B, p, &hs, reinterpret_cast<u64*>(sm), stage, sW);
     __syncthreads();
   }
 }
@@ -1083,6 +1417,11 @@ static tera_status batched_impl(
   B.ticket = ctx->b_scalars + 1;
   B.ptot = ctx->b_ptot;
   B.abort = reinterpret_cast<u32*>(ctx->b_scalars + 2);
+  B.items = ctx->b_items;
+  B.n_items = ctx->b_scalars + 0;
+  B.team = ctx->b_team;
+  B.tsum = ctx->b_tsum;
+  B.tbase = ctx->b_tbase;
 
   if (PR) {
     if ((st = ensure_pred(ctx)) != TERA_OK) return st;
@@ -1101,13 +1440,24 @@ static tera_status batched_impl(
     }
   }
   cudaMemsetAsync(ctx->b_ptot, 0, sizeof(u64) * P * PT_COUNT, s);
+  cudaMemsetAsync(ctx->b_team, 0, sizeof(u32) * P * 8, s);
+  const int c = tn.ctas_per_sm;
+  const u32 want = (u32)tn.table_records;
+  size_t smem_bytes;
+  u32 table_records;
+  persistent_smem(T, PR, c, want, &smem_bytes, &table_records);
+  const u32 blocks = (u32)(ctx->num_sms * c);
+  // teams of at most 64 blocks (never more than the blocks resident at once)
+  const u32 gmax = blocks / 2 < 64 ? (blocks / 2 > 1 ? blocks / 2 : 1) : 64;
+  // pairs smaller than this stay on one block (and in shared memory if they fit)
+  const u64 min_team = (u64)16 * T > 2 * (u64)table_records ? (u64)16 * T : 2 * (u64)table_records;
   prof_begin(ctx, s);
   bat_setup_kernel<<<1, 1024, 0, s>>>(E, D, B, P, mode, reinterpret_cast<u64*>(wire_off),
                                       wire_capacity, ctx->cap_records, recv_capacity_units,
-                                      ctx->d_epoch);
+                                      ctx->d_epoch, T, blocks, gmax, min_team, PR ? 1 : 0,
+                                      ctx->b_items, ctx->b_items_cap, ctx->b_tbase,
+                                      ctx->b_tsum_cap, ctx->b_scalars + 0);
   if ((st = check_launch(ctx, "bat_setup_kernel", s)) != TERA_OK) return st;
-  const int c = tn.ctas_per_sm;
-  const u32 want = (u32)tn.table_records;
   if (PR) {
     if (T == 128) return launch_persistent<128, true>(ctx, E, D, B, c, want, s);
     return launch_persistent<256, true>(ctx, E, D, B, c, want, s);

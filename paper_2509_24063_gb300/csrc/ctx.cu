@@ -287,12 +287,25 @@ tera_status ensure_units(tera_ctx* ctx, uint64_t cap, cudaStream_t s) {
 }
 
 tera_status ensure_batched(tera_ctx* ctx) {
-  if (ctx->b_ptot) return TERA_OK;
+  const u64 P = ctx->n_pairs;
+  // work items: one per pair, plus at most (blocks + pairs) for the teams
+  const u64 items = 2 * P + (u64)ctx->num_sms * 16 + 64;
+  // tile totals of team pairs: (slots + 2 records + receiver slots) / 128 + 3 per pair
+  const u64 tsum = 4 * (ctx->cap_records / 128) + 3 * P + 64;
+  if (ctx->b_ptot && ctx->b_items_cap >= items && ctx->b_tsum_cap >= tsum) return TERA_OK;
   cudaDeviceSynchronize();
   tera_status st;
-  if ((st = alloc_dev(ctx->b_ptot, ctx->n_pairs * 4)) != TERA_OK) return st;
-  if ((st = alloc_dev(ctx->b_scalars, 4)) != TERA_OK) return st;
-  cudaMemset(ctx->b_scalars, 0, 4 * sizeof(u64));
+  if (!ctx->b_ptot) {
+    if ((st = alloc_dev(ctx->b_ptot, P * 4)) != TERA_OK) return st;
+    if ((st = alloc_dev(ctx->b_scalars, 4)) != TERA_OK) return st;
+    if ((st = alloc_dev(ctx->b_team, P * 8)) != TERA_OK) return st;
+    if ((st = alloc_dev(ctx->b_tbase, P)) != TERA_OK) return st;
+    cudaMemset(ctx->b_scalars, 0, 4 * sizeof(u64));
+  }
+  if ((st = alloc_dev(ctx->b_items, items)) != TERA_OK) return st;
+  if ((st = alloc_dev(ctx->b_tsum, tsum)) != TERA_OK) return st;
+  ctx->b_items_cap = items;
+  ctx->b_tsum_cap = tsum;
   return TERA_OK;
 }
 
@@ -429,6 +442,10 @@ tera_status tera_ctx_destroy(tera_ctx* c) {
   free_dev(c->d_stats);
   free_dev(c->b_scalars);
   free_dev(c->b_ptot);
+  free_dev(c->b_items);
+  free_dev(c->b_team);
+  free_dev(c->b_tsum);
+  free_dev(c->b_tbase);
   free_dev(c->cseg_enc);
   free_dev(c->cseg_dec);
   free_dev(c->pscr);

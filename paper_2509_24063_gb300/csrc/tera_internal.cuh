@@ -295,8 +295,14 @@ struct tera_ctx {
   float* mlp_scratch;       // training: compacted samples + gradient partials
   uint64_t mlp_scratch_cap;
   // batched codec (batched.cu)
-  tera::u64* b_scalars;  // [1] pair ticket, [2] abort flag
+  tera::u64* b_scalars;  // [0] work items, [1] ticket, [2] abort flag
   tera::u64* b_ptot;     // [P * 4] per-pair totals of the match step
+  tera::u64* b_items;    // work list (team items first)
+  uint64_t b_items_cap;
+  uint32_t* b_team;      // [P * 8] barrier counters of the teams
+  tera::U64x2* b_tsum;   // per-tile totals of the team pairs
+  uint64_t b_tsum_cap;
+  tera::u64* b_tbase;    // [P] first tile total of each team pair
 };
 
 namespace tera {

@@ -50,6 +50,15 @@ def test_batched_schedule_invariance(tera, tune):
     run_chain(tera, wl, 3, path="batched", tune=tune)
 
 
+@pytest.mark.parametrize("tune", [None, (256, 4, 32, 0), (512, 2, 0, 0)])
+def test_batched_skewed_pairs_carried_by_teams(tera, tune):
+    # two dense blobs: a few pairs hold most records, so they exceed the
+    # average load of a block and are carried by teams of blocks
+    wl = Workload("t", 200000, (0.0,) * 3, (400.0, 400.0, 400.0), (2, 2, 2), 20.0, 3,
+                  layout="blobs", n_blobs=2, p_grow=0.1, p_divide=0.02, p_die=0.02, seed=12)
+    run_chain(tera, wl, 3, path="batched", tune=tune)
+
+
 def test_graph_replay_matches_oracle(tera):
     wl = Workload("t", 50000, (0.0,) * 3, (200.0, 200.0, 100.0), (2, 2, 1), 20.0, 5,
                   p_grow=0.1, p_divide=0.02, p_die=0.02, seed=6)
