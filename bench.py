@@ -384,16 +384,33 @@ def main():
                   file=sys.stderr)
         print(json.dumps(stats), file=sys.stderr)
 
-    # end to end: host-resident state in, wire messages out, through the same API
-    e2e = None
-    if args.e2e_steps > 0:
-        e2e = run_e2e(args, tera, wl, states, nmax, max_records, local, ex.tune)
-
-    cpu = None
+    # the CPU baseline's sample (host copies) and the end-to-end inputs are
+    # taken from the device states; then every device buffer of the measured
+    # run is released, so the end-to-end leg runs on a clean device
+    hs = None
+    ns = 0
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        from synth import scaled
         ns = min(args.cpu_sample, int(states[0]["x"].shape[0]))
         hs = cpu_sample_states(wl, states[args.warmup - 1:args.warmup + 1], ns)
+    agents_cfg = int(states[args.warmup]["x"].shape[0])
+    tune_e2e = ex.tune
+    e2e_host = None
+    if args.e2e_steps > 0:
+        e2e_host = e2e_inputs(args, states)
+    del ex, states
+    ctx.close()
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+
+    # end to end: host-resident state in, wire messages out, through the same API
+    e2e = None
+    if e2e_host is not None:
+        e2e = run_e2e(args, tera, wl, e2e_host, nmax, max_records, local, tune_e2e)
+        del e2e_host
+
+    cpu = None
+    if hs is not None:
+        from synth import scaled
         tms = oracle_time(scaled(wl, ns), hs)
         cpu = {"value": int(hs[1]["x"].shape[0]) / tms[1], "unit": "agents/s", "cores": 1,
                "kind": "oracle",
@@ -406,7 +423,7 @@ def main():
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
         "data": "synthetic",
         "config": {"workload": args.workload + (f"@{args.agents}" if args.agents else ""),
-                   "agents": int(states[args.warmup]["x"].shape[0]),
+                   "agents": agents_cfg,
                    "grid": list(wl.grid), "aura_width": wl.w, "path": args.path,
                    "cuda_graph": use_graph, "tune": tune_info,
                    "l2": "inputs larger than L2 (64 B/agent state per step)",
@@ -423,7 +440,6 @@ def main():
     }
     if rank == 0:
         print(json.dumps(line))
-    ctx.close()
     if world > 1:
         dist.destroy_process_group()
     return 0
@@ -512,7 +528,16 @@ def run_predictor(args):
     return 0
 
 
-def run_e2e(args, tera, wl, states, nmax, max_records, local, tune=None):
+def e2e_inputs(args, states):
+    """Pinned host copies of the states the end-to-end leg runs on (the one
+    before the timed ones, then e2e_steps timed ones)."""
+    from paper_2509_24063_gb300.host import FIELDS
+    k = min(args.e2e_steps, args.steps)
+    return [{f: states[t][f].cpu().pin_memory() for f in FIELDS}
+            for t in range(args.warmup - 1, args.warmup + k)]
+
+
+def run_e2e(args, tera, wl, host, nmax, max_records, local, tune=None):
     """Same metric through the public API on host-resident state
     (paper_2509_24063_gb300.host.HostExchange): every step copies the eight
     state columns from pinned host memory and writes the used wire bytes back
@@ -520,10 +545,7 @@ def run_e2e(args, tera, wl, states, nmax, max_records, local, tune=None):
     computes (double-buffered device inputs)."""
     import torch
     from paper_2509_24063_gb300.host import FIELDS, HostExchange
-    k = min(args.e2e_steps, args.steps)
-    host = []
-    for t in range(args.warmup - 1, args.warmup + k):
-        host.append({f: states[t][f].cpu().pin_memory() for f in FIELDS})
+    k = len(host) - 1
     ctx = tera.Context(wl.lo, wl.hi, wl.grid, wl.w, device=local)
     hx = HostExchange(ctx, nmax, max_records, path=args.path, tune=tune)
     outs = [torch.empty(hx.wire_capacity, dtype=torch.uint8).pin_memory() for _ in range(2)]
