@@ -364,6 +364,9 @@ tera_status tera_ctx_create(tera_ctx** out, const tera_grid* grid, int device, u
     t.klo[a] = key(lo);
     t.khi[a] = key(hi);
     t.n[a] = n;
+    // only a starting guess: the index is fixed by exact key comparisons
+    t.flo[a] = (float)lo;
+    t.fscale[a] = (float)((double)n / (hi - lo));
     ncell_tmp[a] = (uint64_t)std::floor((hi - lo) / grid->w) + 1;
   }
   if (cudaSetDevice(device) != cudaSuccess) return TERA_ECUDA;

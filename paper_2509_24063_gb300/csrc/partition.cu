@@ -25,20 +25,17 @@ struct SmemGrid {
   u64 ktl[3][kMaxAxis];
   u64 kth[3][kMaxAxis];
   u64 klo[3], khi[3];
+  float flo[3], fscale[3];
   int n[3];
-  int top[3];  // largest power of two <= n - 1 (0 when n == 1): first binary-search step
 };
 
 __device__ __forceinline__ void load_grid(SmemGrid& s, const GridTables* __restrict__ g) {
   if (threadIdx.x < 3) {
-    const int n = g->n[threadIdx.x];
-    int top = 0;
-    while (2 * (top ? top : 1) <= n - 1) top = top ? 2 * top : 1;
-    if (top == 0 && n - 1 >= 1) top = 1;
-    s.top[threadIdx.x] = top;
-    s.n[threadIdx.x] = n;
+    s.n[threadIdx.x] = g->n[threadIdx.x];
     s.klo[threadIdx.x] = g->klo[threadIdx.x];
     s.khi[threadIdx.x] = g->khi[threadIdx.x];
+    s.flo[threadIdx.x] = g->flo[threadIdx.x];
+    s.fscale[threadIdx.x] = g->fscale[threadIdx.x];
   }
   for (int a = 0; a < 3; ++a) {
     const int n = g->n[a];
@@ -51,32 +48,41 @@ __device__ __forceinline__ void load_grid(SmemGrid& s, const GridTables* __restr
   __syncthreads();
 }
 
-// One axis: box index i = #{k in 1..n-1 : v >= e[k]} (binary search over the
-// increasing edge keys) and the neighbour offsets whose aura holds v.
-// Returns opts: bit 0 offset -1 qualifies (i > 0 and v < e[i] + w), bit 1
-// offset 0, bit 2 offset +1 (i < n-1 and v >= e[i+1] - w); 0 when v is not in
-// [lo, hi).
-__device__ __forceinline__ u32 classify_axis(u64 k, int a, const SmemGrid& s, int* idx) {
+// One axis: box index i = #{k in 1..n-1 : v >= e[k]} and the neighbour
+// offsets whose aura holds v.  A float32 estimate of i is corrected by exact
+// comparisons of the 64-bit keys (so the result is exactly the rule's; the
+// estimate only saves the binary search).  Returns opts: bit 0 offset -1
+// qualifies (i > 0 and v < e[i] + w), bit 1 offset 0, bit 2 offset +1
+// (i < n-1 and v >= e[i+1] - w); 0 when v is not in [lo, hi).
+__device__ __forceinline__ u32 classify_axis(u64 bits, int a, const SmemGrid& s, int* idx) {
+  const u64 k = key_of(bits);
   if (!(k >= s.klo[a] && k < s.khi[a])) {
     *idx = 0;
     return 0u;
   }
   const int n = s.n[a];
-  int i = 0;
-  for (int step = s.top[a]; step > 0; step >>= 1)
-    if (i + step <= n - 1 && k >= s.ke[a][i + step]) i += step;
+  const float f = (__double2float_rn(__longlong_as_double((long long)bits)) - s.flo[a]) * s.fscale[a];
+  int i = f > 0.0f ? (int)f : 0;
+  i = i < n - 1 ? i : n - 1;
+  while (i > 0 && k < s.ke[a][i]) --i;
+  while (i < n - 1 && k >= s.ke[a][i + 1]) ++i;
   *idx = i;
   const u32 lowq = (i > 0) && (k < s.ktl[a][i]);
   const u32 highq = (i < n - 1) && (k >= s.kth[a][i]);
   return 2u | lowq | (highq << 2);
 }
 
+// Bits 0, 1, 2 of v moved to bits 0, d, 2d.
+__device__ __forceinline__ u32 spread3(u32 v, u32 d) {
+  return (v & 1u) | ((v & 2u) << (d - 1)) | ((v & 4u) << (2 * d - 2));
+}
+
 __device__ __forceinline__ void classify_agent(u64 bx, u64 by, u64 bz, const SmemGrid& s,
                                                int* owner, u32* mask, bool* ok) {
   int ix, iy, iz;
-  const u32 ox = classify_axis(key_of(bx), 0, s, &ix);
-  const u32 oy = classify_axis(key_of(by), 1, s, &iy);
-  const u32 oz = classify_axis(key_of(bz), 2, s, &iz);
+  const u32 ox = classify_axis(bx, 0, s, &ix);
+  const u32 oy = classify_axis(by, 1, s, &iy);
+  const u32 oz = classify_axis(bz, 2, s, &iz);
   *ok = ox && oy && oz;
   if (!*ok) {
     *owner = -1;
@@ -84,14 +90,9 @@ __device__ __forceinline__ void classify_agent(u64 bx, u64 by, u64 bz, const Sme
     return;
   }
   *owner = ix + s.n[0] * (iy + s.n[1] * iz);
-  u32 m = 0;
-#pragma unroll
-  for (int dz = 0; dz < 3; ++dz) {
-#pragma unroll
-    for (int dy = 0; dy < 3; ++dy) {
-      if ((oz >> dz) & (oy >> dy) & 1u) m |= ox << (3 * dy + 9 * dz);
-    }
-  }
+  // bit (dx + 3 dy + 9 dz) for every qualifying offset triple: the products
+  // place copies of ox at 3 dy and of that row at 9 dz (no carries)
+  const u32 m = ox * spread3(oy, 3) * spread3(oz, 9);
   *mask = m & ~(1u << 13);
 }
 

@@ -50,6 +50,7 @@ struct DevStatus {
 struct GridTables {
   int n[3];
   int pad;
+  float flo[3], fscale[3];        // float estimate of the box index: (x - lo) * n / (hi - lo)
   u64 klo[3], khi[3];             // domain [lo, hi)
   u64 ke[3][kMaxAxis + 1];        // box edges e[k]
   u64 ktl[3][kMaxAxis];           // e[k] + w   (aura towards box k-1)

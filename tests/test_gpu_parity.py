@@ -181,6 +181,47 @@ def test_edges_and_thresholds(tera):
     ctx.close()
 
 
+@pytest.mark.parametrize("lo,hi,grid,w", [
+    ((-1.0e9, 0.0, 5.0), (1.0e9, 1.0, 35.0), (256, 3, 1), 0.1),
+    ((1.0e-3, -7.0, 0.0), (1.0e-3 + 97.0 * 0.37, 89.0, 2.0), (97, 89, 2), 0.05),
+    ((3.0e15, -1.0, -1.0), (3.0e15 + 256.0, 1.0, 1.0), (32, 2, 2), 0.5),
+])
+def test_classification_many_boxes_wide_domains(tera, lo, hi, grid, w):
+    # the box index starts from a float32 estimate and is fixed by exact key
+    # comparisons: every owner and mask must equal the oracle's, including
+    # points on edges, on aura thresholds and one ulp away
+    import math
+    rng = np.random.default_rng(sum(grid))
+    n = 50000
+    pts = np.zeros((n, 3))
+    for a in range(3):
+        E = np.array([lo[a] + ((hi[a] - lo[a]) * k) / grid[a] for k in range(grid[a])] + [hi[a]])
+        c = rng.uniform(lo[a], hi[a], n)
+        pick = rng.random(n)
+        cand = E[rng.integers(0, grid[a] + 1, n)]
+        c = np.where(pick < 0.2, cand, c)
+        c = np.where((pick >= 0.2) & (pick < 0.3), cand + w, c)
+        c = np.where((pick >= 0.3) & (pick < 0.4), cand - w, c)
+        c = np.where((pick >= 0.4) & (pick < 0.5), np.nextafter(c, np.inf), c)
+        c = np.where((pick >= 0.5) & (pick < 0.6), np.nextafter(c, -np.inf), c)
+        pts[:, a] = np.clip(c, lo[a], math.nextafter(hi[a], lo[a]))
+    ctx = tera.Context(lo, hi, grid, w)
+    part = tera.PartitionBuffers.allocate(n, ctx.n_pairs, 7 * n, torch.device("cuda"))
+    st = {"id": torch.arange(n, dtype=torch.int64, device="cuda"),
+          "x": torch.from_numpy(pts[:, 0].copy()).cuda(), "y": torch.from_numpy(pts[:, 1].copy()).cuda(),
+          "z": torch.from_numpy(pts[:, 2].copy()).cuda()}
+    for f in ("diameter", "volume", "adherence", "density"):
+        st[f] = torch.ones(n, dtype=torch.float64, device="cuda")
+    ctx.partition(st, part)
+    ctx.status()
+    g = oracle.make_grid(lo, hi, grid, w)
+    code, owner, mask = oracle.classify(g, pts[:, 0].copy(), pts[:, 1].copy(), pts[:, 2].copy())
+    assert code == oracle.OK
+    np.testing.assert_array_equal(part.owner[:n].cpu().numpy(), owner)
+    np.testing.assert_array_equal(u32(part.mask[:n]), mask)
+    ctx.close()
+
+
 def test_special_float_values_round_trip(tera):
     n = 4000
     rng = np.random.default_rng(3)
