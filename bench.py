@@ -245,6 +245,8 @@ def main():
     ap.add_argument("--path", default="batched", choices=["batched", "all_pairs", "per_subdomain"])
     ap.add_argument("--no-graph", action="store_true", help="batched path without CUDA graphs")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--ref-interval", type=int, default=1,
+                    help="reference interval K (the reference is the message of every K-th iteration)")
     ap.add_argument("--tune", default="",
                     help="fixed batched schedule block,ctas_per_sm[,table_records] (skips the tuner)")
     ap.add_argument("--e2e-steps", type=int, default=3)
@@ -296,7 +298,7 @@ def main():
     ctx = tera.Context(wl.lo, wl.hi, wl.grid, wl.w, device=local)
     fixed = tuple(int(v) for v in args.tune.split(",")) if args.tune else None
     ex = tera.AuraExchange(ctx, max_agents=nmax, max_records=max_records, path=args.path,
-                           tune=fixed)
+                           tune=fixed, ref_interval=args.ref_interval)
     stream = torch.cuda.current_stream()
     use_graph = args.path == "batched" and not args.no_graph
     tune_info = {"tune": list(fixed), "candidates": 0} if fixed else None
@@ -425,7 +427,7 @@ def main():
         "config": {"workload": args.workload + (f"@{args.agents}" if args.agents else ""),
                    "agents": agents_cfg,
                    "grid": list(wl.grid), "aura_width": wl.w, "path": args.path,
-                   "cuda_graph": use_graph, "tune": tune_info,
+                   "cuda_graph": use_graph, "tune": tune_info, "ref_interval": args.ref_interval,
                    "l2": "inputs larger than L2 (64 B/agent state per step)",
                    "parallelism": f"replicas{world}"},
         "encode_decode_gbs": codec_gbs,
@@ -547,7 +549,8 @@ def run_e2e(args, tera, wl, host, nmax, max_records, local, tune=None):
     from paper_2509_24063_gb300.host import FIELDS, HostExchange
     k = len(host) - 1
     ctx = tera.Context(wl.lo, wl.hi, wl.grid, wl.w, device=local)
-    hx = HostExchange(ctx, nmax, max_records, path=args.path, tune=tune)
+    hx = HostExchange(ctx, nmax, max_records, path=args.path, tune=tune,
+                      ref_interval=args.ref_interval)
     outs = [torch.empty(hx.wire_capacity, dtype=torch.uint8).pin_memory() for _ in range(2)]
     hx.step(host[0], outs[0]).wait()  # first iteration of this chain (allocates scratch)
     torch.cuda.synchronize()

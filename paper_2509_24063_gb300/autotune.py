@@ -72,14 +72,15 @@ def tune_batched(ex, state: dict, reps: int = 2, candidates=None, use_cache: boo
     t = ex.t
     ex.step(state)
     torch.cuda.synchronize()
-    records = int(ex.pair_off[t % 2][-1].item())
+    records = int(ex.pair_off[ex.slot_of(t)][-1].item())
     if use_cache:
         cached = load_cached(ctx, records)
         if cached is not None:
             ex.tune = cached
             return cached, {}
-    cur, prv = t % 2, (t + 1) % 2
     first = t == 0
+    cur = ex.slot_of(t)
+    prv = ex.slot_of(ex.ref_iteration(t)) if not first else 1 - cur
     args = (ex.rec, ex.pair_off[cur], None if first else ex.ref[prv],
             None if first else ex.pair_off[prv], ex.ref[cur], ex.wire, ex.wire_off, ex.wire_len,
             None if first else ex.recv[prv], None if first else ex.recv_off[prv], ex.recv[cur],

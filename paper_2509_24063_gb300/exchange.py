@@ -10,6 +10,12 @@ Paths (all produce the same bytes):
 
 Buffers are allocated once for a maximum agent count and record count; the
 sender and receiver references are double-buffered (previous / next).
+
+Reference interval K (paper Sec. 2.3: the reference is updated at regular
+intervals): the message of iteration 0 and of every K-th iteration after it
+becomes the reference of the next K iterations; in between, messages are
+encoded (and decoded) against that older reference, and their outputs go to
+the other buffer.  K = 1 updates the reference every iteration.
 """
 from __future__ import annotations
 
@@ -24,9 +30,13 @@ PATHS = ("per_subdomain", "all_pairs", "batched")
 class AuraExchange:
     def __init__(self, ctx: Context, max_agents: int, max_records: int, mode: int = MODE_XOR,
                  per_subdomain: bool = False, path: str | None = None, tune=None,
-                 predictor: bool = False, params=None, allow_residual: bool = True):
+                 predictor: bool = False, params=None, allow_residual: bool = True,
+                 ref_interval: int = 1):
         self.ctx = ctx
         self.mode = mode
+        if ref_interval < 1:
+            raise ValueError("ref_interval must be >= 1")
+        self.K = int(ref_interval)
         self.path = path or ("per_subdomain" if per_subdomain else "all_pairs")
         if self.path not in PATHS:
             raise ValueError(f"path must be one of {PATHS}")
@@ -71,11 +81,21 @@ class AuraExchange:
             return [(0, self.P)]
         return [(27 * s, 27 * s + 27) for s in range(self.P // 27)]
 
+    def slot_of(self, t: int) -> int:
+        """Buffer of iteration t's outputs: ceil(t / K) mod 2."""
+        return ((t + self.K - 1) // self.K) % 2
+
+    def ref_iteration(self, t: int) -> int:
+        """The iteration whose message is iteration t's reference (t >= 1)."""
+        return self.K * ((t - 1) // self.K)
+
     def _launch(self, state: dict, t: int, stream=None):
-        """Enqueue iteration t (reference parity t % 2) on the stream."""
+        """Enqueue iteration t on the stream (outputs to slot_of(t), reference
+        from the buffers of ref_iteration(t))."""
         ctx = self.ctx
-        cur, prv = t % 2, (t + 1) % 2
         first = t == 0
+        cur = self.slot_of(t)
+        prv = self.slot_of(self.ref_iteration(t)) if not first else 1 - cur
         part = self.part
         pair_off = self.pair_off[cur]
         part.pair_off = pair_off  # this iteration's offsets become the next one's reference layout
@@ -122,7 +142,7 @@ class AuraExchange:
         """Classify, pack, encode and decode every pair for one iteration."""
         self._launch(state, self.t, stream)
         self.t += 1
-        return (self.t + 1) % 2
+        return self.last
 
     def capture(self, state: dict, t: int | None = None) -> torch.cuda.CUDAGraph:
         """A CUDA graph of iteration t (default: the next one) on this state's buffers.
@@ -141,7 +161,7 @@ class AuraExchange:
     # --- views of the last iteration's outputs ---
     @property
     def last(self) -> int:
-        return (self.t + 1) % 2
+        return self.slot_of(self.t - 1) if self.t > 0 else 0
 
     def sender_ref(self):
         return self.ref[self.last], self.pair_off[self.last]

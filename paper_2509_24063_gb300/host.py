@@ -34,9 +34,10 @@ class Pending:
 
 class HostExchange:
     def __init__(self, ctx: Context, max_agents: int, max_records: int, path: str = "batched",
-                 tune=None, depth: int = 2):
+                 tune=None, depth: int = 2, ref_interval: int = 1):
         self.ctx = ctx
-        self.ex = AuraExchange(ctx, max_agents, max_records, path=path, tune=tune)
+        self.ex = AuraExchange(ctx, max_agents, max_records, path=path, tune=tune,
+                               ref_interval=ref_interval)
         dev = torch.device("cuda", ctx.device)
         self.depth = depth
         self.inputs = [{f: torch.empty(max_agents, dtype=torch.int64 if f == "id" else torch.float64,

@@ -117,6 +117,39 @@ def test_ragged_population_sizes(tera, n):
     run_chain(tera, wl, 3)
 
 
+@pytest.mark.parametrize("path", ["all_pairs", "batched"])
+@pytest.mark.parametrize("K", [2, 3])
+def test_reference_interval(tera, path, K):
+    # the message of iteration 0 and of every K-th iteration after it is the
+    # reference of the next K iterations, on both sides (the oracle is given
+    # that older reference explicitly)
+    wl = Workload("t", 30000, (0.0,) * 3, (300.0, 200.0, 200.0), (3, 2, 2), 25.0, 8,
+                  p_grow=0.1, p_divide=0.02, p_die=0.02, seed=21)
+    states = list(Generator(wl, device="cuda").series(wl.iterations))
+    nmax = max(int(s["x"].shape[0]) for s in states)
+    ctx = tera.Context(wl.lo, wl.hi, wl.grid, wl.w)
+    ex = tera.AuraExchange(ctx, max_agents=nmax, max_records=4 * nmax + 1024, path=path,
+                           ref_interval=K)
+    g = oracle.make_grid(wl.lo, wl.hi, wl.grid, wl.w)
+    res_of = {}
+    wire = []
+    for t, st in enumerate(states):
+        ex.step(st)
+        ctx.status()
+        if t == 0:
+            ref = recv = None
+        else:
+            r = res_of[K * ((t - 1) // K)]
+            ref, recv = (r["ref_next"], r["pair_off"]), (r["recv"], r["recv_off"])
+        res = oracle.exchange_iteration(g, to_numpy(st), ref=ref, recv_ref=recv)
+        compare_iteration(ctx, ex, st, res, ctx.n_pairs)
+        res_of[t] = res
+        wire.append(int(res["wire_len"].sum()))
+    ctx.close()
+    # a stale reference costs bytes: iterations K..2K-1 all use iteration 0's message
+    assert wire[K] >= wire[1] if K > 1 else True
+
+
 def test_single_box_grid_has_no_messages(tera):
     wl = Workload("t", 5000, (0.0,) * 3, (50.0,) * 3, (1, 1, 1), 10.0, 2, seed=4)
     stats = run_chain(tera, wl, 2)
