@@ -13,6 +13,7 @@ the host cores instead, on a bounded sample of the same workload.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import os
 import statistics
@@ -188,7 +189,7 @@ def cpu_sample_states(wl, states_gpu, n_sample):
 def oracle_time(wl, host_states):
     """Oracle (single thread) over a chain of host states; returns per-state seconds."""
     import oracle
-    g = oracle.make_grid(wl.lo, wl.hi, wl.grid, wl.w)
+    g = oracle.make_grid(wl.lo, wl.hi, wl.grid, wl.w, wl.periodic)
     ref = recv_ref = None
     times = []
     for s in host_states:
@@ -209,7 +210,7 @@ def run_reference(args):
         return 0
     wl0 = WORKLOADS[args.workload]
     n = min(wl0.n0, args.ref_agents)
-    wl = scaled(wl0, n)
+    wl = scaled(wl0, n, boundary=args.boundary)
     dev = "cuda" if torch.cuda.is_available() else "cpu"
     gen = Generator(wl, device=dev)
     states = [to_numpy(s) for s in gen.series(args.warmup + args.steps)]
@@ -245,6 +246,8 @@ def main():
     ap.add_argument("--path", default="batched", choices=["batched", "all_pairs", "per_subdomain"])
     ap.add_argument("--no-graph", action="store_true", help="batched path without CUDA graphs")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--boundary", default="closed", choices=["closed", "toroidal"],
+                    help="space boundary of the workload (toroidal: every axis wraps)")
     ap.add_argument("--ref-interval", type=int, default=1,
                     help="reference interval K (the reference is the message of every K-th iteration)")
     ap.add_argument("--tune", default="",
@@ -284,6 +287,8 @@ def main():
     if args.agents:
         from synth import scaled
         wl = scaled(wl, args.agents)
+    if args.boundary != wl.boundary:
+        wl = dataclasses.replace(wl, boundary=args.boundary)
     total_steps = args.warmup + args.steps
     # replicas: each rank runs its own seeded population (weak scaling, no exchange between ranks)
     gen = Generator(wl, device="cuda", seed=wl.seed + 7919 * rank)
@@ -295,7 +300,7 @@ def main():
     torch.cuda.synchronize()
     nmax = max(int(s["x"].shape[0]) for s in states)
     max_records = int(nmax * 0.35) + 4096 if wl.grid[0] >= 8 else 4 * nmax + 4096
-    ctx = tera.Context(wl.lo, wl.hi, wl.grid, wl.w, device=local)
+    ctx = tera.Context(wl.lo, wl.hi, wl.grid, wl.w, device=local, periodic=wl.periodic)
     fixed = tuple(int(v) for v in args.tune.split(",")) if args.tune else None
     ex = tera.AuraExchange(ctx, max_agents=nmax, max_records=max_records, path=args.path,
                            tune=fixed, ref_interval=args.ref_interval)
@@ -428,6 +433,7 @@ def main():
                    "agents": agents_cfg,
                    "grid": list(wl.grid), "aura_width": wl.w, "path": args.path,
                    "cuda_graph": use_graph, "tune": tune_info, "ref_interval": args.ref_interval,
+                   "boundary": wl.boundary,
                    "l2": "inputs larger than L2 (64 B/agent state per step)",
                    "parallelism": f"replicas{world}"},
         "encode_decode_gbs": codec_gbs,
@@ -464,7 +470,7 @@ def run_predictor(args):
     gen = Generator(wl, device="cuda")
     nmax = int(wl.n0 * 1.05) + 4096
     max_records = 2 * nmax
-    ctx = tera.Context(wl.lo, wl.hi, wl.grid, wl.w, device=local)
+    ctx = tera.Context(wl.lo, wl.hi, wl.grid, wl.w, device=local, periodic=wl.periodic)
     ex = tera.AuraExchange(ctx, nmax, max_records, path="all_pairs", predictor=True)
     every = max(1, args.train_iters // 20)
     picks = set(range(2, args.train_iters, every))
@@ -548,7 +554,7 @@ def run_e2e(args, tera, wl, host, nmax, max_records, local, tune=None):
     import torch
     from paper_2509_24063_gb300.host import FIELDS, HostExchange
     k = len(host) - 1
-    ctx = tera.Context(wl.lo, wl.hi, wl.grid, wl.w, device=local)
+    ctx = tera.Context(wl.lo, wl.hi, wl.grid, wl.w, device=local, periodic=wl.periodic)
     hx = HostExchange(ctx, nmax, max_records, path=args.path, tune=tune,
                       ref_interval=args.ref_interval)
     outs = [torch.empty(hx.wire_capacity, dtype=torch.uint8).pin_memory() for _ in range(2)]

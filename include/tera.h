@@ -97,11 +97,19 @@ typedef struct {
 } tera_soa;
 
 /* Partitioning grid: box edges e[k] = lo + ((hi - lo) * k) / n (k < n),
- * e[n] = hi, per axis; aura width w with 0 < w < every box side. */
+ * e[n] = hi, per axis; aura width w with 0 < w < every box side.
+ * periodic: bit a set makes axis a toroidal (Sec. 2.5 lists open, closed
+ * and toroidal space boundaries): box n-1 and box 0 are neighbours along it,
+ * so the aura towards offset -1 of box 0 goes to box n-1 and that towards
+ * offset +1 of box n-1 to box 0, with the same thresholds as inside the
+ * domain.  Records keep their unshifted coordinates.  A periodic axis needs
+ * n >= 3 (each neighbour bit then names a distinct box).  reserved must be 0. */
 typedef struct {
   double lo[3], hi[3];
   int32_t n[3];
   double w;
+  uint32_t periodic;
+  uint32_t reserved;
 } tera_grid;
 
 /* Outputs of tera_partition; device pointers, caller-owned.
@@ -120,7 +128,8 @@ typedef struct {
 /* Create a context on `device` for one grid (Sec. 2.1 partitioning grid).
  * Box edges and aura thresholds are computed here once, in binary64.
  * Returns TERA_EINVAL when a grid axis has n < 1 or n > 256, lo >= hi, or w is
- * not strictly between 0 and every box side.  class_id is written into every
+ * not strictly between 0 and every box side, a periodic axis has n < 3, or
+ * periodic has bits above 2 or reserved is nonzero.  class_id is written into every
  * buffer header (the paper replaces the vtable pointer by a class id). */
 tera_status tera_ctx_create(tera_ctx** out, const tera_grid* grid, int device,
                             uint32_t class_id);
@@ -137,7 +146,8 @@ tera_status tera_ctx_reserve(tera_ctx* ctx, int64_t max_agents, uint64_t max_rec
 /* Step a1 (Sec. 2.1 "Aura Update"): owner box and aura mask of every agent,
  * and the per-pair stable lists.  Agent i is in the aura of neighbour box at
  * offset o when, on every axis, o = 0, or o = -1 and x < e[i] + w, or o = +1
- * and x >= e[i+1] - w (the neighbour must exist).  Agents outside [lo, hi)
+ * and x >= e[i+1] - w (the neighbour must exist; on a periodic axis it
+ * always does, its index taken modulo n).  Agents outside [lo, hi)
  * get owner -1, mask 0 and latch TERA_EDOMAIN.  More than idx_capacity
  * records latch TERA_ECAPACITY (required capacity reported) and leave every
  * pair empty. */

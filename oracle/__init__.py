@@ -47,14 +47,16 @@ def build(force: bool = False) -> str:
 
 class Grid(C.Structure):
     _fields_ = [("lo", C.c_double * 3), ("hi", C.c_double * 3), ("n", C.c_int32 * 3),
-                ("w", C.c_double)]
+                ("w", C.c_double), ("periodic", C.c_uint32), ("reserved", C.c_uint32)]
 
 
-def make_grid(lo, hi, n, w) -> Grid:
+def make_grid(lo, hi, n, w, periodic: int = 0) -> Grid:
+    """Grid of Sec. 2.1; bit a of ``periodic`` makes axis a toroidal (Sec. 2.5)."""
     g = Grid()
     for a in range(3):
         g.lo[a], g.hi[a], g.n[a] = float(lo[a]), float(hi[a]), int(n[a])
     g.w = float(w)
+    g.periodic = int(periodic)
     return g
 
 

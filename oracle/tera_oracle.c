@@ -53,9 +53,13 @@ static uint64_t f64_bits(double d) {
 /* ---------- grid (Sec. 2.1; Sec. 2.4 "Partitioning Grid") ---------- */
 
 int or_grid_check(const or_grid* g) {
+  if (g->reserved != 0 || (g->periodic & ~7u) != 0) return OR_EINVAL;
   for (int a = 0; a < 3; ++a) {
     if (g->n[a] < 1) return OR_EINVAL;
     if (!(g->lo[a] < g->hi[a])) return OR_EINVAL;
+    /* on a toroidal axis the two neighbours of a box must be two other
+     * boxes, so that a neighbour offset names one box */
+    if ((g->periodic >> a & 1u) && g->n[a] < 3) return OR_EINVAL;
   }
   /* The aura must be narrower than a partitioning box (Sec. 2.1): w is
    * positive and below the smallest box side on every axis. */
@@ -88,7 +92,9 @@ void or_axis_edges(const or_grid* g, int axis, double* e) {
  * Ownership is half-open [e[i], e[i+1]).  An agent is in the aura of the
  * neighbour box at offset o (per axis -1, 0, +1) when it lies within w of that
  * box in the L-infinity sense: for o = -1, x < e[i] + w; for o = +1,
- * x >= e[i+1] - w; o = 0 always qualifies.  The neighbour must exist. */
+ * x >= e[i+1] - w; o = 0 always qualifies.  The neighbour must exist: on a
+ * closed axis box 0 has no -1 neighbour and box n-1 no +1 neighbour; on a
+ * toroidal axis (Sec. 2.5) the neighbour index wraps modulo n. */
 int or_classify(const or_grid* g, const double* x, const double* y, const double* z,
                 int64_t n, int32_t* owner, uint32_t* mask) {
   int st = or_grid_check(g);
@@ -120,9 +126,10 @@ int or_classify(const or_grid* g, const double* x, const double* y, const double
       for (int k = 1; k <= na - 1; ++k)
         if (v[a] >= e[k]) ++cnt;
       idx[a] = cnt;
-      qual[a][0] = (cnt > 0) && (v[a] < e[cnt] + g->w);
+      int wrap = (int)(g->periodic >> a & 1u);
+      qual[a][0] = (cnt > 0 || wrap) && (v[a] < e[cnt] + g->w);
       qual[a][1] = 1;
-      qual[a][2] = (cnt < na - 1) && (v[a] >= e[cnt + 1] - g->w);
+      qual[a][2] = (cnt < na - 1 || wrap) && (v[a] >= e[cnt + 1] - g->w);
     }
     owner[i] = idx[0] + g->n[0] * (idx[1] + g->n[1] * idx[2]);
     uint32_t m = 0;

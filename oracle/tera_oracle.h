@@ -29,10 +29,14 @@ enum {
 
 enum { OR_MODE_RAW = 0, OR_MODE_XOR = 1, OR_MODE_RESIDUAL = 2 };
 
+/* periodic: bit a set makes axis a toroidal (Sec. 2.5 names open, closed
+ * and toroidal space boundaries): box n-1 and box 0 are neighbours on it. */
 typedef struct {
   double lo[3], hi[3];
   int32_t n[3];
   double w;
+  uint32_t periodic;
+  uint32_t reserved;
 } or_grid;
 
 /* Grid edges and parameter check (Sec. 2.1 partitioning grid; Sec. 2.4). */

@@ -28,7 +28,7 @@ class TeraError(RuntimeError):
 
 class Grid(C.Structure):
     _fields_ = [("lo", C.c_double * 3), ("hi", C.c_double * 3), ("n", C.c_int32 * 3),
-                ("w", C.c_double)]
+                ("w", C.c_double), ("periodic", C.c_uint32), ("reserved", C.c_uint32)]
 
 
 class Soa(C.Structure):

@@ -85,7 +85,8 @@ class PartitionBuffers:
 class Context:
     """One partitioning grid on one GPU (owns scratch, hash table, status word)."""
 
-    def __init__(self, lo, hi, n, w, device: int = 0, class_id: int = 1):
+    def __init__(self, lo, hi, n, w, device: int = 0, class_id: int = 1, periodic: int = 0):
+        """``periodic``: bit a makes axis a toroidal (box n-1 next to box 0)."""
         self.lib = _lib.load()
         if not torch.cuda.is_available():
             raise RuntimeError("libtera needs a CUDA device (there is no CPU path)")
@@ -93,6 +94,7 @@ class Context:
         for a in range(3):
             g.lo[a], g.hi[a], g.n[a] = float(lo[a]), float(hi[a]), int(n[a])
         g.w = float(w)
+        g.periodic = int(periodic)
         self.grid = g
         self.device = int(device)
         self.class_id = int(class_id)

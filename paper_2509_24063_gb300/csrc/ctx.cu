@@ -337,6 +337,7 @@ uint64_t tera_ctx_launches(const tera_ctx* ctx) { return ctx ? ctx->launches : 0
 tera_status tera_ctx_create(tera_ctx** out, const tera_grid* grid, int device, uint32_t class_id) {
   if (!out || !grid) return TERA_EINVAL;
   *out = nullptr;
+  if (grid->reserved != 0 || (grid->periodic & ~7u) != 0) return TERA_EINVAL;
   GridTables t;
   memset(&t, 0, sizeof(t));
   uint64_t ncell_tmp[3] = {1, 1, 1};
@@ -348,6 +349,7 @@ tera_status tera_ctx_create(tera_ctx** out, const tera_grid* grid, int device, u
   for (int a = 0; a < 3; ++a) {
     int n = grid->n[a];
     if (n < 1 || n > kMaxAxis) return TERA_EINVAL;
+    if ((grid->periodic >> a & 1u) && n < 3) return TERA_EINVAL;
     if (!(grid->lo[a] < grid->hi[a])) return TERA_EINVAL;
     if (!std::isfinite(grid->lo[a]) || !std::isfinite(grid->hi[a])) return TERA_EINVAL;
     double lo = grid->lo[a], hi = grid->hi[a];
@@ -364,6 +366,7 @@ tera_status tera_ctx_create(tera_ctx** out, const tera_grid* grid, int device, u
     t.klo[a] = key(lo);
     t.khi[a] = key(hi);
     t.n[a] = n;
+    t.periodic = (int)grid->periodic;
     // only a starting guess: the index is fixed by exact key comparisons
     t.flo[a] = (float)lo;
     t.fscale[a] = (float)((double)n / (hi - lo));

@@ -27,6 +27,7 @@ struct SmemGrid {
   u64 klo[3], khi[3];
   float flo[3], fscale[3];
   int n[3];
+  int periodic;
 };
 
 __device__ __forceinline__ void load_grid(SmemGrid& s, const GridTables* __restrict__ g) {
@@ -37,6 +38,7 @@ __device__ __forceinline__ void load_grid(SmemGrid& s, const GridTables* __restr
     s.flo[threadIdx.x] = g->flo[threadIdx.x];
     s.fscale[threadIdx.x] = g->fscale[threadIdx.x];
   }
+  if (threadIdx.x == 0) s.periodic = g->periodic;
   for (int a = 0; a < 3; ++a) {
     const int n = g->n[a];
     for (int k = threadIdx.x; k <= n; k += blockDim.x) s.ke[a][k] = g->ke[a][k];
@@ -53,7 +55,8 @@ __device__ __forceinline__ void load_grid(SmemGrid& s, const GridTables* __restr
 // comparisons of the 64-bit keys (so the result is exactly the rule's; the
 // estimate only saves the binary search).  Returns opts: bit 0 offset -1
 // qualifies (i > 0 and v < e[i] + w), bit 1 offset 0, bit 2 offset +1
-// (i < n-1 and v >= e[i+1] - w); 0 when v is not in [lo, hi).
+// (i < n-1 and v >= e[i+1] - w); on a periodic axis the neighbour always
+// exists.  0 when v is not in [lo, hi).
 __device__ __forceinline__ u32 classify_axis(u64 bits, int a, const SmemGrid& s, int* idx) {
   const u64 k = key_of(bits);
   if (!(k >= s.klo[a] && k < s.khi[a])) {
@@ -67,8 +70,9 @@ __device__ __forceinline__ u32 classify_axis(u64 bits, int a, const SmemGrid& s,
   while (i > 0 && k < s.ke[a][i]) --i;
   while (i < n - 1 && k >= s.ke[a][i + 1]) ++i;
   *idx = i;
-  const u32 lowq = (i > 0) && (k < s.ktl[a][i]);
-  const u32 highq = (i < n - 1) && (k >= s.kth[a][i]);
+  const bool wrap = (s.periodic >> a) & 1;
+  const u32 lowq = (i > 0 || wrap) && (k < s.ktl[a][i]);
+  const u32 highq = (i < n - 1 || wrap) && (k >= s.kth[a][i]);
   return 2u | lowq | (highq << 2);
 }
 

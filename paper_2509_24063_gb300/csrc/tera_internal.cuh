@@ -49,7 +49,7 @@ struct DevStatus {
 // integers: exact, and independent of the GPU's binary64 throughput.
 struct GridTables {
   int n[3];
-  int pad;
+  int periodic;                   // bit a: axis a is toroidal (box n-1 next to box 0)
   float flo[3], fscale[3];        // float estimate of the box index: (x - lo) * n / (hi - lo)
   u64 klo[3], khi[3];             // domain [lo, hi)
   u64 ke[3][kMaxAxis + 1];        // box edges e[k]

@@ -44,6 +44,8 @@ class Workload:
     persistent: bool = False       # velocity = 0.8 v + 0.2 N(0, sigma) + drift
     n_blobs: int = 32
     seed: int = 0
+    boundary: str = "closed"       # "closed" (clamp) or "toroidal" (wrap)
+    wrap_axes: int = 7             # axis bit mask that wraps when toroidal
 
     @property
     def n_boxes(self) -> int:
@@ -52,6 +54,11 @@ class Workload:
     @property
     def n_pairs(self) -> int:
         return self.n_boxes * 27
+
+    @property
+    def periodic(self) -> int:
+        """Axis bit mask of toroidal axes, as the library's grid takes it."""
+        return self.wrap_axes if self.boundary == "toroidal" else 0
 
 
 def _cube(side):
@@ -75,6 +82,10 @@ WORKLOADS = {
     # 16M blob agents with persistent motion in a smooth drift field.
     "drift_16m": Workload("drift_16m", 16 << 20, *_cube(4000), (4, 4, 4), 30.0, 220,
                           layout="blobs", p_move=1.0, persistent=True, seed=0x7E7A0005),
+    # the 1M workload on a toroidal domain (every axis wraps)
+    "torus_1m": Workload("torus_1m", 1 << 20, *_cube(1000), (4, 4, 4), 30.0, 50,
+                         p_grow=0.1, p_divide=0.005, p_die=0.002, boundary="toroidal",
+                         seed=0x7E7A0006),
 }
 
 
@@ -90,6 +101,13 @@ def _clamp(v: torch.Tensor, lo: float, hi: float) -> torch.Tensor:
     return v.clamp_(lo, top)
 
 
+def _wrap(v: torch.Tensor, lo: float, hi: float) -> torch.Tensor:
+    # toroidal boundary: lo + (v - lo) mod (hi - lo); a remainder that rounds
+    # up to the full period is kept just below hi
+    v = lo + torch.remainder(v - lo, hi - lo)
+    return _clamp(v, lo, hi)
+
+
 class Generator:
     """Seeded population + dynamics.  Deterministic for a (workload, device)."""
 
@@ -100,6 +118,8 @@ class Generator:
         self.g = torch.Generator(device=self.device)
         self.g.manual_seed(self.seed)
         self.next_id = wl.n0
+        per = wl.periodic
+        self._bounds = [(_wrap if per >> a & 1 else _clamp) for a in range(3)]
 
     # -- random helpers on the workload's device --
     def _rand(self, n):
@@ -126,7 +146,7 @@ class Generator:
             for a in range(3):
                 pos.append(ctr_t[:, a] + sig_t * self._randn(n))
         for a in range(3):
-            _clamp(pos[a], wl.lo[a], wl.hi[a])
+            pos[a] = self._bounds[a](pos[a], wl.lo[a], wl.hi[a])
         d = 8.0 + 4.0 * self._rand(n)
         st = dict(id=torch.arange(n, dtype=torch.int64, device=self.device),
                   x=pos[0], y=pos[1], z=pos[2], diameter=d,
@@ -150,12 +170,13 @@ class Generator:
             for a, k in enumerate(axes):
                 vk = "v" + k
                 st[vk] = 0.8 * st[vk] + 0.2 * wl.step_sigma * self._randn(n) + 0.5 * drift[a]
-                st[k] = _clamp(st[k] + st[vk], wl.lo[a], wl.hi[a])
+                st[k] = self._bounds[a](st[k] + st[vk], wl.lo[a], wl.hi[a])
         elif wl.p_move > 0:
             mv = self._rand(n) < wl.p_move
             for a, k in enumerate(axes):
                 step = wl.step_sigma * self._randn(n)
-                st[k] = _clamp(torch.where(mv, st[k] + step, st[k]), wl.lo[a], wl.hi[a])
+                st[k] = self._bounds[a](torch.where(mv, st[k] + step, st[k]),
+                                          wl.lo[a], wl.hi[a])
         if wl.p_grow > 0:
             gr = self._rand(n) < wl.p_grow
             d = torch.where(gr, st["diameter"] * wl.grow_factor, st["diameter"])
@@ -171,7 +192,8 @@ class Generator:
                 u = u / u.norm(dim=1, keepdim=True).clamp_min(1e-300)
                 child = {f: st[f][dv].clone() for f in st}
                 for a, ax in enumerate(axes):
-                    child[ax] = _clamp(st[ax][dv] + 0.5 * d_old * u[:, a], wl.lo[a], wl.hi[a])
+                    child[ax] = self._bounds[a](st[ax][dv] + 0.5 * d_old * u[:, a],
+                                                  wl.lo[a], wl.hi[a])
                 st["diameter"][dv] = d
                 st["volume"][dv] = (math.pi / 6.0) * d * d * d
                 child["diameter"] = d.clone()

@@ -64,12 +64,12 @@ def compare_iteration(ctx, ex, st, res, P):
 def run_chain(tera, wl, iters, per_subdomain=False, max_records=None, device="cuda",
               path=None, tune=None):
     gen = Generator(wl, device=device)
-    ctx = tera.Context(wl.lo, wl.hi, wl.grid, wl.w)
+    ctx = tera.Context(wl.lo, wl.hi, wl.grid, wl.w, periodic=wl.periodic)
     states = list(gen.series(iters))
     nmax = max(int(s["x"].shape[0]) for s in states)
     ex = tera.AuraExchange(ctx, max_agents=nmax, max_records=max_records or 4 * nmax + 1024,
                            per_subdomain=per_subdomain, path=path, tune=tune)
-    g = oracle.make_grid(wl.lo, wl.hi, wl.grid, wl.w)
+    g = oracle.make_grid(wl.lo, wl.hi, wl.grid, wl.w, wl.periodic)
     ref = recv_ref = None
     stats = []
     for st in states:
@@ -115,6 +115,25 @@ def test_ragged_population_sizes(tera, n):
     wl = Workload("t", n, (0.0,) * 3, (90.0, 60.0, 60.0), (3, 2, 2), 12.0, 3,
                   p_divide=0.05, p_die=0.05, seed=100 + n)
     run_chain(tera, wl, 3)
+
+
+@pytest.mark.parametrize("path", ["all_pairs", "batched"])
+def test_toroidal_domain(tera, path):
+    # every axis wraps: the boxes on the faces also exchange with the
+    # opposite face (Sec. 2.5 toroidal space boundary)
+    stats = run_chain(tera, scaled(WORKLOADS["torus_1m"], 1 << 18), 4, path=path)
+    assert all(E > 0 for E, _ in stats)
+
+
+@pytest.mark.parametrize("wrap_axes", [1, 4, 5])
+@pytest.mark.parametrize("n", [0, 1, 2049, 70001])
+def test_toroidal_some_axes(tera, wrap_axes, n):
+    # axes 0 and 2 have 3 boxes and may wrap; axis 1 (2 boxes) stays closed
+    wl = Workload("t", n, (0.0,) * 3, (90.0, 60.0, 90.0), (3, 2, 3), 12.0, 3,
+                  p_divide=0.05, p_die=0.05, boundary="toroidal", wrap_axes=wrap_axes,
+                  seed=300 + n + wrap_axes)
+    run_chain(tera, wl, 3)
+    run_chain(tera, wl, 3, path="batched")
 
 
 @pytest.mark.parametrize("path", ["all_pairs", "batched"])

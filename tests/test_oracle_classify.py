@@ -154,3 +154,124 @@ def test_edges_definition(oracle):
     for a, (lo, hi, n) in enumerate([(0.1, 0.7, 3), (-3.0, 5.0, 7), (7.0, 7.3, 1)]):
         assert list(oracle.axis_edges(g, a)) == edges(lo, hi, n)
         assert oracle.axis_edges(g, a)[-1] == hi
+
+
+# ---- toroidal axes (Sec. 2.5 names open, closed and toroidal boundaries) ----
+# On a periodic axis the region of box b expanded by w wraps round the domain:
+# box n-1 also covers [lo, e[0] + w) and box 0 also covers [e[n] - w, hi).  The
+# offset of box b seen from the owner is (b - own) taken modulo n into
+# {-1, 0, +1}, unique because a periodic axis has at least 3 boxes.
+
+def brute_force_periodic(grid_lo, grid_hi, grid_n, w, periodic, pts):
+    E = [edges(grid_lo[a], grid_hi[a], grid_n[a]) for a in range(3)]
+
+    def covers(a, b, v):
+        n = grid_n[a]
+        if E[a][b] - w <= v < E[a][b + 1] + w:
+            return True
+        if periodic >> a & 1:
+            if b == n - 1 and v < E[a][0] + w:
+                return True
+            if b == 0 and v >= E[a][n] - w:
+                return True
+        return False
+
+    owners, masks = [], []
+    for v in pts:
+        own = None
+        inside = []
+        for b in itertools.product(*(range(grid_n[a]) for a in range(3))):
+            if all(E[a][b[a]] <= v[a] < E[a][b[a] + 1] for a in range(3)):
+                assert own is None
+                own = b
+            if all(covers(a, b[a], v[a]) for a in range(3)):
+                inside.append(b)
+        assert own is not None
+        m = 0
+        for b in inside:
+            if b == own:
+                continue
+            o = []
+            for a in range(3):
+                d = b[a] - own[a]
+                if periodic >> a & 1:
+                    d = (d + 1) % grid_n[a] - 1
+                assert -1 <= d <= 1
+                o.append(d)
+            m |= 1 << ((o[0] + 1) + 3 * (o[1] + 1) + 9 * (o[2] + 1))
+        owners.append(own[0] + grid_n[0] * (own[1] + grid_n[1] * own[2]))
+        masks.append(m)
+    return np.array(owners, dtype=np.int32), np.array(masks, dtype=np.uint32)
+
+
+def random_periodic_case(rng):
+    periodic = int(rng.integers(1, 8))
+    lo, hi, n, w, _ = random_case(rng)
+    n = [int(rng.integers(3, 6)) if periodic >> a & 1 else n[a] for a in range(3)]
+    min_side = min(min(np.diff(edges(lo[a], hi[a], n[a]))) for a in range(3))
+    w = float(rng.uniform(0.05, 0.999)) * min_side
+    E = [edges(lo[a], hi[a], n[a]) for a in range(3)]
+    pts = []
+    for _ in range(int(rng.integers(0, 257))):
+        v = []
+        for a in range(3):
+            r = rng.random()
+            if r < 0.3:  # on a threshold, the wrap-round ones included
+                k = int(rng.integers(0, n[a] + 1))
+                t = E[a][k] + (w if rng.random() < 0.5 else -w)
+                v.append(min(max(t, lo[a]), math.nextafter(hi[a], lo[a])))
+            elif r < 0.4:  # within w of the domain faces
+                t = lo[a] + w * rng.random() if rng.random() < 0.5 else hi[a] - w * rng.random()
+                v.append(min(max(t, lo[a]), math.nextafter(hi[a], lo[a])))
+            elif r < 0.45:
+                v.append(lo[a] if rng.random() < 0.5 else math.nextafter(hi[a], lo[a]))
+            else:
+                v.append(float(rng.uniform(lo[a], hi[a])))
+        pts.append(v)
+    return lo, hi, n, w, periodic, pts
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_classify_periodic_matches_wrapped_brute_force(oracle, seed):
+    rng = np.random.default_rng(5000 + seed)
+    lo, hi, n, w, periodic, pts = random_periodic_case(rng)
+    g = oracle.make_grid(lo, hi, n, w, periodic)
+    assert oracle.grid_check(g) == oracle.OK
+    P = np.array(pts, dtype=np.float64).reshape(-1, 3)
+    st, owner, mask = oracle.classify(g, P[:, 0], P[:, 1], P[:, 2])
+    assert st == oracle.OK
+    bo, bm = brute_force_periodic(lo, hi, n, w, periodic, pts)
+    np.testing.assert_array_equal(owner, bo)
+    np.testing.assert_array_equal(mask, bm)
+
+
+def test_periodic_hand_example(oracle):
+    # 90^3 cube, 3x3x3 boxes of side 30, w 10, only x wraps
+    g = oracle.make_grid((0, 0, 0), (90, 90, 90), (3, 3, 3), 10.0, periodic=1)
+    x = np.array([5.0, 85.0, 5.0, 45.0])
+    y = np.array([45.0, 45.0, 5.0, 45.0])
+    z = np.array([45.0, 45.0, 45.0, 45.0])
+    st, owner, mask = oracle.classify(g, x, y, z)
+    assert st == oracle.OK
+    # x = 5 in box 0: the -x neighbour is box 2 across the boundary, bit 12
+    assert owner[0] == 0 + 3 * (1 + 3 * 1) and mask[0] == 1 << 12
+    # x = 85 in box 2: the +x neighbour is box 0, bit 14
+    assert owner[1] == 2 + 3 * (1 + 3 * 1) and mask[1] == 1 << 14
+    # y = 5 does not wrap (y closed): only -x (bit 12); no -y or corner bits
+    assert mask[2] == 1 << 12
+    # the middle of the middle box sends nothing
+    assert mask[3] == 0
+    # the same agents on a closed grid lose the wrap-round bits
+    gc = oracle.make_grid((0, 0, 0), (90, 90, 90), (3, 3, 3), 10.0)
+    st, owner_c, mask_c = oracle.classify(gc, x, y, z)
+    np.testing.assert_array_equal(owner_c, owner)
+    assert list(mask_c) == [0, 0, 0, 0]
+
+
+@pytest.mark.parametrize("n,periodic,reserved,ok", [
+    ((3, 3, 3), 7, 0, True), ((2, 3, 3), 1, 0, False), ((2, 3, 3), 6, 0, True),
+    ((3, 3, 1), 4, 0, False), ((3, 3, 3), 8, 0, False), ((3, 3, 3), 0, 1, False)])
+def test_grid_check_periodic(oracle, n, periodic, reserved, ok):
+    g = oracle.make_grid((0, 0, 0), (30, 30, 30), n, 1.0, periodic)
+    g.reserved = reserved
+    assert (oracle.grid_check(g) == oracle.OK) == ok
