@@ -84,6 +84,9 @@ def lib():
             L.or_decode_all.argtypes = [u64, u32, P, P, P, P, P, u64, P]
             L.or_exchange_iteration.argtypes = [G, P, P, i64, u32, u32, P, P, P, P, P, P, P,
                                                 P, P, u64, P, P, P, P, P, P, u64, P, P]
+            L.or_migrate_inbox_bit.argtypes = [G, i32, i32]
+            L.or_migrate_send.argtypes = [G, P, P, i64, P, u32, P, P, u64, P, P, P]
+            L.or_migrate_recv.argtypes = [G, P, P, u32, P, P, P]
             D3 = C.POINTER(C.c_double)
             L.or_mlp_nparam.argtypes = []
             L.or_mlp_infer_f32.argtypes = [P, P, P]
@@ -115,7 +118,8 @@ def lib():
                       "or_decode_pair", "or_encode_all", "or_decode_all",
                       "or_exchange_iteration", "or_mlp_nparam", "or_features", "or_predict",
                       "or_sample", "or_encode_pair_pred", "or_decode_pair_pred",
-                      "or_encode_all_pred", "or_decode_all_pred"):
+                      "or_encode_all_pred", "or_decode_all_pred", "or_migrate_inbox_bit",
+                      "or_migrate_send", "or_migrate_recv"):
                 getattr(L, f).restype = C.c_int
             _lib = L
     return _lib
@@ -290,6 +294,61 @@ def exchange_iteration(grid: Grid, soa: dict, ref=None, recv_ref=None, class_id=
     return dict(status=st, owner=owner, mask=mask, pair_count=cnt, pair_off=off,
                 pair_idx=idx[:total], rec=rec, wire=wire, wire_off=wo, wire_len=wl,
                 ref_next=nxt, recv=recv, recv_off=ro, t_steps=ts)
+
+
+# ---------------- agent migration (Sec. 2.1 "Agent Migration") ----------------
+
+COLS = ("x", "y", "z", "diameter", "volume", "adherence", "density")
+
+
+def inbox_bit(grid: Grid, s: int, d: int) -> int:
+    """Side b of box d that an agent from box s arrives from (13: not a neighbour)."""
+    return int(lib().or_migrate_inbox_bit(C.byref(grid), int(s), int(d)))
+
+
+def migrate(grid: Grid, soa: dict, box_off_prev, class_id=1, arena_units=None):
+    """Send and receive of one migration step of a box-major state.
+
+    Returns dict(status, inbox_off, arena, box_off_next, next) where next is
+    the box-major state after migration (same keys as soa), arena the raw
+    TAIO inboxes (pair field = inbox index q = d*27 + b)."""
+    n = int(soa["x"].shape[0])
+    nb = int(grid.n[0]) * int(grid.n[1]) * int(grid.n[2])
+    Q = nb * 27
+    ids = np.ascontiguousarray(soa["id"], dtype=np.uint64)
+    cols = soa_cols(soa)
+    arr = (C.c_void_p * 7)(*[c.ctypes.data for c in cols])
+    bo = np.ascontiguousarray(box_off_prev, dtype=np.uint64)
+    assert bo.shape[0] == nb + 1
+    units = n + Q if arena_units is None else int(arena_units)
+    arena = np.zeros(max(units, 1) * REC, dtype=np.uint8)
+    inbox_off = np.zeros(Q + 1, dtype=np.uint64)
+    box_next = np.zeros(nb + 1, dtype=np.uint64)
+    id_next = np.zeros(n, dtype=np.uint64)
+    cn = [np.zeros(n, dtype=np.float64) for _ in range(7)]
+    arr_n = (C.c_void_p * 7)(*[c.ctypes.data for c in cn])
+    st = lib().or_migrate_send(C.byref(grid), _p(ids), arr, n, _p(bo), class_id, _p(inbox_off),
+                               _p(arena), units, _p(box_next), _p(id_next), arr_n)
+    if st == OK:
+        st = lib().or_migrate_recv(C.byref(grid), _p(arena), _p(inbox_off), class_id,
+                                   _p(box_next), _p(id_next), arr_n)
+    nxt = {"id": id_next}
+    nxt.update({k: c for k, c in zip(COLS, cn)})
+    return dict(status=st, inbox_off=inbox_off, arena=arena, box_off_next=box_next, next=nxt)
+
+
+def migrate_recv(grid: Grid, arena, inbox_off, box_off_next, next_soa: dict, class_id=1) -> int:
+    """Deserialize the inboxes into next_soa (modified in place); returns the status."""
+    ids = next_soa["id"]
+    cn = [next_soa[k] for k in COLS]
+    for c in [ids] + cn:
+        assert c.flags["C_CONTIGUOUS"]
+    arr_n = (C.c_void_p * 7)(*[c.ctypes.data for c in cn])
+    return int(lib().or_migrate_recv(C.byref(grid), _p(np.ascontiguousarray(arena)),
+                                     _p(np.ascontiguousarray(inbox_off, dtype=np.uint64)),
+                                     class_id,
+                                     _p(np.ascontiguousarray(box_off_next, dtype=np.uint64)),
+                                     _p(ids), arr_n))
 
 
 # ---------------- learned predictor and residual mode ----------------

@@ -551,6 +551,152 @@ static double now_s(void) {
   return (double)ts.tv_sec + 1e-9 * (double)ts.tv_nsec;
 }
 
+/* ---------- agent migration (Sec. 2.1 "Agent Migration") ----------
+ * Agents whose new position lies in another box move to that box; they are
+ * sent as raw TeraAgent IO records (Sec. 2.2.1), the difference encoding of
+ * Sec. 2.3 being for the aura only.  On one grid the destination of every
+ * agent is its owner box by the classification rule, so the paper's second
+ * case (a collective lookup for positions outside the locally available boxes)
+ * reduces to the same rule; such agents use the inbox side b = 13. */
+
+static void box_coords(const or_grid* g, int32_t b, int c[3]) {
+  c[0] = b % g->n[0];
+  c[1] = (b / g->n[0]) % g->n[1];
+  c[2] = b / (g->n[0] * g->n[1]);
+}
+
+/* Side of box d that an agent from box s arrives from: the neighbour bit of
+ * the offset s - d (per axis -1, 0 or +1, taken modulo n on a toroidal axis),
+ * or 13 when s is not one of d's 26 neighbours. */
+int or_migrate_inbox_bit(const or_grid* g, int32_t s, int32_t d) {
+  int cs[3], cd[3], o[3];
+  box_coords(g, s, cs);
+  box_coords(g, d, cd);
+  for (int a = 0; a < 3; ++a) {
+    int diff = cs[a] - cd[a];
+    if (g->periodic >> a & 1u) {
+      int na = g->n[a];
+      if (diff == na - 1) diff = -1;
+      else if (diff == -(na - 1)) diff = 1;
+    }
+    if (diff < -1 || diff > 1) return 13;
+    o[a] = diff;
+  }
+  return (o[0] + 1) + 3 * (o[1] + 1) + 9 * (o[2] + 1);
+}
+
+static int check_box_off(const uint64_t* box_off, uint64_t n_boxes, int64_t n) {
+  if (box_off[0] != 0 || box_off[n_boxes] != (uint64_t)n) return OR_EINVAL;
+  for (uint64_t b = 0; b < n_boxes; ++b)
+    if (box_off[b + 1] < box_off[b]) return OR_EINVAL;
+  return OR_OK;
+}
+
+int or_migrate_send(const or_grid* g, const uint64_t* id, const double* const cols[7],
+                    int64_t n, const uint64_t* box_off_prev, uint32_t class_id,
+                    uint64_t* inbox_off, uint8_t* arena, uint64_t arena_units,
+                    uint64_t* box_off_next, uint64_t* id_next, double* const cols_next[7]) {
+  int st = or_grid_check(g);
+  if (st != OR_OK) return st;
+  const uint64_t n_boxes = (uint64_t)g->n[0] * (uint64_t)g->n[1] * (uint64_t)g->n[2];
+  const uint64_t n_inbox = n_boxes * 27u;
+  if ((st = check_box_off(box_off_prev, n_boxes, n)) != OR_OK) return st;
+  int32_t* owner = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n ? n : 1));
+  uint32_t* mask = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(n ? n : 1));
+  uint64_t* count = (uint64_t*)calloc((size_t)n_inbox, sizeof(uint64_t));
+  uint64_t* fill = (uint64_t*)calloc((size_t)n_inbox, sizeof(uint64_t));
+  uint64_t* size_next = (uint64_t*)calloc((size_t)n_boxes, sizeof(uint64_t));
+  if (!owner || !mask || !count || !fill || !size_next) {
+    st = OR_ENOMEM;
+    goto done;
+  }
+  /* the owner box of every agent's current position */
+  st = or_classify(g, cols[0], cols[1], cols[2], n, owner, mask);
+  if (st != OR_OK) goto done;
+  /* count the leavers of every inbox, and the agents of every next box */
+  for (uint64_t s = 0; s < n_boxes; ++s) {
+    for (uint64_t i = box_off_prev[s]; i < box_off_prev[s + 1]; ++i) {
+      int32_t d = owner[i];
+      size_next[d] += 1;
+      if ((uint64_t)d != s) count[(uint64_t)d * 27u + (uint64_t)or_migrate_inbox_bit(g, (int32_t)s, d)] += 1;
+    }
+  }
+  inbox_off[0] = 0;
+  for (uint64_t q = 0; q < n_inbox; ++q) inbox_off[q + 1] = inbox_off[q] + count[q];
+  box_off_next[0] = 0;
+  for (uint64_t d = 0; d < n_boxes; ++d) box_off_next[d + 1] = box_off_next[d] + size_next[d];
+  if (inbox_off[n_inbox] + n_inbox > arena_units) {
+    st = OR_ECAPACITY;
+    goto done;
+  }
+  /* serialize: one TAIO header per inbox, then its leavers in agent order */
+  for (uint64_t q = 0; q < n_inbox; ++q)
+    write_taio_header(arena + (inbox_off[q] + q) * REC_BYTES, class_id, (uint32_t)q, count[q]);
+  for (uint64_t s = 0; s < n_boxes; ++s) {
+    for (uint64_t i = box_off_prev[s]; i < box_off_prev[s + 1]; ++i) {
+      int32_t d = owner[i];
+      if ((uint64_t)d == s) continue;
+      uint64_t q = (uint64_t)d * 27u + (uint64_t)or_migrate_inbox_bit(g, (int32_t)s, d);
+      uint8_t* rec = arena + (inbox_off[q] + q + 1 + fill[q]) * REC_BYTES;
+      fill[q] += 1;
+      put_le(rec, id[i], 8);
+      for (int c = 0; c < 7; ++c) put_le(rec + 8 * (c + 1), f64_bits(cols[c][i]), 8);
+    }
+  }
+  /* the stayers of box d, in their previous order, open its next range */
+  for (uint64_t d = 0; d < n_boxes; ++d) {
+    uint64_t pos = box_off_next[d];
+    for (uint64_t i = box_off_prev[d]; i < box_off_prev[d + 1]; ++i) {
+      if ((uint64_t)owner[i] != d) continue;
+      id_next[pos] = id[i];
+      for (int c = 0; c < 7; ++c) cols_next[c][pos] = cols[c][i];
+      pos += 1;
+    }
+  }
+done:
+  free(owner);
+  free(mask);
+  free(count);
+  free(fill);
+  free(size_next);
+  return st;
+}
+
+/* Deserialize every inbox into the next state: the records of box d's
+ * inboxes, in ascending inbox side and then in message order, follow its
+ * stayers.  Each inbox header is checked (magic, version, record size, class
+ * id, inbox index, record count). */
+int or_migrate_recv(const or_grid* g, const uint8_t* arena, const uint64_t* inbox_off,
+                    uint32_t class_id, const uint64_t* box_off_next, uint64_t* id_next,
+                    double* const cols_next[7]) {
+  const uint64_t n_boxes = (uint64_t)g->n[0] * (uint64_t)g->n[1] * (uint64_t)g->n[2];
+  for (uint64_t d = 0; d < n_boxes; ++d) {
+    uint64_t immigrants = inbox_off[d * 27u + 27u] - inbox_off[d * 27u];
+    uint64_t size = box_off_next[d + 1] - box_off_next[d];
+    if (immigrants > size) return OR_ECORRUPT;
+    uint64_t pos = box_off_next[d] + (size - immigrants);
+    for (uint64_t b = 0; b < 27; ++b) {
+      uint64_t q = d * 27u + b;
+      const uint8_t* h = arena + (inbox_off[q] + q) * REC_BYTES;
+      uint64_t m = inbox_off[q + 1] - inbox_off[q];
+      if (get_le(h, 4) != TAIO_MAGIC || get_le(h + 4, 2) != FMT_VERSION ||
+          get_le(h + 6, 2) != REC_BYTES || get_le(h + 8, 4) != class_id ||
+          get_le(h + 12, 4) != (uint32_t)q || get_le(h + 16, 8) != m)
+        return OR_ECORRUPT;
+      for (uint64_t k = 0; k < m; ++k) {
+        const uint8_t* rec = h + HDR_BYTES + k * REC_BYTES;
+        id_next[pos] = rec_word(rec, 0);
+        for (int c = 0; c < 7; ++c) {
+          uint64_t bits = rec_word(rec, c + 1);
+          memcpy(&cols_next[c][pos], &bits, 8);
+        }
+        pos += 1;
+      }
+    }
+  }
+  return OR_OK;
+}
+
 int or_exchange_iteration(const or_grid* g, const uint64_t* id, const double* const cols[7],
                           int64_t n, uint32_t class_id, uint32_t mode,
                           const uint8_t* ref_arena, const uint64_t* ref_off,

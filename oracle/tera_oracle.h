@@ -79,6 +79,25 @@ int or_decode_all(uint64_t n_pairs, uint32_t class_id, const uint8_t* wire,
                   const uint64_t* wire_off, const uint8_t* ref_arena, const uint64_t* ref_off,
                   uint8_t* recv, uint64_t recv_cap_units, uint64_t* recv_off);
 
+/* Agent migration (Sec. 2.1 "Agent Migration"; records are the raw TeraAgent
+ * IO buffers of Sec. 2.2.1).  The state is box-major: box s holds agents
+ * [box_off_prev[s], box_off_prev[s+1]).  An agent whose position now lies in
+ * box d != s leaves s for inbox q = d*27 + b, b the neighbour bit of the
+ * offset from d to s (the side it arrives from), or 13 when s is not a
+ * neighbour of d.  Inbox q holds its leavers in ascending agent index, laid
+ * out as a TAIO arena with inbox_off[P+1].  The next state of box d is its
+ * stayers in their previous order followed by its inboxes in ascending b.
+ * or_migrate_send writes inbox_off, the arena, box_off_next and the stayers;
+ * or_migrate_recv writes the immigrants from the arena. */
+int or_migrate_inbox_bit(const or_grid* g, int32_t s, int32_t d);
+int or_migrate_send(const or_grid* g, const uint64_t* id, const double* const cols[7],
+                    int64_t n, const uint64_t* box_off_prev, uint32_t class_id,
+                    uint64_t* inbox_off, uint8_t* arena, uint64_t arena_units,
+                    uint64_t* box_off_next, uint64_t* id_next, double* const cols_next[7]);
+int or_migrate_recv(const or_grid* g, const uint8_t* arena, const uint64_t* inbox_off,
+                    uint32_t class_id, const uint64_t* box_off_next, uint64_t* id_next,
+                    double* const cols_next[7]);
+
 /* Whole iteration, for the CPU baseline timing. */
 int or_exchange_iteration(const or_grid* g, const uint64_t* id, const double* const cols[7],
                           int64_t n, uint32_t class_id, uint32_t mode,
