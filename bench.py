@@ -48,6 +48,13 @@ def kernel_bytes(name, t):
         # (message, reference, new reference and wire on the sender; wire,
         # reference and receive buffers on the receiver)
         "codec_persistent_kernel": 64 * (3 * E + 2 * R) + 2 * t["wire_bytes"],
+        # migration (N agents per step, L leavers): positions read to find the
+        # owners; every record read and written once by the stable regroup;
+        # leavers serialized (gather + arena write) and deserialized
+        "mig_count_kernel": 24 * N,
+        "mig_move_kernel": 128 * N + 8 * t.get("leavers", 0),
+        "mig_pack_kernel": 128 * t.get("leavers", 0),
+        "mig_unpack_kernel": 128 * t.get("leavers", 0),
     }
     return table.get(name)
 
@@ -236,6 +243,154 @@ def run_reference(args):
     return 0
 
 
+def run_migration(args):
+    """Agent migration of a box-major state (one send + receive per step).
+
+    The inputs are a chain of real transitions of the workload with its moves
+    only (migration carries no births or deaths): the state after each
+    migration, with the positions of the next iteration.  They are prepared
+    before the timed region; each timed step migrates one of them."""
+    import torch
+    import torch.distributed as dist
+
+    import paper_2509_24063_gb300 as tera
+    from synth import WORKLOADS, Generator, scaled
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    wl = WORKLOADS[args.workload]
+    if args.agents:
+        wl = scaled(wl, args.agents)
+    wl = dataclasses.replace(wl, p_grow=0.0, p_divide=0.0, p_die=0.0, boundary=args.boundary)
+    total = args.warmup + args.steps
+    gen = Generator(wl, device="cuda", seed=wl.seed + 7919 * rank)
+    it = gen.series(total + 1)
+    ctx = tera.Context(wl.lo, wl.hi, wl.grid, wl.w, device=local, periodic=wl.periodic)
+    n = wl.n0
+    # the regroup from box 0 moves nearly every agent: room for n leavers
+    mig = tera.Migration(ctx, n, max_leavers=n)
+    cur, off = mig.regroup(next(it))
+    ctx.status()  # raises before any migrated id is used as an index
+    inputs, leavers = [], []
+    for _ in range(total):
+        st = next(it)
+        idx = cur["id"]  # move-only dynamics: agent id = index in the generated state
+        moved = {k: (st[k][idx] if k in ("x", "y", "z") else cur[k]) for k in cur}
+        del st
+        nxt, off_next = mig.step(moved, off)
+        ctx.status()
+        leavers.append(int(mig.inbox_off[-1]))
+        inputs.append((moved, off))
+        cur, off = nxt, off_next
+    del cur, off, gen, it
+    ctx.status()
+    out = mig.empty_like(inputs[0][0])
+    off_out = torch.empty_like(inputs[0][1])
+    for t in range(args.warmup):
+        mig.step(inputs[t][0], inputs[t][1], out, off_out)
+    ctx.status()
+    ctx.profile_table(reset=True)
+    ctx.profile(True)
+    launches0 = ctx.launches
+    stream = torch.cuda.current_stream()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(None if world == 1 else local) as clk:
+        ev0.record(stream)
+        for t in range(args.warmup, total):
+            mig.step(inputs[t][0], inputs[t][1], out, off_out)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    elapsed_ms = ev0.elapsed_time(ev1)
+    launches = ctx.launches - launches0
+    ctx.profile(False)
+    prof = ctx.profile_table(reset=True)
+    ctx.status()
+    t_max, agents_all = job_totals(elapsed_ms, n * args.steps, world, "cuda")
+    value = agents_all / (t_max / 1e3)
+    lv = sum(leavers[args.warmup:])
+    totals = {"agents": n * args.steps, "records": 0, "ref_slots": 0, "new_records": 0,
+              "payload_bytes": 0, "holes": 0, "wire_bytes": 0, "leavers": lv}
+    peaks, peak_kind = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    dname, (dn, dms) = max(prof.items(), key=lambda kv: kv[1][1])
+    dbytes = kernel_bytes(dname, totals)
+    roofline = None
+    if dbytes is not None and dn > 0:
+        achieved = dbytes / dn / (dms / dn / 1e3) / 1e9
+        roofline = {"bound": "hbm", "kernel": dname, "achieved": achieved, "peak": hbm,
+                    "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
+                    "peak_kind": peak_kind, "launches": dn, "avg_ms": dms / dn,
+                    "algorithmic_bytes_per_launch": dbytes / dn}
+    if args.profile_table and rank == 0:
+        tot = sum(v[1] for v in prof.values())
+        for k, (n_, ms_) in sorted(prof.items(), key=lambda kv: -kv[1][1]):
+            b = kernel_bytes(k, totals)
+            gbs = f"{b / (ms_ / 1e3) / 1e9:8.1f} GB/s" if b and ms_ > 0 else ""
+            print(f"{k:24s} {n_:6d} launches {ms_:9.3f} ms {100 * ms_ / tot:5.1f}% {gbs}",
+                  file=sys.stderr)
+    del inputs, out, mig
+    ctx.close()
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = migration_oracle_time(wl, min(args.cpu_sample, n))
+    line = {
+        "metric": "migration agents/s", "value": value, "unit": "agents/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic",
+        "config": {"workload": wl.name + (f"@{args.agents}" if args.agents else ""),
+                   "agents": n, "grid": list(wl.grid), "boundary": wl.boundary,
+                   "dynamics": "moves only (p_move, step_sigma of the workload)",
+                   "leavers_per_step": lv / args.steps,
+                   "l2": "inputs larger than L2 (64 B/agent state per step)",
+                   "parallelism": f"replicas{world}"},
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": None,
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def migration_oracle_time(wl, ns):
+    """Oracle migration step on a bounded sample: the workload scaled to ns
+    agents (same cube, grid and moves), box-major, then moved once."""
+    import numpy as np
+
+    import oracle
+    from synth import Generator, scaled, to_numpy
+    w = scaled(wl, ns)
+    g = oracle.make_grid(w.lo, w.hi, w.grid, w.w, w.periodic)
+    states = [to_numpy(s) for s in Generator(w, device="cpu").series(2)]
+    s0, s1 = states
+    st, owner, _ = oracle.classify(g, s0["x"], s0["y"], s0["z"])
+    perm = np.argsort(owner, kind="stable")
+    nb = w.n_boxes
+    off = np.zeros(nb + 1, dtype=np.uint64)
+    off[1:] = np.cumsum(np.bincount(owner, minlength=nb))
+    moved = {k: np.ascontiguousarray((s1 if k in ("x", "y", "z") else s0)[k][perm])
+             for k in s0}
+    t0 = time.perf_counter()
+    res = oracle.migrate(g, moved, off)
+    dt = time.perf_counter() - t0
+    assert res["status"] == oracle.OK
+    return {"value": ns / dt, "unit": "agents/s", "cores": 1, "kind": "oracle",
+            "sample": f"one migration step of {wl.name} scaled to {ns} agents "
+                      f"(same cube, grid, moves); single-threaded C oracle"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -262,6 +417,8 @@ def main():
     ap.add_argument("--predictor", action="store_true",
                     help="learned predictor: train on the workload's generated iterations, then "
                          "time and compare bytes/agent against plain XOR on fresh iterations")
+    ap.add_argument("--migration", action="store_true",
+                    help="agent migration of the box-major state instead of the aura exchange")
     ap.add_argument("--train-iters", type=int, default=200)
     ap.add_argument("--eval-iters", type=int, default=20)
     args = ap.parse_args()
@@ -271,6 +428,8 @@ def main():
         return run_reference(args)
     if args.predictor:
         return run_predictor(args)
+    if args.migration:
+        return run_migration(args)
 
     import numpy as np
     import torch

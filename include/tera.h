@@ -18,6 +18,9 @@
  *                      other reads or writes       (Sec. 2.2.1 "Deserialization")
  *   tera_wire_to_host  the wire messages of an iteration into host memory, with
  *                      the length known only on the device (no host wait)
+ *   tera_migrate_send / tera_migrate_recv
+ *                      agent migration between boxes of a box-major state,
+ *                      as raw TAIO records                (paper Sec. 2.1)
  *
  * Conventions shared by every entry point:
  *  - Device pointers are owned by the caller (allocated e.g. by PyTorch); the
@@ -95,6 +98,14 @@ typedef struct {
   const double *x, *y, *z, *diameter, *volume, *adherence, *density;
   int64_t n;
 } tera_soa;
+
+/* Writable struct-of-arrays agent state (outputs); device pointers,
+ * caller-owned, n < 2^32. */
+typedef struct {
+  uint64_t* id;
+  double *x, *y, *z, *diameter, *volume, *adherence, *density;
+  int64_t n;
+} tera_soa_mut;
 
 /* Partitioning grid: box edges e[k] = lo + ((hi - lo) * k) / n (k < n),
  * e[n] = hi, per axis; aura width w with 0 < w < every box side.
@@ -361,6 +372,41 @@ tera_status tera_unpack_inplace(const uint8_t* buf, uint64_t len, uint32_t class
  * version, size, class id, pair or count (off[p+1]-off[p]) is wrong. */
 tera_status tera_unpack_validate(tera_ctx* ctx, const uint8_t* arena, const uint64_t* off,
                                  void* stream);
+
+/* Agent migration (Sec. 2.1 "Agent Migration"): agents whose position now
+ * lies in another box move there, as raw TeraAgent IO records (Sec. 2.2.1;
+ * no difference encoding, which is for the aura).
+ *
+ * The state is box-major: box s holds agents [box_off_prev[s],
+ * box_off_prev[s+1]) of `prev` (box_off_prev[0] = 0, non-decreasing,
+ * box_off_prev[B] = n; B = n[0]*n[1]*n[2]).  The destination of an agent is
+ * the owner box of its position by the rule of tera_partition.  Leavers of
+ * box s for box d go to inbox q = d*27 + b, b the neighbour bit of the offset
+ * from d to s (the side they arrive from; on a toroidal axis modulo n), or
+ * b = 13 when s is not a neighbour of d (the paper's case of a destination
+ * outside the locally available boxes, whose lookup here is the same rule).
+ * An inbox holds its leavers in ascending agent index.
+ *
+ * tera_migrate_send writes inbox_off[Q+1] (Q = 27 B; records per inbox,
+ * exclusive prefix), the inboxes into `arena` as a TAIO arena (inbox q at
+ * units [inbox_off[q] + q, inbox_off[q+1] + q + 1): header with pair field q,
+ * then its records), box_off_next[B+1], and every stayer into `next`: box d
+ * starts with its stayers in their previous order.  More than arena_units
+ * units latch TERA_ECAPACITY (required units reported) and abort the step;
+ * a box_off_prev that breaks the rules above latches TERA_EINVAL.  An agent
+ * outside [lo, hi) latches TERA_EDOMAIN and is kept in its box.
+ * tera_migrate_recv deserializes every inbox of the arena into `next`: the
+ * records of box d's inboxes, in ascending side and message order, follow
+ * its stayers.  Headers are checked (TERA_ECORRUPT), and so is every index
+ * against the arena and the state; nothing outside them is touched.
+ * prev and next (n agents each) must not overlap; columns and the arena are
+ * 16-byte aligned.  Both calls are asynchronous on `stream`. */
+tera_status tera_migrate_send(tera_ctx* ctx, const tera_soa* prev, const uint64_t* box_off_prev,
+                              uint8_t* arena, uint64_t arena_units, uint64_t* inbox_off,
+                              const tera_soa_mut* next, uint64_t* box_off_next, void* stream);
+tera_status tera_migrate_recv(tera_ctx* ctx, const uint8_t* arena, uint64_t arena_units,
+                              const uint64_t* inbox_off, const uint64_t* box_off_next,
+                              const tera_soa_mut* next, void* stream);
 
 /* Read (and clear) the latched device status; synchronizes `stream`.
  * *required_capacity (optional) receives the largest capacity a call asked

@@ -9,7 +9,9 @@ from ._lib import (ECAPACITY, ECORRUPT, EDOMAIN, EINVAL, ENOMEM, EREFMISMATCH, E
                    MODE_RAW, MODE_XOR, OK, TeraError)
 from .api import Context, PartitionBuffers, soa_from_state
 from .exchange import AuraExchange
+from .migrate import Migration
 
-__all__ = ["Context", "PartitionBuffers", "AuraExchange", "soa_from_state", "TeraError", "OK",
+__all__ = ["Context", "PartitionBuffers", "AuraExchange", "Migration", "soa_from_state",
+           "TeraError", "OK",
            "EINVAL", "ENOMEM", "ECAPACITY", "ECORRUPT", "EDOMAIN", "EREFMISMATCH", "ETIMEOUT",
            "ECUDA", "MODE_RAW", "MODE_XOR"]

@@ -86,6 +86,9 @@ SIGNATURES = {
                                       C.POINTER(C.c_uint64), P]),
     "tera_unpack_validate": (C.c_int, [P, P, P, P]),
     "tera_wire_to_host": (C.c_int, [P, P, P, P, u64, P, P]),
+    # tera_soa_mut has the layout of tera_soa
+    "tera_migrate_send": (C.c_int, [P, C.POINTER(Soa), P, P, u64, P, C.POINTER(Soa), P, P]),
+    "tera_migrate_recv": (C.c_int, [P, P, u64, P, P, C.POINTER(Soa), P]),
     "tera_ctx_status": (C.c_int, [P, C.POINTER(C.c_uint64), P]),
     "tera_reset_reference": (C.c_int, [P, u32]),
     "tera_ctx_launches": (u64, [P]),

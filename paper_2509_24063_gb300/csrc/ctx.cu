@@ -309,6 +309,41 @@ tera_status ensure_batched(tera_ctx* ctx) {
   return TERA_OK;
 }
 
+tera_status ensure_migrate(tera_ctx* ctx, uint64_t n, uint64_t leavers) {
+  tera_status st;
+  if (!ctx->m_from) {
+    cudaDeviceSynchronize();
+    if ((st = alloc_dev(ctx->m_from, ctx->n_boxes)) != TERA_OK) return st;
+    if ((st = alloc_dev(ctx->m_before, ctx->n_boxes)) != TERA_OK) return st;
+    if ((st = alloc_dev(ctx->m_cnt, ctx->n_pairs)) != TERA_OK) return st;
+  }
+  if (n > ctx->m_cap_agents || !ctx->m_tile_cnt) {
+    cudaDeviceSynchronize();
+    u64 cap = n + n / 8 + kClassifyTile;
+    u64 tiles = (cap + kClassifyTile - 1) / kClassifyTile;
+    if ((st = alloc_dev(ctx->m_tile_cnt, tiles + 1)) != TERA_OK) return st;
+    if ((st = alloc_dev(ctx->m_tile_base, tiles + 1)) != TERA_OK) return st;
+    if ((st = ensure_scan_part(ctx, tiles + 1)) != TERA_OK) return st;
+    ctx->m_cap_agents = cap;
+  }
+  if (leavers > ctx->m_cap_leavers || !ctx->m_key) {
+    cudaDeviceSynchronize();
+    u64 c = leavers < 1024 ? 1024 : leavers;
+    if ((st = alloc_dev(ctx->m_key, c)) != TERA_OK) return st;
+    if ((st = alloc_dev(ctx->m_agent, c)) != TERA_OK) return st;
+    if ((st = alloc_dev(ctx->m_sorted, c)) != TERA_OK) return st;
+    if ((st = alloc_dev(ctx->m_keys_b, c)) != TERA_OK) return st;
+    if ((st = alloc_dev(ctx->m_keys_c, c)) != TERA_OK) return st;
+    if ((st = alloc_dev(ctx->m_vals_b, c)) != TERA_OK) return st;
+    if ((st = alloc_dev(ctx->m_vals_c, c)) != TERA_OK) return st;
+    u64 tiles = (c + kSortTile - 1) / kSortTile;
+    if ((st = alloc_dev(ctx->m_hist, (u64)kRadix * tiles + 1)) != TERA_OK) return st;
+    if ((st = ensure_scan_part(ctx, (u64)kRadix * tiles + 1)) != TERA_OK) return st;
+    ctx->m_cap_leavers = c;
+  }
+  return TERA_OK;
+}
+
 tera_status ensure_pred(tera_ctx* ctx) {
   const u64 cap = ctx->cap_records, P = ctx->n_pairs;
   if (ctx->cseg_enc && ctx->pred_cap >= cap && ctx->unit_res && ctx->unit_res_cap >= ctx->cap_units)
@@ -452,6 +487,19 @@ tera_status tera_ctx_destroy(tera_ctx* c) {
   free_dev(c->b_team);
   free_dev(c->b_tsum);
   free_dev(c->b_tbase);
+  free_dev(c->m_tile_cnt);
+  free_dev(c->m_tile_base);
+  free_dev(c->m_from);
+  free_dev(c->m_before);
+  free_dev(c->m_cnt);
+  free_dev(c->m_key);
+  free_dev(c->m_agent);
+  free_dev(c->m_sorted);
+  free_dev(c->m_keys_b);
+  free_dev(c->m_keys_c);
+  free_dev(c->m_vals_b);
+  free_dev(c->m_vals_c);
+  free_dev(c->m_hist);
   free_dev(c->cseg_enc);
   free_dev(c->cseg_dec);
   free_dev(c->pscr);

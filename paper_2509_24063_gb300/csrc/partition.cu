@@ -13,92 +13,12 @@
 //                    the last pass writes the agent of every record and the
 //                    record index of every entry (pack reads in agent order)
 //   pair_off_kernel  per-pair counts and offsets from the sorted keys
+#include "classify.cuh"
 #include "tera_internal.cuh"
 
 using namespace tera;
 
 namespace {
-
-// Per-block copy of the grid keys that this grid uses.
-struct SmemGrid {
-  u64 ke[3][kMaxAxis + 1];
-  u64 ktl[3][kMaxAxis];
-  u64 kth[3][kMaxAxis];
-  u64 klo[3], khi[3];
-  float flo[3], fscale[3];
-  int n[3];
-  int periodic;
-};
-
-__device__ __forceinline__ void load_grid(SmemGrid& s, const GridTables* __restrict__ g) {
-  if (threadIdx.x < 3) {
-    s.n[threadIdx.x] = g->n[threadIdx.x];
-    s.klo[threadIdx.x] = g->klo[threadIdx.x];
-    s.khi[threadIdx.x] = g->khi[threadIdx.x];
-    s.flo[threadIdx.x] = g->flo[threadIdx.x];
-    s.fscale[threadIdx.x] = g->fscale[threadIdx.x];
-  }
-  if (threadIdx.x == 0) s.periodic = g->periodic;
-  for (int a = 0; a < 3; ++a) {
-    const int n = g->n[a];
-    for (int k = threadIdx.x; k <= n; k += blockDim.x) s.ke[a][k] = g->ke[a][k];
-    for (int k = threadIdx.x; k < n; k += blockDim.x) {
-      s.ktl[a][k] = g->ktl[a][k];
-      s.kth[a][k] = g->kth[a][k];
-    }
-  }
-  __syncthreads();
-}
-
-// One axis: box index i = #{k in 1..n-1 : v >= e[k]} and the neighbour
-// offsets whose aura holds v.  A float32 estimate of i is corrected by exact
-// comparisons of the 64-bit keys (so the result is exactly the rule's; the
-// estimate only saves the binary search).  Returns opts: bit 0 offset -1
-// qualifies (i > 0 and v < e[i] + w), bit 1 offset 0, bit 2 offset +1
-// (i < n-1 and v >= e[i+1] - w); on a periodic axis the neighbour always
-// exists.  0 when v is not in [lo, hi).
-__device__ __forceinline__ u32 classify_axis(u64 bits, int a, const SmemGrid& s, int* idx) {
-  const u64 k = key_of(bits);
-  if (!(k >= s.klo[a] && k < s.khi[a])) {
-    *idx = 0;
-    return 0u;
-  }
-  const int n = s.n[a];
-  const float f = (__double2float_rn(__longlong_as_double((long long)bits)) - s.flo[a]) * s.fscale[a];
-  int i = f > 0.0f ? (int)f : 0;
-  i = i < n - 1 ? i : n - 1;
-  while (i > 0 && k < s.ke[a][i]) --i;
-  while (i < n - 1 && k >= s.ke[a][i + 1]) ++i;
-  *idx = i;
-  const bool wrap = (s.periodic >> a) & 1;
-  const u32 lowq = (i > 0 || wrap) && (k < s.ktl[a][i]);
-  const u32 highq = (i < n - 1 || wrap) && (k >= s.kth[a][i]);
-  return 2u | lowq | (highq << 2);
-}
-
-// Bits 0, 1, 2 of v moved to bits 0, d, 2d.
-__device__ __forceinline__ u32 spread3(u32 v, u32 d) {
-  return (v & 1u) | ((v & 2u) << (d - 1)) | ((v & 4u) << (2 * d - 2));
-}
-
-__device__ __forceinline__ void classify_agent(u64 bx, u64 by, u64 bz, const SmemGrid& s,
-                                               int* owner, u32* mask, bool* ok) {
-  int ix, iy, iz;
-  const u32 ox = classify_axis(bx, 0, s, &ix);
-  const u32 oy = classify_axis(by, 1, s, &iy);
-  const u32 oz = classify_axis(bz, 2, s, &iz);
-  *ok = ox && oy && oz;
-  if (!*ok) {
-    *owner = -1;
-    *mask = 0;
-    return;
-  }
-  *owner = ix + s.n[0] * (iy + s.n[1] * iz);
-  // bit (dx + 3 dy + 9 dz) for every qualifying offset triple: the products
-  // place copies of ox at 3 dy and of that row at 9 dz (no carries)
-  const u32 m = ox * spread3(oy, 3) * spread3(oz, 9);
-  *mask = m & ~(1u << 13);
-}
 
 // Each block classifies one tile of kClassifyTile agents.  In round k thread t
 // holds agents 512k + 2t and 512k + 2t + 1 of the tile (one 16-byte load per
@@ -291,7 +211,7 @@ __global__ void __launch_bounds__(kSortThreads)
       keys_out[pos] = key;
       if (agent) {
         vals_out[pos] = agent[val];
-        dest[val] = pos;
+        if (dest) dest[val] = pos;
       } else {
         vals_out[pos] = val;
       }
@@ -331,6 +251,52 @@ __global__ void pair_off_kernel(const u32* __restrict__ sorted_keys,
 
 }  // namespace
 
+namespace tera {
+
+// Stable LSD radix sort of entries by a u32 key (every key < key_limit),
+// ceil(bits / 8) digit passes.  The entry count is read on the device
+// (*total_ptr; nothing is sorted when it exceeds cap).  Pass k reads (kin,
+// vin) and writes the b buffers (k even) or the c buffers; the last pass
+// writes the sorted keys to the buffer it does not read, vals_final[pos] =
+// agent[e] for the entry e sorted to pos, and dest[e] = pos (dest may be null).
+tera_status radix_sort_entries(tera_ctx* ctx, const SortBufs& b, const u32* keys_in,
+                               const u32* agent, u32* dest, u32* vals_final, const u64* total_ptr,
+                               u64 cap, u64 key_limit, const u32** sorted_keys, cudaStream_t s) {
+  int bits = 1;
+  while ((1ull << bits) < key_limit) ++bits;
+  const int passes = (bits + kRadixBits - 1) / kRadixBits;
+  const int dbits = (bits + passes - 1) / passes;
+  const u32 radix = 1u << dbits;
+  const u64 sort_tiles = cap == 0 ? 1 : (cap + kSortTile - 1) / kSortTile;
+  const u32* kin = keys_in;
+  const u32* vin = nullptr;
+  u32* kfinal = (passes & 1) ? b.keys_b : b.keys_c;
+  tera_status st;
+  for (int pass = 0; pass < passes && cap > 0; ++pass) {
+    const u32 shift = (u32)(pass * dbits);
+    const bool last = pass + 1 == passes;
+    u32* kout = last ? kfinal : ((pass & 1) ? b.keys_c : b.keys_b);
+    u32* vout = last ? vals_final : ((pass & 1) ? b.vals_c : b.vals_b);
+    prof_begin(ctx, s);
+    rs_hist_kernel<<<(unsigned)sort_tiles, kSortThreads, 0, s>>>(kin, total_ptr, cap, shift, radix,
+                                                                 b.hist, (u32)sort_tiles);
+    if ((st = check_launch(ctx, "rs_hist_kernel", s)) != TERA_OK) return st;
+    if ((st = scan_u32(ctx, b.hist, nullptr, b.hist, (u64)radix * sort_tiles, s)) != TERA_OK)
+      return st;
+    prof_begin(ctx, s);
+    rs_scatter_kernel<<<(unsigned)sort_tiles, kSortThreads, 0, s>>>(
+        kin, vin, kout, vout, last ? agent : nullptr, last ? dest : nullptr, total_ptr, cap, shift,
+        radix, b.hist, (u32)sort_tiles);
+    if ((st = check_launch(ctx, "rs_scatter_kernel", s)) != TERA_OK) return st;
+    kin = kout;
+    vin = vout;
+  }
+  *sorted_keys = kin;
+  return TERA_OK;
+}
+
+}  // namespace tera
+
 extern "C" tera_status tera_partition(tera_ctx* ctx, const tera_soa* soa, tera_partition_out* out,
                                       void* stream) {
   if (!ctx || !soa || !out) return TERA_EINVAL;
@@ -362,13 +328,7 @@ extern "C" tera_status tera_partition(tera_ctx* ctx, const tera_soa* soa, tera_p
   if ((st = check_launch(ctx, "classify_kernel", s)) != TERA_OK) return st;
   if ((st = scan_u32(ctx, ctx->tile_cnt, ctx->tile_base, nullptr, tiles, s)) != TERA_OK) return st;
 
-  // Sort passes over ceil(bits / 8) digits of the pair index.
   const u64 P = ctx->n_pairs;
-  int bits = 1;
-  while ((1ull << bits) < P) ++bits;
-  const int passes = (bits + kRadixBits - 1) / kRadixBits;
-  const int dbits = (bits + passes - 1) / passes;
-  const u32 radix = 1u << dbits;
   const u64 cap = out->idx_capacity;
   const u64* total_ptr = ctx->tile_base + tiles;
   if (cap > 0 || n > 0) {
@@ -378,37 +338,15 @@ extern "C" tera_status tera_partition(tera_ctx* ctx, const tera_soa* soa, tera_p
         ctx->d_status);
     if ((st = check_launch(ctx, "emit_kernel", s)) != TERA_OK) return st;
   }
-  // pass k reads (kin, vin) and writes the b buffers (k even) or the c buffers;
-  // the last pass writes the sorted keys to the buffer it does not read
-  const u64 sort_tiles = cap == 0 ? 1 : (cap + kSortTile - 1) / kSortTile;
-  const u32* kin = ctx->keys_a;
-  const u32* vin = nullptr;
-  u32* kfinal = passes == 1 ? ctx->keys_b : ((passes & 1) ? ctx->keys_b : ctx->keys_c);
-  for (int pass = 0; pass < passes && cap > 0; ++pass) {
-    const u32 shift = (u32)(pass * dbits);
-    const bool last = pass + 1 == passes;
-    u32* kout = last ? kfinal : ((pass & 1) ? ctx->keys_c : ctx->keys_b);
-    u32* vout = last ? out->pair_idx : ((pass & 1) ? ctx->vals_c : ctx->vals_b);
-    prof_begin(ctx, s);
-    rs_hist_kernel<<<(unsigned)sort_tiles, kSortThreads, 0, s>>>(kin, total_ptr, cap, shift, radix,
-                                                                 ctx->rs_hist, (u32)sort_tiles);
-    if ((st = check_launch(ctx, "rs_hist_kernel", s)) != TERA_OK) return st;
-    if ((st = scan_u32(ctx, ctx->rs_hist, nullptr, ctx->rs_hist, (u64)radix * sort_tiles, s)) !=
-        TERA_OK)
-      return st;
-    prof_begin(ctx, s);
-    rs_scatter_kernel<<<(unsigned)sort_tiles, kSortThreads, 0, s>>>(
-        kin, vin, kout, vout, last ? ctx->ent_agent : nullptr, last ? ctx->ent_dest : nullptr,
-        total_ptr, cap, shift, radix, ctx->rs_hist, (u32)sort_tiles);
-    if ((st = check_launch(ctx, "rs_scatter_kernel", s)) != TERA_OK) return st;
-    kin = kout;
-    vin = vout;
-  }
-  // after the loop, kin holds the sorted keys and out->pair_idx the agents
-  ctx->rec_pair = const_cast<u32*>(kin);
+  const SortBufs bufs{ctx->keys_b, ctx->keys_c, ctx->vals_b, ctx->vals_c, ctx->rs_hist};
+  const u32* sorted = nullptr;
+  if ((st = radix_sort_entries(ctx, bufs, ctx->keys_a, ctx->ent_agent, ctx->ent_dest, out->pair_idx,
+                               total_ptr, cap, P, &sorted, s)) != TERA_OK)
+    return st;
+  ctx->rec_pair = const_cast<u32*>(sorted);
   prof_begin(ctx, s);
   pair_off_kernel<<<(unsigned)((P + 256) / 256), 256, 0, s>>>(
-      kin, total_ptr, cap, P, reinterpret_cast<u64*>(out->pair_off),
+      sorted, total_ptr, cap, P, reinterpret_cast<u64*>(out->pair_off),
       reinterpret_cast<u64*>(out->pair_count), ctx->d_stats);
   return check_launch(ctx, "pair_off_kernel", s);
 }

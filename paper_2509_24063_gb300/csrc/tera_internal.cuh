@@ -304,6 +304,22 @@ struct tera_ctx {
   tera::U64x2* b_tsum;   // per-tile totals of the team pairs
   uint64_t b_tsum_cap;
   tera::u64* b_tbase;    // [P] first tile total of each team pair
+  // agent migration (migrate.cu)
+  uint64_t m_cap_agents;   // agents the tile arrays cover
+  uint64_t m_cap_leavers;  // leavers the list and sort buffers hold
+  uint32_t* m_tile_cnt;    // [tiles + 1] leavers per tile
+  tera::u64* m_tile_base;  // [tiles + 1] leavers before each tile (total last)
+  tera::u64* m_from;       // [boxes] leavers per source box
+  tera::u64* m_before;     // [boxes] leavers of the boxes before each box
+  tera::u64* m_cnt;        // [boxes * 27] leavers per inbox
+  uint32_t* m_key;         // [m_cap_leavers] inbox of leaver k (agent order)
+  uint32_t* m_agent;       // [m_cap_leavers] agent of leaver k
+  uint32_t* m_sorted;      // [m_cap_leavers] agent of inbox record j
+  uint32_t* m_keys_b;
+  uint32_t* m_keys_c;
+  uint32_t* m_vals_b;
+  uint32_t* m_vals_c;
+  uint32_t* m_hist;
 };
 
 namespace tera {
@@ -323,4 +339,18 @@ tera_status launch_unit_map(tera_ctx* ctx, u32 p0, u64 npr, cudaStream_t s);
 tera_status ensure_pred(tera_ctx* ctx);
 // Scratch of the batched codec.
 tera_status ensure_batched(tera_ctx* ctx);
+// Scratch of agent migration for n agents and up to `leavers` leavers.
+tera_status ensure_migrate(tera_ctx* ctx, uint64_t n, uint64_t leavers);
+
+// partition.cu: stable LSD radix sort of entries by u32 key.
+struct SortBufs {
+  u32* keys_b;
+  u32* keys_c;
+  u32* vals_b;
+  u32* vals_c;
+  u32* hist;  // [kRadix * sort tiles + 1]
+};
+tera_status radix_sort_entries(tera_ctx* ctx, const SortBufs& b, const u32* keys_in,
+                               const u32* agent, u32* dest, u32* vals_final, const u64* total_ptr,
+                               u64 cap, u64 key_limit, const u32** sorted_keys, cudaStream_t s);
 }  // namespace tera
