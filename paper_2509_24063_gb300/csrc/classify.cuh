@@ -7,48 +7,78 @@
 
 namespace tera {
 
-// Per-block copy of the grid keys that this grid uses.
+// Keys of one box along one axis: its edges e[i], e[i+1] and the aura
+// thresholds e[i] + w (towards box i-1), e[i+1] - w (towards box i+1).
+struct __align__(16) BoxKeys {
+  u64 e0, e1, tl, th;
+};
+
+// Per-block copy of the grid: the box rows of the three axes sit in dynamic
+// shared memory (grid_smem_bytes), axis a from row koff[a].
 struct SmemGrid {
-  u64 ke[3][kMaxAxis + 1];
-  u64 ktl[3][kMaxAxis];
-  u64 kth[3][kMaxAxis];
   u64 klo[3], khi[3];
   float flo[3], fscale[3];
   int n[3];
+  int koff[3];
   int periodic;
 };
 
+__device__ __forceinline__ BoxKeys* grid_rows() {
+  extern __shared__ BoxKeys tera_grid_rows[];
+  return tera_grid_rows;
+}
+
+// Dynamic shared memory a kernel that calls load_grid is launched with.
+inline size_t grid_smem_bytes(const tera_grid& g) {
+  return sizeof(BoxKeys) * (size_t)(g.n[0] + g.n[1] + g.n[2]);
+}
+
 __device__ __forceinline__ void load_grid(SmemGrid& s, const GridTables* __restrict__ g) {
   if (threadIdx.x < 3) {
-    s.n[threadIdx.x] = g->n[threadIdx.x];
-    s.klo[threadIdx.x] = g->klo[threadIdx.x];
-    s.khi[threadIdx.x] = g->khi[threadIdx.x];
-    s.flo[threadIdx.x] = g->flo[threadIdx.x];
-    s.fscale[threadIdx.x] = g->fscale[threadIdx.x];
+    const int a = threadIdx.x;
+    s.n[a] = g->n[a];
+    s.klo[a] = g->klo[a];
+    s.khi[a] = g->khi[a];
+    s.flo[a] = g->flo[a];
+    s.fscale[a] = g->fscale[a];
+    s.koff[a] = a == 0 ? 0 : (a == 1 ? g->n[0] : g->n[0] + g->n[1]);
   }
   if (threadIdx.x == 0) s.periodic = g->periodic;
+  BoxKeys* rows = grid_rows();
+  int off = 0;
   for (int a = 0; a < 3; ++a) {
     const int n = g->n[a];
-    for (int k = threadIdx.x; k <= n; k += blockDim.x) s.ke[a][k] = g->ke[a][k];
-    for (int k = threadIdx.x; k < n; k += blockDim.x) {
-      s.ktl[a][k] = g->ktl[a][k];
-      s.kth[a][k] = g->kth[a][k];
-    }
+    for (int k = threadIdx.x; k < n; k += blockDim.x)
+      rows[off + k] = BoxKeys{g->ke[a][k], g->ke[a][k + 1], g->ktl[a][k], g->kth[a][k]};
+    off += n;
   }
   __syncthreads();
 }
 
+// A float32 near a positive binary64 value from the high word of its bits,
+// by integer operations only (exponent re-biased, mantissa cut to 20 bits;
+// a binary64 conversion instruction runs at the GPU's low binary64 rate).
+// Values outside the normal float range give a meaningless estimate, which
+// the exact correction below still turns into the right index.
+__device__ __forceinline__ float approx_f32(u64 bits) {
+  const u32 hi = (u32)(bits >> 32);
+  return __uint_as_float((hi & 0x80000000u) | (((hi & 0x7FFFFFFFu) - 0x38000000u) << 3));
+}
+
 // Box index along one axis of a value inside [lo, hi) (k = key_of(bits)):
-// i = #{k in 1..n-1 : v >= e[k]}.  A float32 estimate of i is corrected by
-// exact comparisons of the 64-bit keys, so the result is exactly the rule's;
-// the estimate only saves the binary search.
-__device__ __forceinline__ int axis_index(u64 bits, u64 k, int a, const SmemGrid& s) {
+// i = #{k in 1..n-1 : v >= e[k]}, and the keys of that box in *r.  A float32
+// estimate of i is corrected by exact comparisons of the 64-bit keys, so the
+// result is exactly the rule's; the estimate only saves the binary search.
+__device__ __forceinline__ int axis_index(u64 bits, u64 k, int a, const SmemGrid& s, BoxKeys* r) {
   const int n = s.n[a];
-  const float f = (__double2float_rn(__longlong_as_double((long long)bits)) - s.flo[a]) * s.fscale[a];
+  const BoxKeys* rows = grid_rows() + s.koff[a];
+  const float f = (approx_f32(bits) - s.flo[a]) * s.fscale[a];
   int i = f > 0.0f ? (int)f : 0;
   i = i < n - 1 ? i : n - 1;
-  while (i > 0 && k < s.ke[a][i]) --i;
-  while (i < n - 1 && k >= s.ke[a][i + 1]) ++i;
+  BoxKeys b = rows[i];
+  while (i > 0 && k < b.e0) b = rows[--i];
+  while (i < n - 1 && k >= b.e1) b = rows[++i];
+  *r = b;
   return i;
 }
 
@@ -63,11 +93,12 @@ __device__ __forceinline__ u32 classify_axis(u64 bits, int a, const SmemGrid& s,
     return 0u;
   }
   const int n = s.n[a];
-  const int i = axis_index(bits, k, a, s);
+  BoxKeys b;
+  const int i = axis_index(bits, k, a, s, &b);
   *idx = i;
   const bool wrap = (s.periodic >> a) & 1;
-  const u32 lowq = (i > 0 || wrap) && (k < s.ktl[a][i]);
-  const u32 highq = (i < n - 1 || wrap) && (k >= s.kth[a][i]);
+  const u32 lowq = (i > 0 || wrap) && (k < b.tl);
+  const u32 highq = (i < n - 1 || wrap) && (k >= b.th);
   return 2u | lowq | (highq << 2);
 }
 
@@ -104,7 +135,8 @@ __device__ __forceinline__ int locate_agent(u64 bx, u64 by, u64 bz, const SmemGr
   for (int a = 0; a < 3; ++a) {
     const u64 k = key_of(b[a]);
     if (!(k >= s.klo[a] && k < s.khi[a])) return -1;
-    i[a] = axis_index(b[a], k, a, s);
+    BoxKeys r;
+    i[a] = axis_index(b[a], k, a, s, &r);
   }
   return i[0] + s.n[0] * (i[1] + s.n[1] * i[2]);
 }

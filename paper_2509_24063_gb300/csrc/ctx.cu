@@ -240,12 +240,12 @@ tera_status ensure_agents(tera_ctx* ctx, int64_t n, cudaStream_t s) {
   if (n <= ctx->cap_agents && ctx->tile_cnt && ctx->tile_base) return TERA_OK;
   cudaDeviceSynchronize();
   int64_t cap = n + n / 8 + kClassifyTile;
-  u64 tiles = ((u64)cap + kClassifyTile - 1) / kClassifyTile;
+  u64 tiles = ((u64)cap + kRunAgents - 1) / kRunAgents;  // runs of the classification
   tera_status st;
   if ((st = alloc_dev(ctx->tile_cnt, tiles + 1)) != TERA_OK) return st;
   if ((st = alloc_dev(ctx->tile_base, tiles + 1)) != TERA_OK) return st;
   ctx->cap_agents = cap;
-  return TERA_OK;
+  return ensure_scan_part(ctx, tiles + 1);
 }
 
 tera_status ensure_records(tera_ctx* ctx, uint64_t cap, cudaStream_t s) {
@@ -320,7 +320,7 @@ tera_status ensure_migrate(tera_ctx* ctx, uint64_t n, uint64_t leavers) {
   if (n > ctx->m_cap_agents || !ctx->m_tile_cnt) {
     cudaDeviceSynchronize();
     u64 cap = n + n / 8 + kClassifyTile;
-    u64 tiles = (cap + kClassifyTile - 1) / kClassifyTile;
+    u64 tiles = (cap + kWarpAgents - 1) / kWarpAgents;  // warp tiles
     if ((st = alloc_dev(ctx->m_tile_cnt, tiles + 1)) != TERA_OK) return st;
     if ((st = alloc_dev(ctx->m_tile_base, tiles + 1)) != TERA_OK) return st;
     if ((st = ensure_scan_part(ctx, tiles + 1)) != TERA_OK) return st;
@@ -332,6 +332,7 @@ tera_status ensure_migrate(tera_ctx* ctx, uint64_t n, uint64_t leavers) {
     if ((st = alloc_dev(ctx->m_key, c)) != TERA_OK) return st;
     if ((st = alloc_dev(ctx->m_agent, c)) != TERA_OK) return st;
     if ((st = alloc_dev(ctx->m_sorted, c)) != TERA_OK) return st;
+    if ((st = alloc_dev(ctx->m_dest, c)) != TERA_OK) return st;
     if ((st = alloc_dev(ctx->m_keys_b, c)) != TERA_OK) return st;
     if ((st = alloc_dev(ctx->m_keys_c, c)) != TERA_OK) return st;
     if ((st = alloc_dev(ctx->m_vals_b, c)) != TERA_OK) return st;
@@ -495,6 +496,7 @@ tera_status tera_ctx_destroy(tera_ctx* c) {
   free_dev(c->m_key);
   free_dev(c->m_agent);
   free_dev(c->m_sorted);
+  free_dev(c->m_dest);
   free_dev(c->m_keys_b);
   free_dev(c->m_keys_c);
   free_dev(c->m_vals_b);

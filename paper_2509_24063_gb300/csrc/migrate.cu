@@ -14,14 +14,16 @@
 //
 // tera_migrate_send
 //   mig_count_kernel   one pass over x, y, z: owner box of every agent; leavers
-//                      per tile, per source box and per inbox
-//   scan of the tile counts (leavers before every tile)
+//                      per warp tile, per source box and per inbox
+//   scan of the warp-tile counts (leavers before every warp tile)
 //   mig_scan_kernel    one block: checks box_off_prev; inbox offsets, next box
 //                      offsets, leavers of the boxes before each box, capacity
 //   mig_move_kernel    one pass over the 8 columns: every stayer to its place in
 //                      the next state, every leaver listed with its inbox
-//   stable radix sort of the leaver list by inbox (agent order kept)
-//   mig_pack_kernel    inbox headers, then every leaver's record (serialization)
+//   stable radix sort of the leaver list by inbox (agent order kept): each
+//                      leaver's position in inbox order
+//   mig_pack_kernel    inbox headers, then every leaver's record, read in
+//                      agent order (serialization)
 // tera_migrate_recv
 //   mig_unpack_kernel  every inbox record into the next state after the
 //                      receiver's stayers (deserialization), headers checked
@@ -73,41 +75,111 @@ __device__ __forceinline__ u32 inbox_side(u32 s, u32 d, const SmemGrid& g) {
   return bit;
 }
 
-// Box range of the agents [tile0, tile_end) of one tile, found once per block.
-__device__ __forceinline__ void tile_boxes(const u64* __restrict__ box_off, u32 n_boxes, u64 tile0,
-                                           u64 tile_end, u32* srange) {
-  if (threadIdx.x == 0) {
-    const u32 lo = box_search(box_off, 0, n_boxes - 1, tile0);
-    srange[0] = lo;
-    srange[1] = box_search(box_off, lo, n_boxes - 1, tile_end - 1);
+// Keys of the edges of one box on the three axes: a position is in the box
+// when key_lo[a] <= key(v[a]) < key_hi[a] on every axis.
+struct BoxBounds {
+  u64 lo[3], hi[3];
+};
+
+__device__ __forceinline__ void box_bounds(u32 s, const SmemGrid& g, BoxBounds* b) {
+  const u32 n0 = (u32)g.n[0], n1 = (u32)g.n[1];
+  const u32 c[3] = {s % n0, (s / n0) % n1, s / (n0 * n1)};
+  const BoxKeys* rows = grid_rows();
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const BoxKeys& r = rows[g.koff[a] + (int)c[a]];
+    b->lo[a] = r.e0;
+    b->hi[a] = r.e1;
   }
-  __syncthreads();
 }
 
-constexpr int kPairAgents = 2 * kClassifyThreads;  // agents per round of a tile
+__device__ __forceinline__ bool inside_box(u64 bx, u64 by, u64 bz, const BoxBounds& b) {
+  const u64 kx = key_of(bx), ky = key_of(by), kz = key_of(bz);
+  return kx >= b.lo[0] && kx < b.hi[0] && ky >= b.lo[1] && ky < b.hi[1] && kz >= b.lo[2] &&
+         kz < b.hi[2];
+}
 
-__global__ void __launch_bounds__(kClassifyThreads)
+// Owner box of an agent of box s: s itself when the position is still inside
+// it (the common case, six key comparisons with the warp's cached bounds of
+// box s_lo), else the full classification (-1 outside the domain).
+__device__ __forceinline__ int new_owner(u64 bx, u64 by, u64 bz, u32 s, u32 s_lo,
+                                         const BoxBounds& lo_bounds, const SmemGrid& g) {
+  if (s == s_lo) {
+    if (inside_box(bx, by, bz, lo_bounds)) return (int)s;
+  } else {
+    BoxBounds b;
+    box_bounds(s, g, &b);
+    if (inside_box(bx, by, bz, b)) return (int)s;
+  }
+  return locate_agent(bx, by, bz, g);
+}
+
+// atomicAdd(&ctr[key], 1) for every lane with `on`, one atomic per distinct
+// key of the warp (all lanes of the warp take part).
+__device__ __forceinline__ void warp_count(u64* ctr, u32 key, bool on) {
+  const u32 k = on ? key : 0xFFFFFFFFu;
+  const u32 peers = __match_any_sync(0xFFFFFFFFu, k);
+  const u32 lane = threadIdx.x & 31;
+  if (on && (__ffs(peers) - 1) == (int)lane) atomicAdd(&ctr[key], (u64)__popc(peers));
+}
+
+// Largest s in [lo, hi] with off[s] <= a, found by the whole warp: each step
+// probes 32 evenly spaced boxes at once (two steps for 513 offsets); lo when
+// there is none.  Every lane returns the same result, in [lo, hi].
+__device__ __forceinline__ u32 warp_box_search(const u64* __restrict__ off, u32 lo, u32 hi, u64 a) {
+  const u32 lane = threadIdx.x & 31;
+  while (lo < hi) {
+    const u32 step = (hi - lo + 32) / 32;  // ceil((hi - lo + 1) / 32)
+    const u32 idx = lo + lane * step;
+    const bool ok = idx <= hi && off[idx] <= a;
+    const u32 bal = __ballot_sync(0xFFFFFFFFu, ok);
+    if (bal == 0u) break;  // off[lo] > a
+    const u32 last = 31u - (u32)__clz(bal);
+    const u32 nlo = lo + last * step;
+    const u32 nhi = nlo + step - 1u;
+    lo = nlo;
+    hi = nhi < hi ? nhi : hi;
+    if (step == 1u) break;
+  }
+  return lo;
+}
+
+// Box range of the agents [w0, w_end) of one warp tile.
+__device__ __forceinline__ void warp_boxes(const u64* __restrict__ box_off, u32 n_boxes, u64 w0,
+                                           u64 w_end, u32* lo, u32* hi) {
+  *lo = warp_box_search(box_off, 0, n_boxes - 1, w0);
+  *hi = warp_box_search(box_off, *lo, n_boxes - 1, w_end - 1);
+}
+
+// Leavers are counted per warp tile (kWarpAgents agents), so their order
+// (agent order) needs no block-wide step.
+
+__global__ void __launch_bounds__(kClassifyThreads, 5)
     mig_count_kernel(const u64* __restrict__ x, const u64* __restrict__ y,
                      const u64* __restrict__ z, u64 n, const u64* __restrict__ box_off,
                      u32 n_boxes, const GridTables* __restrict__ g, u32* __restrict__ tile_cnt,
-                     u64* __restrict__ from, u64* __restrict__ cnt, DevStatus* st) {
+                     u64 n_wtiles, u64* __restrict__ from, u64* __restrict__ cnt, DevStatus* st) {
   __shared__ SmemGrid sg;
-  __shared__ u32 srange[2];
-  __shared__ u64 sm[33];
   load_grid(sg, g);
-  const u64 tile0 = (u64)blockIdx.x * kClassifyTile;
-  if (tile0 >= n) {
-    if (threadIdx.x == 0) tile_cnt[blockIdx.x] = 0;
+  const int lane = threadIdx.x & 31;
+  const u64 w = (u64)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+  const u64 w0 = w * kWarpAgents;
+  if (w0 >= n) {
+    if (lane == 0 && w < n_wtiles) tile_cnt[w] = 0;
     return;
   }
-  const u64 tile_end = tile0 + kClassifyTile < n ? tile0 + kClassifyTile : n;
-  tile_boxes(box_off, n_boxes, tile0, tile_end, srange);
-  const u32 s_lo = srange[0], s_hi = srange[1];
+  const u64 w_end = w0 + kWarpAgents < n ? w0 + kWarpAgents : n;
+  u32 s_lo, s_hi;
+  warp_boxes(box_off, n_boxes, w0, w_end, &s_lo, &s_hi);
+  __shared__ BoxBounds wbounds[kWarpsPerBlock];
+  BoxBounds& lo_bounds = wbounds[threadIdx.x >> 5];
+  if (lane == 0) box_bounds(s_lo, sg, &lo_bounds);
+  __syncwarp();
   u32 leavers = 0;
   bool bad = false;
 #pragma unroll
-  for (int k = 0; k < kClassifyPerThread / 2; ++k) {
-    const u64 a0 = tile0 + (u64)k * kPairAgents + 2u * threadIdx.x;
+  for (int k = 0; k < kWarpRounds; ++k) {
+    const u64 a0 = w0 + (u64)k * 64 + 2u * lane;
     u64 vx[2], vy[2], vz[2];
     if (a0 + 1 < n) {
       const ulonglong2 tx = *reinterpret_cast<const ulonglong2*>(x + a0);
@@ -126,24 +198,28 @@ __global__ void __launch_bounds__(kClassifyThreads)
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
       const u64 a = a0 + q;
-      if (a >= n) continue;
-      const int d = locate_agent(vx[q], vy[q], vz[q], sg);
-      if (d < 0) {
-        bad = true;  // stays in its box; TERA_EDOMAIN
-        continue;
+      bool leave = false;
+      u32 s = 0, key = 0;
+      if (a < n) {
+        s = box_search(box_off, s_lo, s_hi, a);
+        const int d = new_owner(vx[q], vy[q], vz[q], s, s_lo, lo_bounds, sg);
+        if (d < 0) {
+          bad = true;  // stays in its box; TERA_EDOMAIN
+        } else if ((u32)d != s) {
+          leave = true;
+          key = (u32)d * 27u + inbox_side(s, (u32)d, sg);
+        }
       }
-      const u32 s = box_search(box_off, s_lo, s_hi, a);
-      if ((u32)d != s) {
-        ++leavers;
-        atomicAdd(&from[s], 1ull);
-        atomicAdd(&cnt[(u64)d * 27u + inbox_side(s, (u32)d, sg)], 1ull);
+      if (__any_sync(0xFFFFFFFFu, leave)) {
+        leavers += leave;
+        warp_count(from, s, leave);
+        warp_count(cnt, key, leave);
       }
     }
   }
   if (bad) latch(st, TERA_EDOMAIN);
-  u64 tot;
-  block_excl_scan<u64>((u64)leavers, sm, &tot);
-  if (threadIdx.x == 0) tile_cnt[blockIdx.x] = (u32)tot;
+  leavers = warp_sum(leavers);
+  if (lane == 0) tile_cnt[w] = leavers;
 }
 
 // One block: checks box_off_prev (0 first, n last, non-decreasing), then
@@ -212,27 +288,33 @@ __device__ __forceinline__ bool aborted(const DevStatus* st) {
 
 // Stayer a of box s goes to box_off_next[s] + (a - box_off_prev[s]) minus the
 // leavers of box s before it; leaver k (in agent order) is listed with its
-// inbox.  Same tiling and rounds as mig_count_kernel.
-__global__ void __launch_bounds__(kClassifyThreads)
+// inbox.  Same warp tiles as mig_count_kernel; a leaver's rank is the count
+// before its warp tile plus two ballots per round.
+__global__ void __launch_bounds__(kClassifyThreads, 4)
     mig_move_kernel(Cols prev, u64 n, const u64* __restrict__ box_off_prev, u32 n_boxes,
                     const GridTables* __restrict__ g, const u64* __restrict__ tile_base,
                     const u64* __restrict__ box_off_next, const u64* __restrict__ before,
                     ColsOut next, u32* __restrict__ lv_key, u32* __restrict__ lv_agent, u64 lv_cap,
                     const DevStatus* st) {
   __shared__ SmemGrid sg;
-  __shared__ u32 srange[2];
-  __shared__ u64 sm[33];
   if (aborted(st)) return;
   load_grid(sg, g);
-  const u64 tile0 = (u64)blockIdx.x * kClassifyTile;
-  if (tile0 >= n) return;
-  const u64 tile_end = tile0 + kClassifyTile < n ? tile0 + kClassifyTile : n;
-  tile_boxes(box_off_prev, n_boxes, tile0, tile_end, srange);
-  const u32 s_lo = srange[0], s_hi = srange[1];
-  u64 run = tile_base[blockIdx.x];
-  for (int k = 0; k < kClassifyPerThread / 2; ++k) {
-    const u64 a0 = tile0 + (u64)k * kPairAgents + 2u * threadIdx.x;
-    if (tile0 + (u64)k * kPairAgents >= n) break;  // block-uniform
+  const int lane = threadIdx.x & 31;
+  const u32 lt = (1u << lane) - 1u;
+  const u64 w = (u64)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+  const u64 w0 = w * kWarpAgents;
+  if (w0 >= n) return;
+  const u64 w_end = w0 + kWarpAgents < n ? w0 + kWarpAgents : n;
+  u32 s_lo, s_hi;
+  warp_boxes(box_off_prev, n_boxes, w0, w_end, &s_lo, &s_hi);
+  __shared__ BoxBounds wbounds[kWarpsPerBlock];
+  BoxBounds& lo_bounds = wbounds[threadIdx.x >> 5];
+  if (lane == 0) box_bounds(s_lo, sg, &lo_bounds);
+  __syncwarp();
+  u64 run = tile_base[w];
+  for (int k = 0; k < kWarpRounds; ++k) {
+    const u64 a0 = w0 + (u64)k * 64 + 2u * lane;
+    if (w0 + (u64)k * 64 >= n) break;  // warp-uniform
     u64 v[8][2];
     if (a0 + 1 < n) {
 #pragma unroll
@@ -255,20 +337,20 @@ __global__ void __launch_bounds__(kClassifyThreads)
       const u64 a = a0 + q;
       if (a >= n) continue;
       box[q] = box_search(box_off_prev, s_lo, s_hi, a);
-      const int d = locate_agent(v[1][q], v[2][q], v[3][q], sg);
+      const int d = new_owner(v[1][q], v[2][q], v[3][q], box[q], s_lo, lo_bounds, sg);
       if (d >= 0 && (u32)d != box[q]) {
         leave[q] = true;
         key[q] = (u32)d * 27u + inbox_side(box[q], (u32)d, sg);
       }
     }
-    u64 tot;
-    const u64 ex = block_excl_scan<u64>((u64)leave[0] + (u64)leave[1], sm, &tot);
-    const u64 k0 = run + ex;
+    const u32 b0 = __ballot_sync(0xFFFFFFFFu, leave[0]);
+    const u32 b1 = __ballot_sync(0xFFFFFFFFu, leave[1]);
+    const u64 k0 = run + __popc(b0 & lt) + __popc(b1 & lt);  // leavers before agent a0
     u64 dst[2] = {0ull, 0ull};
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
       const u64 a = a0 + q;
-      const u64 kq = k0 + (q == 1 && leave[0] ? 1u : 0u);  // leavers before agent a
+      const u64 kq = k0 + (q == 1 && leave[0] ? 1u : 0u);
       if (a < n && !leave[q])
         dst[q] = box_off_next[box[q]] + (a - box_off_prev[box[q]]) - (kq - before[box[q]]);
     }
@@ -294,17 +376,19 @@ __global__ void __launch_bounds__(kClassifyThreads)
         }
       }
     }
-    run += tot;
+    run += __popc(b0) + __popc(b1);
   }
 }
 
 // Serialization: thread t < Q writes the header of inbox t; the 4 threads of
-// record j (inbox order) write its 16-byte quarters, words 2c and 2c+1 of the
-// leaver's columns, at unit j + q + 1.
+// leaver k (agent order, so the reads of each column are ascending) write the
+// 16-byte quarters of its record, words 2c and 2c+1, at unit dest[k] + q + 1
+// (dest[k] = its position in inbox order, from the sort).
 __global__ void __launch_bounds__(256)
     mig_pack_kernel(Cols prev, const u64* __restrict__ inbox_off, u64 Q,
-                    const u32* __restrict__ sorted_key, const u32* __restrict__ sorted_agent,
-                    u32 class_id, uint8_t* __restrict__ arena, const DevStatus* st) {
+                    const u32* __restrict__ lv_key, const u32* __restrict__ lv_agent,
+                    const u32* __restrict__ lv_dest, u32 class_id, uint8_t* __restrict__ arena,
+                    const DevStatus* st) {
   if (aborted(st)) return;
   const u64 L = inbox_off[Q];
   const u64 total = Q + 4 * L;
@@ -321,12 +405,19 @@ __global__ void __launch_bounds__(256)
       h[3] = make_ulonglong2(0ull, 0ull);
     } else {
       const u64 r = t - Q;
-      const u64 j = r >> 2;
+      const u64 k = r >> 2;
       const u32 c = (u32)(r & 3u);
-      const u32 a = sorted_agent[j];
-      const u64 q = sorted_key[j];
-      ulonglong2* dst = reinterpret_cast<ulonglong2*>(arena + (j + q + 1) * kRecBytes) + c;
-      *dst = make_ulonglong2(prev.c[2 * c][a], prev.c[2 * c + 1][a]);
+      const u32 a = lv_agent[k];
+      const u64 unit = (u64)lv_dest[k] + lv_key[k] + 1;
+      ulonglong2* dst = reinterpret_cast<ulonglong2*>(arena + unit * kRecBytes) + c;
+      u64 w0v, w1v;
+      switch (c) {  // constant column indexes keep the pointers in registers
+        case 0: w0v = prev.c[0][a]; w1v = prev.c[1][a]; break;
+        case 1: w0v = prev.c[2][a]; w1v = prev.c[3][a]; break;
+        case 2: w0v = prev.c[4][a]; w1v = prev.c[5][a]; break;
+        default: w0v = prev.c[6][a]; w1v = prev.c[7][a]; break;
+      }
+      *dst = make_ulonglong2(w0v, w1v);
     }
   }
 }
@@ -385,8 +476,15 @@ __global__ void __launch_bounds__(256)
         continue;
       }
       const ulonglong2 w = *(reinterpret_cast<const ulonglong2*>(arena + unit * kRecBytes) + c);
-      next.c[2 * c][dst] = w.x;
-      next.c[2 * c + 1][dst] = w.y;
+      u64 *p0, *p1;
+      switch (c) {  // constant column indexes keep the pointers in registers
+        case 0: p0 = next.c[0]; p1 = next.c[1]; break;
+        case 1: p0 = next.c[2]; p1 = next.c[3]; break;
+        case 2: p0 = next.c[4]; p1 = next.c[5]; break;
+        default: p0 = next.c[6]; p1 = next.c[7]; break;
+      }
+      p0[dst] = w.x;
+      p1[dst] = w.y;
     }
   }
   if (bad) latch(st, TERA_ECORRUPT);
@@ -438,13 +536,14 @@ extern "C" tera_status tera_migrate_send(tera_ctx* ctx, const tera_soa* prev,
   cudaMemsetAsync(&ctx->d_status->abort, 0, sizeof(u32), s);
   cudaMemsetAsync(ctx->m_from, 0, sizeof(u64) * B, s);
   cudaMemsetAsync(ctx->m_cnt, 0, sizeof(u64) * Q, s);
-  const u64 tiles = n == 0 ? 1 : (n + kClassifyTile - 1) / kClassifyTile;
+  const u64 blocks = n == 0 ? 1 : (n + kBlockAgents - 1) / kBlockAgents;
+  const u64 wtiles = n == 0 ? 1 : (n + kWarpAgents - 1) / kWarpAgents;
   prof_begin(ctx, s);
-  mig_count_kernel<<<(unsigned)tiles, kClassifyThreads, 0, s>>>(
-      cp.c[1], cp.c[2], cp.c[3], n, off_prev, (u32)B, ctx->d_grid, ctx->m_tile_cnt, ctx->m_from,
-      ctx->m_cnt, ctx->d_status);
+  mig_count_kernel<<<(unsigned)blocks, kClassifyThreads, grid_smem_bytes(ctx->grid), s>>>(
+      cp.c[1], cp.c[2], cp.c[3], n, off_prev, (u32)B, ctx->d_grid, ctx->m_tile_cnt, wtiles,
+      ctx->m_from, ctx->m_cnt, ctx->d_status);
   if ((st = check_launch(ctx, "mig_count_kernel", s)) != TERA_OK) return st;
-  if ((st = scan_u32(ctx, ctx->m_tile_cnt, ctx->m_tile_base, nullptr, tiles, s)) != TERA_OK)
+  if ((st = scan_u32(ctx, ctx->m_tile_cnt, ctx->m_tile_base, nullptr, wtiles, s)) != TERA_OK)
     return st;
   prof_begin(ctx, s);
   mig_scan_kernel<<<1, 1024, 0, s>>>(off_prev, n, (u32)B, ctx->m_from, ctx->m_cnt, arena_units,
@@ -452,7 +551,7 @@ extern "C" tera_status tera_migrate_send(tera_ctx* ctx, const tera_soa* prev,
   if ((st = check_launch(ctx, "mig_scan_kernel", s)) != TERA_OK) return st;
   if (n > 0) {
     prof_begin(ctx, s);
-    mig_move_kernel<<<(unsigned)tiles, kClassifyThreads, 0, s>>>(
+    mig_move_kernel<<<(unsigned)blocks, kClassifyThreads, grid_smem_bytes(ctx->grid), s>>>(
         cp, n, off_prev, (u32)B, ctx->d_grid, ctx->m_tile_base, off_next, ctx->m_before, cn,
         ctx->m_key, ctx->m_agent, lv_cap, ctx->d_status);
     if ((st = check_launch(ctx, "mig_move_kernel", s)) != TERA_OK) return st;
@@ -461,13 +560,13 @@ extern "C" tera_status tera_migrate_send(tera_ctx* ctx, const tera_soa* prev,
   // lv_cap leavers (capacity error, latched above) sorts nothing
   const SortBufs bufs{ctx->m_keys_b, ctx->m_keys_c, ctx->m_vals_b, ctx->m_vals_c, ctx->m_hist};
   const u32* sorted = ctx->m_key;
-  if ((st = radix_sort_entries(ctx, bufs, ctx->m_key, ctx->m_agent, nullptr, ctx->m_sorted,
+  if ((st = radix_sort_entries(ctx, bufs, ctx->m_key, ctx->m_agent, ctx->m_dest, ctx->m_sorted,
                                inbox + Q, lv_cap, Q, &sorted, s)) != TERA_OK)
     return st;
   prof_begin(ctx, s);
-  mig_pack_kernel<<<(unsigned)grid_for(ctx, 4), 256, 0, s>>>(cp, inbox, Q, sorted,
-                                                             ctx->m_sorted, ctx->class_id, arena,
-                                                             ctx->d_status);
+  mig_pack_kernel<<<(unsigned)grid_for(ctx, 4), 256, 0, s>>>(cp, inbox, Q, ctx->m_key,
+                                                             ctx->m_agent, ctx->m_dest,
+                                                             ctx->class_id, arena, ctx->d_status);
   return check_launch(ctx, "mig_pack_kernel", s);
 }
 

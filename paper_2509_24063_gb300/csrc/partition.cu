@@ -4,9 +4,10 @@
 //
 // Kernels:
 //   classify_kernel  one pass over x,y,z (coalesced 16-byte loads): owner box,
-//                    26-bit aura mask, per-tile count of (agent, pair) entries
-//   emit_kernel      stable compaction of the entries in agent order
-//                    (block scan over each tile, tile bases from a scan)
+//                    26-bit aura mask, count of (agent, pair) entries of every
+//                    run of 64 consecutive agents
+//   emit_kernel      stable compaction of the entries in agent order (warp
+//                    scans inside a run, run bases from a scan)
 //   rs_hist_kernel / rs_scatter_kernel
 //                    stable LSD radix sort of the entry indices by pair
 //                    index, so each pair's list keeps ascending agent order;
@@ -22,21 +23,22 @@ namespace {
 
 // Each block classifies one tile of kClassifyTile agents.  In round k thread t
 // holds agents 512k + 2t and 512k + 2t + 1 of the tile (one 16-byte load per
-// coordinate), so every warp load is fully coalesced.
-__global__ void __launch_bounds__(kClassifyThreads)
+// coordinate), so every warp load is fully coalesced, and each warp covers a
+// run of kRunAgents consecutive agents per round; the number of (agent, pair)
+// entries of every run is written (runs are in agent order).
+__global__ void __launch_bounds__(kClassifyThreads, 6)
     classify_kernel(const u64* __restrict__ x, const u64* __restrict__ y,
                     const u64* __restrict__ z, u64 n, const GridTables* __restrict__ g,
-                    int* __restrict__ owner, u32* __restrict__ mask, u32* __restrict__ tile_cnt,
-                    DevStatus* st, DevStats* stats) {
-  __shared__ u64 sm[33];
+                    int* __restrict__ owner, u32* __restrict__ mask, u32* __restrict__ run_cnt,
+                    u64 n_runs, DevStatus* st, DevStats* stats) {
   __shared__ SmemGrid sg;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     stats->iterations += 1;
     stats->agents += n;
   }
   load_grid(sg, g);
+  const int lane = threadIdx.x & 31;
   const u64 tile0 = (u64)blockIdx.x * kClassifyTile;
-  u32 cnt = 0;
   bool bad = false;
 #pragma unroll
   for (int k = 0; k < kClassifyPerThread / 2; ++k) {
@@ -59,6 +61,7 @@ __global__ void __launch_bounds__(kClassifyThreads)
     }
     int o[2];
     u32 m[2];
+    u32 cnt = 0;
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
       bool ok;
@@ -75,21 +78,21 @@ __global__ void __launch_bounds__(kClassifyThreads)
       owner[a0] = o[0];
       mask[a0] = m[0];
     }
+    cnt = warp_sum(cnt);
+    const u64 run = (a0 - 2u * lane) / kRunAgents;
+    if (lane == 0 && run < n_runs) run_cnt[run] = cnt;
   }
   if (bad) latch(st, TERA_EDOMAIN);
-  u64 tot;
-  block_excl_scan<u64>((u64)cnt, sm, &tot);
-  if (threadIdx.x == 0) tile_cnt[blockIdx.x] = (u32)tot;
 }
 
-// Emit (pair, agent) entries in agent order: tile t writes its entries at
-// tile_base[t]; within the tile, round k and thread t as in classify_kernel.
+// Emit (pair, agent) entries in agent order, with the rounds and runs of
+// classify_kernel: run r writes its entries from run_base[r]; within a run,
+// lanes are ranked by a warp scan.
 __global__ void __launch_bounds__(kClassifyThreads)
     emit_kernel(const int* __restrict__ owner, const u32* __restrict__ mask, u64 n,
-                const u64* __restrict__ tile_base, u64 n_tiles, u32* __restrict__ keys,
+                const u64* __restrict__ run_base, u64 n_runs, u32* __restrict__ keys,
                 u32* __restrict__ vals, u64 cap, DevStatus* st) {
-  __shared__ u64 sm[33];
-  const u64 total = tile_base[n_tiles];
+  const u64 total = run_base[n_runs];
   if (total > cap) {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
       latch(st, TERA_ECAPACITY);
@@ -98,10 +101,12 @@ __global__ void __launch_bounds__(kClassifyThreads)
     }
     return;
   }
+  const int lane = threadIdx.x & 31;
   const u64 tile0 = (u64)blockIdx.x * kClassifyTile;
-  u64 run = tile_base[blockIdx.x];
   for (int k = 0; k < kClassifyPerThread / 2; ++k) {
     const u64 a0 = tile0 + (u64)k * (2 * kClassifyThreads) + 2u * threadIdx.x;
+    const u64 first = a0 - 2u * lane;
+    if (first >= n) break;  // warp-uniform
     u32 m[2] = {0u, 0u};
     int o[2] = {0, 0};
     if (a0 + 1 < n) {
@@ -116,9 +121,8 @@ __global__ void __launch_bounds__(kClassifyThreads)
       if (m[0]) o[0] = owner[a0];
     }
     const u32 c = __popc(m[0]) + __popc(m[1]);
-    u64 tot;
-    u64 ex = block_excl_scan<u64>((u64)c, sm, &tot);
-    u64 pos = run + ex;
+    const u32 inc = warp_incl_scan<u32>(c);
+    u64 pos = run_base[first / kRunAgents] + (inc - c);
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
       u32 mm = m[q];
@@ -130,7 +134,6 @@ __global__ void __launch_bounds__(kClassifyThreads)
         ++pos;
       }
     }
-    run += tot;
   }
 }
 
@@ -318,23 +321,25 @@ extern "C" tera_status tera_partition(tera_ctx* ctx, const tera_soa* soa, tera_p
   if ((st = ensure_records(ctx, out->idx_capacity, s)) != TERA_OK) return st;
   ctx->iterations += 1;
   cudaMemsetAsync(&ctx->d_status->abort, 0, sizeof(u32), s);
-  const u64 tiles = n == 0 ? 1 : (n + kClassifyTile - 1) / kClassifyTile;
+  const u64 blocks = n == 0 ? 1 : (n + kClassifyTile - 1) / kClassifyTile;
+  const u64 runs = n == 0 ? 1 : (n + kRunAgents - 1) / kRunAgents;
   if (n == 0) cudaMemsetAsync(ctx->tile_cnt, 0, sizeof(u32), s);
   prof_begin(ctx, s);
-  classify_kernel<<<(unsigned)tiles, kClassifyThreads, 0, s>>>(
+  classify_kernel<<<(unsigned)blocks, kClassifyThreads, grid_smem_bytes(ctx->grid), s>>>(
       reinterpret_cast<const u64*>(soa->x), reinterpret_cast<const u64*>(soa->y),
       reinterpret_cast<const u64*>(soa->z), n, ctx->d_grid, out->owner, out->mask, ctx->tile_cnt,
-      ctx->d_status, ctx->d_stats);
+      runs, ctx->d_status, ctx->d_stats);
   if ((st = check_launch(ctx, "classify_kernel", s)) != TERA_OK) return st;
-  if ((st = scan_u32(ctx, ctx->tile_cnt, ctx->tile_base, nullptr, tiles, s)) != TERA_OK) return st;
+  if ((st = scan_u32(ctx, ctx->tile_cnt, ctx->tile_base, nullptr, runs, s)) != TERA_OK)
+    return st;
 
   const u64 P = ctx->n_pairs;
   const u64 cap = out->idx_capacity;
-  const u64* total_ptr = ctx->tile_base + tiles;
+  const u64* total_ptr = ctx->tile_base + runs;
   if (cap > 0 || n > 0) {
     prof_begin(ctx, s);
-    emit_kernel<<<(unsigned)tiles, kClassifyThreads, 0, s>>>(
-        out->owner, out->mask, n, ctx->tile_base, tiles, ctx->keys_a, ctx->ent_agent, cap,
+    emit_kernel<<<(unsigned)blocks, kClassifyThreads, 0, s>>>(
+        out->owner, out->mask, n, ctx->tile_base, runs, ctx->keys_a, ctx->ent_agent, cap,
         ctx->d_status);
     if ((st = check_launch(ctx, "emit_kernel", s)) != TERA_OK) return st;
   }

@@ -24,6 +24,18 @@ constexpr int kClassifyThreads = 256;
 constexpr int kClassifyPerThread = 8;
 constexpr int kClassifyTile = kClassifyThreads * kClassifyPerThread;  // 2048
 constexpr int kCodecTile = 256;
+// Warp tiles of the agent passes (classification, emit, migration): warp w
+// owns agents [w * kWarpAgents, (w+1) * kWarpAgents); in round r lane l holds
+// agents 64 r + 2 l and 64 r + 2 l + 1 of it (16-byte loads, coalesced).
+// Per-warp counts give every warp its output position with no block-wide
+// step; a block of kClassifyThreads threads covers kBlockAgents agents.
+constexpr int kWarpAgents = 256;
+constexpr int kWarpRounds = kWarpAgents / 64;
+constexpr int kWarpsPerBlock = kClassifyThreads / 32;
+constexpr int kBlockAgents = kWarpAgents * kWarpsPerBlock;  // 2048
+// Runs of the partition's classification: 64 consecutive agents (one warp,
+// one round of a classification tile), counted one by one.
+constexpr int kRunAgents = 64;
 
 // Radix sort of (pair, agent) entries.
 constexpr int kSortThreads = 256;
@@ -253,8 +265,8 @@ struct tera_ctx {
   // partition scratch
   int64_t cap_agents;
   uint64_t cap_records;
-  uint32_t* tile_cnt;      // [tiles + 1]
-  tera::u64* tile_base;     // [tiles + 1]
+  uint32_t* tile_cnt;      // [runs + 1] entries per run of 64 agents
+  tera::u64* tile_base;     // [runs + 1] entries before each run
   // entries (agent, pair) of the last partition in agent order, and where
   // each went in the pair-sorted order (pack reads them in agent order)
   uint32_t* keys_a;        // [cap_records] pair of entry e
@@ -307,14 +319,15 @@ struct tera_ctx {
   // agent migration (migrate.cu)
   uint64_t m_cap_agents;   // agents the tile arrays cover
   uint64_t m_cap_leavers;  // leavers the list and sort buffers hold
-  uint32_t* m_tile_cnt;    // [tiles + 1] leavers per tile
-  tera::u64* m_tile_base;  // [tiles + 1] leavers before each tile (total last)
+  uint32_t* m_tile_cnt;    // [warp tiles + 1] leavers per warp tile of 256 agents
+  tera::u64* m_tile_base;  // [warp tiles + 1] leavers before each warp tile (total last)
   tera::u64* m_from;       // [boxes] leavers per source box
   tera::u64* m_before;     // [boxes] leavers of the boxes before each box
   tera::u64* m_cnt;        // [boxes * 27] leavers per inbox
   uint32_t* m_key;         // [m_cap_leavers] inbox of leaver k (agent order)
   uint32_t* m_agent;       // [m_cap_leavers] agent of leaver k
   uint32_t* m_sorted;      // [m_cap_leavers] agent of inbox record j
+  uint32_t* m_dest;        // [m_cap_leavers] inbox-order position of leaver k
   uint32_t* m_keys_b;
   uint32_t* m_keys_c;
   uint32_t* m_vals_b;
