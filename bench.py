@@ -62,7 +62,8 @@ def kernel_bytes(name, t):
 # DRAM traffic of the dominant kernel per launch, from a one-pass ncu capture of
 # the full-size run recorded in profiles/; used only while the kernel's sources
 # are the ones the capture was taken with (their digest is recorded beside it).
-KERNEL_SOURCES = {"codec_persistent_kernel": ("batched.cu", "codec.cuh", "tera_internal.cuh")}
+KERNEL_SOURCES = {"codec_persistent_kernel": ("batched.cu", "codec.cuh", "tera_device.cuh"),
+                  "mig_move_kernel": ("migrate.cu", "classify.cuh", "tera_device.cuh")}
 
 
 def kernel_digest(name):
@@ -78,8 +79,9 @@ def kernel_digest(name):
 
 
 def recorded_traffic(name, workload):
-    """(bytes per launch, records per launch) recorded for this kernel and
-    workload, or None when absent or taken with other kernel sources."""
+    """(bytes per launch, units per launch) recorded for this kernel and
+    workload (units: records, or agents for migration kernels), or None when
+    absent or taken with other kernel sources."""
     path = os.path.join(ROOT, "profiles", f"{name}_{workload}.md")
     try:
         with open(path) as f:
@@ -93,9 +95,10 @@ def recorded_traffic(name, workload):
             vals[k.strip()] = v.strip().strip("`")
     if vals.get("kernel source digest") != kernel_digest(name):
         return None
+    units = vals.get("records per launch", vals.get("agents per launch"))
     try:
-        return float(vals["DRAM bytes per launch"]), float(vals["records per launch"])
-    except (KeyError, ValueError):
+        return float(vals["DRAM bytes per launch"]), float(units)
+    except (KeyError, TypeError, ValueError):
         return None
 
 
@@ -324,8 +327,10 @@ def run_migration(args):
     roofline = None
     if dbytes is not None and dn > 0:
         achieved = dbytes / dn / (dms / dn / 1e3) / 1e9
+        rec = recorded_traffic(dname, wl.name) if not args.agents else None
+        traffic = rec[0] * n / rec[1] if rec is not None else None  # grows with the agents
         roofline = {"bound": "hbm", "kernel": dname, "achieved": achieved, "peak": hbm,
-                    "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
+                    "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
                     "peak_kind": peak_kind, "launches": dn, "avg_ms": dms / dn,
                     "algorithmic_bytes_per_launch": dbytes / dn}
     if args.profile_table and rank == 0:
