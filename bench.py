@@ -211,6 +211,71 @@ def oracle_time(wl, host_states):
     return times
 
 
+def lz4_library():
+    """liblz4 through its public C API, or None when the library is absent."""
+    import ctypes as C
+    for name in ("liblz4.so.1", "liblz4.so"):
+        try:
+            L = C.CDLL(name)
+        except OSError:
+            continue
+        L.LZ4_compressBound.argtypes = [C.c_int]
+        L.LZ4_compressBound.restype = C.c_int
+        L.LZ4_compress_default.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_int]
+        L.LZ4_compress_default.restype = C.c_int
+        return L
+    return None
+
+
+def compression_comparison(wl, host_states):
+    """The paper's compression framing (Sec. 3.11) on the CPU sample, message
+    by message: LZ4 alone on the raw TeraAgent IO buffers (header + records),
+    LZ4 after the difference encoding (the XOR-serialized message of Sec. 2.3),
+    and this codec's wire messages (header, codes, payload, padding)."""
+    import numpy as np
+
+    import oracle
+    L = lz4_library()
+    if L is None:
+        return {"available": False, "reason": "liblz4 is not installed on this host"}
+
+    def lz4_bytes(a):
+        a = np.ascontiguousarray(a).view(np.uint8)
+        n = int(a.nbytes)
+        cap = L.LZ4_compressBound(n)
+        out = np.empty(max(cap, 1), dtype=np.uint8)
+        r = L.LZ4_compress_default(a.ctypes.data, out.ctypes.data, n, cap)
+        assert r > 0 or n == 0
+        return r
+
+    g = oracle.make_grid(wl.lo, wl.hi, wl.grid, wl.w, wl.periodic)
+    r0 = oracle.exchange_iteration(g, host_states[0])
+    r1 = oracle.exchange_iteration(g, host_states[1], ref=(r0["ref_next"], r0["pair_off"]),
+                                   recv_ref=(r0["recv"], r0["recv_off"]))
+    assert r0["status"] == oracle.OK and r1["status"] == oracle.OK
+    off0, off1 = r0["pair_off"], r1["pair_off"]
+    raw = lz_raw = lz_delta = wire = msgs = 0
+    for p in range(len(off1) - 1):
+        m = int(off1[p + 1] - off1[p])
+        if m == 0:
+            continue
+        a = (int(off1[p]) + p) * 64
+        buf = r1["rec"][a:a + 64 * (m + 1)]  # header + records
+        msg = buf[64:].view(np.uint64).reshape(-1, 8)
+        ref = oracle.arena_pair(r0["ref_next"], off0, p)
+        raw += buf.nbytes
+        lz_raw += lz4_bytes(buf)
+        lz_delta += lz4_bytes(oracle.delta_records(msg, ref))
+        wire += int(r1["wire_len"][p])
+        msgs += 1
+    return {"available": True, "messages": msgs, "raw_bytes": raw, "lz4_bytes": lz_raw,
+            "delta_lz4_bytes": lz_delta, "codec_bytes": wire,
+            "raw_over_lz4": raw / lz_raw, "lz4_over_delta_lz4": lz_raw / lz_delta,
+            "raw_over_codec": raw / wire,
+            "sample": "second of two consecutive states of the CPU-baseline sample, every "
+                      "non-empty message compressed on its own"}
+
+
 def run_reference(args):
     """CPU oracle arm: W warm-up + K timed iterations on a bounded sample."""
     import torch
@@ -579,10 +644,11 @@ def main():
         e2e = run_e2e(args, tera, wl, e2e_host, nmax, max_records, local, tune_e2e)
         del e2e_host
 
-    cpu = None
+    cpu = compression = None
     if hs is not None:
         from synth import scaled
         tms = oracle_time(scaled(wl, ns), hs)
+        compression = compression_comparison(scaled(wl, ns), hs)
         cpu = {"value": int(hs[1]["x"].shape[0]) / tms[1], "unit": "agents/s", "cores": 1,
                "kind": "oracle",
                "sample": f"one iteration (with reference) of the first {ns} agents of two "
@@ -606,6 +672,7 @@ def main():
         "records_per_step": E / args.steps,
         "roofline": roofline,
         "cpu_baseline": cpu,
+        "compression": compression,
         "e2e": e2e,
         "gpu_launches": launches,
         "clocks": clk_sum,

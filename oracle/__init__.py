@@ -84,6 +84,7 @@ def lib():
             L.or_decode_all.argtypes = [u64, u32, P, P, P, P, P, u64, P]
             L.or_exchange_iteration.argtypes = [G, P, P, i64, u32, u32, P, P, P, P, P, P, P,
                                                 P, P, u64, P, P, P, P, P, P, u64, P, P]
+            L.or_delta_records.argtypes = [P, u64, P, u64, P, C.POINTER(C.c_uint64)]
             L.or_migrate_inbox_bit.argtypes = [G, i32, i32]
             L.or_migrate_send.argtypes = [G, P, P, i64, P, u32, P, P, u64, P, P, P]
             L.or_migrate_recv.argtypes = [G, P, P, u32, P, P, P]
@@ -119,6 +120,7 @@ def lib():
                       "or_exchange_iteration", "or_mlp_nparam", "or_features", "or_predict",
                       "or_sample", "or_encode_pair_pred", "or_decode_pair_pred",
                       "or_encode_all_pred", "or_decode_all_pred", "or_migrate_inbox_bit",
+                      "or_delta_records",
                       "or_migrate_send", "or_migrate_recv"):
                 getattr(L, f).restype = C.c_int
             _lib = L
@@ -211,6 +213,19 @@ def decode_pair(wire: np.ndarray, ref: np.ndarray, class_id=1, pair=0, out_cap=N
     st = lib().or_decode_pair(_p(buf), wire.size, _p(ref), ref.shape[0], class_id, pair,
                               _p(out), cap, _p(m))
     return st, out[:int(m[0])].copy()
+
+
+def delta_records(msg: np.ndarray, ref: np.ndarray) -> np.ndarray:
+    """Difference-serialized message before compression (Sec. 2.3 B and C):
+    (r + a, 8) uint64 words, XOR for matched slots, zeros for placeholders,
+    then the records absent from the reference."""
+    msg = np.ascontiguousarray(msg, dtype=np.uint64).reshape(-1, 8)
+    ref = np.ascontiguousarray(ref, dtype=np.uint64).reshape(-1, 8)
+    out = np.zeros((len(msg) + len(ref), 8), dtype=np.uint64)
+    ne = C.c_uint64(0)
+    st = lib().or_delta_records(_p(msg), len(msg), _p(ref), len(ref), _p(out), C.byref(ne))
+    assert st == OK, st
+    return out[:ne.value]
 
 
 def wire_slabs(pair_off, ref_off=None) -> np.ndarray:

@@ -551,6 +551,52 @@ static double now_s(void) {
   return (double)ts.tv_sec + 1e-9 * (double)ts.tv_nsec;
 }
 
+/* The difference-serialized message of Sec. 2.3 (steps B and C) before the
+ * compression stage: entry e < r is reference slot e, the XOR of the current
+ * record with the slot's id and the slot's record, or 64 zero bytes for a
+ * placeholder; entries r .. r+a-1 are the records absent from the
+ * reference, raw, in message order.  This is what a general-purpose
+ * compressor (LZ4 in the paper, Sec. 3.11) is given after the difference
+ * encoding.  out holds r + m entries at most; *n_entries = r + a. */
+int or_delta_records(const uint8_t* msg, uint64_t m, const uint8_t* ref, uint64_t r,
+                     uint8_t* out, uint64_t* n_entries) {
+  id_pos* sorted = (id_pos*)malloc(sizeof(id_pos) * (size_t)(m ? m : 1));
+  uint8_t* matched = (uint8_t*)calloc(m ? m : 1, 1);
+  int status = OR_OK;
+  if (!sorted || !matched) {
+    status = OR_ENOMEM;
+    goto done;
+  }
+  for (uint64_t k = 0; k < m; ++k) {
+    sorted[k].id = rec_word(msg + k * REC_BYTES, 0);
+    sorted[k].k = k;
+  }
+  qsort(sorted, (size_t)m, sizeof(id_pos), cmp_id_pos);
+  uint64_t e = 0;
+  for (uint64_t j = 0; j < r; ++j, ++e) {
+    uint8_t* o = out + e * REC_BYTES;
+    int64_t k = find_id(sorted, m, rec_word(ref + j * REC_BYTES, 0));
+    if (k < 0) {
+      memset(o, 0, REC_BYTES);
+      continue;
+    }
+    matched[k] = 1;
+    for (int w = 0; w < REC_WORDS; ++w)
+      put_le(o + 8 * w, rec_word(msg + (uint64_t)k * REC_BYTES, w) ^ rec_word(ref + j * REC_BYTES, w),
+             8);
+  }
+  for (uint64_t k = 0; k < m; ++k) {
+    if (matched[k]) continue;
+    memcpy(out + e * REC_BYTES, msg + k * REC_BYTES, REC_BYTES);
+    e += 1;
+  }
+  *n_entries = e;
+done:
+  free(sorted);
+  free(matched);
+  return status;
+}
+
 /* ---------- agent migration (Sec. 2.1 "Agent Migration") ----------
  * Agents whose new position lies in another box move to that box; they are
  * sent as raw TeraAgent IO records (Sec. 2.2.1), the difference encoding of

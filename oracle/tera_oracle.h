@@ -79,6 +79,11 @@ int or_decode_all(uint64_t n_pairs, uint32_t class_id, const uint8_t* wire,
                   const uint64_t* wire_off, const uint8_t* ref_arena, const uint64_t* ref_off,
                   uint8_t* recv, uint64_t recv_cap_units, uint64_t* recv_off);
 
+/* Difference-serialized message before compression (Sec. 2.3 B and C): XOR
+ * for matched slots, 64 zero bytes for placeholders, then the new records. */
+int or_delta_records(const uint8_t* msg, uint64_t m, const uint8_t* ref, uint64_t r,
+                     uint8_t* out, uint64_t* n_entries);
+
 /* Agent migration (Sec. 2.1 "Agent Migration"; records are the raw TeraAgent
  * IO buffers of Sec. 2.2.1).  The state is box-major: box s holds agents
  * [box_off_prev[s], box_off_prev[s+1]).  An agent whose position now lies in
