@@ -540,7 +540,8 @@ def main():
     for t in range(args.warmup):
         if t == 1 and args.path == "batched" and not args.no_autotune and fixed is None:
             from paper_2509_24063_gb300 import autotune
-            tune, table = autotune.tune_batched(ex, states[t])
+            # tuned afresh on this workload (untimed warm-up), not from the cache
+            tune, table = autotune.tune_batched(ex, states[t], use_cache=False)
             tune_info = {"tune": list(tune), "candidates": len(table)}
         else:
             ex.step(states[t])

@@ -162,13 +162,19 @@ __global__ void __launch_bounds__(kSortThreads)
   for (u32 d = threadIdx.x; d < radix; d += blockDim.x) hist[(u64)d * n_tiles + blockIdx.x] = cnt[d];
 }
 
-// Stable scatter of one sort tile.  The tile is consumed in kSortPerThread
-// rounds of kSortThreads consecutive entries (entry r*256 + t to thread t);
-// inside a round, equal digits are ranked by warp (match_any) and warp index.
-// The values are entry indices: vals_in == nullptr on the first pass (entry i
-// is at position i).  On the last pass (agent != nullptr) the outputs are the
-// record's agent (vals_out[pos] = agent[e]) and the entry's record index
-// (dest[e] = pos).
+// Stable scatter of one sort tile of kSortTile entries, staged in shared
+// memory.  The tile is ranked in kSortPerThread / 4 rounds: in a round warp w
+// takes 128 consecutive entries (4 sub-steps of 32, lane order), ranks equal
+// digits with match_any against warp-private counters, and one prefix over the
+// warps places them; every entry goes to its tile-local sorted position
+// (digit start + rank) in shared memory.  The tile is then written out in
+// sorted order, so consecutive threads write consecutive addresses of a
+// digit's run.  The values are entry indices: vals_in == nullptr on the first
+// pass (entry i is at position i).  On the last pass (agent != nullptr) the
+// outputs are the record's agent (vals_out[pos] = agent[e]) and, when dest is
+// given, the entry's record index (dest[e] = pos).
+constexpr int kSortSub = 4;  // sub-steps of 32 entries per warp and round
+
 __global__ void __launch_bounds__(kSortThreads)
     rs_scatter_kernel(const u32* __restrict__ keys_in, const u32* __restrict__ vals_in,
                       u32* __restrict__ keys_out, u32* __restrict__ vals_out,
@@ -176,55 +182,83 @@ __global__ void __launch_bounds__(kSortThreads)
                       const u64* __restrict__ total_ptr, u64 cap, u32 shift, u32 radix,
                       const u32* __restrict__ hist_scan, u32 n_tiles) {
   constexpr int kWarps = kSortThreads / 32;
-  __shared__ u32 base[kRadix];
+  constexpr int kRoundEntries = kSortThreads * kSortSub;
+  __shared__ u32 base[kRadix];    // global start of each digit for this tile
+  __shared__ u32 lstart[kRadix];  // tile-local start of each digit
+  __shared__ u32 run[kRadix];     // entries of each digit placed in earlier rounds
   __shared__ u32 wcnt[kWarps][kRadix];
-  __shared__ u32 rtot[kRadix];
+  __shared__ u32 skey[kSortTile];
+  __shared__ u32 sval[kSortTile];
+  __shared__ u32 sm[33];
   const u64 E = live_entries(total_ptr, cap);
   const u64 t0 = (u64)blockIdx.x * kSortTile;
   if (t0 >= E) return;
+  const u32 tile_n = (u32)(E - t0 < (u64)kSortTile ? E - t0 : (u64)kSortTile);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (u32 d = threadIdx.x; d < radix; d += blockDim.x) {
-    base[d] = hist_scan[(u64)d * n_tiles + blockIdx.x];
-    for (int w = 0; w < kWarps; ++w) wcnt[w][d] = 0;
+  const u32 lt = (1u << lane) - 1u;
+  {
+    const u32 d = threadIdx.x;
+    u32 c = 0;
+    if (d < radix) {
+      const u64 at = (u64)d * n_tiles + blockIdx.x;
+      base[d] = hist_scan[at];
+      c = hist_scan[at + 1] - hist_scan[at];
+      run[d] = 0;
+    }
+    u32 tot;
+    const u32 ex = block_excl_scan<u32>(c, sm, &tot);
+    if (d < radix) lstart[d] = ex;
   }
-  __syncthreads();
-  for (int k = 0; k < kSortPerThread; ++k) {
-    const u64 i = t0 + (u64)k * kSortThreads + threadIdx.x;
-    if (t0 + (u64)k * kSortThreads >= E) break;  // block-uniform
-    const bool live = i < E;
-    u32 key = live ? keys_in[i] : 0u;
-    u32 val = live ? (vals_in ? vals_in[i] : (u32)i) : 0u;
-    u32 d = live ? ((key >> shift) & (radix - 1)) : radix;  // sentinel digit for padding
-    u32 peers = __match_any_sync(0xFFFFFFFFu, d);
-    u32 rank = __popc(peers & ((1u << lane) - 1u));
-    if (live && rank == 0) wcnt[warp][d] = __popc(peers);
+  for (u32 r0 = 0; r0 < tile_n; r0 += kRoundEntries) {  // block-uniform
+    for (u32 d = lane; d < radix; d += 32) wcnt[warp][d] = 0;
+    __syncwarp();
+    u32 key[kSortSub], val[kSortSub], dig[kSortSub], rank[kSortSub];
+#pragma unroll
+    for (int q = 0; q < kSortSub; ++q) {
+      const u32 li = r0 + (u32)warp * (32 * kSortSub) + (u32)q * 32 + (u32)lane;
+      const bool live = li < tile_n;
+      const u64 i = t0 + li;
+      key[q] = live ? keys_in[i] : 0u;
+      val[q] = live ? (vals_in ? vals_in[i] : (u32)i) : 0u;
+      dig[q] = live ? ((key[q] >> shift) & (radix - 1)) : radix;  // sentinel for padding
+      const u32 peers = __match_any_sync(0xFFFFFFFFu, dig[q]);
+      rank[q] = (live ? wcnt[warp][dig[q]] : 0u) + __popc(peers & lt);
+      __syncwarp();
+      if (live && (peers & lt) == 0u) wcnt[warp][dig[q]] += __popc(peers);
+      __syncwarp();
+    }
     __syncthreads();
-    for (u32 dd = threadIdx.x; dd < radix; dd += blockDim.x) {
-      u32 s = 0;
+    for (u32 d = threadIdx.x; d < radix; d += blockDim.x) {
+      u32 sacc = run[d];
       for (int w = 0; w < kWarps; ++w) {
-        u32 c = wcnt[w][dd];
-        wcnt[w][dd] = s;
-        s += c;
+        const u32 c = wcnt[w][d];
+        wcnt[w][d] = sacc;
+        sacc += c;
       }
-      rtot[dd] = s;
+      run[d] = sacc;
     }
     __syncthreads();
-    if (live) {
-      u32 pos = base[d] + wcnt[warp][d] + rank;
-      keys_out[pos] = key;
-      if (agent) {
-        vals_out[pos] = agent[val];
-        if (dest) dest[val] = pos;
-      } else {
-        vals_out[pos] = val;
+#pragma unroll
+    for (int q = 0; q < kSortSub; ++q) {
+      if (dig[q] < radix) {
+        const u32 lp = lstart[dig[q]] + wcnt[warp][dig[q]] + rank[q];
+        skey[lp] = key[q];
+        sval[lp] = val[q];
       }
     }
     __syncthreads();
-    for (u32 dd = threadIdx.x; dd < radix; dd += blockDim.x) {
-      base[dd] += rtot[dd];
-      for (int w = 0; w < kWarps; ++w) wcnt[w][dd] = 0;
+  }
+  for (u32 li = threadIdx.x; li < tile_n; li += blockDim.x) {
+    const u32 key = skey[li], v = sval[li];
+    const u32 d = (key >> shift) & (radix - 1);
+    const u32 pos = base[d] + (li - lstart[d]);
+    keys_out[pos] = key;
+    if (agent) {
+      vals_out[pos] = agent[v];
+      if (dest) dest[v] = pos;
+    } else {
+      vals_out[pos] = v;
     }
-    __syncthreads();
   }
 }
 
