@@ -39,6 +39,9 @@ def kernel_bytes(name, t):
         "rs_hist_kernel": 4 * E,
         "rs_scatter_kernel": 16 * E,
         "pack_kernel": (4 + 64 + 64 + 16 + 4) * E,
+        # record fields read and the record written per entry, its record
+        # index; the mask of every agent
+        "pack_runs_kernel": (64 + 64 + 4) * E + 4 * N,
         "enc_match_kernel": (64 + 16 + 4 + 4 + 4) * R + 64 * (R - t["holes"]),
         "enc_new_kernel": 4 * E + (64 + 16) * A,
         "enc_emit_kernel": 4 * R + 128 * (R - t["holes"]) + 4 * E + 64 * A + 4 * A + Y + 64 * M,

@@ -3,11 +3,14 @@
 // class identity is written once in the buffer header.  The receiver can use
 // the buffer in place.
 //
-// pack_entries_kernel (all pairs): one thread per (agent, pair) entry, in
-// agent order, as tera_partition emitted them: consecutive threads read
-// nearby agents, so the column reads sweep the state arrays instead of
-// jumping, and each record leaves as one 64-byte store to its place
-// (entry -> record index from the partition's sort).
+// pack_runs_kernel (all pairs, columns 16-byte aligned): one pass over the
+// agents in the classification's runs of 64; a lane loads the columns of its
+// two agents once (16-byte loads) and stores the record once per entry, at
+// the record index the partition's sort gave the entry.
+//
+// pack_entries_kernel (all pairs, any alignment): one thread per (agent,
+// pair) entry, in agent order, as tera_partition emitted them, each record
+// one 64-byte store to its place.
 //
 // pack_kernel (a range of pairs): eight adjacent threads build one record
 // (each gathers one of the eight struct-of-arrays columns and writes one
@@ -102,6 +105,87 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// All pairs, after tera_partition of the same state: one pass over the agents
+// in the classification's tiles and rounds, each warp a run of 64 consecutive
+// agents, two per lane.  A lane whose agents have entries loads their eight
+// columns with 16-byte loads (every warp request covers whole sectors) and
+// stores each agent's record once per entry, at the record index the
+// partition's sort gave the entry; the entries of a run are numbered from
+// run_base[run] in agent order.
+__global__ void __launch_bounds__(kClassifyThreads)
+    pack_runs_kernel(SoaPtrs soa, u64 n, const int* __restrict__ owner,
+                     const u32* __restrict__ mask, const u64* __restrict__ run_base, u64 n_runs,
+                     const u32* __restrict__ ent_dest, const u64* __restrict__ pair_off, u64 P,
+                     uint8_t* __restrict__ arena, u64 arena_units, u32 class_id, DevStatus* st) {
+  const u64 E = pair_off[P];
+  if (E + P > arena_units) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      latch(st, TERA_ECAPACITY);
+      need(st, E + P);
+    }
+    return;
+  }
+  const u64 stride = (u64)gridDim.x * blockDim.x;
+  const u64 tid = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+  for (u64 p = tid; p < P; p += stride) {
+    const u64 m = pair_off[p + 1] - pair_off[p];
+    write_taio_header(arena + (pair_off[p] + p) * kRecBytes, class_id, (u32)p, m);
+  }
+  // a partition that overflowed its capacity left no record indices
+  if (run_base[n_runs] != E) return;
+  const int lane = threadIdx.x & 31;
+  const u64 tile0 = (u64)blockIdx.x * kClassifyTile;
+  for (int k = 0; k < kClassifyPerThread / 2; ++k) {
+    const u64 a0 = tile0 + (u64)k * (2 * kClassifyThreads) + 2u * threadIdx.x;
+    const u64 first = a0 - 2u * lane;
+    if (first >= n) break;  // warp-uniform
+    u32 m[2] = {0u, 0u};
+    if (a0 + 1 < n) {
+      const uint2 mm = *reinterpret_cast<const uint2*>(mask + a0);
+      m[0] = mm.x;
+      m[1] = mm.y;
+    } else if (a0 < n) {
+      m[0] = mask[a0];
+    }
+    const u32 c = __popc(m[0]) + __popc(m[1]);
+    const u32 inc = warp_incl_scan<u32>(c);
+    u64 e = run_base[first / kRunAgents] + (inc - c);
+    if (!(m[0] | m[1])) continue;
+    u64 v[8][2];
+    int o[2];
+    if (a0 + 1 < n) {
+      const int2 oo = *reinterpret_cast<const int2*>(owner + a0);
+      o[0] = oo.x;
+      o[1] = oo.y;
+#pragma unroll
+      for (int w = 0; w < 8; ++w) {
+        const ulonglong2 t = *reinterpret_cast<const ulonglong2*>(soa.col[w] + a0);
+        v[w][0] = t.x;
+        v[w][1] = t.y;
+      }
+    } else {
+      o[0] = owner[a0];
+      o[1] = 0;
+#pragma unroll
+      for (int w = 0; w < 8; ++w) {
+        v[w][0] = soa.col[w][a0];
+        v[w][1] = 0ull;
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      Rec R;
+#pragma unroll
+      for (int w = 0; w < 8; ++w) R.w[w] = v[w][q];
+      for (u32 mm = m[q]; mm; mm &= mm - 1) {
+        const u64 p = (u64)o[q] * 27u + (u64)(__ffs(mm) - 1);
+        store_rec(arena + ((u64)ent_dest[e] + p + 1) * kRecBytes, R);
+        ++e;
+      }
+    }
+  }
+}
+
 }  // namespace
 
 extern "C" tera_status tera_pack(tera_ctx* ctx, const tera_soa* soa, const tera_partition_out* part,
@@ -133,6 +217,20 @@ extern "C" tera_status tera_pack(tera_ctx* ctx, const tera_soa* soa, const tera_
   u64 maxg = (u64)grid_for(ctx, 8);
   unsigned blocks = (unsigned)(est < maxg ? est : maxg);
   if (!ctx->rec_pair) return TERA_EINVAL;  // tera_partition has not run on this context
+  bool aligned = part->owner && part->mask && ((uintptr_t)part->owner & 7u) == 0 &&
+                 ((uintptr_t)part->mask & 7u) == 0;
+  for (int w = 0; w < 8; ++w) aligned = aligned && ((uintptr_t)p.col[w] & 15u) == 0;
+  if (pair_begin == 0 && pair_end == ctx->n_pairs && aligned && ctx->pack_n == soa->n) {
+    const u64 n = (u64)soa->n;
+    const u64 blocks = n == 0 ? 1 : (n + kClassifyTile - 1) / kClassifyTile;
+    const u64 runs = n == 0 ? 1 : (n + kRunAgents - 1) / kRunAgents;
+    prof_begin(ctx, s);
+    pack_runs_kernel<<<(unsigned)blocks, kClassifyThreads, 0, s>>>(
+        p, n, part->owner, part->mask, ctx->tile_base, runs, ctx->ent_dest,
+        reinterpret_cast<const u64*>(part->pair_off), ctx->n_pairs, rec_arena, arena_units,
+        ctx->class_id, ctx->d_status);
+    return check_launch(ctx, "pack_runs_kernel", s);
+  }
   if (pair_begin == 0 && pair_end == ctx->n_pairs) {
     prof_begin(ctx, s);
     pack_entries_kernel<<<(unsigned)grid_for(ctx, 8), 256, 0, s>>>(

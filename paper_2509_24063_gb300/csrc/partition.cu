@@ -383,6 +383,7 @@ extern "C" tera_status tera_partition(tera_ctx* ctx, const tera_soa* soa, tera_p
                                total_ptr, cap, P, &sorted, s)) != TERA_OK)
     return st;
   ctx->rec_pair = const_cast<u32*>(sorted);
+  ctx->pack_n = soa->n;
   prof_begin(ctx, s);
   pair_off_kernel<<<(unsigned)((P + 256) / 256), 256, 0, s>>>(
       sorted, total_ptr, cap, P, reinterpret_cast<u64*>(out->pair_off),

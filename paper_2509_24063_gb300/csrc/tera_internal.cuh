@@ -36,6 +36,7 @@ struct tera_ctx {
   uint32_t* vals_b;
   uint32_t* vals_c;
   uint32_t* rec_pair;      // pair of each record of the last partition (sorted keys)
+  int64_t pack_n;          // agents of the last partition (its runs cover them)
   uint32_t* rs_hist;       // [kRadix * sort tiles]
   tera::u64* scan_part;     // partials of the generic scan
   uint64_t scan_part_cap;
