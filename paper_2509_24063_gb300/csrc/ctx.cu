@@ -261,6 +261,8 @@ tera_status ensure_records(tera_ctx* ctx, uint64_t cap, cudaStream_t s) {
   if ((st = alloc_dev(ctx->keys_c, c)) != TERA_OK) return st;
   if ((st = alloc_dev(ctx->vals_b, c)) != TERA_OK) return st;
   if ((st = alloc_dev(ctx->vals_c, c)) != TERA_OK) return st;
+  if ((st = alloc_dev(ctx->agents_b, c)) != TERA_OK) return st;
+  if ((st = alloc_dev(ctx->agents_c, c)) != TERA_OK) return st;
   u64 tiles = (c + kSortTile - 1) / kSortTile;
   if ((st = alloc_dev(ctx->rs_hist, (u64)kRadix * tiles + 1)) != TERA_OK) return st;
   if ((st = alloc_dev(ctx->matched, c)) != TERA_OK) return st;
@@ -337,6 +339,8 @@ tera_status ensure_migrate(tera_ctx* ctx, uint64_t n, uint64_t leavers) {
     if ((st = alloc_dev(ctx->m_keys_c, c)) != TERA_OK) return st;
     if ((st = alloc_dev(ctx->m_vals_b, c)) != TERA_OK) return st;
     if ((st = alloc_dev(ctx->m_vals_c, c)) != TERA_OK) return st;
+    if ((st = alloc_dev(ctx->m_agents_b, c)) != TERA_OK) return st;
+    if ((st = alloc_dev(ctx->m_agents_c, c)) != TERA_OK) return st;
     u64 tiles = (c + kSortTile - 1) / kSortTile;
     if ((st = alloc_dev(ctx->m_hist, (u64)kRadix * tiles + 1)) != TERA_OK) return st;
     if ((st = ensure_scan_part(ctx, (u64)kRadix * tiles + 1)) != TERA_OK) return st;
@@ -469,6 +473,8 @@ tera_status tera_ctx_destroy(tera_ctx* c) {
   free_dev(c->keys_c);
   free_dev(c->vals_b);
   free_dev(c->vals_c);
+  free_dev(c->agents_b);
+  free_dev(c->agents_c);
   free_dev(c->rs_hist);
   free_dev(c->scan_part);
   free_dev(c->d_total);
@@ -501,6 +507,8 @@ tera_status tera_ctx_destroy(tera_ctx* c) {
   free_dev(c->m_keys_c);
   free_dev(c->m_vals_b);
   free_dev(c->m_vals_c);
+  free_dev(c->m_agents_b);
+  free_dev(c->m_agents_c);
   free_dev(c->m_hist);
   free_dev(c->cseg_enc);
   free_dev(c->cseg_dec);

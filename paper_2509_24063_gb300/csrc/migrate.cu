@@ -558,7 +558,8 @@ extern "C" tera_status tera_migrate_send(tera_ctx* ctx, const tera_soa* prev,
   }
   // the leaver count is read on the device from inbox[Q]; more than
   // lv_cap leavers (capacity error, latched above) sorts nothing
-  const SortBufs bufs{ctx->m_keys_b, ctx->m_keys_c, ctx->m_vals_b, ctx->m_vals_c, ctx->m_hist};
+  const SortBufs bufs{ctx->m_keys_b,   ctx->m_keys_c,   ctx->m_vals_b, ctx->m_vals_c,
+                      ctx->m_agents_b, ctx->m_agents_c, ctx->m_hist};
   const u32* sorted = ctx->m_key;
   if ((st = radix_sort_entries(ctx, bufs, ctx->m_key, ctx->m_agent, ctx->m_dest, ctx->m_sorted,
                                inbox + Q, lv_cap, Q, &sorted, s)) != TERA_OK)

@@ -169,26 +169,31 @@ __global__ void __launch_bounds__(kSortThreads)
 // warps places them; every entry goes to its tile-local sorted position
 // (digit start + rank) in shared memory.  The tile is then written out in
 // sorted order, so consecutive threads write consecutive addresses of a
-// digit's run.  The values are entry indices: vals_in == nullptr on the first
-// pass (entry i is at position i).  On the last pass (agent != nullptr) the
-// outputs are the record's agent (vals_out[pos] = agent[e]) and, when dest is
-// given, the entry's record index (dest[e] = pos).
+// digit's run.  Each entry carries its index (vals_in == nullptr on the first
+// pass: entry i is at position i) and its agent (agents_in, read in input
+// order: the entry list's agents on the first pass, the previous pass's
+// output after it).  Every pass but the last writes both; the last writes the
+// agent as the value (vals_out[pos] = agent) and, when dest is given, the
+// entry's record index (dest[e] = pos).
 constexpr int kSortSub = 4;  // sub-steps of 32 entries per warp and round
+constexpr size_t kSortSmem = 3 * sizeof(u32) * kSortTile;  // staged keys, entries, agents
 
 __global__ void __launch_bounds__(kSortThreads)
     rs_scatter_kernel(const u32* __restrict__ keys_in, const u32* __restrict__ vals_in,
-                      u32* __restrict__ keys_out, u32* __restrict__ vals_out,
-                      const u32* __restrict__ agent, u32* __restrict__ dest,
-                      const u64* __restrict__ total_ptr, u64 cap, u32 shift, u32 radix,
-                      const u32* __restrict__ hist_scan, u32 n_tiles) {
+                      const u32* __restrict__ agents_in, u32* __restrict__ keys_out,
+                      u32* __restrict__ vals_out, u32* __restrict__ agents_out,
+                      u32* __restrict__ dest, int last, const u64* __restrict__ total_ptr, u64 cap,
+                      u32 shift, u32 radix, const u32* __restrict__ hist_scan, u32 n_tiles) {
   constexpr int kWarps = kSortThreads / 32;
   constexpr int kRoundEntries = kSortThreads * kSortSub;
+  extern __shared__ __align__(16) u32 sort_stage[];
+  u32* skey = sort_stage;
+  u32* sval = sort_stage + kSortTile;
+  u32* sagt = sort_stage + 2 * kSortTile;
   __shared__ u32 base[kRadix];    // global start of each digit for this tile
   __shared__ u32 lstart[kRadix];  // tile-local start of each digit
   __shared__ u32 run[kRadix];     // entries of each digit placed in earlier rounds
   __shared__ u32 wcnt[kWarps][kRadix];
-  __shared__ u32 skey[kSortTile];
-  __shared__ u32 sval[kSortTile];
   __shared__ u32 sm[33];
   const u64 E = live_entries(total_ptr, cap);
   const u64 t0 = (u64)blockIdx.x * kSortTile;
@@ -212,7 +217,7 @@ __global__ void __launch_bounds__(kSortThreads)
   for (u32 r0 = 0; r0 < tile_n; r0 += kRoundEntries) {  // block-uniform
     for (u32 d = lane; d < radix; d += 32) wcnt[warp][d] = 0;
     __syncwarp();
-    u32 key[kSortSub], val[kSortSub], dig[kSortSub], rank[kSortSub];
+    u32 key[kSortSub], val[kSortSub], agt[kSortSub], dig[kSortSub], rank[kSortSub];
 #pragma unroll
     for (int q = 0; q < kSortSub; ++q) {
       const u32 li = r0 + (u32)warp * (32 * kSortSub) + (u32)q * 32 + (u32)lane;
@@ -220,6 +225,7 @@ __global__ void __launch_bounds__(kSortThreads)
       const u64 i = t0 + li;
       key[q] = live ? keys_in[i] : 0u;
       val[q] = live ? (vals_in ? vals_in[i] : (u32)i) : 0u;
+      agt[q] = live ? agents_in[i] : 0u;
       dig[q] = live ? ((key[q] >> shift) & (radix - 1)) : radix;  // sentinel for padding
       const u32 peers = __match_any_sync(0xFFFFFFFFu, dig[q]);
       rank[q] = (live ? wcnt[warp][dig[q]] : 0u) + __popc(peers & lt);
@@ -244,20 +250,22 @@ __global__ void __launch_bounds__(kSortThreads)
         const u32 lp = lstart[dig[q]] + wcnt[warp][dig[q]] + rank[q];
         skey[lp] = key[q];
         sval[lp] = val[q];
+        sagt[lp] = agt[q];
       }
     }
     __syncthreads();
   }
   for (u32 li = threadIdx.x; li < tile_n; li += blockDim.x) {
-    const u32 key = skey[li], v = sval[li];
+    const u32 key = skey[li], v = sval[li], a = sagt[li];
     const u32 d = (key >> shift) & (radix - 1);
     const u32 pos = base[d] + (li - lstart[d]);
     keys_out[pos] = key;
-    if (agent) {
-      vals_out[pos] = agent[v];
+    if (last) {
+      vals_out[pos] = a;
       if (dest) dest[v] = pos;
     } else {
       vals_out[pos] = v;
+      agents_out[pos] = a;
     }
   }
 }
@@ -292,10 +300,11 @@ namespace tera {
 
 // Stable LSD radix sort of entries by a u32 key (every key < key_limit),
 // ceil(bits / 8) digit passes.  The entry count is read on the device
-// (*total_ptr; nothing is sorted when it exceeds cap).  Pass k reads (kin,
-// vin) and writes the b buffers (k even) or the c buffers; the last pass
+// (*total_ptr; nothing is sorted when it exceeds cap).  Pass k reads (kin, vin,
+// ain) and writes the b buffers (k even) or the c buffers; the last pass
 // writes the sorted keys to the buffer it does not read, vals_final[pos] =
 // agent[e] for the entry e sorted to pos, and dest[e] = pos (dest may be null).
+// The agents travel with the entries (read in order on every pass).
 tera_status radix_sort_entries(tera_ctx* ctx, const SortBufs& b, const u32* keys_in,
                                const u32* agent, u32* dest, u32* vals_final, const u64* total_ptr,
                                u64 cap, u64 key_limit, const u32** sorted_keys, cudaStream_t s) {
@@ -307,13 +316,21 @@ tera_status radix_sort_entries(tera_ctx* ctx, const SortBufs& b, const u32* keys
   const u64 sort_tiles = cap == 0 ? 1 : (cap + kSortTile - 1) / kSortTile;
   const u32* kin = keys_in;
   const u32* vin = nullptr;
+  const u32* ain = agent;
   u32* kfinal = (passes & 1) ? b.keys_b : b.keys_c;
   tera_status st;
+  static bool smem_set = false;
+  if (!smem_set) {
+    cudaFuncSetAttribute(rs_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)kSortSmem);
+    smem_set = true;
+  }
   for (int pass = 0; pass < passes && cap > 0; ++pass) {
     const u32 shift = (u32)(pass * dbits);
     const bool last = pass + 1 == passes;
     u32* kout = last ? kfinal : ((pass & 1) ? b.keys_c : b.keys_b);
     u32* vout = last ? vals_final : ((pass & 1) ? b.vals_c : b.vals_b);
+    u32* aout = last ? nullptr : ((pass & 1) ? b.agents_c : b.agents_b);
     prof_begin(ctx, s);
     rs_hist_kernel<<<(unsigned)sort_tiles, kSortThreads, 0, s>>>(kin, total_ptr, cap, shift, radix,
                                                                  b.hist, (u32)sort_tiles);
@@ -321,12 +338,13 @@ tera_status radix_sort_entries(tera_ctx* ctx, const SortBufs& b, const u32* keys
     if ((st = scan_u32(ctx, b.hist, nullptr, b.hist, (u64)radix * sort_tiles, s)) != TERA_OK)
       return st;
     prof_begin(ctx, s);
-    rs_scatter_kernel<<<(unsigned)sort_tiles, kSortThreads, 0, s>>>(
-        kin, vin, kout, vout, last ? agent : nullptr, last ? dest : nullptr, total_ptr, cap, shift,
-        radix, b.hist, (u32)sort_tiles);
+    rs_scatter_kernel<<<(unsigned)sort_tiles, kSortThreads, kSortSmem, s>>>(
+        kin, vin, ain, kout, vout, aout, last ? dest : nullptr, last ? 1 : 0, total_ptr, cap,
+        shift, radix, b.hist, (u32)sort_tiles);
     if ((st = check_launch(ctx, "rs_scatter_kernel", s)) != TERA_OK) return st;
     kin = kout;
     vin = vout;
+    ain = aout;
   }
   *sorted_keys = kin;
   return TERA_OK;
@@ -377,7 +395,8 @@ extern "C" tera_status tera_partition(tera_ctx* ctx, const tera_soa* soa, tera_p
         ctx->d_status);
     if ((st = check_launch(ctx, "emit_kernel", s)) != TERA_OK) return st;
   }
-  const SortBufs bufs{ctx->keys_b, ctx->keys_c, ctx->vals_b, ctx->vals_c, ctx->rs_hist};
+  const SortBufs bufs{ctx->keys_b,   ctx->keys_c,   ctx->vals_b, ctx->vals_c,
+                      ctx->agents_b, ctx->agents_c, ctx->rs_hist};
   const u32* sorted = nullptr;
   if ((st = radix_sort_entries(ctx, bufs, ctx->keys_a, ctx->ent_agent, ctx->ent_dest, out->pair_idx,
                                total_ptr, cap, P, &sorted, s)) != TERA_OK)

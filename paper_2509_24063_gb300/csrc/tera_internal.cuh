@@ -35,6 +35,8 @@ struct tera_ctx {
   uint32_t* keys_c;
   uint32_t* vals_b;
   uint32_t* vals_c;
+  uint32_t* agents_b;      // agents carried through the sort passes
+  uint32_t* agents_c;
   uint32_t* rec_pair;      // pair of each record of the last partition (sorted keys)
   int64_t pack_n;          // agents of the last partition (its runs cover them)
   uint32_t* rs_hist;       // [kRadix * sort tiles]
@@ -92,6 +94,8 @@ struct tera_ctx {
   uint32_t* m_keys_c;
   uint32_t* m_vals_b;
   uint32_t* m_vals_c;
+  uint32_t* m_agents_b;
+  uint32_t* m_agents_c;
   uint32_t* m_hist;
 };
 
@@ -121,6 +125,8 @@ struct SortBufs {
   u32* keys_c;
   u32* vals_b;
   u32* vals_c;
+  u32* agents_b;  // agents carried with the entries between passes
+  u32* agents_c;
   u32* hist;  // [kRadix * sort tiles + 1]
 };
 tera_status radix_sort_entries(tera_ctx* ctx, const SortBufs& b, const u32* keys_in,
