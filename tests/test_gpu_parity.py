@@ -237,11 +237,13 @@ def test_edges_and_thresholds(tera):
     ((-1.0e9, 0.0, 5.0), (1.0e9, 1.0, 35.0), (256, 3, 1), 0.1),
     ((1.0e-3, -7.0, 0.0), (1.0e-3 + 97.0 * 0.37, 89.0, 2.0), (97, 89, 2), 0.05),
     ((3.0e15, -1.0, -1.0), (3.0e15 + 256.0, 1.0, 1.0), (32, 2, 2), 0.5),
+    ((-500.0, -3.0e-3, -7.5), (500.0, 3.0e-3, 2.5), (10, 6, 5), 1.0e-4),
 ])
 def test_classification_many_boxes_wide_domains(tera, lo, hi, grid, w):
     # the box index starts from a float32 estimate and is fixed by exact key
     # comparisons: every owner and mask must equal the oracle's, including
-    # points on edges, on aura thresholds and one ulp away
+    # points on edges, on aura thresholds, one ulp away, and a little beyond
+    # the thresholds (a relative 2^-17 of the largest magnitude)
     import math
     rng = np.random.default_rng(sum(grid))
     n = 50000
@@ -256,6 +258,11 @@ def test_classification_many_boxes_wide_domains(tera, lo, hi, grid, w):
         c = np.where((pick >= 0.3) & (pick < 0.4), cand - w, c)
         c = np.where((pick >= 0.4) & (pick < 0.5), np.nextafter(c, np.inf), c)
         c = np.where((pick >= 0.5) & (pick < 0.6), np.nextafter(c, -np.inf), c)
+        # just beyond the aura thresholds, either side of a box
+        margin = math.ldexp(max(abs(lo[a]), abs(hi[a])), -17)
+        u = rng.uniform(0.0, 2.0, n) * margin
+        c = np.where((pick >= 0.6) & (pick < 0.7), cand + w + u, c)
+        c = np.where((pick >= 0.7) & (pick < 0.8), cand - w - u, c)
         pts[:, a] = np.clip(c, lo[a], math.nextafter(hi[a], lo[a]))
     ctx = tera.Context(lo, hi, grid, w)
     part = tera.PartitionBuffers.allocate(n, ctx.n_pairs, 7 * n, torch.device("cuda"))
