@@ -82,25 +82,22 @@ __device__ __forceinline__ U64x2 tile_scan(u32 bytes, u32 recs, U64x2* sm, U64x2
   return U64x2{ex & 0xFFFFFFFFull, ex >> 32};
 }
 
-// Exclusive block scan of packed counts (low / high 32 bits) with two
-// barriers: the caller alternates `buf` (33 words) between consecutive scans,
-// so it is never written while another warp may still read it.  After the
-// last scan of a run, one __syncthreads() must precede other uses of buf.
+// Exclusive block scan of packed counts (low / high 32 bits) with one
+// barrier: each warp publishes its total, and after the barrier every warp
+// scans the warps' totals itself.  The caller alternates `buf` (33 words)
+// between consecutive scans: a buffer is written again only after the next
+// scan's barrier, which every warp passes after its reads of this one.  After
+// the last scan of a run, one __syncthreads() must precede other uses of buf.
 __device__ __forceinline__ u64 scan_packed(u64 v, u64* buf, u64* total) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nwarps = (blockDim.x + 31) >> 5;
   const u64 incl = warp_incl_scan<u64>(v);
   if (lane == 31) buf[warp] = incl;
   __syncthreads();
-  if (warp == 0) {
-    const u64 x = lane < nwarps ? buf[lane] : 0ull;
-    const u64 xi = warp_incl_scan<u64>(x);
-    if (lane < nwarps) buf[lane] = xi - x;
-    if (lane == nwarps - 1) buf[32] = xi;
-  }
-  __syncthreads();
-  *total = buf[32];
-  return buf[warp] + incl - v;
+  const u64 x = lane < nwarps ? buf[lane] : 0ull;
+  const u64 xi = warp_incl_scan<u64>(x);
+  *total = __shfl_sync(0xFFFFFFFFu, xi, nwarps - 1);
+  return __shfl_sync(0xFFFFFFFFu, xi - x, warp) + incl - v;
 }
 
 // Each warp stages its own contiguous byte range in a private region (32
@@ -828,6 +825,18 @@ __device__ __forceinline__ void bat_new_list(const EncArgs& A, u32 p, u64 r, u64
 
 // ---------------- decode phase ----------------
 
+// The L (0..8) bytes at byte offset o of an 8-byte-aligned stage, as a
+// little-endian word: two aligned 8-byte loads and a funnel shift (the stage
+// is followed by at least 16 bytes of shared memory, so the second load stays
+// inside the allocation; bytes past the staged data are masked off).
+__device__ __forceinline__ u64 stage_bytes_at(const uint8_t* st, u32 o, u32 L) {
+  const u64* w = reinterpret_cast<const u64*>(st + (o & ~7u));
+  const u32 sh = (o & 7u) * 8u;
+  const u64 lo = w[0], hi = w[1];
+  const u64 x = sh ? (lo >> sh) | (hi << (64u - sh)) : lo;
+  return L >= 8u ? x : (x & ((1ull << (8u * L)) - 1ull));
+}
+
 struct DecShared {
   u64 ns, nn, pay, mode;
   int ok;
@@ -883,10 +892,8 @@ __device__ __forceinline__ void bat_dec_tile(const DecArgs& A, const BatchArgs& 
 #pragma unroll
     for (int w = 0; w < 8; ++w) {
       const u32 L = (code >> (4 * w)) & 0xFu;
-      u64 x = 0;
-      for (u32 q = 0; q < L; ++q) x |= (u64)wst[o + q] << (8 * q);
+      rec.w[w] = stage_bytes_at(wst, o, L);
       o += L;
-      rec.w[w] = x;
     }
     const u64 pos = pre.b + ex.b;
     if (e < ns) {
@@ -1307,10 +1314,12 @@ inline void persistent_smem(u32 T, bool PR, int ctas_per_sm, u32 want_records, s
   u32 rec = 0;
   if (!PR) {
     for (u32 c = 32; c <= 8192; c <<= 1)
-      if (region_bytes(T, c) + c / 8 <= cap && (want_records == 0 || c <= want_records)) rec = c;
+      if (region_bytes(T, c) + c / 8 + 16 <= cap && (want_records == 0 || c <= want_records))
+        rec = c;
   }
   *records = rec;
-  *bytes = region_bytes(T, rec) + weights + rec / 8;
+  // + 16 bytes: the decode's 8-byte reads may pass the end of the stage
+  *bytes = region_bytes(T, rec) + weights + rec / 8 + 16;
 }
 
 template <int T, bool PR>
