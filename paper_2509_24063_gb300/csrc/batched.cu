@@ -105,6 +105,26 @@ __device__ __forceinline__ u64 scan_packed(u64 v, u64* buf, u64* total) {
 // inside and byte stores on the edges it shares with the neighbouring warps.
 constexpr u32 kWarpStage = 32 * kRecBytes + 16;
 
+// The L significant bytes of v (its higher bytes are zero) at byte offset o of
+// a zeroed, 4-byte-aligned stage: ORed into the at most three 32-bit words
+// they touch, so neighbouring lanes' bytes in a shared word are kept.
+__device__ __forceinline__ void stage_or(uint8_t* st, u32 o, u64 v, u32 L) {
+  if (L == 0) return;
+  u32* w = reinterpret_cast<u32*>(st + (o & ~3u));
+  const u32 sh = (o & 3u) * 8u;
+  const u64 lo = v << sh;
+  const u32 nb = (o & 3u) + L;  // bytes from the first word's start, at most 11
+  atomicOr(&w[0], (u32)lo);
+  if (nb > 4) atomicOr(&w[1], (u32)(lo >> 32));
+  if (nb > 8) atomicOr(&w[2], (u32)(v >> (64u - sh)));
+}
+
+// Zero the first n bytes of a 16-byte-aligned warp stage (rounded up to 16).
+__device__ __forceinline__ void warp_zero(uint8_t* wst, u32 n) {
+  for (u32 c = threadIdx.x & 31; c < ((n + 15u) >> 4); c += 32)
+    *reinterpret_cast<uint4*>(wst + (c << 4)) = make_uint4(0u, 0u, 0u, 0u);
+}
+
 __device__ __forceinline__ void warp_flush(const uint8_t* wst, uint8_t* gW, u32 n) {
   const u32 s0 = (u32)((uintptr_t)gW & 15u);
   uint8_t* g16 = gW - s0;
@@ -613,10 +633,17 @@ __device__ __forceinline__ void bat_slot(const EncArgs& A, const BatchArgs& B, u
   const u32 wend = __shfl_sync(0xFFFFFFFFu, (u32)ex.a + vb, 31);
   uint8_t* gW = A.wire + A.wire_off[p] + kHdrBytes + 4 * (r + n_new) + pre.a + wstart;
   uint8_t* wst = stage + (threadIdx.x >> 5) * kWarpStage;
+  const u32 s0w = (u32)((uintptr_t)gW & 15u);
+  warp_zero(wst, s0w + (wend - wstart));
+  __syncwarp();
   if (vn) {
-    u32 o = (u32)((uintptr_t)gW & 15u) + ((u32)ex.a - wstart);
+    u32 o = s0w + ((u32)ex.a - wstart);
 #pragma unroll
-    for (int w = 0; w < 8; ++w) stage_word(wst, o, d.w[w], sig_bytes(d.w[w]));
+    for (int w = 0; w < 8; ++w) {
+      const u32 L = sig_bytes(d.w[w]);
+      stage_or(wst, o, d.w[w], L);
+      o += L;
+    }
     const u64 pos = pre.b + ex.b;
     store_rec(A.ref_next + (A.pair_off[p] + p + 1 + pos) * kRecBytes, cur);
     if constexpr (PR) {
