@@ -122,17 +122,32 @@ __global__ void __launch_bounds__(kClassifyThreads)
     }
     const u32 c = __popc(m[0]) + __popc(m[1]);
     const u32 inc = warp_incl_scan<u32>(c);
-    u64 pos = run_base[first / kRunAgents] + (inc - c);
+    const u32 total = __shfl_sync(0xFFFFFFFFu, inc, 31);
+    const u64 base = run_base[first / kRunAgents];
+    // the run's entries written by the whole warp, lane i taking entry i of
+    // each 32: its source lane is the first whose inclusive count exceeds i
+    for (u32 r0 = 0; r0 < total; r0 += 32) {  // warp-uniform
+      const u32 idx = r0 + (u32)lane;
+      u32 src = 0;
 #pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      u32 mm = m[q];
-      while (mm) {
-        int b = __ffs(mm) - 1;
-        mm &= mm - 1;
-        keys[pos] = (u32)o[q] * 27u + (u32)b;
-        vals[pos] = (u32)(a0 + q);  // the entry's agent
-        ++pos;
-      }
+      for (u32 b = 16; b >= 1; b >>= 1)
+        if (__shfl_sync(0xFFFFFFFFu, inc, (int)(src + b - 1)) <= idx) src += b;
+      const u32 s_inc = __shfl_sync(0xFFFFFFFFu, inc, (int)src);
+      const u32 s_c = __shfl_sync(0xFFFFFFFFu, c, (int)src);
+      const u32 s_m0 = __shfl_sync(0xFFFFFFFFu, m[0], (int)src);
+      const u32 s_m1 = __shfl_sync(0xFFFFFFFFu, m[1], (int)src);
+      const int s_o0 = __shfl_sync(0xFFFFFFFFu, o[0], (int)src);
+      const int s_o1 = __shfl_sync(0xFFFFFFFFu, o[1], (int)src);
+      if (idx >= total) continue;
+      u32 k = idx - (s_inc - s_c);  // entry k of the source lane's two agents
+      const u32 n0 = __popc(s_m0);
+      const bool second = k >= n0;
+      u32 mm = second ? s_m1 : s_m0;
+      k = second ? k - n0 : k;
+      for (u32 t = 0; t < k; ++t) mm &= mm - 1;
+      const u32 b = (u32)(__ffs(mm) - 1);
+      keys[base + idx] = (u32)(second ? s_o1 : s_o0) * 27u + b;
+      vals[base + idx] = (u32)(first + 2u * src + (second ? 1u : 0u));  // the entry's agent
     }
   }
 }
