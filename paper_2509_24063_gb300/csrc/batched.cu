@@ -158,14 +158,39 @@ __device__ __forceinline__ u64 team_tiles(u64 r, u64 m, u64 rr, u32 T) {
 
 // ---------------- setup: per-pair facts, layouts, capacity checks ----------------
 
-// One block; thread t owns a contiguous run of pairs (one pass of loads, one scan).
+// Per-pair facts of the setup (raw or XOR mode, slots, records, slab, team).
+struct PairFacts {
+  u64 r, r_full, m, rr, slab;
+  u32 g;
+  bool raw;
+};
+
+__device__ __forceinline__ PairFacts pair_facts(const EncArgs& E, const DecArgs& D, u64 p, int mode,
+                                                u64 thresh, u32 gmax, int pred) {
+  PairFacts f;
+  f.m = E.pair_off[p + 1] - E.pair_off[p];
+  f.r_full = E.ref_off ? E.ref_off[p + 1] - E.ref_off[p] : 0;
+  f.raw = mode == TERA_MODE_RAW || E.reset[p];
+  f.r = (f.raw || E.ref_off == nullptr) ? 0 : f.r_full;
+  f.rr = D.ref_off ? D.ref_off[p + 1] - D.ref_off[p] : 0;
+  f.slab = round16((u64)kHdrBytes + 4 * (f.r_full + f.m) + (u64)kRecBytes * f.m);
+  f.g = team_size(f.r + f.m + f.rr, thresh, gmax, pred);
+  return f;
+}
+
+// One block, pairs in chunks of blockDim.x (pair c * blockDim.x + t to thread
+// t, coalesced): a first pass writes the per-pair facts and sums the block's
+// totals; a second pass scans each chunk (carried from chunk to chunk) into
+// the wire slab offsets, the work list (team items first, so the large pairs
+// start early, then one item per other pair, each in pair order) and the
+// teams' first tile totals.
 __global__ void __launch_bounds__(1024)
     bat_setup_kernel(EncArgs E, DecArgs D, BatchArgs B, u64 P, int mode,
                      u64* __restrict__ wire_off, u64 wire_cap, u64 rec_cap, u64 recv_cap,
                      u32* epoch, u32 T, u32 blocks, u32 gmax, u64 min_team, int pred,
                      u64* __restrict__ items, u64 items_cap, u64* __restrict__ tbase,
                      u64 tsum_cap, u64* __restrict__ n_items) {
-  __shared__ u64 sm[33];
+  __shared__ U64x2 sm2[33];
   __shared__ u64 s_thresh;
   if (threadIdx.x == 0) {
     const u32 ep = *epoch + 1u;
@@ -178,55 +203,45 @@ __global__ void __launch_bounds__(1024)
   }
   __syncthreads();
   const u64 thresh = s_thresh;
-  const u64 per = (P + blockDim.x - 1) / blockDim.x;
-  const u64 q0 = (u64)threadIdx.x * per;
-  const u64 q1 = q0 + per < P ? q0 + per : P;
-  u64 sw = 0, nbig = 0, nsmall = 0, ntiles = 0;
-  for (u64 p = q0; p < q1; ++p) {
-    const u64 m = E.pair_off[p + 1] - E.pair_off[p];
-    const u64 r_full = E.ref_off ? E.ref_off[p + 1] - E.ref_off[p] : 0;
-    const bool raw = mode == TERA_MODE_RAW || E.reset[p];
-    const u64 r = (raw || E.ref_off == nullptr) ? 0 : r_full;
+  U64x2 acc_a{0, 0}, acc_b{0, 0};  // (slab bytes, team tiles), (team items, other items)
+  for (u64 c = 0; c < P; c += blockDim.x) {
+    const u64 p = c + threadIdx.x;
+    if (p >= P) continue;
+    const PairFacts f = pair_facts(E, D, p, mode, thresh, gmax, pred);
     u64* pi = E.info + p * 8;
-    pi[PI_R] = r;
-    pi[PI_M] = m;
-    pi[PI_MODE] = raw ? TERA_MODE_RAW : TERA_MODE_XOR;
-    const u64 slab = round16((u64)kHdrBytes + 4 * (r_full + m) + (u64)kRecBytes * m);
-    wire_off[p] = slab;
-    sw += slab;
+    pi[PI_R] = f.r;
+    pi[PI_M] = f.m;
+    pi[PI_MODE] = f.raw ? TERA_MODE_RAW : TERA_MODE_XOR;
     D.recv_off[p] = E.pair_off[p];  // receive buffers sized by the record counts
-    const u64 rr = D.ref_off ? D.ref_off[p + 1] - D.ref_off[p] : 0;
-    const u32 g = team_size(r + m + rr, thresh, gmax, pred);
-    if (g > 1) {
-      nbig += g;
-      ntiles += team_tiles(r, m, rr, T);
-    } else {
-      ++nsmall;
-    }
+    acc_a += U64x2{f.slab, f.g > 1 ? team_tiles(f.r, f.m, f.rr, T) : 0};
+    acc_b += U64x2{f.g > 1 ? f.g : 0u, f.g > 1 ? 0u : 1u};
   }
-  u64 tw, tbig, tsmall, ttiles;
-  u64 run = block_excl_scan<u64>(sw, sm, &tw);
-  u64 pbig = block_excl_scan<u64>(nbig, sm, &tbig);
-  u64 psmall = block_excl_scan<u64>(nsmall, sm, &tsmall);
-  u64 ptile = block_excl_scan<u64>(ntiles, sm, &ttiles);
+  U64x2 tot_a, tot_b;
+  block_excl_scan2(acc_a, sm2, &tot_a);
+  block_excl_scan2(acc_b, sm2, &tot_b);
+  const u64 tw = tot_a.a, ttiles = tot_a.b, tbig = tot_b.a, tsmall = tot_b.b;
   const bool fits = tbig + tsmall <= items_cap && ttiles <= tsum_cap;
-  psmall += tbig;  // team items first: the large pairs start early
-  for (u64 p = q0; p < q1; ++p) {
-    const u64 slab = wire_off[p];
-    wire_off[p] = run;
-    run += slab;
+  U64x2 carry_a{0, 0}, carry_b{0, tbig};  // team items first
+  for (u64 c = 0; c < P; c += blockDim.x) {  // block-uniform
+    const u64 p = c + threadIdx.x;
+    PairFacts f{};
+    if (p < P) f = pair_facts(E, D, p, mode, thresh, gmax, pred);
+    const bool team = p < P && f.g > 1;
+    const U64x2 va{p < P ? f.slab : 0, team ? team_tiles(f.r, f.m, f.rr, T) : 0};
+    const U64x2 vb{team ? f.g : 0u, (p < P && !team) ? 1u : 0u};
+    U64x2 ta, tb;
+    const U64x2 ea = carry_a + block_excl_scan2(va, sm2, &ta);
+    const U64x2 eb = carry_b + block_excl_scan2(vb, sm2, &tb);
+    carry_a += ta;
+    carry_b += tb;
+    if (p >= P) continue;
+    wire_off[p] = ea.a;
     if (!fits) continue;
-    const u64 m = E.pair_off[p + 1] - E.pair_off[p];
-    const u64 r = (mode == TERA_MODE_RAW || E.reset[p] || E.ref_off == nullptr)
-                      ? 0 : E.ref_off[p + 1] - E.ref_off[p];
-    const u64 rr = D.ref_off ? D.ref_off[p + 1] - D.ref_off[p] : 0;
-    const u32 g = team_size(r + m + rr, thresh, gmax, pred);
-    if (g > 1) {
-      for (u32 i = 0; i < g; ++i) items[pbig++] = make_item(p, i, g);
-      tbase[p] = ptile;
-      ptile += team_tiles(r, m, rr, T);
+    if (team) {
+      for (u32 i = 0; i < f.g; ++i) items[eb.a + i] = make_item(p, i, f.g);
+      tbase[p] = ea.b;
     } else {
-      items[psmall++] = make_item(p, 0, 1);
+      items[eb.b] = make_item(p, 0, 1);
     }
   }
   if (threadIdx.x == 0) {
