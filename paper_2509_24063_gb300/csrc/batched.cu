@@ -105,6 +105,46 @@ __device__ __forceinline__ u64 scan_packed(u64 v, u64* buf, u64* total) {
 // inside and byte stores on the edges it shares with the neighbouring warps.
 constexpr u32 kWarpStage = 32 * kRecBytes + 16;
 
+// Per-thread record stash in shared memory: 16-byte part k of thread i's
+// record at stash[k T + i], so each part of a warp's records is one
+// contiguous 512-byte row.  It holds the record a slot or decode tile needs
+// after its block scan, which would otherwise stay in registers across the
+// barrier (and spill).  Only the owning thread reads its entries, so no
+// barrier guards them.
+template <int T>
+__device__ __forceinline__ void stash_put(ulonglong2* st, const Rec& r) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+    st[k * T + threadIdx.x] = make_ulonglong2(r.w[2 * k], r.w[2 * k + 1]);
+}
+
+template <int T>
+__device__ __forceinline__ Rec stash_get(const ulonglong2* st) {
+  Rec r;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const ulonglong2 v = st[k * T + threadIdx.x];
+    r.w[2 * k] = v.x;
+    r.w[2 * k + 1] = v.y;
+  }
+  return r;
+}
+
+// The record at g (16-byte aligned) into the stash by asynchronous
+// copies; stash_wait() before reading it.
+template <int T>
+__device__ __forceinline__ void stash_async(ulonglong2* st, const uint8_t* g) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const u32 dst = (u32)__cvta_generic_to_shared(st + k * T + threadIdx.x);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" : : "r"(dst), "l"(g + 16 * k)
+                 : "memory");
+  }
+  asm volatile("cp.async.commit_group;" : : : "memory");
+}
+
+__device__ __forceinline__ void stash_wait() { asm volatile("cp.async.wait_all;" : : : "memory"); }
+
 // The L significant bytes of v (its higher bytes are zero) at byte offset o of
 // a zeroed, 4-byte-aligned stage: ORed into the at most three 32-bit words
 // they touch, so neighbouring lanes' bytes in a shared word are kept.
@@ -125,17 +165,38 @@ __device__ __forceinline__ void warp_zero(uint8_t* wst, u32 n) {
     *reinterpret_cast<uint4*>(wst + (c << 4)) = make_uint4(0u, 0u, 0u, 0u);
 }
 
+// Store the n bytes at the start of a warp stage to gW, whatever its
+// alignment: each whole 16-byte chunk of the destination is assembled from
+// five 32-bit stage words by funnel shifts and stored at once; the edge
+// chunks, shared with the neighbouring warps' bytes, are stored byte by byte.
+// The stage has at least 16 bytes beyond n, so the fifth word stays inside it.
 __device__ __forceinline__ void warp_flush(const uint8_t* wst, uint8_t* gW, u32 n) {
   const u32 s0 = (u32)((uintptr_t)gW & 15u);
   uint8_t* g16 = gW - s0;
   const u32 end = s0 + n;
   const u32 nchunks = (end + 15u) >> 4;
+  const u32* w32 = reinterpret_cast<const u32*>(wst);
   for (u32 c = threadIdx.x & 31; c < nchunks; c += 32) {
     const u32 lo = c << 4, hi = lo + 16u;
     if (lo >= s0 && hi <= end) {
-      *reinterpret_cast<uint4*>(g16 + lo) = *reinterpret_cast<const uint4*>(wst + lo);
+      const u32 o = lo - s0;  // stage offset of the chunk's first byte
+      const u32 i = o >> 2, sh = (o & 3u) * 8u;
+      u32 v[4];
+      if (sh == 0) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) v[k] = w32[i + k];
+      } else {
+        u32 a = w32[i];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const u32 b = w32[i + k + 1];
+          v[k] = __funnelshift_r(a, b, sh);
+          a = b;
+        }
+      }
+      *reinterpret_cast<uint4*>(g16 + lo) = make_uint4(v[0], v[1], v[2], v[3]);
     } else {
-      for (u32 x = (lo > s0 ? lo : s0); x < (hi < end ? hi : end); ++x) g16[x] = wst[x];
+      for (u32 x = (lo > s0 ? lo : s0); x < (hi < end ? hi : end); ++x) g16[x] = wst[x - s0];
     }
   }
 }
@@ -595,15 +656,39 @@ __device__ __forceinline__ u64 pair_mode(const EncArgs& A, const BatchArgs& B, u
   return mode;
 }
 
-// One tile of slots; g = this thread's slot source (read one tile ahead).
-// Registers: the difference d is formed in place of the reference record, and
-// the byte counts are recomputed from d when staging.
-template <int T, bool PR>
-__device__ __forceinline__ void bat_slot(const EncArgs& A, const BatchArgs& B, u32 p, u64 tile,
-                                         u32 g, u64* buf, uint8_t* stage, U64x2& run) {
+// Offsets of pair p that every tile of its encode steps uses, read once per
+// pair: read inside each tile they put dependent global loads in front of
+// the tile's record loads and stores.
+struct SlotPair {
+  u64 r, m;      // reference slots, message records
+  u64 ro, g_lo;  // first slot in the reference, first record in the arena
+  u64 n_new;     // records no slot takes (m - matched, known after the match)
+  uint8_t* w8;   // the pair's message
+};
+
+__device__ __forceinline__ SlotPair slot_pair(const EncArgs& A, const BatchArgs& B, u32 p) {
   const u64* pi = A.info + (u64)p * 8;
-  const u64 r = pi[PI_R], m = pi[PI_M];
-  const u64 ro = A.ref_off[p];
+  SlotPair q;
+  q.r = pi[PI_R];
+  q.m = pi[PI_M];
+  q.ro = A.ref_off ? A.ref_off[p] : 0;
+  q.g_lo = A.pair_off[p];
+  q.n_new = q.m - __ldcg(B.ptot + (u64)p * PT_COUNT + PT_MATCHED);
+  q.w8 = A.wire + A.wire_off[p];
+  return q;
+}
+
+// One tile of slots; g = this thread's slot source (read one tile ahead).
+// The difference d is formed in place of the reference record and its bytes
+// are staged before the block scan, at offsets within the warp's range (a
+// warp scan); the scan then only places the warp's range in the message.  So
+// across the barrier a thread holds no record but the message record, and
+// that one waits in the stash.
+template <int T, bool PR>
+__device__ __forceinline__ void bat_slot(const EncArgs& A, const BatchArgs& B, u32 p,
+                                         const SlotPair& q, u64 tile, u32 g, u64* buf,
+                                         uint8_t* stage, ulonglong2* stash, U64x2& run) {
+  const u64 r = q.r, ro = q.ro;
   const u64 j = tile * T + threadIdx.x;
   Rec cur, d;
   u32 vb = 0, vn = 0;
@@ -634,37 +719,40 @@ __device__ __forceinline__ void bat_slot(const EncArgs& A, const BatchArgs& B, u
       }
       vb = b;
       vn = 1;
+      stash_put<T>(stash, cur);  // the new reference's record, stored after the scan
     }
-    reinterpret_cast<u32*>(A.wire + A.wire_off[p] + kHdrBytes)[j] = code;
+    reinterpret_cast<u32*>(q.w8 + kHdrBytes)[j] = code;
   }
-  u64 tot64;
-  const u64 ex64 = scan_packed((u64)vb | ((u64)vn << 32), buf, &tot64);
-  const U64x2 ex{ex64 & 0xFFFFFFFFull, ex64 >> 32}, tot{tot64 & 0xFFFFFFFFull, tot64 >> 32};
-  const U64x2 pre = run;
-  run = pre + tot;
-  const u64 n_new = m - __ldcg(B.ptot + (u64)p * PT_COUNT + PT_MATCHED);
-  // this warp's bytes: [wstart, wend) of the tile's payload
-  const u32 wstart = __shfl_sync(0xFFFFFFFFu, (u32)ex.a, 0);
-  const u32 wend = __shfl_sync(0xFFFFFFFFu, (u32)ex.a + vb, 31);
-  uint8_t* gW = A.wire + A.wire_off[p] + kHdrBytes + 4 * (r + n_new) + pre.a + wstart;
+  // this warp's payload bytes, staged from offset 0 of its stage
+  const u32 wincl = warp_incl_scan<u32>(vb);
+  const u32 wbytes = __shfl_sync(0xFFFFFFFFu, wincl, 31);
   uint8_t* wst = stage + (threadIdx.x >> 5) * kWarpStage;
-  const u32 s0w = (u32)((uintptr_t)gW & 15u);
-  warp_zero(wst, s0w + (wend - wstart));
+  warp_zero(wst, wbytes);
   __syncwarp();
   if (vn) {
-    u32 o = s0w + ((u32)ex.a - wstart);
+    u32 o = wincl - vb;
 #pragma unroll
     for (int w = 0; w < 8; ++w) {
       const u32 L = sig_bytes(d.w[w]);
       stage_or(wst, o, d.w[w], L);
       o += L;
     }
+  }
+  u64 tot64;
+  const u64 ex64 = scan_packed((u64)vb | ((u64)vn << 32), buf, &tot64);
+  const U64x2 ex{ex64 & 0xFFFFFFFFull, ex64 >> 32}, tot{tot64 & 0xFFFFFFFFull, tot64 >> 32};
+  const U64x2 pre = run;
+  run = pre + tot;
+  // this warp's bytes start at wstart of the tile's payload
+  const u32 wstart = __shfl_sync(0xFFFFFFFFu, (u32)ex.a, 0);
+  uint8_t* gW = q.w8 + kHdrBytes + 4 * (r + q.n_new) + pre.a + wstart;
+  if (vn) {
     const u64 pos = pre.b + ex.b;
-    store_rec(A.ref_next + (A.pair_off[p] + p + 1 + pos) * kRecBytes, cur);
+    store_rec(A.ref_next + (q.g_lo + p + 1 + pos) * kRecBytes, stash_get<T>(stash));
     if constexpr (PR) {
       if (A.pr.hist_next) {
         const Rec R = load_rec(A.ref + (ro + p + 1 + j) * kRecBytes);
-        uint8_t* hn = A.pr.hist_next + kHistBytes * (A.pair_off[p] + pos);
+        uint8_t* hn = A.pr.hist_next + kHistBytes * (q.g_lo + pos);
         if (A.pr.hist) {
           const Hist H = load_hist(A.pr.hist + kHistBytes * (ro + j));
           store_hist_next(hn, &R, &H);
@@ -675,7 +763,7 @@ __device__ __forceinline__ void bat_slot(const EncArgs& A, const BatchArgs& B, u
     }
   }
   __syncwarp();
-  warp_flush(wst, gW, wend - wstart);
+  warp_flush(wst, gW, wbytes);
   __syncwarp();
 }
 
@@ -817,52 +905,62 @@ __device__ __forceinline__ u32 smem_new_list(const SmemTable& tb, u64 m, unsigne
 }
 
 // One tile of T new records (list entries tile*T + thread): codes, payload
-// and new-reference records; the running prefix is carried in `run`.
+// and new-reference records; the running prefix is carried in `run`.  Every
+// list entry is a new record and the list is in message order, so entry i's
+// rank among the new records is i: its code and new-reference record are
+// written before the block scan, and its payload is staged within the warp's
+// range as in the slot step, so no record is held across the barrier.
 template <int T, bool PR>
-__device__ __forceinline__ void bat_new_list(const EncArgs& A, u32 p, u64 r, u64 m, u64 matched,
-                                             U64x2 slot_tot, const unsigned short* list, u32 n_list,
-                                             u64 tile, U64x2* sm, uint8_t* stage, u32 stage_cap,
-                                             U64x2& run) {
-  const u64 n_new = m - matched;
-  const u64 g_lo = A.pair_off[p];
+__device__ __forceinline__ void bat_new_list(const EncArgs& A, u32 p, const SlotPair& q,
+                                             u64 matched, U64x2 slot_tot,
+                                             const unsigned short* list, u32 n_list, u64 tile,
+                                             u64* buf, uint8_t* stage, U64x2& run) {
+  const u64 r = q.r, n_new = q.m - matched;
+  const u64 g_lo = q.g_lo;
   const u64 i = tile * T + threadIdx.x;
+  const bool live = i < n_list;
+  u32 vb = 0;
   Rec M;
-  u32 vb = 0, vn = 0;
-  if (i < n_list) {
+  if (live) {
     M = load_rec(A.rec + (g_lo + list[i] + p + 1) * kRecBytes);
-#pragma unroll
-    for (int w = 0; w < 8; ++w) vb += sig_bytes(M.w[w]);
-    vn = 1;
-  }
-  U64x2 tot;
-  const U64x2 ex = tile_scan(vb, vn, sm, &tot);
-  const U64x2 pre = run;
-  run = pre + tot;
-  uint8_t* w8 = A.wire + A.wire_off[p];
-  uint8_t* gA = w8 + kHdrBytes + 4 * (r + n_new) + slot_tot.a + pre.a;
-  const u32 s0 = (u32)((uintptr_t)gA & 15u);
-  const bool staged = s0 + tot.a <= stage_cap;  // block-uniform
-  if (vn) {
-    u32 o = staged ? s0 + (u32)ex.a : 0u;
-    uint8_t* dst = staged ? stage : gA + ex.a;
     u32 code = 0;
 #pragma unroll
     for (int w = 0; w < 8; ++w) {
       const u32 L = sig_bytes(M.w[w]);
+      vb += L;
       code |= L << (4 * w);
-      put_word(dst, o, M.w[w], L);
     }
-    const u64 rank = pre.b + ex.b;
-    reinterpret_cast<u32*>(w8 + kHdrBytes)[r + rank] = code;
-    store_rec(A.ref_next + (g_lo + p + 1 + matched + rank) * kRecBytes, M);
+    reinterpret_cast<u32*>(q.w8 + kHdrBytes)[r + i] = code;
+    store_rec(A.ref_next + (g_lo + p + 1 + matched + i) * kRecBytes, M);
     if constexpr (PR) {
       if (A.pr.hist_next)
-        store_hist_next(A.pr.hist_next + kHistBytes * (g_lo + matched + rank), nullptr, nullptr);
+        store_hist_next(A.pr.hist_next + kHistBytes * (g_lo + matched + i), nullptr, nullptr);
     }
   }
-  __syncthreads();
-  if (staged) flush_stage(stage, gA, tot.a);
-  __syncthreads();
+  const u32 wincl = warp_incl_scan<u32>(vb);
+  const u32 wbytes = __shfl_sync(0xFFFFFFFFu, wincl, 31);
+  uint8_t* wst = stage + (threadIdx.x >> 5) * kWarpStage;
+  warp_zero(wst, wbytes);
+  __syncwarp();
+  if (live) {
+    u32 o = wincl - vb;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) {
+      const u32 L = sig_bytes(M.w[w]);
+      stage_or(wst, o, M.w[w], L);
+      o += L;
+    }
+  }
+  u64 tot;
+  const u64 ex = scan_packed((u64)vb, buf, &tot);
+  const u64 left = (u64)n_list - tile * T;
+  const U64x2 pre = run;
+  run = pre + U64x2{tot, left < (u64)T ? left : (u64)T};
+  const u32 wstart = __shfl_sync(0xFFFFFFFFu, (u32)ex, 0);
+  uint8_t* gW = q.w8 + kHdrBytes + 4 * (r + n_new) + slot_tot.a + pre.a + wstart;
+  __syncwarp();
+  warp_flush(wst, gW, wbytes);
+  __syncwarp();
 }
 
 // ---------------- decode phase ----------------
@@ -884,25 +982,37 @@ struct DecShared {
   int ok;
 };
 
+// Offsets of pair p that every decode tile uses, read once per pair.
+struct DecPair {
+  u64 ro;             // first slot of the receiver's reference
+  u64 rv;             // first record of the receive buffer
+  const uint8_t* w8;  // the pair's message
+};
+
+__device__ __forceinline__ DecPair dec_pair(const DecArgs& A, u32 p) {
+  return DecPair{A.ref_off ? A.ref_off[p] : 0, A.recv_off[p], A.wire + A.wire_off[p]};
+}
+
 // One tile of entries; code = this thread's entry code (read one tile ahead).
 template <int T, bool PR>
 __device__ __forceinline__ void bat_dec_tile(const DecArgs& A, const BatchArgs& B, u32 p,
-                                             u64 tile, u32 code, const DecShared& h, u64 m,
-                                             u64* buf, uint8_t* stage, U64x2& run,
+                                             const DecPair& q, u64 tile, u32 code,
+                                             const DecShared& h, u64 m, u64* buf,
+                                             uint8_t* stage, ulonglong2* stash, U64x2& run,
                                              const float* sW) {
   const u64 ns = h.ns, n = h.ns + h.nn;
-  const uint8_t* w8 = A.wire + A.wire_off[p];
+  const uint8_t* w8 = q.w8;
   const u64 e = tile * T + threadIdx.x;
   u32 b = 0;
   bool hole = true;
   int bad = 0;
-  // the slot's reference record is read before (and while) the prefix is found
-  Rec R;
-  if (e < ns) R = load_rec(A.ref + (A.ref_off[p] + p + 1 + e) * kRecBytes);
   if (e < n && !check_code(code, e, ns, &hole, &b)) {
     bad = 1;
     latch(A.st, TERA_ECORRUPT);  // malformed code: its entry is not decoded
   }
+  // the slot's reference record is copied into the stash while the prefix
+  // is found
+  if (e < ns && !hole && !bad) stash_async<T>(stash, A.ref + (q.ro + p + 1 + e) * kRecBytes);
   const u32 vn = (e < n && !hole) ? 1u : 0u;
   u64 tot64;
   const u64 ex64 = scan_packed((u64)b | ((u64)vn << 32), buf, &tot64);
@@ -927,6 +1037,7 @@ __device__ __forceinline__ void bat_dec_tile(const DecArgs& A, const BatchArgs& 
       *reinterpret_cast<uint4*>(wst + (c << 4)) =
           __ldcg(reinterpret_cast<const uint4*>(g16 + (c << 4)));
   }
+  stash_wait();
   __syncwarp();
   if (ok && vn && !bad) {
     u32 o = s0 + ((u32)ex.a - wstart);
@@ -939,11 +1050,12 @@ __device__ __forceinline__ void bat_dec_tile(const DecArgs& A, const BatchArgs& 
     }
     const u64 pos = pre.b + ex.b;
     if (e < ns) {
+      const Rec R = stash_get<T>(stash);
       bool pred_ok = false;
       u64 pred[3];
       if constexpr (PR) {
         Hist H;
-        if (A.pr.hist) H = load_hist(A.pr.hist + kHistBytes * (A.ref_off[p] + e));
+        if (A.pr.hist) H = load_hist(A.pr.hist + kHistBytes * (q.ro + e));
         if (A.pr.hist && h.mode == kModeResidual) {
           const u64 r = A.ref_off[p + 1] - A.ref_off[p];
           const u32 nc = cell_count(A.pr.cseg, seg_base(A.ref_off[p], p), seg_size(r),
@@ -952,7 +1064,7 @@ __device__ __forceinline__ void bat_dec_tile(const DecArgs& A, const BatchArgs& 
           if (features(R, H, nc, f)) pred_ok = predict_from(sW, R, f, pred);
         }
         if (A.pr.hist_next)
-          store_hist_next(A.pr.hist_next + kHistBytes * (A.recv_off[p] + pos), &R,
+          store_hist_next(A.pr.hist_next + kHistBytes * (q.rv + pos), &R,
                           A.pr.hist ? &H : nullptr);
       }
 #pragma unroll
@@ -963,10 +1075,10 @@ __device__ __forceinline__ void bat_dec_tile(const DecArgs& A, const BatchArgs& 
     } else {
       if constexpr (PR) {
         if (A.pr.hist_next)
-          store_hist_next(A.pr.hist_next + kHistBytes * (A.recv_off[p] + pos), nullptr, nullptr);
+          store_hist_next(A.pr.hist_next + kHistBytes * (q.rv + pos), nullptr, nullptr);
       }
     }
-    store_rec(A.recv + (A.recv_off[p] + p + 1 + pos) * kRecBytes, rec);
+    store_rec(A.recv + (q.rv + p + 1 + pos) * kRecBytes, rec);
   }
   __syncwarp();
   // the last tile: every byte and record the header announced was decoded
@@ -1001,20 +1113,21 @@ __device__ __forceinline__ DecShared dec_header(const DecArgs& A, u32 p, u64 m, 
 template <int T, bool PR>
 __device__ __forceinline__ void bat_dec(const DecArgs& A, const BatchArgs& B, u32 p,
                                         DecShared* hs, u64* bufs, uint8_t* stage,
-                                        const float* sW) {
+                                        ulonglong2* stash, const float* sW) {
   const u64 m = A.recv_off[p + 1] - A.recv_off[p];
   const DecShared h = dec_header<PR>(A, p, m, hs, true);
   if (!h.ok) return;  // block-uniform
   const u64 n = h.ns + h.nn;
   const u64 ntiles = n ? ceil_div(n, T) : 1;
   U64x2 run{0, 0};
-  const u32* codes = reinterpret_cast<const u32*>(A.wire + A.wire_off[p] + kHdrBytes);
+  const DecPair q = dec_pair(A, p);
+  const u32* codes = reinterpret_cast<const u32*>(q.w8 + kHdrBytes);
   u32 c_next = threadIdx.x < n ? __ldcg(codes + threadIdx.x) : 0u;
   for (u64 t = 0; t < ntiles; ++t) {
     const u32 c = c_next;
     const u64 en = (t + 1) * T + threadIdx.x;
     c_next = en < n ? __ldcg(codes + en) : 0u;
-    bat_dec_tile<T, PR>(A, B, p, t, c, h, m, bufs + 33 * (t & 1), stage, run, sW);
+    bat_dec_tile<T, PR>(A, B, p, q, t, c, h, m, bufs + 33 * (t & 1), stage, stash, run, sW);
   }
   __syncthreads();  // the scan buffers and the stage are reused next
 }
@@ -1156,7 +1269,7 @@ __device__ __forceinline__ void team_dec_sum(const DecArgs& A, u32 p, const DecS
 template <int T>
 __device__ __noinline__ void team_pair(const EncArgs& E, const DecArgs& D, const BatchArgs& B,
                                           u32 p, u32 i, u32 g, u32 epoch, U64x2* sm, u64* red,
-                                          uint8_t* stage, DecShared* hs) {
+                                          uint8_t* stage, ulonglong2* stash, DecShared* hs) {
   constexpr u32 kStageCap = (u32)T * kRecBytes + 48;
   const u64* pi = E.info + (u64)p * 8;
   const u64 r = pi[PI_R], m = pi[PI_M];
@@ -1176,11 +1289,12 @@ __device__ __noinline__ void team_pair(const EncArgs& E, const DecArgs& D, const
   for (u64 t = i; t < ntn; t += g) team_new_sum<T>(E, p, m, V, t, epoch, nts, red);
   team_barrier(ctr + 2, g, E.st);
   u32 k = 0;
+  const SlotPair q = slot_pair(E, B, p);
   for (u64 t = i; t < nst; t += g, ++k) {
     U64x2 run = tiles_prefix<T>(ts, t, red);
     const u64 j = t * T + threadIdx.x;
     const u32 src = j < r ? __ldcg(E.slot_src + ro + j) : kNoMatch;
-    bat_slot<T, false>(E, B, p, t, src, bufs + 33 * (k & 1), stage, run);
+    bat_slot<T, false>(E, B, p, q, t, src, bufs + 33 * (k & 1), stage, stash, run);
   }
   __syncthreads();
   // the new records (the member with the last new tile writes the header)
@@ -1198,32 +1312,40 @@ __device__ __noinline__ void team_pair(const EncArgs& E, const DecArgs& D, const
   U64x2* ds = nts + ceil_div(m, T);
   for (u64 t = i; t < ndt; t += g) team_dec_sum<T>(D, p, h, t, ds, red);
   team_barrier(ctr + 4, g, E.st);
-  const u32* codes = reinterpret_cast<const u32*>(D.wire + D.wire_off[p] + kHdrBytes);
+  const DecPair dq = dec_pair(D, p);
+  const u32* codes = reinterpret_cast<const u32*>(dq.w8 + kHdrBytes);
   k = 0;
   for (u64 t = i; t < ndt; t += g, ++k) {
     U64x2 run = tiles_prefix<T>(ds, t, red);
     const u64 e = t * T + threadIdx.x;
     const u32 c = e < n ? __ldcg(codes + e) : 0u;
-    bat_dec_tile<T, false>(D, B, p, t, c, h, mr, bufs + 33 * (k & 1), stage, run, nullptr);
+    bat_dec_tile<T, false>(D, B, p, dq, t, c, h, mr, bufs + 33 * (k & 1), stage, stash, run,
+                           nullptr);
   }
   __syncthreads();
 }
 
 // ---------------- the persistent kernel ----------------
 
-// Shared memory, for c = table_records: one region of max(4c, 2c + stage)
-// bytes that holds the hash table (2c u16, match step), then the list of new
-// records (c u16, new step) followed by the stage (the block's T records + 48
-// bytes for the new step, or one region per warp for the slot and decode
-// steps) | MLP weights (predictor) | taken bits (c / 8).
+// Shared memory, for c = table_records: one region that holds the hash table
+// (up to 2c u16 entries, match step), then the list of new records (c u16,
+// new step) or the record stash (T records, slot and decode steps),
+// followed by the stage (the block's T records + 48 bytes for the new step,
+// or one region per warp for the slot and decode steps) | MLP weights
+// (predictor) | taken bits (c / 8).
 __host__ __device__ constexpr size_t stage_bytes(u32 T) {
   // the block stage (T records + 48 bytes) or the warps' stages, the larger
   return (size_t)(T / 32) * kWarpStage > (size_t)T * kRecBytes + 48 ? (size_t)(T / 32) * kWarpStage
                                                                       : (size_t)T * kRecBytes + 48;
 }
+__host__ __device__ constexpr size_t stash_bytes(u32 T) { return (size_t)T * kRecBytes; }
+// where the stage starts: after the list and after the stash
+__host__ __device__ constexpr size_t stage_off(u32 T, u32 c) {
+  return 2 * (size_t)c > stash_bytes(T) ? 2 * (size_t)c : stash_bytes(T);
+}
 __host__ __device__ constexpr size_t region_bytes(u32 T, u32 c) {
-  return (4 * (size_t)c > 2 * (size_t)c + stage_bytes(T)) ? 4 * (size_t)c
-                                                          : 2 * (size_t)c + stage_bytes(T);
+  return (4 * (size_t)c > stage_off(T, c) + stage_bytes(T)) ? 4 * (size_t)c
+                                                            : stage_off(T, c) + stage_bytes(T);
 }
 
 template <int T, bool PR>
@@ -1234,7 +1356,8 @@ __global__ void __launch_bounds__(T, (1024 / T) > 0 ? (1024 / T) : 1)
   const size_t region = region_bytes(T, table_records);
   unsigned short* tbl = reinterpret_cast<unsigned short*>(dyn);
   unsigned short* list = tbl;
-  uint8_t* stage = dyn + 2 * (size_t)table_records;
+  uint8_t* stage = dyn + stage_off(T, table_records);
+  ulonglong2* stash = reinterpret_cast<ulonglong2*>(dyn);
   float* sW = reinterpret_cast<float*>(dyn + region);
   u32* bits = reinterpret_cast<u32*>(dyn + region + (PR ? sizeof(float) * kMlpParams : 0));
   __shared__ U64x2 sm[33];
@@ -1263,7 +1386,8 @@ __global__ void __launch_bounds__(T, (1024 / T) > 0 ? (1024 / T) : 1)
     const u32 g = (u32)it & 0xFFFFu;
     if (g > 1) {
       if constexpr (!PR)
-        team_pair<T>(E, D, B, p, (u32)(it >> 16) & 0xFFFFu, g, epoch, sm, red, stage, &hs);
+        team_pair<T>(E, D, B, p, (u32)(it >> 16) & 0xFFFFu, g, epoch, sm, red, stage, stash,
+                     &hs);
       continue;
     }
     const u64* pi = E.info + (u64)p * 8;
@@ -1304,14 +1428,15 @@ __global__ void __launch_bounds__(T, (1024 / T) > 0 ? (1024 / T) : 1)
     __syncthreads();
     U64x2 run{0, 0};
     const u64 nst = ceil_div(r, T);
+    const SlotPair q = slot_pair(E, B, p);
     {
-      const u64 ro = E.ref_off ? E.ref_off[p] : 0;
-      u32 g_next = threadIdx.x < r ? __ldcg(E.slot_src + ro + threadIdx.x) : kNoMatch;
+      u32 g_next = threadIdx.x < r ? __ldcg(E.slot_src + q.ro + threadIdx.x) : kNoMatch;
       for (u64 t = 0; t < nst; ++t) {
         const u32 g = g_next;
         const u64 jn = (t + 1) * T + threadIdx.x;
-        g_next = jn < r ? __ldcg(E.slot_src + ro + jn) : kNoMatch;
-        bat_slot<T, PR>(E, B, p, t, g, reinterpret_cast<u64*>(sm) + 33 * (t & 1), stage, run);
+        g_next = jn < r ? __ldcg(E.slot_src + q.ro + jn) : kNoMatch;
+        bat_slot<T, PR>(E, B, p, q, t, g, reinterpret_cast<u64*>(sm) + 33 * (t & 1), stage,
+                        stash, run);
       }
       __syncthreads();  // the scan buffers and the stage are reused next
     }
@@ -1322,8 +1447,8 @@ __global__ void __launch_bounds__(T, (1024 / T) > 0 ? (1024 / T) : 1)
       const u32 n_list = smem_new_list<T>(tb, m, list, reinterpret_cast<u32*>(sm));
       const u64 tl = ceil_div(n_list, T);
       for (u64 t = 0; t < tl; ++t)
-        bat_new_list<T, PR>(E, p, r, m, matched, slot_tot, list, n_list, t, sm, stage,
-                            kStageCap, run);
+        bat_new_list<T, PR>(E, p, q, matched, slot_tot, list, n_list, t,
+                            reinterpret_cast<u64*>(sm) + 33 * (t & 1), stage, run);
       finish_pair<PR>(E, B, p, r, m, matched, slot_tot, run);
     } else {
       const u64 tn = ceil_div(m, (u64)T * new_per_thread(pi[PI_MODE]));
@@ -1339,7 +1464,7 @@ __global__ void __launch_bounds__(T, (1024 / T) > 0 ? (1024 / T) : 1)
         __syncthreads();
       }
     }
-    bat_dec<T, PR>(D, B, p, &hs, reinterpret_cast<u64*>(sm), stage, sW);
+    bat_dec<T, PR>(D, B, p, &hs, reinterpret_cast<u64*>(sm), stage, stash, sW);
     __syncthreads();
   }
 }
@@ -1412,7 +1537,7 @@ static tera_status batched_impl(
   cudaStream_t s = (cudaStream_t)stream;
   const u64 P = ctx->n_pairs;
   const bool PR = enc_pred != nullptr || dec_pred != nullptr;
-  if (PR && tn.block > 256) tn.block = 256;  // stage + weights stay within 48 KB
+  if (PR && tn.block > 256) tn.block = 256;  // stash, stage and weights stay within 70 KB
   const u32 T = (u32)tn.block;
   tera_status st = ensure_records(ctx, ctx->cap_records, s);
   if (st != TERA_OK) return st;
