@@ -1008,6 +1008,7 @@ __device__ __forceinline__ void bat_dec_tile(const DecArgs& A, const BatchArgs& 
   int bad = 0;
   if (e < n && !check_code(code, e, ns, &hole, &b)) {
     bad = 1;
+    b = 0;  // a malformed nibble may claim more than a record: it takes no payload
     latch(A.st, TERA_ECORRUPT);  // malformed code: its entry is not decoded
   }
   // the slot's reference record is copied into the stash while the prefix
@@ -1110,6 +1111,105 @@ __device__ __forceinline__ DecShared dec_header(const DecArgs& A, u32 p, u64 m, 
   return *hs;
 }
 
+// Facts of one entry of a decode tile from its code.
+struct DecEnt {
+  u32 b, vn;  // payload bytes, record decoded (not a placeholder)
+  bool hole;
+  bool bad;   // malformed code: not decoded, no payload
+};
+
+__device__ __forceinline__ DecEnt dec_entry(DevStatus* st, u32 code, u64 e, u64 n, u64 ns) {
+  DecEnt x{0u, 0u, true, false};
+  if (e < n && !check_code(code, e, ns, &x.hole, &x.b)) {
+    x.bad = true;
+    x.b = 0;
+    latch(st, TERA_ECORRUPT);
+  }
+  x.vn = (e < n && !x.hole) ? 1u : 0u;
+  return x;
+}
+
+// The decode step of pair p (no predictor) as bat_dec_tile, software
+// pipelined: a tile's byte counts come from its codes alone, so the block
+// scan of tile t + 1 runs while tile t's payload and reference records are
+// in flight (both copied into shared memory by cp.async), and tile t's
+// payload is requested as soon as the tile starts.
+template <int T>
+__device__ __forceinline__ void dec_tiles_pipelined(const DecArgs& A, u32 p, const DecPair& q,
+                                                    const DecShared& h, u64 m, u64* bufs,
+                                                    uint8_t* stage, ulonglong2* stash) {
+  const u64 ns = h.ns, n = h.ns + h.nn;
+  const u64 ntiles = n ? ceil_div(n, T) : 1;
+  const u32* codes = reinterpret_cast<const u32*>(q.w8 + kHdrBytes);
+  const uint8_t* pay = q.w8 + kHdrBytes + 4 * n;
+  uint8_t* wst = stage + (threadIdx.x >> 5) * kWarpStage;
+  u64 e = threadIdx.x;
+  u32 code = e < n ? __ldcg(codes + e) : 0u;
+  u32 c_next = e + T < n ? __ldcg(codes + e + T) : 0u;
+  DecEnt x = dec_entry(A.st, code, e, n, ns);
+  u64 tot64;
+  u64 ex64 = scan_packed((u64)x.b | ((u64)x.vn << 32), bufs, &tot64);
+  U64x2 run{0, 0};
+  for (u64 t = 0; t < ntiles; ++t, e += T) {
+    const U64x2 ex{ex64 & 0xFFFFFFFFull, ex64 >> 32}, tot{tot64 & 0xFFFFFFFFull, tot64 >> 32};
+    const U64x2 pre = run;
+    run = pre + tot;
+    // more payload / records than the header announces (block-uniform)
+    const bool ok = pre.a + tot.a <= h.pay && pre.b + tot.b <= m;
+    if (!ok && threadIdx.x == 0) latch(A.st, TERA_ECORRUPT);
+    // this warp's payload bytes [wstart, wend) of the tile; the slab is
+    // 16-byte aligned and padded, and the range was checked, so the copies
+    // stay inside the message
+    const u32 wstart = __shfl_sync(0xFFFFFFFFu, (u32)ex.a, 0);
+    const u32 wend = __shfl_sync(0xFFFFFFFFu, (u32)ex.a + x.b, 31);
+    const uint8_t* gW = pay + pre.a + wstart;
+    const u32 s0 = (u32)((uintptr_t)gW & 15u);
+    if (ok) {
+      const uint8_t* g16 = gW - s0;
+      const u32 n16 = (s0 + (wend - wstart) + 15u) >> 4;
+      for (u32 k = threadIdx.x & 31; k < n16; k += 32) {
+        const u32 dst = (u32)__cvta_generic_to_shared(wst + (k << 4));
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" : : "r"(dst), "l"(g16 + (k << 4))
+                     : "memory");
+      }
+    }
+    if (e < ns && !x.hole && !x.bad) stash_async<T>(stash, A.ref + (q.ro + p + 1 + e) * kRecBytes);
+    asm volatile("cp.async.commit_group;" : : : "memory");
+    // the next tile's facts and prefix while the copies are in flight
+    const DecEnt xt = x;
+    const u32 ct = code;
+    code = c_next;
+    const u64 e2 = e + 2 * (u64)T;
+    c_next = e2 < n ? __ldcg(codes + e2) : 0u;
+    if (t + 1 < ntiles) {  // block-uniform
+      x = dec_entry(A.st, code, e + T, n, ns);
+      ex64 = scan_packed((u64)x.b | ((u64)x.vn << 32), bufs + 33 * ((t + 1) & 1), &tot64);
+    }
+    stash_wait();
+    __syncwarp();
+    if (ok && xt.vn && !xt.bad) {
+      u32 o = s0 + ((u32)ex.a - wstart);
+      Rec rec;
+#pragma unroll
+      for (int w = 0; w < 8; ++w) {
+        const u32 L = (ct >> (4 * w)) & 0xFu;
+        rec.w[w] = stage_bytes_at(wst, o, L);
+        o += L;
+      }
+      if (e < ns) {
+        const Rec R = stash_get<T>(stash);
+#pragma unroll
+        for (int w = 0; w < 8; ++w) rec.w[w] ^= R.w[w];
+      }
+      store_rec(A.recv + (q.rv + p + 1 + pre.b + ex.b) * kRecBytes, rec);
+    }
+    __syncwarp();
+    // the last tile: every byte and record the header announced was decoded
+    if (ok && threadIdx.x == 0 && t + 1 == ntiles && (run.a != h.pay || run.b != m))
+      latch(A.st, TERA_ECORRUPT);
+  }
+}
+
 template <int T, bool PR>
 __device__ __forceinline__ void bat_dec(const DecArgs& A, const BatchArgs& B, u32 p,
                                         DecShared* hs, u64* bufs, uint8_t* stage,
@@ -1118,9 +1218,14 @@ __device__ __forceinline__ void bat_dec(const DecArgs& A, const BatchArgs& B, u3
   const DecShared h = dec_header<PR>(A, p, m, hs, true);
   if (!h.ok) return;  // block-uniform
   const u64 n = h.ns + h.nn;
+  const DecPair q = dec_pair(A, p);
+  if constexpr (!PR) {
+    dec_tiles_pipelined<T>(A, p, q, h, m, bufs, stage, stash);
+    __syncthreads();  // the scan buffers and the stage are reused next
+    return;
+  }
   const u64 ntiles = n ? ceil_div(n, T) : 1;
   U64x2 run{0, 0};
-  const DecPair q = dec_pair(A, p);
   const u32* codes = reinterpret_cast<const u32*>(q.w8 + kHdrBytes);
   u32 c_next = threadIdx.x < n ? __ldcg(codes + threadIdx.x) : 0u;
   for (u64 t = 0; t < ntiles; ++t) {
@@ -1254,7 +1359,10 @@ __device__ __forceinline__ void team_dec_sum(const DecArgs& A, u32 p, const DecS
     const u32 code = __ldcg(reinterpret_cast<const u32*>(A.wire + A.wire_off[p] + kHdrBytes) + e);
     bool hole;
     u32 bb;
-    if (!check_code(code, e, ns, &hole, &bb)) latch(A.st, TERA_ECORRUPT);
+    if (!check_code(code, e, ns, &hole, &bb)) {
+      latch(A.st, TERA_ECORRUPT);
+      bb = 0;  // as in bat_dec_tile: a malformed entry takes no payload
+    }
     b = bb;
     f = hole ? 0 : 1;
   }
