@@ -347,13 +347,21 @@ __device__ __forceinline__ void smem_build(const EncArgs& A, u32 p, u64 m, const
   const u64 g_lo = A.pair_off[p];
   for (u32 i = threadIdx.x; i <= tb.mask; i += T) tb.tbl[i] = 0;
   for (u32 i = threadIdx.x; i < (u32)((m + 31) / 32); i += T) tb.bits[i] = 0u;
+  // message ids are read one batch ahead, so they arrive while a batch inserts
+  u64 id_next[kIlp];
+#pragma unroll
+  for (u32 i = 0; i < kIlp; ++i) {
+    const u64 k = (u64)i * T + threadIdx.x;
+    id_next[i] = k < m ? msg_id(A, p, g_lo + k) : 0;
+  }
   __syncthreads();
   for (u64 k0 = 0; k0 < m; k0 += (u64)T * kIlp) {
     u64 id[kIlp];
 #pragma unroll
     for (u32 i = 0; i < kIlp; ++i) {
-      const u64 k = k0 + (u64)i * T + threadIdx.x;
-      id[i] = k < m ? msg_id(A, p, g_lo + k) : 0;
+      id[i] = id_next[i];
+      const u64 k = k0 + (u64)(kIlp + i) * T + threadIdx.x;
+      id_next[i] = k < m ? msg_id(A, p, g_lo + k) : 0;
     }
 #pragma unroll
     for (u32 i = 0; i < kIlp; ++i) {
@@ -393,14 +401,23 @@ __device__ __forceinline__ u32 smem_find(const EncArgs& A, u32 p, const SmemTabl
 // kNoMatch; bits mark the taken records.  Returns this thread's match count.
 template <int T>
 __device__ __forceinline__ u32 smem_match(const EncArgs& A, u32 p, u64 r, const SmemTable& tb) {
-  const u64 ro = A.ref_off[p], g_lo = A.pair_off[p];
+  // no reference (r = 0): ref_off is null and no slot is read
+  const u64 ro = A.ref_off ? A.ref_off[p] : 0, g_lo = A.pair_off[p];
   u32 found = 0;
+  // slot ids are read one batch ahead, so they arrive while a batch probes
+  u64 id_next[kIlp];
+#pragma unroll
+  for (u32 i = 0; i < kIlp; ++i) {
+    const u64 j = (u64)i * T + threadIdx.x;
+    id_next[i] = j < r ? *reinterpret_cast<const u64*>(A.ref + (ro + p + 1 + j) * kRecBytes) : 0;
+  }
   for (u64 j0 = 0; j0 < r; j0 += (u64)T * kIlp) {
     u64 id[kIlp];
 #pragma unroll
     for (u32 i = 0; i < kIlp; ++i) {
-      const u64 j = j0 + (u64)i * T + threadIdx.x;
-      id[i] = j < r ? *reinterpret_cast<const u64*>(A.ref + (ro + p + 1 + j) * kRecBytes) : 0;
+      id[i] = id_next[i];
+      const u64 j = j0 + (u64)(kIlp + i) * T + threadIdx.x;
+      id_next[i] = j < r ? *reinterpret_cast<const u64*>(A.ref + (ro + p + 1 + j) * kRecBytes) : 0;
     }
     // first fingerprint hit of every slot (shared memory only), then the
     // id checks of all of them in flight together
