@@ -1,9 +1,10 @@
 // Batched codec: steps a3-a5 (paper Sec. 2.3, steps B, C and D) for every
 // pair of one iteration in ONE persistent launch.
 //
-// Each block takes whole pairs (an atomic ticket over the pair index; the
-// next ticket is claimed while the current pair runs) and carries a pair
-// through every step on its own, so no block ever waits for another:
+// Each block takes whole pairs (an atomic ticket over the work list, claimed
+// whenever the block is free) and carries a pair through every step on its
+// own, so no block ever waits for another (pairs far above the average load
+// go to a team of blocks instead):
 //
 //   match   index the message ids, look every reference slot's id up, mark
 //           the message records the slots take.  A pair with at most
@@ -19,6 +20,8 @@
 //           header, the padding and the iteration totals
 //   decode  the receiver's side from the wire and its own reference: codes,
 //           payload and receive buffer, again with an on-chip running prefix
+//           (a tile's prefix is scanned while the previous tile's bytes and
+//           reference records arrive)
 //
 // Tile size T (block size) and blocks per SM come from the caller (tera_tune,
 // picked by the autotuner); the bytes produced do not depend on them.  The
@@ -100,9 +103,11 @@ __device__ __forceinline__ u64 scan_packed(u64 v, u64* buf, u64* total) {
   return __shfl_sync(0xFFFFFFFFu, xi - x, warp) + incl - v;
 }
 
-// Each warp stages its own contiguous byte range in a private region (32
-// records + 16 bytes of alignment slack) and stores it with 16-byte stores
-// inside and byte stores on the edges it shares with the neighbouring warps.
+// Each warp stages its own contiguous byte range in a private region and
+// stores it with 16-byte stores inside and byte stores on the edges it shares
+// with the neighbouring warps.  32 records + 16 bytes: the decode stages from
+// the 16-byte boundary below its first byte, and the encode's flush reads one
+// word past its last.
 constexpr u32 kWarpStage = 32 * kRecBytes + 16;
 
 // Per-thread record stash in shared memory: 16-byte part k of thread i's
