@@ -26,9 +26,9 @@ sys.path.insert(0, ROOT)
 
 METRIC = "aura-exchange agents/s and encode+decode GB/s (% HBM peak); bytes/agent"
 
-# Algorithmic bytes per launch of each kernel, from the totals of the launches
-# ("Kernels and their rooflines").  N agents, E records, R
-# reference slots, H placeholders, A new records, Y payload bytes.
+# Algorithmic bytes per launch of each kernel, from the totals of the launches:
+# what each step must read and write.  N agents, E records, R reference slots,
+# H placeholders, A new records, Y payload bytes.
 def kernel_bytes(name, t):
     N, E, R, A, Y = t["agents"], t["records"], t["ref_slots"], t["new_records"], \
         t["payload_bytes"]
@@ -199,15 +199,24 @@ def cpu_sample_states(wl, states_gpu, n_sample):
     return out
 
 
-def oracle_time(wl, host_states):
-    """Oracle (single thread) over a chain of host states; returns per-state seconds."""
+def host_cores():
+    """Host cores this process may run on."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
+
+
+def oracle_time(wl, host_states, threads=1):
+    """Oracle over a chain of host states (single-threaded, or with agents and
+    pairs spread over `threads` host threads); returns per-state seconds."""
     import oracle
     g = oracle.make_grid(wl.lo, wl.hi, wl.grid, wl.w, wl.periodic)
     ref = recv_ref = None
     times = []
     for s in host_states:
         t0 = time.perf_counter()
-        res = oracle.exchange_iteration(g, s, ref=ref, recv_ref=recv_ref)
+        res = oracle.exchange_iteration(g, s, ref=ref, recv_ref=recv_ref, threads=threads)
         times.append(time.perf_counter() - t0)
         assert res["status"] == oracle.OK, res["status"]
         ref, recv_ref = (res["ref_next"], res["pair_off"]), (res["recv"], res["recv_off"])
@@ -292,7 +301,8 @@ def run_reference(args):
     dev = "cuda" if torch.cuda.is_available() else "cpu"
     gen = Generator(wl, device=dev)
     states = [to_numpy(s) for s in gen.series(args.warmup + args.steps)]
-    times = oracle_time(wl, states)
+    cores = host_cores()
+    times = oracle_time(wl, states, threads=cores)
     timed = times[args.warmup:]
     agents = sum(int(s["x"].shape[0]) for s in states[args.warmup:])
     total = sum(timed)
@@ -304,9 +314,10 @@ def run_reference(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": {"workload": args.workload, "agents_per_step": n,
                    "note": f"oracle on the first {n} agents per state of the same workload"},
-        "cpu_baseline": {"value": value, "unit": "agents/s", "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": "agents/s", "cores": cores, "kind": "oracle",
                          "sample": f"{args.warmup}+{args.steps} iterations of {args.workload} "
-                                   f"scaled to {n} agents (same cube, grid, aura, dynamics)"},
+                                   f"scaled to {n} agents (same cube, grid, aura, dynamics); "
+                                   f"agents and pairs spread over {cores} host threads"},
         "e2e": {"value": value, "unit": "agents/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -651,12 +662,17 @@ def main():
     cpu = compression = None
     if hs is not None:
         from synth import scaled
-        tms = oracle_time(scaled(wl, ns), hs)
+        cores = host_cores()
+        tms1 = oracle_time(scaled(wl, ns), hs)
+        tmsn = oracle_time(scaled(wl, ns), hs, threads=cores)
         compression = compression_comparison(scaled(wl, ns), hs)
-        cpu = {"value": int(hs[1]["x"].shape[0]) / tms[1], "unit": "agents/s", "cores": 1,
+        na = int(hs[1]["x"].shape[0])
+        cpu = {"value": na / tmsn[1], "unit": "agents/s", "cores": cores,
                "kind": "oracle",
                "sample": f"one iteration (with reference) of the first {ns} agents of two "
-                         f"consecutive states of {args.workload}; single-threaded C oracle"}
+                         f"consecutive states of {args.workload}; C oracle with agents and pairs "
+                         f"spread over {cores} host threads",
+               "single_core": {"value": na / tms1[1], "unit": "agents/s", "cores": 1}}
     clk_sum = clk.summary()
     line = {
         "metric": METRIC, "value": value, "unit": "agents/s", "n_gpus": world,

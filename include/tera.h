@@ -204,27 +204,30 @@ tera_status tera_delta_decode(tera_ctx* ctx, const uint8_t* wire, const uint64_t
                               uint64_t recv_capacity_units, uint64_t* recv_off, void* stream);
 
 /* The decode step for callers that cannot allocate device memory (no
- * counterpart in the paper).  Callers that are capturing a stream into a CUDA
- * graph, hosts whose device memory is reserved up front by their own pool,
- * and loops that forbid allocation after start-up cannot call cudaMalloc, and
- * so cannot create a tera_ctx.  This variant decodes every pair [0, n_pairs)
- * exactly as tera_delta_decode does (same arguments and outputs, same bytes),
- * but takes all of its scratch memory from one fixed array in the library's
- * device memory (about 16.5 MB per GPU that loads the library, held until the
- * process exits); it calls no cudaMalloc, cudaFree or allocating routine.
+ * counterpart in the paper).  Hosts whose device memory is reserved up front
+ * by their own pool, and real-time loops that forbid allocation after
+ * start-up, cannot call cudaMalloc, and so cannot create a tera_ctx.  This
+ * variant decodes every pair [0, n_pairs) exactly as tera_delta_decode does
+ * (same arguments and outputs, same bytes), but takes all of its scratch
+ * memory from one fixed array in the library's device memory (about 16.5 MB
+ * per GPU that loads the library, held until the process exits); it calls no
+ * cudaMalloc, cudaFree or allocating routine.
  *  - Limits: n_pairs <= 32768 (TERA_ECAPACITY beyond, returned at once) and
  *    at most 393216 codec tiles of 256 entries (about 100M slots + new
- *    records; TERA_ECAPACITY, latched on the device, beyond).
- *  - n_pairs must be a multiple of 27 (the grid's box count times 27).
+ *    records).  Beyond the tile limit the call returns TERA_ECAPACITY with
+ *    *required_capacity = 0 (no receive capacity would help); a receive
+ *    buffer that is too small returns TERA_ECAPACITY with the required units.
+ *  - n_pairs must be a multiple of 27 (the grid's box count times 27);
+ *    TERA_EINVAL otherwise.
  *  - The first call on a device looks up the array's device address for
- *    that device (with it current); make that first call before any stream
- *    capture.
+ *    that device (with it current) and keeps it for the life of the process;
+ *    after cudaDeviceReset on that device, do not call it there again.
  *  - Every call shares the array, which keeps the last call's contents: calls
  *    that overlap on the GPU (other streams, other threads) race on it; the
  *    caller must serialize them.
  *  - Returns the device status of this call: it synchronizes `stream` and
  *    reads the status word back; *required_capacity (optional) is set on
- *    TERA_ECAPACITY.  No context status is touched. */
+ *    TERA_ECAPACITY as above.  No context status is touched. */
 tera_status tera_delta_decode_noalloc(const uint8_t* wire, const uint64_t* wire_off,
                                       const uint8_t* ref_prev, const uint64_t* ref_off_prev,
                                       uint64_t n_pairs, uint32_t class_id, uint8_t* recv,
@@ -301,11 +304,22 @@ tera_status tera_mlp_train(tera_ctx* ctx, const float* samples, uint64_t n, floa
  * 2048), and the largest message (records) matched in a block's shared-memory
  * hash table: 0 = as large as the shared memory left to the block allows, else
  * a power of two >= 32 (smaller when it does not fit); larger messages use the
- * pair's hash segment in global memory.  reserved must be 0. */
+ * pair's hash segment in global memory.
+ * team_blocks: 0 = a pair far above the average load per block is carried by
+ * a team of blocks sized by its load (at most 64, at most half the blocks of
+ * the launch); 2..1024 = every such pair is carried by exactly that many
+ * blocks.  Team members meet at barriers whose wait is bounded by
+ * wait_limit_us microseconds of the GPU's global timer (0 = 1 s; at most
+ * 60 s): a team that cannot meet in time (e.g. more members than blocks that
+ * can run at once) latches TERA_ETIMEOUT and its pair is abandoned (that
+ * pair's outputs are then unspecified; every other pair is still encoded and
+ * decoded).  reserved must be 0. */
 typedef struct {
   int block;
   int ctas_per_sm;
   int table_records;
+  int team_blocks;
+  int wait_limit_us;
   int reserved;
 } tera_tune;
 
@@ -321,7 +335,7 @@ typedef struct {
  * reference is ref_prev/ref_off_prev, the receiver's recv_prev/recv_off_prev
  * (NULL pairs = empty references).  rec_arena is any packed arena laid out
  * with pair_off (record ids are read from the records).  tune == NULL uses
- * {256, 4, 0, 0}.  Asynchronous, no host synchronization (graph-capturable once
+ * {256, 4, 0, 0, 0, 0}.  Asynchronous, no host synchronization (graph-capturable once
  * scratch is reserved); device errors are latched in the status word. */
 tera_status tera_codec_batched(tera_ctx* ctx, const uint8_t* rec_arena, const uint64_t* pair_off,
                                const uint8_t* ref_prev, const uint64_t* ref_off_prev,
@@ -407,6 +421,20 @@ tera_status tera_migrate_send(tera_ctx* ctx, const tera_soa* prev, const uint64_
 tera_status tera_migrate_recv(tera_ctx* ctx, const uint8_t* arena, uint64_t arena_units,
                               const uint64_t* inbox_off, const uint64_t* box_off_next,
                               const tera_soa_mut* next, void* stream);
+
+/* Reference interval (Sec. 2.3: the reference is updated "at regular
+ * intervals"; every K-th iteration here, K = ref_interval >= 1).  The message
+ * of iteration 0 and of every multiple of K becomes the reference of the
+ * following iterations, so iteration t >= 1 encodes (and decodes) against the
+ * message of iteration K * floor((t - 1) / K).  A caller keeps two reference
+ * buffers on each side (sender reference + its offsets, receive buffer + its
+ * offsets); iteration t writes its outputs into buffer *out_buf =
+ * ceil(t / K) mod 2, and reads its references from buffer *ref_buf (the
+ * out_buf of that reference iteration; -1 at t = 0, which has no reference).
+ * *ref_iteration (optional) receives K * floor((t - 1) / K) (0 at t = 0).
+ * Host-only arithmetic; TERA_EINVAL when ref_interval is 0 or out_buf is NULL. */
+tera_status tera_ref_schedule(uint64_t t, uint32_t ref_interval, int32_t* out_buf,
+                              int32_t* ref_buf, uint64_t* ref_iteration);
 
 /* Read (and clear) the latched device status; synchronizes `stream`.
  * *required_capacity (optional) receives the largest capacity a call asked

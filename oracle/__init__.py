@@ -20,7 +20,8 @@ import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "liboracle.so")
-SOURCES = [os.path.join(HERE, "tera_oracle.c"), os.path.join(HERE, "mlp_oracle.c")]
+SOURCES = [os.path.join(HERE, "tera_oracle.c"), os.path.join(HERE, "tera_oracle_mt.c"),
+           os.path.join(HERE, "mlp_oracle.c")]
 
 OK, EINVAL, ENOMEM, ECAPACITY, ECORRUPT, EDOMAIN, EREFMISMATCH = range(7)
 MODE_RAW, MODE_XOR, MODE_RESIDUAL = 0, 1, 2
@@ -39,7 +40,7 @@ def build(force: bool = False) -> str:
     if force or not os.path.exists(LIB_PATH) or os.path.getmtime(LIB_PATH) < newest:
         tmp = LIB_PATH + f".tmp{os.getpid()}"
         cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
-               "-fno-fast-math", "-o", tmp] + SOURCES + ["-lm"]
+               "-fno-fast-math", "-pthread", "-o", tmp] + SOURCES + ["-lm"]
         subprocess.run(cmd, check=True)
         os.replace(tmp, LIB_PATH)
     return LIB_PATH
@@ -84,6 +85,9 @@ def lib():
             L.or_decode_all.argtypes = [u64, u32, P, P, P, P, P, u64, P]
             L.or_exchange_iteration.argtypes = [G, P, P, i64, u32, u32, P, P, P, P, P, P, P,
                                                 P, P, u64, P, P, P, P, P, P, u64, P, P]
+            L.or_exchange_iteration_mt.argtypes = [G, P, P, i64, u32, u32, P, P, P, P, P, P, P,
+                                                   P, P, u64, P, P, P, P, P, P, u64, P, P,
+                                                   C.c_int]
             L.or_delta_records.argtypes = [P, u64, P, u64, P, C.POINTER(C.c_uint64)]
             L.or_migrate_inbox_bit.argtypes = [G, i32, i32]
             L.or_migrate_send.argtypes = [G, P, P, i64, P, u32, P, P, u64, P, P, P]
@@ -117,7 +121,7 @@ def lib():
                                              P, P]
             for f in ("or_grid_check", "or_classify", "or_pair_lists", "or_encode_pair",
                       "or_decode_pair", "or_encode_all", "or_decode_all",
-                      "or_exchange_iteration", "or_mlp_nparam", "or_features", "or_predict",
+                      "or_exchange_iteration", "or_exchange_iteration_mt", "or_mlp_nparam", "or_features", "or_predict",
                       "or_sample", "or_encode_pair_pred", "or_decode_pair_pred",
                       "or_encode_all_pred", "or_decode_all_pred", "or_migrate_inbox_bit",
                       "or_delta_records",
@@ -273,10 +277,12 @@ def arena_pair(arena: np.ndarray, off: np.ndarray, p: int) -> np.ndarray:
 
 
 def exchange_iteration(grid: Grid, soa: dict, ref=None, recv_ref=None, class_id=1,
-                       mode=MODE_XOR):
+                       mode=MODE_XOR, threads: int = 1):
     """One whole iteration (classify, lists, pack, encode, decode) in one C call.
 
     ref / recv_ref: (arena, off) of the sender / receiver reference or None.
+    threads > 1 spreads agents and pairs over that many host threads
+    (or_exchange_iteration_mt; same outputs).
     Returns a dict of every output plus per-step seconds."""
     n = int(soa["x"].shape[0])
     P = n_pairs(grid)
@@ -302,10 +308,13 @@ def exchange_iteration(grid: Grid, soa: dict, ref=None, recv_ref=None, class_id=
     ts = np.zeros(4, dtype=np.float64)
     ra, rof = (None, None) if ref is None else ref
     va, vof = (None, None) if recv_ref is None else recv_ref
-    st = lib().or_exchange_iteration(C.byref(grid), _p(ids), arr, n, class_id, mode, _p(ra),
-                                     _p(rof), _p(va), _p(vof), _p(owner), _p(mask), _p(cnt),
-                                     _p(off), _p(idx), cap, _p(rec), _p(wire), _p(wo), _p(wl),
-                                     _p(nxt), _p(recv), total + P, _p(ro), _p(ts))
+    args = (C.byref(grid), _p(ids), arr, n, class_id, mode, _p(ra), _p(rof), _p(va), _p(vof),
+            _p(owner), _p(mask), _p(cnt), _p(off), _p(idx), cap, _p(rec), _p(wire), _p(wo),
+            _p(wl), _p(nxt), _p(recv), total + P, _p(ro), _p(ts))
+    if threads > 1:
+        st = lib().or_exchange_iteration_mt(*args, int(threads))
+    else:
+        st = lib().or_exchange_iteration(*args)
     return dict(status=st, owner=owner, mask=mask, pair_count=cnt, pair_off=off,
                 pair_idx=idx[:total], rec=rec, wire=wire, wire_off=wo, wire_len=wl,
                 ref_next=nxt, recv=recv, recv_off=ro, t_steps=ts)

@@ -195,7 +195,14 @@ static void write_taio_header(uint8_t* h, uint32_t class_id, uint32_t pair, uint
 void or_pack(const uint64_t* id, const double* const cols[7], uint64_t n_pairs,
              const uint64_t* pair_off, const uint32_t* pair_idx, uint32_t class_id,
              uint8_t* arena) {
-  for (uint64_t p = 0; p < n_pairs; ++p) {
+  or_pack_range(id, cols, 0, n_pairs, pair_off, pair_idx, class_id, arena);
+}
+
+/* or_pack for pairs [p0, p1) only (the arena layout is that of all pairs). */
+void or_pack_range(const uint64_t* id, const double* const cols[7], uint64_t p0, uint64_t p1,
+                   const uint64_t* pair_off, const uint32_t* pair_idx, uint32_t class_id,
+                   uint8_t* arena) {
+  for (uint64_t p = p0; p < p1; ++p) {
     uint8_t* buf = arena + (pair_off[p] + p) * REC_BYTES;
     uint64_t m = pair_off[p + 1] - pair_off[p];
     write_taio_header(buf, class_id, (uint32_t)p, m);
@@ -480,8 +487,17 @@ int or_encode_all(uint64_t n_pairs, uint32_t class_id, uint32_t mode, const uint
                   const uint64_t* pair_off, const uint8_t* ref_arena, const uint64_t* ref_off,
                   const uint8_t* reset, uint8_t* wire, const uint64_t* wire_off,
                   uint64_t* wire_len, uint8_t* ref_next) {
+  return or_encode_range(0, n_pairs, class_id, mode, rec_arena, pair_off, ref_arena, ref_off,
+                         reset, wire, wire_off, wire_len, ref_next);
+}
+
+/* or_encode_all for pairs [p0, p1) only; the status of the first failing pair. */
+int or_encode_range(uint64_t p0, uint64_t p1, uint32_t class_id, uint32_t mode,
+                    const uint8_t* rec_arena, const uint64_t* pair_off, const uint8_t* ref_arena,
+                    const uint64_t* ref_off, const uint8_t* reset, uint8_t* wire,
+                    const uint64_t* wire_off, uint64_t* wire_len, uint8_t* ref_next) {
   int status = OR_OK;
-  for (uint64_t p = 0; p < n_pairs; ++p) {
+  for (uint64_t p = p0; p < p1; ++p) {
     uint64_t m = pair_off[p + 1] - pair_off[p];
     uint64_t r = ref_arena ? ref_off[p + 1] - ref_off[p] : 0;
     const uint8_t* msg_buf = rec_arena + (pair_off[p] + p) * REC_BYTES;
@@ -505,11 +521,10 @@ int or_encode_all(uint64_t n_pairs, uint32_t class_id, uint32_t mode, const uint
   return status;
 }
 
-int or_decode_all(uint64_t n_pairs, uint32_t class_id, const uint8_t* wire,
-                  const uint64_t* wire_off, const uint8_t* ref_arena, const uint64_t* ref_off,
-                  uint8_t* recv, uint64_t recv_cap_units, uint64_t* recv_off) {
-  /* Receive-buffer sizes come from the headers: m_p = n_slots - n_holes + n_new. */
-  int status = OR_OK;
+/* Receive-buffer sizes come from the headers: m_p = n_slots - n_holes + n_new
+ * (0 for a header that cannot be read); recv_off[P+1] is their prefix. */
+void or_recv_layout(uint64_t n_pairs, const uint8_t* wire, const uint64_t* wire_off,
+                    uint64_t* recv_off) {
   recv_off[0] = 0;
   for (uint64_t p = 0; p < n_pairs; ++p) {
     const uint8_t* h = wire + wire_off[p];
@@ -521,8 +536,24 @@ int or_decode_all(uint64_t n_pairs, uint32_t class_id, const uint8_t* wire,
     }
     recv_off[p + 1] = recv_off[p] + m;
   }
+}
+
+int or_decode_all(uint64_t n_pairs, uint32_t class_id, const uint8_t* wire,
+                  const uint64_t* wire_off, const uint8_t* ref_arena, const uint64_t* ref_off,
+                  uint8_t* recv, uint64_t recv_cap_units, uint64_t* recv_off) {
+  or_recv_layout(n_pairs, wire, wire_off, recv_off);
   if (recv_off[n_pairs] + n_pairs > recv_cap_units) return OR_ECAPACITY;
-  for (uint64_t p = 0; p < n_pairs; ++p) {
+  return or_decode_range(0, n_pairs, class_id, wire, wire_off, ref_arena, ref_off, recv,
+                         recv_off);
+}
+
+/* The per-pair part of or_decode_all for pairs [p0, p1), once recv_off is laid
+ * out (and checked against the capacity) for all pairs. */
+int or_decode_range(uint64_t p0, uint64_t p1, uint32_t class_id, const uint8_t* wire,
+                    const uint64_t* wire_off, const uint8_t* ref_arena, const uint64_t* ref_off,
+                    uint8_t* recv, const uint64_t* recv_off) {
+  int status = OR_OK;
+  for (uint64_t p = p0; p < p1; ++p) {
     uint64_t r = ref_arena ? ref_off[p + 1] - ref_off[p] : 0;
     const uint8_t* ref_buf = ref_arena ? ref_arena + (ref_off[p] + p) * REC_BYTES : NULL;
     uint8_t* out = recv + (recv_off[p] + p) * REC_BYTES;

@@ -79,6 +79,23 @@ int or_decode_all(uint64_t n_pairs, uint32_t class_id, const uint8_t* wire,
                   const uint64_t* wire_off, const uint8_t* ref_arena, const uint64_t* ref_off,
                   uint8_t* recv, uint64_t recv_cap_units, uint64_t* recv_off);
 
+/* Receive layout of or_decode_all: recv_off[P+1] from the message headers. */
+void or_recv_layout(uint64_t n_pairs, const uint8_t* wire, const uint64_t* wire_off,
+                    uint64_t* recv_off);
+
+/* The same drivers over pairs [p0, p1) of the arenas (used to spread the
+ * pairs of one iteration over host threads; each pair is independent). */
+void or_pack_range(const uint64_t* id, const double* const cols[7], uint64_t p0, uint64_t p1,
+                   const uint64_t* pair_off, const uint32_t* pair_idx, uint32_t class_id,
+                   uint8_t* arena);
+int or_encode_range(uint64_t p0, uint64_t p1, uint32_t class_id, uint32_t mode,
+                    const uint8_t* rec_arena, const uint64_t* pair_off, const uint8_t* ref_arena,
+                    const uint64_t* ref_off, const uint8_t* reset, uint8_t* wire,
+                    const uint64_t* wire_off, uint64_t* wire_len, uint8_t* ref_next);
+int or_decode_range(uint64_t p0, uint64_t p1, uint32_t class_id, const uint8_t* wire,
+                    const uint64_t* wire_off, const uint8_t* ref_arena, const uint64_t* ref_off,
+                    uint8_t* recv, const uint64_t* recv_off);
+
 /* Difference-serialized message before compression (Sec. 2.3 B and C): XOR
  * for matched slots, 64 zero bytes for placeholders, then the new records. */
 int or_delta_records(const uint8_t* msg, uint64_t m, const uint8_t* ref, uint64_t r,
@@ -113,6 +130,22 @@ int or_exchange_iteration(const or_grid* g, const uint64_t* id, const double* co
                           uint8_t* rec_arena, uint8_t* wire, uint64_t* wire_off,
                           uint64_t* wire_len, uint8_t* ref_next, uint8_t* recv,
                           uint64_t recv_cap_units, uint64_t* recv_off, double* t_steps);
+
+/* or_exchange_iteration with its work spread over `threads` host threads
+ * (tera_oracle_mt.c): classification over contiguous agent ranges, packing,
+ * encoding and decoding over contiguous pair ranges, each range done by the
+ * single-threaded functions above; the lists, slabs and receive layout stay
+ * single-threaded.  Same outputs, byte for byte. */
+int or_exchange_iteration_mt(const or_grid* g, const uint64_t* id, const double* const cols[7],
+                             int64_t n, uint32_t class_id, uint32_t mode,
+                             const uint8_t* ref_arena, const uint64_t* ref_off,
+                             const uint8_t* recv_ref_arena, const uint64_t* recv_ref_off,
+                             int32_t* owner, uint32_t* mask, uint64_t* pair_count,
+                             uint64_t* pair_off, uint32_t* pair_idx, uint64_t idx_capacity,
+                             uint8_t* rec_arena, uint8_t* wire, uint64_t* wire_off,
+                             uint64_t* wire_len, uint8_t* ref_next, uint8_t* recv,
+                             uint64_t recv_cap_units, uint64_t* recv_off, double* t_steps,
+                             int threads);
 
 /* Learned predictor and residual mode (mlp_oracle.c; not in the paper). */
 int or_mlp_nparam(void);

@@ -49,7 +49,7 @@ class Stats(C.Structure):
 
 class Tune(C.Structure):
     _fields_ = [("block", C.c_int), ("ctas_per_sm", C.c_int), ("table_records", C.c_int),
-                ("reserved", C.c_int)]
+                ("team_blocks", C.c_int), ("wait_limit_us", C.c_int), ("reserved", C.c_int)]
 
 
 class Predictor(C.Structure):
@@ -100,6 +100,8 @@ SIGNATURES = {
                                          C.POINTER(C.c_uint64), C.POINTER(C.c_double)]),
     "tera_ctx_profile_reset": (C.c_int, [P]),
     "tera_version": (C.c_char_p, []),
+    "tera_ref_schedule": (C.c_int, [u64, u32, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                    C.POINTER(C.c_uint64)]),
 }
 
 _lock = threading.Lock()

@@ -82,6 +82,24 @@ class PartitionBuffers:
         return o
 
 
+def _tune(tune):
+    """tera_tune from (block, ctas_per_sm[, table_records[, team_blocks[, wait_limit_us]]])."""
+    if tune is None:
+        return None
+    v = [int(x) for x in tune] + [0] * (5 - len(tune))
+    return _lib.Tune(v[0], v[1], v[2], v[3], v[4], 0)
+
+
+def ref_schedule(t: int, ref_interval: int):
+    """tera_ref_schedule: (output buffer, reference buffer (-1 at t = 0),
+    reference iteration) of iteration t with reference interval K."""
+    lib = _lib.load()
+    ob, rb, ri = C.c_int32(), C.c_int32(), C.c_uint64()
+    check(lib.tera_ref_schedule(int(t), int(ref_interval), C.byref(ob), C.byref(rb),
+                                C.byref(ri)), "tera_ref_schedule")
+    return int(ob.value), int(rb.value), int(ri.value)
+
+
 class Context:
     """One partitioning grid on one GPU (owns scratch, hash table, status word)."""
 
@@ -190,10 +208,7 @@ class Context:
                       wire_len, recv_prev, recv_off_prev, recv, recv_off, mode=_lib.MODE_XOR,
                       tune=None, stream=None):
         """Encode + decode of every pair in one persistent launch (tera_codec_batched)."""
-        t = None
-        if tune is not None:
-            t = _lib.Tune(int(tune[0]), int(tune[1]), int(tune[2]) if len(tune) > 2 else 0,
-                          int(tune[3]) if len(tune) > 3 else 0)
+        t = _tune(tune)
         check(self.lib.tera_codec_batched(
             self.h, _ptr(rec_arena), _ptr(pair_off), _ptr(ref_prev), _ptr(ref_off_prev),
             _ptr(ref_next), _ptr(wire), wire.numel(), _ptr(wire_off), _ptr(wire_len),
@@ -236,10 +251,7 @@ class Context:
                            wire_off, wire_len, recv_prev, recv_off_prev, recv, recv_off,
                            enc_pred: dict, dec_pred: dict, mode=_lib.MODE_XOR, tune=None,
                            stream=None):
-        t = None
-        if tune is not None:
-            t = _lib.Tune(int(tune[0]), int(tune[1]), int(tune[2]) if len(tune) > 2 else 0,
-                          int(tune[3]) if len(tune) > 3 else 0)
+        t = _tune(tune)
         pe, pd = self._pred(enc_pred), self._pred(dec_pred)
         check(self.lib.tera_codec_batched_pred(
             self.h, _ptr(rec_arena), _ptr(pair_off), _ptr(ref_prev), _ptr(ref_off_prev),

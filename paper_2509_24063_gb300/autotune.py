@@ -17,7 +17,7 @@ import os
 
 import torch
 
-# (threads per block, blocks per SM, table records (0: what fits), reserved)
+# (threads per block, blocks per SM, table records (0: what fits), team blocks (0: by load))
 CANDIDATES = [(b, c, 0, 0) for b in (128, 256, 512, 1024) for c in (1, 2, 4, 8, 16)
               if b * c <= 2048]
 
@@ -79,8 +79,9 @@ def tune_batched(ex, state: dict, reps: int = 2, candidates=None, use_cache: boo
             ex.tune = cached
             return cached, {}
     first = t == 0
-    cur = ex.slot_of(t)
-    prv = ex.slot_of(ex.ref_iteration(t)) if not first else 1 - cur
+    cur, prv, _ = ex.schedule(t)
+    if first:
+        prv = 1 - cur
     args = (ex.rec, ex.pair_off[cur], None if first else ex.ref[prv],
             None if first else ex.pair_off[prv], ex.ref[cur], ex.wire, ex.wire_off, ex.wire_len,
             None if first else ex.recv[prv], None if first else ex.recv_off[prv], ex.recv[cur],

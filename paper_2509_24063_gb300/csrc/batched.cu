@@ -50,6 +50,7 @@ struct BatchArgs {
   u32* team;          // [P * 8] barrier counters of the teams
   U64x2* tsum;        // per-tile totals of team pairs (slot tiles, then decode tiles)
   const u64* tbase;   // [P] first tile total of a team pair
+  u64 wait_ns;        // time limit of one team barrier (global timer)
 };
 
 __device__ __forceinline__ u64 make_item(u64 p, u32 member, u32 g) {
@@ -209,9 +210,11 @@ __device__ __forceinline__ void warp_flush(const uint8_t* wst, uint8_t* gW, u32 
 // Blocks that carry a pair of `size` entries (reference slots + message
 // records + receiver slots): 1, or a team when the pair exceeds the average
 // load of a block (so no single block holds up the end of the launch).  The
-// predictor path keeps one block per pair.
-__device__ __forceinline__ u32 team_size(u64 size, u64 thresh, u32 gmax, int pred) {
+// predictor path keeps one block per pair.  forced > 0 (the schedule's
+// team_blocks) gives every such pair exactly that many blocks.
+__device__ __forceinline__ u32 team_size(u64 size, u64 thresh, u32 gmax, int pred, u32 forced) {
   if (pred || size <= thresh) return 1u;
+  if (forced) return forced;
   const u64 g = ceil_div(size, thresh);
   return (u32)(g < gmax ? g : gmax);
 }
@@ -232,7 +235,7 @@ struct PairFacts {
 };
 
 __device__ __forceinline__ PairFacts pair_facts(const EncArgs& E, const DecArgs& D, u64 p, int mode,
-                                                u64 thresh, u32 gmax, int pred) {
+                                                u64 thresh, u32 gmax, int pred, u32 forced) {
   PairFacts f;
   f.m = E.pair_off[p + 1] - E.pair_off[p];
   f.r_full = E.ref_off ? E.ref_off[p + 1] - E.ref_off[p] : 0;
@@ -240,7 +243,7 @@ __device__ __forceinline__ PairFacts pair_facts(const EncArgs& E, const DecArgs&
   f.r = (f.raw || E.ref_off == nullptr) ? 0 : f.r_full;
   f.rr = D.ref_off ? D.ref_off[p + 1] - D.ref_off[p] : 0;
   f.slab = round16((u64)kHdrBytes + 4 * (f.r_full + f.m) + (u64)kRecBytes * f.m);
-  f.g = team_size(f.r + f.m + f.rr, thresh, gmax, pred);
+  f.g = team_size(f.r + f.m + f.rr, thresh, gmax, pred, forced);
   return f;
 }
 
@@ -253,7 +256,7 @@ __device__ __forceinline__ PairFacts pair_facts(const EncArgs& E, const DecArgs&
 __global__ void __launch_bounds__(1024)
     bat_setup_kernel(EncArgs E, DecArgs D, BatchArgs B, u64 P, int mode,
                      u64* __restrict__ wire_off, u64 wire_cap, u64 rec_cap, u64 recv_cap,
-                     u32* epoch, u32 T, u32 blocks, u32 gmax, u64 min_team, int pred,
+                     u32* epoch, u32 T, u32 blocks, u32 gmax, u32 forced, u64 min_team, int pred,
                      u64* __restrict__ items, u64 items_cap, u64* __restrict__ tbase,
                      u64 tsum_cap, u64* __restrict__ n_items) {
   __shared__ U64x2 sm2[33];
@@ -273,7 +276,7 @@ __global__ void __launch_bounds__(1024)
   for (u64 c = 0; c < P; c += blockDim.x) {
     const u64 p = c + threadIdx.x;
     if (p >= P) continue;
-    const PairFacts f = pair_facts(E, D, p, mode, thresh, gmax, pred);
+    const PairFacts f = pair_facts(E, D, p, mode, thresh, gmax, pred, forced);
     u64* pi = E.info + p * 8;
     pi[PI_R] = f.r;
     pi[PI_M] = f.m;
@@ -291,7 +294,7 @@ __global__ void __launch_bounds__(1024)
   for (u64 c = 0; c < P; c += blockDim.x) {  // block-uniform
     const u64 p = c + threadIdx.x;
     PairFacts f{};
-    if (p < P) f = pair_facts(E, D, p, mode, thresh, gmax, pred);
+    if (p < P) f = pair_facts(E, D, p, mode, thresh, gmax, pred, forced);
     const bool team = p < P && f.g > 1;
     const U64x2 va{p < P ? f.slab : 0, team ? team_tiles(f.r, f.m, f.rr, T) : 0};
     const U64x2 vb{team ? f.g : 0u, (p < P && !team) ? 1u : 0u};
@@ -1271,25 +1274,43 @@ __device__ __forceinline__ void red_release_add(u32* p, u32 v) {
   asm volatile("red.release.gpu.global.add.u32 [%0], %1;" : : "l"(p), "r"(v) : "memory");
 }
 
-constexpr u64 kSpinLimit = 1ull << 25;  // x ~64 ns sleeps: about two seconds
+__device__ __forceinline__ u64 global_ns() {
+  u64 t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 
-// Every member of a team arrives, then waits for the others.  The members
-// were claimed, in list order, by running blocks that wait for nothing else,
-// so the wait ends; past the bound it latches TERA_ETIMEOUT and goes on.
-__device__ __forceinline__ void team_barrier(u32* ctr, u32 g, DevStatus* st) {
+// Backstop on the number of polls of one wait, should the global timer not
+// advance: a poll (an L2 round trip plus a 64 ns sleep) takes far longer than
+// 16 ns, so the time limit always ends the wait first.
+__device__ __forceinline__ u64 spin_cap(u64 limit_ns) { return limit_ns / 16 + 1024; }
+
+// Every member of a team arrives, then waits for the others, for at most
+// limit_ns nanoseconds of the global timer.  The members were claimed, in
+// list order, by running blocks that wait for nothing else, so the wait ends
+// when every member can be resident at once.  Returns false (block-uniform)
+// when it gave up: TERA_ETIMEOUT is latched, and the caller abandons the pair
+// without touching its outputs again.  A member that returns true has seen
+// every member arrive, so everything the team wrote before the barrier is
+// complete.
+__device__ __forceinline__ bool team_barrier(u32* ctr, u32 g, DevStatus* st, u64 limit_ns) {
   __syncthreads();
+  int late = 0;
   if (threadIdx.x == 0) {
     red_release_add(ctr, 1u);
+    const u64 t0 = global_ns();
+    const u64 cap = spin_cap(limit_ns);
     u64 spin = 0;
     while (ld_acquire(ctr) < g) {
-      if (++spin > kSpinLimit) {
+      if (global_ns() - t0 > limit_ns || ++spin > cap) {
         latch(st, TERA_ETIMEOUT);
+        late = 1;
         break;
       }
       __nanosleep(64);
     }
   }
-  __syncthreads();
+  return __syncthreads_or(late) == 0;
 }
 
 // Block sum of two counts (red: 66 words of shared memory).
@@ -1407,9 +1428,9 @@ __device__ __noinline__ void team_pair(const EncArgs& E, const DecArgs& D, const
   u32* ctr = B.team + (u64)p * 8;
   u64* bufs = reinterpret_cast<u64*>(sm);
   for (u64 t = i; t < ceil_div(m, (u64)T * kIlp); t += g) bat_build<T>(E, p, t, epoch);
-  team_barrier(ctr + 0, g, E.st);
+  if (!team_barrier(ctr + 0, g, E.st, B.wait_ns)) return;
   for (u64 t = i; t < ceil_div(r, (u64)T * kIlp); t += g) bat_match_ilp<T>(E, B, p, t, epoch);
-  team_barrier(ctr + 1, g, E.st);
+  if (!team_barrier(ctr + 1, g, E.st, B.wait_ns)) return;
   const u64 nst = ceil_div(r, T);
   const u32 V = new_per_thread(pi[PI_MODE]);
   const u64 ntn = ceil_div(m, (u64)T * V);
@@ -1417,7 +1438,7 @@ __device__ __noinline__ void team_pair(const EncArgs& E, const DecArgs& D, const
   U64x2* nts = ts + nst;
   for (u64 t = i; t < nst; t += g) team_slot_sum<T>(E, p, r, ro, t, ts, red);
   for (u64 t = i; t < ntn; t += g) team_new_sum<T>(E, p, m, V, t, epoch, nts, red);
-  team_barrier(ctr + 2, g, E.st);
+  if (!team_barrier(ctr + 2, g, E.st, B.wait_ns)) return;
   u32 k = 0;
   const SlotPair q = slot_pair(E, B, p);
   for (u64 t = i; t < nst; t += g, ++k) {
@@ -1434,14 +1455,14 @@ __device__ __noinline__ void team_pair(const EncArgs& E, const DecArgs& D, const
     U64x2 run = tiles_prefix<T>(nts, t, red);
     bat_new<T, false>(E, B, p, t, epoch, sm, stage, kStageCap, run, slot_tot, none);
   }
-  team_barrier(ctr + 3, g, E.st);
+  if (!team_barrier(ctr + 3, g, E.st, B.wait_ns)) return;
   const u64 mr = D.recv_off[p + 1] - D.recv_off[p];
   const DecShared h = dec_header<false>(D, p, mr, hs, i == 0);
   const u64 n = h.ok ? h.ns + h.nn : 0;
   const u64 ndt = h.ok ? (n ? ceil_div(n, T) : 1) : 0;
   U64x2* ds = nts + ceil_div(m, T);
   for (u64 t = i; t < ndt; t += g) team_dec_sum<T>(D, p, h, t, ds, red);
-  team_barrier(ctr + 4, g, E.st);
+  if (!team_barrier(ctr + 4, g, E.st, B.wait_ns)) return;
   const DecPair dq = dec_pair(D, p);
   const u32* codes = reinterpret_cast<const u32*>(dq.w8 + kHdrBytes);
   k = 0;
@@ -1654,7 +1675,7 @@ static tera_status batched_impl(
   if (((uintptr_t)rec_arena | (uintptr_t)ref_next | (uintptr_t)wire | (uintptr_t)recv |
        (uintptr_t)(ref_prev ? ref_prev : wire) | (uintptr_t)(recv_prev ? recv_prev : wire)) & 15u)
     return TERA_EINVAL;
-  tera_tune tn = tune ? *tune : tera_tune{256, 4, 0, 0};
+  tera_tune tn = tune ? *tune : tera_tune{256, 4, 0, 0, 0, 0};
   if (enc_pred && enc_pred->params && ((uintptr_t)enc_pred->params & 3u)) return TERA_EINVAL;
   if (tn.block != 128 && tn.block != 256 && tn.block != 512 && tn.block != 1024) return TERA_EINVAL;
   if (tn.ctas_per_sm < 1 || tn.ctas_per_sm > 16 || tn.block * tn.ctas_per_sm > 2048)
@@ -1662,6 +1683,8 @@ static tera_status batched_impl(
   if (tn.table_records < 0 || (tn.table_records > 0 && (tn.table_records < 32 ||
                                                         (tn.table_records & (tn.table_records - 1)))))
     return TERA_EINVAL;
+  if (tn.team_blocks != 0 && (tn.team_blocks < 2 || tn.team_blocks > 1024)) return TERA_EINVAL;
+  if (tn.wait_limit_us < 0 || tn.wait_limit_us > 60000000) return TERA_EINVAL;
   if (tn.reserved != 0) return TERA_EINVAL;
   cudaSetDevice(ctx->device);
   cudaStream_t s = (cudaStream_t)stream;
@@ -1728,6 +1751,7 @@ static tera_status batched_impl(
   B.team = ctx->b_team;
   B.tsum = ctx->b_tsum;
   B.tbase = ctx->b_tbase;
+  B.wait_ns = 1000ull * (u64)(tn.wait_limit_us ? tn.wait_limit_us : 1000000);
 
   if (PR) {
     if ((st = ensure_pred(ctx)) != TERA_OK) return st;
@@ -1760,7 +1784,8 @@ static tera_status batched_impl(
   prof_begin(ctx, s);
   bat_setup_kernel<<<1, 1024, 0, s>>>(E, D, B, P, mode, reinterpret_cast<u64*>(wire_off),
                                       wire_capacity, ctx->cap_records, recv_capacity_units,
-                                      ctx->d_epoch, T, blocks, gmax, min_team, PR ? 1 : 0,
+                                      ctx->d_epoch, T, blocks, gmax, (u32)tn.team_blocks,
+                                      min_team, PR ? 1 : 0,
                                       ctx->b_items, ctx->b_items_cap, ctx->b_tbase,
                                       ctx->b_tsum_cap, ctx->b_scalars + 0);
   if ((st = check_launch(ctx, "bat_setup_kernel", s)) != TERA_OK) return st;

@@ -370,6 +370,22 @@ extern "C" {
 
 const char* tera_version(void) { return "tera-gb300 1.0 (sm_103a)"; }
 
+tera_status tera_ref_schedule(uint64_t t, uint32_t ref_interval, int32_t* out_buf,
+                              int32_t* ref_buf, uint64_t* ref_iteration) {
+  if (ref_interval < 1 || !out_buf) return TERA_EINVAL;
+  const uint64_t K = ref_interval;
+  *out_buf = (int32_t)(((t + K - 1) / K) % 2);  // ceil(t / K) mod 2
+  if (t == 0) {  // no reference yet
+    if (ref_buf) *ref_buf = -1;
+    if (ref_iteration) *ref_iteration = 0;
+    return TERA_OK;
+  }
+  const uint64_t ri = K * ((t - 1) / K);  // the latest multiple of K before t
+  if (ref_buf) *ref_buf = (int32_t)(((ri + K - 1) / K) % 2);
+  if (ref_iteration) *ref_iteration = ri;
+  return TERA_OK;
+}
+
 uint64_t tera_n_pairs(const tera_ctx* ctx) { return ctx ? ctx->n_pairs : 0; }
 
 uint64_t tera_ctx_launches(const tera_ctx* ctx) { return ctx ? ctx->launches : 0; }

@@ -74,7 +74,10 @@ __global__ void __launch_bounds__(1024) dec_setup_kernel(DecArgs A, u64 P, u64 r
   }
   if (threadIdx.x == 0) {
     const_cast<u64*>(A.unit_off)[npr] = ucarry;
-    const bool over = ucarry > units_cap;  // cannot happen: scratch is sized for it
+    // a context's scratch is sized for every tile; the fixed scratch of
+    // tera_delta_decode_noalloc can overflow: TERA_ECAPACITY with no required
+    // capacity recorded (no receive capacity would help)
+    const bool over = ucarry > units_cap;
     if (over) latch(A.st, TERA_ECAPACITY);
     units_total[0] = (abort || over) ? 0 : ucarry;
     units_total[1] = (abort || over) ? 1 : 0;

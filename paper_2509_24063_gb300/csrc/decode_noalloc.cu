@@ -1,21 +1,24 @@
 // tera_delta_decode_noalloc — the decode step with no allocation at all.
 //
 // Some callers cannot allocate device memory at the point where they decode:
-// code running while a stream is being captured into a CUDA graph (cudaMalloc
-// is not allowed there), hosts whose device memory is reserved up front by
-// their own pool so that third-party code may not call cudaMalloc, and
-// real-time loops that forbid allocation after start-up.  They cannot create a
-// tera_ctx either (context creation allocates).  This entry point runs the
-// same decode kernels as tera_delta_decode with every piece of scratch memory
-// — unit layout, per-pair facts, per-unit sums and bases, status word — taken
-// from one file-scope device array of fixed size, so it calls no cudaMalloc,
-// cudaFree or allocating routine.  The caller still passes the inputs and
-// outputs.
+// hosts whose device memory is reserved up front by their own pool, so that
+// third-party code may not call cudaMalloc, and real-time loops that forbid
+// allocation after start-up.  They cannot create a tera_ctx either (context
+// creation allocates).  This entry point runs the same decode kernels as
+// tera_delta_decode with every piece of scratch memory — unit layout, per-pair
+// facts, per-unit sums and bases, status word — taken from one file-scope
+// device array of fixed size, so it calls no cudaMalloc, cudaFree or
+// allocating routine.  The caller still passes the inputs and outputs.
 //
 // The array (kScratchBytes below, about 16.5 MB) exists on every GPU that
 // loads this library, until the process exits.  Every call shares it and it
 // keeps the last call's contents; calls that overlap on the GPU (from two
 // streams or two threads) race on it and must be serialized by the caller.
+//
+// The array's device address is looked up once per device, by the first call
+// made with that device current, and kept for the life of the process; after
+// cudaDeviceReset on that device the kept address is stale, so the library
+// must not be called there again.
 #define TERA_DECODE_KERNELS_ONLY
 #include "decode.cu"
 
@@ -48,7 +51,7 @@ std::mutex g_setup_mutex;
 unsigned char* g_scratch_addr[kMaxDevices] = {nullptr};
 
 // Device address of the scratch array on the current device (looked up once
-// per device, under a lock).
+// per device, under a lock; not looked up again after a device reset).
 tera_status scratch_address(int device, unsigned char** out) {
   if (device < 0 || device >= kMaxDevices) return TERA_EINVAL;
   std::lock_guard<std::mutex> lock(g_setup_mutex);

@@ -22,7 +22,7 @@ from __future__ import annotations
 import torch
 
 from ._lib import MODE_XOR
-from .api import Context, PartitionBuffers
+from .api import Context, PartitionBuffers, ref_schedule
 
 PATHS = ("per_subdomain", "all_pairs", "batched")
 
@@ -81,21 +81,23 @@ class AuraExchange:
             return [(0, self.P)]
         return [(27 * s, 27 * s + 27) for s in range(self.P // 27)]
 
-    def slot_of(self, t: int) -> int:
-        """Buffer of iteration t's outputs: ceil(t / K) mod 2."""
-        return ((t + self.K - 1) // self.K) % 2
+    def schedule(self, t: int):
+        """(output buffer, reference buffer or -1, reference iteration) of
+        iteration t under the reference interval K (tera_ref_schedule)."""
+        return ref_schedule(t, self.K)
 
-    def ref_iteration(self, t: int) -> int:
-        """The iteration whose message is iteration t's reference (t >= 1)."""
-        return self.K * ((t - 1) // self.K)
+    def slot_of(self, t: int) -> int:
+        """Buffer of iteration t's outputs."""
+        return self.schedule(t)[0]
 
     def _launch(self, state: dict, t: int, stream=None):
-        """Enqueue iteration t on the stream (outputs to slot_of(t), reference
-        from the buffers of ref_iteration(t))."""
+        """Enqueue iteration t on the stream (outputs and references in the
+        buffers tera_ref_schedule names)."""
         ctx = self.ctx
         first = t == 0
-        cur = self.slot_of(t)
-        prv = self.slot_of(self.ref_iteration(t)) if not first else 1 - cur
+        cur, prv, _ = self.schedule(t)
+        if first:
+            prv = 1 - cur
         part = self.part
         pair_off = self.pair_off[cur]
         part.pair_off = pair_off  # this iteration's offsets become the next one's reference layout

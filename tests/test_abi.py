@@ -74,3 +74,32 @@ def test_product_never_imports_the_oracle():
                 text = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in text and "from oracle" not in text, f
                 assert "tera_oracle" not in text, f
+
+
+@pytest.mark.parametrize("K", [1, 2, 3, 5])
+def test_reference_schedule_follows_the_interval(libpath, K):
+    """tera_ref_schedule against a direct simulation of the two buffers: the
+    message of iteration 0 and of every multiple of K becomes the reference;
+    an iteration writes into the buffer that does not hold its reference, and
+    a reference iteration's buffer is kept until the next one replaces it."""
+    from paper_2509_24063_gb300.api import ref_schedule
+    holder = {}   # buffer -> iteration whose message it holds
+    latest = None  # latest reference iteration so far
+    for t in range(0, 4 * K + 3):
+        out, refb, ri = ref_schedule(t, K)
+        if t == 0:
+            assert refb == -1
+        else:
+            assert ri == latest and holder[refb] == latest
+            assert out != refb  # the reference is never overwritten while read
+        holder[out] = t
+        if t % K == 0:
+            latest = t
+
+
+def test_reference_schedule_rejects_zero_interval(libpath):
+    from paper_2509_24063_gb300 import _lib
+    lib = _lib.load()
+    ob, rb, ri = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_uint64()
+    assert lib.tera_ref_schedule(3, 0, ctypes.byref(ob), ctypes.byref(rb),
+                                 ctypes.byref(ri)) == _lib.EINVAL

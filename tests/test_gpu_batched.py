@@ -59,6 +59,60 @@ def test_batched_skewed_pairs_carried_by_teams(tera, tune):
     run_chain(tera, wl, 3, path="batched", tune=tune)
 
 
+@pytest.mark.parametrize("tune", [(256, 4, 32, 2), (256, 2, 32, 3), (128, 4, 32, 7),
+                                  (256, 1, 0, 32)])
+def test_batched_forced_team_sizes(tera, tune):
+    # every heavy pair carried by exactly team_blocks blocks: the bytes do not
+    # depend on how a pair's tiles are split among the members
+    wl = Workload("t", 200000, (0.0,) * 3, (400.0, 400.0, 400.0), (2, 2, 2), 20.0, 3,
+                  layout="blobs", n_blobs=2, p_grow=0.1, p_divide=0.02, p_die=0.02, seed=12)
+    run_chain(tera, wl, 3, path="batched", tune=tune)
+
+
+def _two_face_pairs(n=100000):
+    # 2 x 1 x 1 boxes: the two face pairs hold every record (about n/10 each)
+    return Workload("t", n, (0.0,) * 3, (200.0, 100.0, 100.0), (2, 1, 1), 20.0, 2,
+                    p_grow=0.1, p_divide=0.02, p_die=0.02, seed=31)
+
+
+def test_team_wait_runs_out_and_latches_timeout(tera):
+    # teams of 1024 blocks, but the launch has one block per SM: no team can
+    # ever meet.  Each wait gives up after 50 us of the global timer, latches
+    # TERA_ETIMEOUT and abandons its pair; the launch ends, and the context
+    # stays usable (the next iteration with the default schedule is exact).
+    import time
+    wl = _two_face_pairs()
+    states = list(Generator(wl, device="cuda").series(2))
+    ctx = tera.Context(wl.lo, wl.hi, wl.grid, wl.w)
+    ex = tera.AuraExchange(ctx, max_agents=150000, max_records=400000, path="batched",
+                           tune=(256, 1, 32, 1024, 50))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ex.step(states[0])
+    torch.cuda.synchronize()
+    elapsed = time.perf_counter() - t0
+    code, _ = ctx.status(raise_on_error=False)
+    assert code == tera.ETIMEOUT
+    assert elapsed < 5.0
+    ex.tune = None
+    ex.reset()
+    g = oracle.make_grid(wl.lo, wl.hi, wl.grid, wl.w)
+    ref = recv_ref = None
+    for st in states:
+        ex.step(st)
+        ctx.status()
+        res = oracle.exchange_iteration(g, to_numpy(st), ref=ref, recv_ref=recv_ref)
+        compare_iteration(ctx, ex, st, res, ctx.n_pairs)
+        ref, recv_ref = (res["ref_next"], res["pair_off"]), (res["recv"], res["recv_off"])
+    ctx.close()
+
+
+def test_team_members_meet_within_a_short_limit(tera):
+    # the same pairs with teams that can meet (4 blocks each): a 20 ms limit
+    # is never reached, and the bytes are the oracle's
+    run_chain(tera, _two_face_pairs(), 2, path="batched", tune=(256, 1, 32, 4, 20000))
+
+
 def test_graph_replay_matches_oracle(tera):
     wl = Workload("t", 50000, (0.0,) * 3, (200.0, 200.0, 100.0), (2, 2, 1), 20.0, 5,
                   p_grow=0.1, p_divide=0.02, p_die=0.02, seed=6)

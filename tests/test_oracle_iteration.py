@@ -126,3 +126,24 @@ def test_chain_with_predictor_histories_stay_identical(oracle):
         modes += [int(wire[int(wo[q]) + 12]) for q in range(wl.n_pairs) if wl_[q]]
         ref, recv = (nxt, off, hn), (rcv, rvo, rhn)
     assert oracle.MODE_RESIDUAL in modes
+
+
+@pytest.mark.parametrize("threads", [2, 7])
+def test_threaded_iteration_equals_single_threaded(oracle, threads):
+    """The all-cores CPU baseline (agents and pairs spread over threads) gives
+    the single-threaded iteration's outputs byte for byte, over a chain."""
+    from synth import Generator, Workload, to_numpy
+    wl = Workload("t", 30000, (0.0,) * 3, (300.0, 200.0, 200.0), (3, 2, 2), 25.0, 3,
+                  p_grow=0.1, p_divide=0.02, p_die=0.02, seed=9)
+    g = oracle.make_grid(wl.lo, wl.hi, wl.grid, wl.w)
+    prev = None
+    for st in Generator(wl, device="cpu").series(3):
+        soa = to_numpy(st)
+        kw = {} if prev is None else dict(ref=prev[0], recv_ref=prev[1])
+        a = oracle.exchange_iteration(g, soa, **kw)
+        b = oracle.exchange_iteration(g, soa, threads=threads, **kw)
+        assert a["status"] == b["status"] == oracle.OK
+        for k in ("owner", "mask", "pair_count", "pair_off", "pair_idx", "rec", "wire",
+                  "wire_off", "wire_len", "ref_next", "recv", "recv_off"):
+            assert a[k].tobytes() == b[k].tobytes(), k
+        prev = ((a["ref_next"], a["pair_off"]), (a["recv"], a["recv_off"]))
