@@ -174,6 +174,16 @@ tera_status tera_pack(tera_ctx* ctx, const tera_soa* soa, const tera_partition_o
                       uint32_t pair_begin, uint32_t pair_end, uint8_t* rec_arena,
                       uint64_t arena_units, void* stream);
 
+/* tera_pack of every pair, also writing the id column of the packed records:
+ * rec_ids[g] = id (word 0) of record g, g the global record index (pair p's
+ * records are g in [pair_off[p], pair_off[p+1])).  rec_ids (device, 8-byte
+ * aligned, caller-owned) has room for arena_units entries.  The column lets
+ * the batched codec match ids (Sec. 2.3 step B) without reading the 64-byte
+ * records a second time (tera_codec_batched_ids).  No counterpart in the paper. */
+tera_status tera_pack_ids(tera_ctx* ctx, const tera_soa* soa, const tera_partition_out* part,
+                          uint8_t* rec_arena, uint64_t arena_units, uint64_t* rec_ids,
+                          void* stream);
+
 /* Steps a3+a4 (Sec. 2.3 B and C): encode messages [pair_begin, pair_end)
  * against the sender reference (ref_prev laid out with ref_off_prev; both
  * NULL means every reference is empty, as at the first iteration).
@@ -344,6 +354,39 @@ tera_status tera_codec_batched(tera_ctx* ctx, const uint8_t* rec_arena, const ui
                                const uint64_t* recv_off_prev, uint8_t* recv,
                                uint64_t recv_capacity_units, uint64_t* recv_off, int mode,
                                const tera_tune* tune, void* stream);
+
+/* Id columns of the batched codec (no counterpart in the paper).  The match
+ * of Sec. 2.3 (step B) needs the id of every message record and of every
+ * reference slot before any difference can be formed; read from the records
+ * themselves, every 64-byte record is fetched from memory once for its id and
+ * again for the difference.  With these columns (device, 8-byte aligned,
+ * caller-owned) the codec reads the ids from compact arrays instead:
+ *   msg       [E] id of packed record g (as tera_pack_ids writes it);
+ *   ref_prev  [R] ids of the sender reference's records, slot j of pair p at
+ *             ref_off_prev[p] + j (NULL exactly when ref_prev is NULL): the
+ *             ref_next column of the call that wrote that reference;
+ *   ref_next  [E] written: ids of the new sender reference's records (record
+ *             k of pair p at pair_off[p] + k).
+ * Each column must hold the ids of its arena's records (word 0); the codec
+ * trusts them for the match, and a column that disagrees with its records
+ * gives unspecified messages (the decoder rejects a matched slot whose id
+ * word differs). */
+typedef struct {
+  const uint64_t* msg;
+  const uint64_t* ref_prev;
+  uint64_t* ref_next;
+} tera_ids;
+
+/* tera_codec_batched with the id columns above (same arguments and outputs,
+ * same bytes; also writes ids->ref_next). */
+tera_status tera_codec_batched_ids(tera_ctx* ctx, const uint8_t* rec_arena,
+                                   const uint64_t* pair_off, const uint8_t* ref_prev,
+                                   const uint64_t* ref_off_prev, uint8_t* ref_next, uint8_t* wire,
+                                   uint64_t wire_capacity, uint64_t* wire_off, uint64_t* wire_len,
+                                   const uint8_t* recv_prev, const uint64_t* recv_off_prev,
+                                   uint8_t* recv, uint64_t recv_capacity_units, uint64_t* recv_off,
+                                   int mode, const tera_tune* tune, const tera_ids* ids,
+                                   void* stream);
 
 /* tera_codec_batched with the predictor: enc_pred for the sender side (its
  * hist_prev / hist_next travel with ref_prev / ref_next), dec_pred for the

@@ -149,13 +149,35 @@ def axis_edges(grid: Grid, axis: int) -> np.ndarray:
     return e
 
 
-def classify(grid: Grid, x, y, z):
+def classify(grid: Grid, x, y, z, threads: int = 1):
+    """or_classify; threads > 1 classifies contiguous agent ranges on host
+    threads (every agent independently, so the outputs are the same)."""
     x, y, z = (np.ascontiguousarray(a, dtype=np.float64) for a in (x, y, z))
     n = x.shape[0]
     owner = np.zeros(n, dtype=np.int32)
     mask = np.zeros(n, dtype=np.uint32)
-    st = lib().or_classify(C.byref(grid), _p(x), _p(y), _p(z), n, _p(owner), _p(mask))
+    if threads <= 1 or n < 65536:
+        st = lib().or_classify(C.byref(grid), _p(x), _p(y), _p(z), n, _p(owner), _p(mask))
+        return st, owner, mask
+    import concurrent.futures as cf
+    step = -(-n // threads)
+    L = lib()
+
+    def part(a):
+        b = min(n, a + step)
+        return L.or_classify(C.byref(grid), _p(x[a:b]), _p(y[a:b]), _p(z[a:b]), b - a,
+                             _p(owner[a:b]), _p(mask[a:b]))
+    with cf.ThreadPoolExecutor(threads) as ex:
+        sts = list(ex.map(part, range(0, n, step)))
+    st = next((s for s in sts if s != OK), OK)
     return st, owner, mask
+
+
+def _popcount(words) -> int:
+    """Set bits of a uint32 array (how many records the masks give)."""
+    if hasattr(np, "bitwise_count"):
+        return int(np.bitwise_count(words).sum(dtype=np.uint64))
+    return int(np.unpackbits(words.view(np.uint8)).sum())
 
 
 def pair_lists(grid: Grid, owner, mask, idx_capacity=None):
@@ -164,7 +186,7 @@ def pair_lists(grid: Grid, owner, mask, idx_capacity=None):
     cnt = np.zeros(P, dtype=np.uint64)
     off = np.zeros(P + 1, dtype=np.uint64)
     total = int(sum(bin(int(m)).count("1") for m in mask[owner >= 0])) if n < 4096 else \
-        int(np.unpackbits(mask[owner >= 0].view(np.uint8)).sum())
+        _popcount(mask[owner >= 0])
     cap = total if idx_capacity is None else idx_capacity
     idx = np.zeros(max(cap, 1), dtype=np.uint32)
     st = lib().or_pair_lists(C.byref(grid), _p(np.ascontiguousarray(owner)),
@@ -290,7 +312,7 @@ def exchange_iteration(grid: Grid, soa: dict, ref=None, recv_ref=None, class_id=
     cols = soa_cols(soa)
     arr = (C.c_void_p * 7)(*[c.ctypes.data for c in cols])
     st, owner, mask = classify(grid, cols[0], cols[1], cols[2])
-    total = int(np.unpackbits(mask[owner >= 0].view(np.uint8)).sum()) if n else 0
+    total = _popcount(mask[owner >= 0]) if n else 0
     cap = max(total, 1)
     r_tot = 0 if ref is None else int(ref[1][-1])
     owner = np.zeros(n, dtype=np.int32)

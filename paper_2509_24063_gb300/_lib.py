@@ -52,6 +52,10 @@ class Tune(C.Structure):
                 ("team_blocks", C.c_int), ("wait_limit_us", C.c_int), ("reserved", C.c_int)]
 
 
+class Ids(C.Structure):
+    _fields_ = [("msg", C.c_void_p), ("ref_prev", C.c_void_p), ("ref_next", C.c_void_p)]
+
+
 class Predictor(C.Structure):
     _fields_ = [("params", C.c_void_p), ("hist_prev", C.c_void_p), ("hist_next", C.c_void_p),
                 ("samples", C.c_void_p), ("allow_residual", C.c_int)]
@@ -66,6 +70,9 @@ SIGNATURES = {
     "tera_ctx_reserve": (C.c_int, [P, i64, u64]),
     "tera_partition": (C.c_int, [P, C.POINTER(Soa), C.POINTER(PartitionOut), P]),
     "tera_pack": (C.c_int, [P, C.POINTER(Soa), C.POINTER(PartitionOut), u32, u32, P, u64, P]),
+    "tera_pack_ids": (C.c_int, [P, C.POINTER(Soa), C.POINTER(PartitionOut), P, u64, P, P]),
+    "tera_codec_batched_ids": (C.c_int, [P, P, P, P, P, P, P, u64, P, P, P, P, P, u64, P,
+                                         C.c_int, C.POINTER(Tune), C.POINTER(Ids), P]),
     "tera_delta_encode": (C.c_int, [P, P, P, P, P, u32, u32, P, P, u64, P, P, C.c_int, P]),
     "tera_delta_decode": (C.c_int, [P, P, P, P, P, u32, u32, P, u64, P, P]),
     "tera_delta_decode_noalloc": (C.c_int, [P, P, P, P, u64, u32, P, u64, P,

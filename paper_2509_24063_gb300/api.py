@@ -188,6 +188,15 @@ class Context:
         check(self.lib.tera_pack(self.h, C.byref(soa), C.byref(o), pair_begin, pe, _ptr(arena),
                                  arena.numel() // 64, _stream(stream)), "tera_pack")
 
+    def pack_ids(self, state: dict, part: PartitionBuffers, arena: torch.Tensor,
+                 rec_ids: torch.Tensor, stream=None):
+        """tera_pack of every pair plus the records' id column (tera_pack_ids)."""
+        soa = soa_from_state(state)
+        o = part.c_struct()
+        check(self.lib.tera_pack_ids(self.h, C.byref(soa), C.byref(o), _ptr(arena),
+                                     arena.numel() // 64, _ptr(rec_ids), _stream(stream)),
+              "tera_pack_ids")
+
     def delta_encode(self, rec_arena, pair_off, ref_prev, ref_off_prev, ref_next, wire, wire_off,
                      wire_len, mode=_lib.MODE_XOR, pair_begin=0, pair_end=None, stream=None):
         pe = self.n_pairs if pair_end is None else pair_end
@@ -206,9 +215,21 @@ class Context:
 
     def codec_batched(self, rec_arena, pair_off, ref_prev, ref_off_prev, ref_next, wire, wire_off,
                       wire_len, recv_prev, recv_off_prev, recv, recv_off, mode=_lib.MODE_XOR,
-                      tune=None, stream=None):
-        """Encode + decode of every pair in one persistent launch (tera_codec_batched)."""
+                      tune=None, stream=None, ids=None):
+        """Encode + decode of every pair in one persistent launch (tera_codec_batched;
+        with ids = dict(msg, ref_prev, ref_next) of id columns, tera_codec_batched_ids)."""
         t = _tune(tune)
+        if ids is not None:
+            c = _lib.Ids(_ptr(ids["msg"]).value,
+                         None if ids.get("ref_prev") is None else _ptr(ids["ref_prev"]).value,
+                         _ptr(ids["ref_next"]).value)
+            check(self.lib.tera_codec_batched_ids(
+                self.h, _ptr(rec_arena), _ptr(pair_off), _ptr(ref_prev), _ptr(ref_off_prev),
+                _ptr(ref_next), _ptr(wire), wire.numel(), _ptr(wire_off), _ptr(wire_len),
+                _ptr(recv_prev), _ptr(recv_off_prev), _ptr(recv), recv.numel() // 64,
+                _ptr(recv_off), int(mode), C.byref(t) if t is not None else None, C.byref(c),
+                _stream(stream)), "tera_codec_batched_ids")
+            return
         check(self.lib.tera_codec_batched(
             self.h, _ptr(rec_arena), _ptr(pair_off), _ptr(ref_prev), _ptr(ref_off_prev),
             _ptr(ref_next), _ptr(wire), wire.numel(), _ptr(wire_off), _ptr(wire_len),

@@ -78,21 +78,14 @@ def tune_batched(ex, state: dict, reps: int = 2, candidates=None, use_cache: boo
         if cached is not None:
             ex.tune = cached
             return cached, {}
-    first = t == 0
-    cur, prv, _ = ex.schedule(t)
-    if first:
-        prv = 1 - cur
-    args = (ex.rec, ex.pair_off[cur], None if first else ex.ref[prv],
-            None if first else ex.pair_off[prv], ex.ref[cur], ex.wire, ex.wire_off, ex.wire_len,
-            None if first else ex.recv[prv], None if first else ex.recv_off[prv], ex.recv[cur],
-            ex.recv_off[cur])
+    args, kw = ex.codec_args(t)
     results = []
     for cand in (candidates or CANDIDATES):
-        ctx.codec_batched(*args, mode=ex.mode, tune=cand, stream=stream)  # warm
+        ctx.codec_batched(*args, **kw, mode=ex.mode, tune=cand, stream=stream)  # warm
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(reps):
-            ctx.codec_batched(*args, mode=ex.mode, tune=cand, stream=stream)
+            ctx.codec_batched(*args, **kw, mode=ex.mode, tune=cand, stream=stream)
         e1.record(stream)
         e1.synchronize()
         results.append((cand, e0.elapsed_time(e1) / reps))

@@ -417,7 +417,7 @@ __device__ __forceinline__ u32 smem_match(const EncArgs& A, u32 p, u64 r, const 
 #pragma unroll
   for (u32 i = 0; i < kIlp; ++i) {
     const u64 j = (u64)i * T + threadIdx.x;
-    id_next[i] = j < r ? *reinterpret_cast<const u64*>(A.ref + (ro + p + 1 + j) * kRecBytes) : 0;
+    id_next[i] = j < r ? ref_id(A, p, ro, j) : 0;
   }
   for (u64 j0 = 0; j0 < r; j0 += (u64)T * kIlp) {
     u64 id[kIlp];
@@ -425,7 +425,7 @@ __device__ __forceinline__ u32 smem_match(const EncArgs& A, u32 p, u64 r, const 
     for (u32 i = 0; i < kIlp; ++i) {
       id[i] = id_next[i];
       const u64 j = j0 + (u64)(kIlp + i) * T + threadIdx.x;
-      id_next[i] = j < r ? *reinterpret_cast<const u64*>(A.ref + (ro + p + 1 + j) * kRecBytes) : 0;
+      id_next[i] = j < r ? ref_id(A, p, ro, j) : 0;
     }
     // first fingerprint hit of every slot (shared memory only), then the
     // id checks of all of them in flight together
@@ -570,7 +570,7 @@ __device__ __forceinline__ void bat_match_ilp(const EncArgs& A, const BatchArgs&
   for (u32 i = 0; i < kIlp; ++i) {
     const u64 j = tile * T * kIlp + (u64)i * T + threadIdx.x;
     live[i] = j < r;
-    id[i] = live[i] ? *reinterpret_cast<const u64*>(A.ref + (ro + p + 1 + j) * kRecBytes) : 0;
+    id[i] = live[i] ? ref_id(A, p, ro, j) : 0;
   }
 #pragma unroll
   for (u32 i = 0; i < kIlp; ++i) {
@@ -773,7 +773,7 @@ __device__ __forceinline__ void bat_slot(const EncArgs& A, const BatchArgs& B, u
   uint8_t* gW = q.w8 + kHdrBytes + 4 * (r + q.n_new) + pre.a + wstart;
   if (vn) {
     const u64 pos = pre.b + ex.b;
-    store_rec(A.ref_next + (q.g_lo + p + 1 + pos) * kRecBytes, stash_get<T>(stash));
+    store_ref_next(A, p, q.g_lo + pos, stash_get<T>(stash));
     if constexpr (PR) {
       if (A.pr.hist_next) {
         const Rec R = load_rec(A.ref + (ro + p + 1 + j) * kRecBytes);
@@ -887,7 +887,7 @@ __device__ __forceinline__ void bat_new(const EncArgs& A, const BatchArgs& B, u3
         put_word(dst, o, M.w[w], L);
       }
       reinterpret_cast<u32*>(w8 + kHdrBytes)[r + rank] = code;
-      store_rec(A.ref_next + (g_lo + p + 1 + matched + rank) * kRecBytes, M);
+      store_ref_next(A, p, g_lo + matched + rank, M);
       if constexpr (PR) {
         if (A.pr.hist_next)
           store_hist_next(A.pr.hist_next + kHistBytes * (g_lo + matched + rank), nullptr, nullptr);
@@ -956,7 +956,7 @@ __device__ __forceinline__ void bat_new_list(const EncArgs& A, u32 p, const Slot
       code |= L << (4 * w);
     }
     reinterpret_cast<u32*>(q.w8 + kHdrBytes)[r + i] = code;
-    store_rec(A.ref_next + (g_lo + p + 1 + matched + i) * kRecBytes, M);
+    store_ref_next(A, p, g_lo + matched + i, M);
     if constexpr (PR) {
       if (A.pr.hist_next)
         store_hist_next(A.pr.hist_next + kHistBytes * (g_lo + matched + i), nullptr, nullptr);
@@ -1665,10 +1665,17 @@ static tera_status batched_impl(
     uint64_t* wire_off, uint64_t* wire_len, const uint8_t* recv_prev,
     const uint64_t* recv_off_prev, uint8_t* recv, uint64_t recv_capacity_units,
     uint64_t* recv_off, int mode, const tera_tune* tune, const tera_predictor* enc_pred,
-    const tera_predictor* dec_pred, void* stream) {
+    const tera_predictor* dec_pred, const tera_ids* ids, void* stream) {
   if (!ctx || !rec_arena || !pair_off || !ref_next || !wire || !wire_off || !wire_len || !recv ||
       !recv_off)
     return TERA_EINVAL;
+  if (ids) {
+    if (!ids->msg || !ids->ref_next || (ids->ref_prev == nullptr) != (ref_prev == nullptr))
+      return TERA_EINVAL;
+    if (((uintptr_t)ids->msg | (uintptr_t)ids->ref_next |
+         (uintptr_t)(ids->ref_prev ? ids->ref_prev : ids->msg)) & 7u)
+      return TERA_EINVAL;
+  }
   if ((ref_prev == nullptr) != (ref_off_prev == nullptr)) return TERA_EINVAL;
   if ((recv_prev == nullptr) != (recv_off_prev == nullptr)) return TERA_EINVAL;
   if (mode != TERA_MODE_RAW && mode != TERA_MODE_XOR) return TERA_EINVAL;
@@ -1722,6 +1729,11 @@ static tera_status batched_impl(
   E.class_id = ctx->class_id;
   E.st = ctx->d_status;
   E.stats = ctx->d_stats;
+  if (ids) {
+    E.msg_ids = reinterpret_cast<const u64*>(ids->msg);
+    E.ref_ids = reinterpret_cast<const u64*>(ids->ref_prev);
+    E.ref_ids_next = reinterpret_cast<u64*>(ids->ref_next);
+  }
 
   DecArgs D;
   D.wire = wire;
@@ -1809,7 +1821,20 @@ extern "C" tera_status tera_codec_batched(
     uint64_t* recv_off, int mode, const tera_tune* tune, void* stream) {
   return batched_impl(ctx, rec_arena, pair_off, ref_prev, ref_off_prev, ref_next, wire,
                       wire_capacity, wire_off, wire_len, recv_prev, recv_off_prev, recv,
-                      recv_capacity_units, recv_off, mode, tune, nullptr, nullptr, stream);
+                      recv_capacity_units, recv_off, mode, tune, nullptr, nullptr, nullptr,
+                      stream);
+}
+
+extern "C" tera_status tera_codec_batched_ids(
+    tera_ctx* ctx, const uint8_t* rec_arena, const uint64_t* pair_off, const uint8_t* ref_prev,
+    const uint64_t* ref_off_prev, uint8_t* ref_next, uint8_t* wire, uint64_t wire_capacity,
+    uint64_t* wire_off, uint64_t* wire_len, const uint8_t* recv_prev,
+    const uint64_t* recv_off_prev, uint8_t* recv, uint64_t recv_capacity_units,
+    uint64_t* recv_off, int mode, const tera_tune* tune, const tera_ids* ids, void* stream) {
+  if (!ids) return TERA_EINVAL;
+  return batched_impl(ctx, rec_arena, pair_off, ref_prev, ref_off_prev, ref_next, wire,
+                      wire_capacity, wire_off, wire_len, recv_prev, recv_off_prev, recv,
+                      recv_capacity_units, recv_off, mode, tune, nullptr, nullptr, ids, stream);
 }
 
 extern "C" tera_status tera_codec_batched_pred(
@@ -1821,5 +1846,6 @@ extern "C" tera_status tera_codec_batched_pred(
     const tera_predictor* dec_pred, void* stream) {
   return batched_impl(ctx, rec_arena, pair_off, ref_prev, ref_off_prev, ref_next, wire,
                       wire_capacity, wire_off, wire_len, recv_prev, recv_off_prev, recv,
-                      recv_capacity_units, recv_off, mode, tune, enc_pred, dec_pred, stream);
+                      recv_capacity_units, recv_off, mode, tune, enc_pred, dec_pred, nullptr,
+                      stream);
 }

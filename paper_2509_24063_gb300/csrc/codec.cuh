@@ -105,6 +105,12 @@ struct EncArgs {
   DevStatus* st;
   DevStats* stats;
   PredArgs pr{};
+  // optional id columns (batched path): ids of the packed records by global
+  // record index, of the sender reference's slots (index ref_off[p] + j), and
+  // of the new sender reference (written, index pair_off[p] + position)
+  const u64* msg_ids = nullptr;
+  const u64* ref_ids = nullptr;
+  u64* ref_ids_next = nullptr;
 };
 
 struct DecArgs {
@@ -370,10 +376,25 @@ __device__ __forceinline__ u32 seg_lookup(const U64x2* __restrict__ seg, u32 epo
   return seg_lookup_from<CG>(seg, epoch, seg_base(g_lo, p), size, g_lo, id, seg_start(id, size));
 }
 
-// Id of message record g (global record index) of pair p: word 0 of the
-// record in the packed arena.
+// Id of message record g (global record index) of pair p: from the id
+// column when there is one, else word 0 of the record in the packed arena.
 __device__ __forceinline__ u64 msg_id(const EncArgs& A, u32 p, u64 g) {
+  if (A.msg_ids) return A.msg_ids[g];
   return *reinterpret_cast<const u64*>(A.rec + (g + p + 1) * kRecBytes);
+}
+
+// Id of slot j of pair p's sender reference (ro = ref_off[p]): from the id
+// column when there is one, else word 0 of the reference record.
+__device__ __forceinline__ u64 ref_id(const EncArgs& A, u32 p, u64 ro, u64 j) {
+  if (A.ref_ids) return A.ref_ids[ro + j];
+  return *reinterpret_cast<const u64*>(A.ref + (ro + p + 1 + j) * kRecBytes);
+}
+
+// A record of the new sender reference at global index g (pair p), and its
+// id in the id column when there is one.
+__device__ __forceinline__ void store_ref_next(const EncArgs& A, u32 p, u64 g, const Rec& R) {
+  store_rec(A.ref_next + (g + p + 1) * kRecBytes, R);
+  if (A.ref_ids_next) A.ref_ids_next[g] = R.w[0];
 }
 
 // ---------------- encode ----------------

@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(256)
     pack_entries_kernel(SoaPtrs soa, const u32* __restrict__ ent_key,
                         const u32* __restrict__ ent_agent, const u32* __restrict__ ent_dest,
                         const u64* __restrict__ pair_off, u64 P, uint8_t* __restrict__ arena,
-                        u64 arena_units, u32 class_id, DevStatus* st) {
+                        u64 arena_units, u32 class_id, DevStatus* st, u64* __restrict__ rec_ids) {
   const u64 E = pair_off[P];
   if (E + P > arena_units) {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -102,6 +102,7 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
     for (int w = 0; w < 8; ++w) R.w[w] = soa.col[w][a];
     store_rec(arena + (g + p + 1) * kRecBytes, R);
+    if (rec_ids) rec_ids[g] = R.w[0];
   }
 }
 
@@ -116,7 +117,8 @@ __global__ void __launch_bounds__(kClassifyThreads)
     pack_runs_kernel(SoaPtrs soa, u64 n, const int* __restrict__ owner,
                      const u32* __restrict__ mask, const u64* __restrict__ run_base, u64 n_runs,
                      const u32* __restrict__ ent_dest, const u64* __restrict__ pair_off, u64 P,
-                     uint8_t* __restrict__ arena, u64 arena_units, u32 class_id, DevStatus* st) {
+                     uint8_t* __restrict__ arena, u64 arena_units, u32 class_id, DevStatus* st,
+                     u64* __restrict__ rec_ids) {
   const u64 E = pair_off[P];
   if (E + P > arena_units) {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -179,7 +181,9 @@ __global__ void __launch_bounds__(kClassifyThreads)
       for (int w = 0; w < 8; ++w) R.w[w] = v[w][q];
       for (u32 mm = m[q]; mm; mm &= mm - 1) {
         const u64 p = (u64)o[q] * 27u + (u64)(__ffs(mm) - 1);
-        store_rec(arena + ((u64)ent_dest[e] + p + 1) * kRecBytes, R);
+        const u64 g = ent_dest[e];
+        store_rec(arena + (g + p + 1) * kRecBytes, R);
+        if (rec_ids) rec_ids[g] = R.w[0];
         ++e;
       }
     }
@@ -188,9 +192,9 @@ __global__ void __launch_bounds__(kClassifyThreads)
 
 }  // namespace
 
-extern "C" tera_status tera_pack(tera_ctx* ctx, const tera_soa* soa, const tera_partition_out* part,
-                                 uint32_t pair_begin, uint32_t pair_end, uint8_t* rec_arena,
-                                 uint64_t arena_units, void* stream) {
+static tera_status pack_impl(tera_ctx* ctx, const tera_soa* soa, const tera_partition_out* part,
+                             uint32_t pair_begin, uint32_t pair_end, uint8_t* rec_arena,
+                             uint64_t arena_units, uint64_t* rec_ids, void* stream) {
   if (!ctx || !soa || !part || !rec_arena) return TERA_EINVAL;
   if (pair_begin > pair_end || pair_end > ctx->n_pairs) return TERA_EINVAL;
   if (!part->pair_off || (!part->pair_idx && part->idx_capacity > 0)) return TERA_EINVAL;
@@ -228,7 +232,7 @@ extern "C" tera_status tera_pack(tera_ctx* ctx, const tera_soa* soa, const tera_
     pack_runs_kernel<<<(unsigned)blocks, kClassifyThreads, 0, s>>>(
         p, n, part->owner, part->mask, ctx->tile_base, runs, ctx->ent_dest,
         reinterpret_cast<const u64*>(part->pair_off), ctx->n_pairs, rec_arena, arena_units,
-        ctx->class_id, ctx->d_status);
+        ctx->class_id, ctx->d_status, reinterpret_cast<u64*>(rec_ids));
     return check_launch(ctx, "pack_runs_kernel", s);
   }
   if (pair_begin == 0 && pair_end == ctx->n_pairs) {
@@ -236,12 +240,27 @@ extern "C" tera_status tera_pack(tera_ctx* ctx, const tera_soa* soa, const tera_
     pack_entries_kernel<<<(unsigned)grid_for(ctx, 8), 256, 0, s>>>(
         p, ctx->keys_a, ctx->ent_agent, ctx->ent_dest,
         reinterpret_cast<const u64*>(part->pair_off), ctx->n_pairs, rec_arena, arena_units,
-        ctx->class_id, ctx->d_status);
+        ctx->class_id, ctx->d_status, reinterpret_cast<u64*>(rec_ids));
     return check_launch(ctx, "pack_entries_kernel", s);
   }
+  if (rec_ids) return TERA_EINVAL;  // the id column is written for all pairs only
   prof_begin(ctx, s);
   pack_kernel<<<blocks, 256, 0, s>>>(p, part->pair_idx, reinterpret_cast<const u64*>(part->pair_off),
                                      ctx->rec_pair, pair_begin, pair_end, rec_arena, arena_units,
                                      ctx->class_id, ctx->d_status);
   return check_launch(ctx, "pack_kernel", s);
+}
+
+extern "C" tera_status tera_pack(tera_ctx* ctx, const tera_soa* soa, const tera_partition_out* part,
+                                 uint32_t pair_begin, uint32_t pair_end, uint8_t* rec_arena,
+                                 uint64_t arena_units, void* stream) {
+  return pack_impl(ctx, soa, part, pair_begin, pair_end, rec_arena, arena_units, nullptr, stream);
+}
+
+extern "C" tera_status tera_pack_ids(tera_ctx* ctx, const tera_soa* soa,
+                                     const tera_partition_out* part, uint8_t* rec_arena,
+                                     uint64_t arena_units, uint64_t* rec_ids, void* stream) {
+  if (!ctx || !rec_ids || ((uintptr_t)rec_ids & 7u)) return TERA_EINVAL;
+  return pack_impl(ctx, soa, part, 0, (uint32_t)ctx->n_pairs, rec_arena, arena_units, rec_ids,
+                   stream);
 }

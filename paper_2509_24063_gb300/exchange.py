@@ -31,7 +31,7 @@ class AuraExchange:
     def __init__(self, ctx: Context, max_agents: int, max_records: int, mode: int = MODE_XOR,
                  per_subdomain: bool = False, path: str | None = None, tune=None,
                  predictor: bool = False, params=None, allow_residual: bool = True,
-                 ref_interval: int = 1):
+                 ref_interval: int = 1, id_columns: bool = True):
         self.ctx = ctx
         self.mode = mode
         if ref_interval < 1:
@@ -56,6 +56,14 @@ class AuraExchange:
         self.ref = [torch.empty(units * 64, **u8), torch.empty(units * 64, **u8)]
         self.recv = [torch.empty(units * 64, **u8), torch.empty(units * 64, **u8)]
         self.recv_off = [torch.zeros(P + 1, **i64), torch.zeros(P + 1, **i64)]
+        # id columns of the packed records and of both sender references (the
+        # batched codec matches ids from them instead of re-reading records)
+        self.id_columns = bool(id_columns) and self.path == "batched" and not (
+            predictor or params is not None)
+        if self.id_columns:
+            self.rec_ids = torch.empty(units, dtype=torch.int64, device=dev)
+            self.ref_ids = [torch.empty(units, dtype=torch.int64, device=dev),
+                            torch.empty(units, dtype=torch.int64, device=dev)]
         self.wire_cap = 80 * P + 72 * max_records + 64
         self.wire = torch.empty(self.wire_cap, **u8)
         self.wire_off = torch.zeros(P + 1, **i64)
@@ -106,8 +114,11 @@ class AuraExchange:
         ref_off_prev = None if first else self.pair_off[prv]
         recv_prev = None if first else self.recv[prv]
         recv_off_prev = None if first else self.recv_off[prv]
-        for (a, b) in self.ranges():
-            ctx.pack(state, part, self.rec, a, b, stream)
+        if self.id_columns:
+            ctx.pack_ids(state, part, self.rec, self.rec_ids, stream)
+        else:
+            for (a, b) in self.ranges():
+                ctx.pack(state, part, self.rec, a, b, stream)
         if self.predictor:
             enc = dict(params=self.params, hist_prev=None if first else self.hist[prv],
                        hist_next=self.hist[cur], samples=self.samples,
@@ -129,9 +140,8 @@ class AuraExchange:
                                       self.recv[cur], self.recv_off[cur], dec, a, b, stream)
             return
         if self.path == "batched":
-            ctx.codec_batched(self.rec, pair_off, ref_prev, ref_off_prev, self.ref[cur], self.wire,
-                              self.wire_off, self.wire_len, recv_prev, recv_off_prev,
-                              self.recv[cur], self.recv_off[cur], self.mode, self.tune, stream)
+            args, kw = self.codec_args(t)
+            ctx.codec_batched(*args, **kw, mode=self.mode, tune=self.tune, stream=stream)
             return
         for (a, b) in self.ranges():
             ctx.delta_encode(self.rec, pair_off, ref_prev, ref_off_prev, self.ref[cur],
@@ -139,6 +149,21 @@ class AuraExchange:
         for (a, b) in self.ranges():
             ctx.delta_decode(self.wire, self.wire_off, recv_prev, recv_off_prev, self.recv[cur],
                              self.recv_off[cur], a, b, stream)
+
+    def codec_args(self, t: int):
+        """Positional and keyword arguments of the batched codec of iteration t
+        (buffers from the reference schedule), without mode, tune and stream."""
+        cur, prv, _ = self.schedule(t)
+        first = t == 0
+        args = (self.rec, self.pair_off[cur], None if first else self.ref[prv],
+                None if first else self.pair_off[prv], self.ref[cur], self.wire, self.wire_off,
+                self.wire_len, None if first else self.recv[prv],
+                None if first else self.recv_off[prv], self.recv[cur], self.recv_off[cur])
+        kw = {}
+        if self.id_columns:
+            kw["ids"] = dict(msg=self.rec_ids, ref_prev=None if first else self.ref_ids[prv],
+                             ref_next=self.ref_ids[cur])
+        return args, kw
 
     def step(self, state: dict, stream=None):
         """Classify, pack, encode and decode every pair for one iteration."""

@@ -47,12 +47,15 @@ class Migration:
                                          _ptr(self.inbox_off), C.byref(sn), _ptr(box_off_next),
                                          _stream(stream)), "tera_migrate_send")
 
-    def recv(self, nxt: dict, box_off_next, stream=None):
-        """Deserialize every inbox into the next state after its box's stayers."""
+    def recv(self, nxt: dict, box_off_next, stream=None, arena=None, inbox_off=None):
+        """Deserialize every inbox into the next state after its box's stayers
+        (from this object's arena, or from another inbox arena and offsets)."""
         sn = _soa(nxt)
-        check(self.lib.tera_migrate_recv(self.ctx.h, _ptr(self.arena), self.arena_units,
-                                         _ptr(self.inbox_off), _ptr(box_off_next), C.byref(sn),
-                                         _stream(stream)), "tera_migrate_recv")
+        a = self.arena if arena is None else arena
+        o = self.inbox_off if inbox_off is None else inbox_off
+        check(self.lib.tera_migrate_recv(self.ctx.h, _ptr(a), a.numel() // 64, _ptr(o),
+                                         _ptr(box_off_next), C.byref(sn), _stream(stream)),
+              "tera_migrate_recv")
 
     def step(self, prev: dict, box_off_prev, nxt: dict | None = None, box_off_next=None,
              stream=None):

@@ -32,6 +32,36 @@ def test_batched_skewed_blobs(tera):
     run_chain(tera, scaled(WORKLOADS["blobs_16m"], 1 << 20), 3, path="batched")
 
 
+@pytest.mark.parametrize("tune", [None, (256, 4, 32, 0), (512, 2, 0, 0)])
+def test_batched_without_id_columns(tera, tune):
+    # ids read from the records themselves (tera_codec_batched): same bytes
+    wl = Workload("t", 60000, (0.0,) * 3, (300.0, 200.0, 200.0), (3, 2, 2), 25.0, 3,
+                  p_grow=0.1, p_divide=0.02, p_die=0.02, seed=5)
+    run_chain(tera, wl, 3, path="batched", tune=tune, id_columns=False)
+
+
+def test_id_columns_hold_the_record_ids(tera):
+    # tera_pack_ids' column is word 0 of every packed record, and the codec's
+    # ref_next column is word 0 of every record of the new sender reference
+    wl = Workload("t", 40000, (0.0,) * 3, (300.0, 200.0, 200.0), (3, 2, 2), 25.0, 3,
+                  p_grow=0.1, p_divide=0.02, p_die=0.02, seed=8)
+    ctx = tera.Context(wl.lo, wl.hi, wl.grid, wl.w)
+    ex = tera.AuraExchange(ctx, max_agents=60000, max_records=200000, path="batched")
+    P = ctx.n_pairs
+    for st in Generator(wl, device="cuda").series(3):
+        ex.step(st)
+        ctx.status()
+        off = u64(ex.pair_off[ex.last])
+        E = int(off[-1])
+        recs = ex.rec[:(E + P) * 64].cpu().numpy().view(np.uint64).reshape(-1, 8)
+        sref = ex.ref[ex.last][:(E + P) * 64].cpu().numpy().view(np.uint64).reshape(-1, 8)
+        units = np.concatenate([np.arange(int(off[p]) + p + 1, int(off[p + 1]) + p + 1)
+                                for p in range(P)]).astype(np.int64)
+        np.testing.assert_array_equal(u64(ex.rec_ids[:E]), recs[units, 0])
+        np.testing.assert_array_equal(u64(ex.ref_ids[ex.last][:E]), sref[units, 0])
+    ctx.close()
+
+
 @pytest.mark.parametrize("n", [0, 1, 3, 2049, 70001])
 def test_batched_ragged_sizes(tera, n):
     wl = Workload("t", n, (0.0,) * 3, (90.0, 60.0, 60.0), (3, 2, 2), 12.0, 3,

@@ -62,13 +62,14 @@ def compare_iteration(ctx, ex, st, res, P):
 
 
 def run_chain(tera, wl, iters, per_subdomain=False, max_records=None, device="cuda",
-              path=None, tune=None):
+              path=None, tune=None, id_columns=True):
     gen = Generator(wl, device=device)
     ctx = tera.Context(wl.lo, wl.hi, wl.grid, wl.w, periodic=wl.periodic)
     states = list(gen.series(iters))
     nmax = max(int(s["x"].shape[0]) for s in states)
     ex = tera.AuraExchange(ctx, max_agents=nmax, max_records=max_records or 4 * nmax + 1024,
-                           per_subdomain=per_subdomain, path=path, tune=tune)
+                           per_subdomain=per_subdomain, path=path, tune=tune,
+                           id_columns=id_columns)
     g = oracle.make_grid(wl.lo, wl.hi, wl.grid, wl.w, wl.periodic)
     ref = recv_ref = None
     stats = []

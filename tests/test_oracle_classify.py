@@ -275,3 +275,16 @@ def test_grid_check_periodic(oracle, n, periodic, reserved, ok):
     g = oracle.make_grid((0, 0, 0), (30, 30, 30), n, 1.0, periodic)
     g.reserved = reserved
     assert (oracle.grid_check(g) == oracle.OK) == ok
+
+
+def test_threaded_classification_equals_single_threaded(oracle):
+    rng = np.random.default_rng(4)
+    g = oracle.make_grid((0, 0, 0), (100, 80, 60), (5, 4, 3), 6.0)
+    n = 300001
+    x, y, z = rng.uniform(0, 100, n), rng.uniform(0, 80, n), rng.uniform(0, 60, n)
+    x[17] = np.nan  # an agent outside the domain, in the first range
+    a = oracle.classify(g, x, y, z)
+    b = oracle.classify(g, x, y, z, threads=6)
+    assert a[0] == b[0] == oracle.EDOMAIN
+    np.testing.assert_array_equal(a[1], b[1])
+    np.testing.assert_array_equal(a[2], b[2])
