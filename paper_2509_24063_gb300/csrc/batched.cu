@@ -209,11 +209,12 @@ __device__ __forceinline__ void warp_flush(const uint8_t* wst, uint8_t* gW, u32 
 
 // Blocks that carry a pair of `size` entries (reference slots + message
 // records + receiver slots): 1, or a team when the pair exceeds the average
-// load of a block (so no single block holds up the end of the launch).  The
-// predictor path keeps one block per pair.  forced > 0 (the schedule's
-// team_blocks) gives every such pair exactly that many blocks.
+// load of a block (so no single block holds up the end of the launch).
+// forced > 0 (the schedule's team_blocks) gives every such pair exactly that
+// many blocks.
 __device__ __forceinline__ u32 team_size(u64 size, u64 thresh, u32 gmax, int pred, u32 forced) {
-  if (pred || size <= thresh) return 1u;
+  (void)pred;
+  if (size <= thresh) return 1u;
   if (forced) return forced;
   const u64 g = ceil_div(size, thresh);
   return (u32)(g < gmax ? g : gmax);
@@ -1351,10 +1352,12 @@ __device__ __forceinline__ U64x2 tiles_prefix(const U64x2* ts, u64 t, u64* red) 
   return block_sum2(a, b, red);
 }
 
-// Totals (payload bytes, matched) of one slot tile.
-template <int T>
-__device__ __forceinline__ void team_slot_sum(const EncArgs& A, u32 p, u64 r, u64 ro, u64 tile,
-                                              U64x2* ts, u64* red) {
+// Totals (payload bytes, matched) of one slot tile: the bytes bat_slot
+// writes (XOR difference, or with the predictor in residual mode the
+// residual on the position words of each predictable slot).
+template <int T, bool PR>
+__device__ __forceinline__ void team_slot_sum(const EncArgs& A, const BatchArgs& B, u32 p, u64 r,
+                                              u64 ro, u64 tile, U64x2* ts, u64* red) {
   const u64 j = tile * T + threadIdx.x;
   u64 b = 0, f = 0;
   if (j < r) {
@@ -1362,8 +1365,20 @@ __device__ __forceinline__ void team_slot_sum(const EncArgs& A, u32 p, u64 r, u6
     if (g != kNoMatch) {
       const Rec R = load_rec(A.ref + (ro + p + 1 + j) * kRecBytes);
       const Rec M = load_rec(A.rec + ((u64)g + p + 1) * kRecBytes);
+      Rec d;
 #pragma unroll
-      for (int w = 0; w < 8; ++w) b += sig_bytes(R.w[w] ^ M.w[w]);
+      for (int w = 0; w < 8; ++w) d.w[w] = R.w[w] ^ M.w[w];
+      if constexpr (PR) {
+        if (pair_mode<PR>(A, B, p) == kModeResidual) {
+          const u64* ps = A.pr.pscr + 4 * (ro + j);
+          if (__ldcg(ps + 3)) {
+#pragma unroll
+            for (int a = 0; a < 3; ++a) d.w[1 + a] = zigzag(M.w[1 + a] - __ldcg(ps + a));
+          }
+        }
+      }
+#pragma unroll
+      for (int w = 0; w < 8; ++w) b += sig_bytes(d.w[w]);
       f = 1;
     }
   }
@@ -1414,29 +1429,45 @@ __device__ __forceinline__ void team_dec_sum(const DecArgs& A, u32 p, const DecS
 }
 
 // Member i of a team of g blocks carries its share of pair p's tiles through
-// every step (global hash segments; no predictor).  Team barriers separate
-// the steps; the payload positions of a member's tiles come from the sums of
-// all tile totals before them (written in a first pass over the tiles).
-template <int T>
+// every step (global hash segments).  Team barriers separate the steps; the
+// payload positions of a member's tiles come from the sums of all tile totals
+// before them (written in a first pass over the tiles).  With the predictor,
+// both sides' cell counts are taken with the index (before the first
+// barrier), the match makes the predictions and the residual sizes, and the
+// message mode is read once the match is complete.
+template <int T, bool PR>
 __device__ __noinline__ void team_pair(const EncArgs& E, const DecArgs& D, const BatchArgs& B,
                                           u32 p, u32 i, u32 g, u32 epoch, U64x2* sm, u64* red,
-                                          uint8_t* stage, ulonglong2* stash, DecShared* hs) {
+                                          uint8_t* stage, ulonglong2* stash, DecShared* hs,
+                                          const float* sW) {
   constexpr u32 kStageCap = (u32)T * kRecBytes + 48;
   const u64* pi = E.info + (u64)p * 8;
   const u64 r = pi[PI_R], m = pi[PI_M];
   const u64 ro = E.ref_off ? E.ref_off[p] : 0;
   u32* ctr = B.team + (u64)p * 8;
   u64* bufs = reinterpret_cast<u64*>(sm);
-  for (u64 t = i; t < ceil_div(m, (u64)T * kIlp); t += g) bat_build<T>(E, p, t, epoch);
-  if (!team_barrier(ctr + 0, g, E.st, B.wait_ns)) return;
-  for (u64 t = i; t < ceil_div(r, (u64)T * kIlp); t += g) bat_match_ilp<T>(E, B, p, t, epoch);
-  if (!team_barrier(ctr + 1, g, E.st, B.wait_ns)) return;
   const u64 nst = ceil_div(r, T);
+  for (u64 t = i; t < ceil_div(m, (u64)T * kIlp); t += g) bat_build<T>(E, p, t, epoch);
+  if constexpr (PR) {
+    if (E.pr.hist)
+      for (u64 t = i; t < nst; t += g) cells_unit(E.pr, E.ref, E.ref_off, p, t, r, T);
+    if (D.pr.hist) {
+      const u64 rr = D.ref_off[p + 1] - D.ref_off[p];
+      for (u64 t = i; t < ceil_div(rr, T); t += g) cells_unit(D.pr, D.ref, D.ref_off, p, t, rr, T);
+    }
+  }
+  if (!team_barrier(ctr + 0, g, E.st, B.wait_ns)) return;
+  if constexpr (PR) {
+    for (u64 t = i; t < nst; t += g) bat_match<T, PR>(E, B, p, t, epoch, sm, sW);
+  } else {
+    for (u64 t = i; t < ceil_div(r, (u64)T * kIlp); t += g) bat_match_ilp<T>(E, B, p, t, epoch);
+  }
+  if (!team_barrier(ctr + 1, g, E.st, B.wait_ns)) return;
   const u32 V = new_per_thread(pi[PI_MODE]);
   const u64 ntn = ceil_div(m, (u64)T * V);
   U64x2* ts = B.tsum + B.tbase[p];
   U64x2* nts = ts + nst;
-  for (u64 t = i; t < nst; t += g) team_slot_sum<T>(E, p, r, ro, t, ts, red);
+  for (u64 t = i; t < nst; t += g) team_slot_sum<T, PR>(E, B, p, r, ro, t, ts, red);
   for (u64 t = i; t < ntn; t += g) team_new_sum<T>(E, p, m, V, t, epoch, nts, red);
   if (!team_barrier(ctr + 2, g, E.st, B.wait_ns)) return;
   u32 k = 0;
@@ -1445,7 +1476,7 @@ __device__ __noinline__ void team_pair(const EncArgs& E, const DecArgs& D, const
     U64x2 run = tiles_prefix<T>(ts, t, red);
     const u64 j = t * T + threadIdx.x;
     const u32 src = j < r ? __ldcg(E.slot_src + ro + j) : kNoMatch;
-    bat_slot<T, false>(E, B, p, q, t, src, bufs + 33 * (k & 1), stage, stash, run);
+    bat_slot<T, PR>(E, B, p, q, t, src, bufs + 33 * (k & 1), stage, stash, run);
   }
   __syncthreads();
   // the new records (the member with the last new tile writes the header)
@@ -1453,11 +1484,11 @@ __device__ __noinline__ void team_pair(const EncArgs& E, const DecArgs& D, const
   const SmemTable none{nullptr, 0u, nullptr};
   for (u64 t = i; t < (ntn ? ntn : 1); t += g) {
     U64x2 run = tiles_prefix<T>(nts, t, red);
-    bat_new<T, false>(E, B, p, t, epoch, sm, stage, kStageCap, run, slot_tot, none);
+    bat_new<T, PR>(E, B, p, t, epoch, sm, stage, kStageCap, run, slot_tot, none);
   }
   if (!team_barrier(ctr + 3, g, E.st, B.wait_ns)) return;
   const u64 mr = D.recv_off[p + 1] - D.recv_off[p];
-  const DecShared h = dec_header<false>(D, p, mr, hs, i == 0);
+  const DecShared h = dec_header<PR>(D, p, mr, hs, i == 0);
   const u64 n = h.ok ? h.ns + h.nn : 0;
   const u64 ndt = h.ok ? (n ? ceil_div(n, T) : 1) : 0;
   U64x2* ds = nts + ceil_div(m, T);
@@ -1470,8 +1501,7 @@ __device__ __noinline__ void team_pair(const EncArgs& E, const DecArgs& D, const
     U64x2 run = tiles_prefix<T>(ds, t, red);
     const u64 e = t * T + threadIdx.x;
     const u32 c = e < n ? __ldcg(codes + e) : 0u;
-    bat_dec_tile<T, false>(D, B, p, dq, t, c, h, mr, bufs + 33 * (k & 1), stage, stash, run,
-                           nullptr);
+    bat_dec_tile<T, PR>(D, B, p, dq, t, c, h, mr, bufs + 33 * (k & 1), stage, stash, run, sW);
   }
   __syncthreads();
 }
@@ -1536,9 +1566,8 @@ __global__ void __launch_bounds__(T, (1024 / T) > 0 ? (1024 / T) : 1)
     const u32 p = (u32)(it >> 32);
     const u32 g = (u32)it & 0xFFFFu;
     if (g > 1) {
-      if constexpr (!PR)
-        team_pair<T>(E, D, B, p, (u32)(it >> 16) & 0xFFFFu, g, epoch, sm, red, stage, stash,
-                     &hs);
+      team_pair<T, PR>(E, D, B, p, (u32)(it >> 16) & 0xFFFFu, g, epoch, sm, red, stage, stash,
+                       &hs, sW);
       continue;
     }
     const u64* pi = E.info + (u64)p * 8;

@@ -50,14 +50,14 @@ def test_gradient_matches_oracle(tera):
     ctx.close()
 
 
-def run_pred_chain(tera, wl, params, path):
+def run_pred_chain(tera, wl, params, path, tune=None):
     gen = Generator(wl, device="cuda")
     states = list(gen.series(wl.iterations))
     nmax = max(int(s["x"].shape[0]) for s in states)
     ctx = tera.Context(wl.lo, wl.hi, wl.grid, wl.w)
     pt = torch.from_numpy(params).cuda()
     ex = tera.AuraExchange(ctx, max_agents=nmax, max_records=4 * nmax + 1024, path=path,
-                           params=pt)
+                           params=pt, tune=tune)
     g = oracle.make_grid(wl.lo, wl.hi, wl.grid, wl.w)
     ref = recv = None
     modes = []
@@ -102,6 +102,16 @@ def run_pred_chain(tera, wl, params, path):
 def test_residual_codec_matches_oracle_velocity_net(tera, path):
     modes = run_pred_chain(tera, drift(), velocity_network(), path)
     assert oracle.MODE_RESIDUAL in modes and oracle.MODE_XOR in modes
+
+
+@pytest.mark.parametrize("tune", [(256, 4, 0, 2), (128, 4, 0, 5), (256, 2, 0, 0)])
+def test_residual_codec_carried_by_teams(tera, tune):
+    # the predictor path with its heavy pairs carried by teams of blocks
+    # (forced sizes, and sized by load): same bytes and histories as the oracle
+    wl = Workload("drift", 150000, (0.0,) * 3, (600.0, 600.0, 300.0), (2, 2, 2), 30.0, 5,
+                  layout="blobs", n_blobs=3, p_move=1.0, persistent=True, seed=77)
+    modes = run_pred_chain(tera, wl, velocity_network(), "batched", tune=tune)
+    assert oracle.MODE_RESIDUAL in modes
 
 
 @pytest.mark.parametrize("path", ["all_pairs", "batched"])
