@@ -503,6 +503,9 @@ def main():
                          "time and compare bytes/agent against plain XOR on fresh iterations")
     ap.add_argument("--migration", action="store_true",
                     help="agent migration of the box-major state instead of the aura exchange")
+    ap.add_argument("--compare-paths", action="store_true",
+                    help="agents/s of the per-subdomain, all-pairs and batched paths on the same "
+                         "states (one JSON line)")
     ap.add_argument("--train-iters", type=int, default=200)
     ap.add_argument("--eval-iters", type=int, default=20)
     args = ap.parse_args()
@@ -514,6 +517,8 @@ def main():
         return run_predictor(args)
     if args.migration:
         return run_migration(args)
+    if args.compare_paths:
+        return run_compare_paths(args)
 
     import numpy as np
     import torch
@@ -784,6 +789,77 @@ def run_predictor(args):
     }
     print(json.dumps(line))
     ctx.close()
+    return 0
+
+
+def run_compare_paths(args):
+    """The three paths of the exchange on the same states: one launch per
+    sending box (per_subdomain), one launch per step for all pairs
+    (all_pairs), and the persistent batched codec replayed from CUDA graphs
+    (batched, schedule tuned at warm-up).  Each path runs W warm-up and K timed
+    iterations of the same chain; the bytes produced are the same on every
+    path (the parity tests check it), so only the time differs."""
+    import torch
+
+    import paper_2509_24063_gb300 as tera
+    from paper_2509_24063_gb300 import autotune
+    from synth import WORKLOADS, Generator, scaled
+    wl = WORKLOADS[args.workload]
+    if args.agents:
+        wl = scaled(wl, args.agents)
+    total = args.warmup + args.steps
+    states = [{k: v for k, v in st.items() if k in
+               ("id", "x", "y", "z", "diameter", "volume", "adherence", "density")}
+              for st in Generator(wl, device="cuda").series(total)]
+    nmax = max(int(s["x"].shape[0]) for s in states)
+    max_records = int(nmax * 0.35) + 4096 if wl.grid[0] >= 8 else 4 * nmax + 4096
+    out = {}
+    stream = torch.cuda.current_stream()
+    with ClockSampler(None) as clk:
+        for path in ("per_subdomain", "all_pairs", "batched"):
+            ctx = tera.Context(wl.lo, wl.hi, wl.grid, wl.w, periodic=wl.periodic)
+            ex = tera.AuraExchange(ctx, max_agents=nmax, max_records=max_records, path=path)
+            for t in range(args.warmup):
+                if t == 1 and path == "batched":
+                    autotune.tune_batched(ex, states[t], use_cache=False)
+                else:
+                    ex.step(states[t])
+            ctx.status()
+            graphs = None
+            if path == "batched":
+                graphs = [ex.capture(states[t], t) for t in range(args.warmup, total)]
+            launches0 = ctx.launches
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for t in range(args.warmup, total):
+                if graphs is not None:
+                    graphs[t - args.warmup].replay()
+                    ex.advance()
+                else:
+                    ex.step(states[t])
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ctx.status()
+            ms = e0.elapsed_time(e1)
+            agents = sum(int(states[t]["x"].shape[0]) for t in range(args.warmup, total))
+            out[path] = {"agents_per_s": agents / (ms / 1e3), "ms_per_step": ms / args.steps,
+                         "launches_per_step": None if graphs is not None else
+                         (ctx.launches - launches0) / args.steps,
+                         "cuda_graph": graphs is not None}
+            del graphs, ex
+            ctx.close()
+            torch.cuda.synchronize()
+            torch.cuda.empty_cache()
+    base = out["per_subdomain"]["agents_per_s"]
+    line = {"metric": "aura-exchange agents/s by path", "unit": "agents/s",
+            "workload": wl.name + (f"@{args.agents}" if args.agents else ""),
+            "agents": int(states[args.warmup]["x"].shape[0]), "steps": args.steps,
+            "warmup": args.warmup, "paths": out,
+            "batched_over_per_subdomain": out["batched"]["agents_per_s"] / base,
+            "all_pairs_over_per_subdomain": out["all_pairs"]["agents_per_s"] / base,
+            "clocks": clk.summary()}
+    print(json.dumps(line))
     return 0
 
 
