@@ -503,6 +503,8 @@ def main():
                          "time and compare bytes/agent against plain XOR on fresh iterations")
     ap.add_argument("--migration", action="store_true",
                     help="agent migration of the box-major state instead of the aura exchange")
+    ap.add_argument("--no-id-columns", action="store_true",
+                    help="batched codec reads record ids from the records (no id columns)")
     ap.add_argument("--compare-paths", action="store_true",
                     help="agents/s of the per-subdomain, all-pairs and batched paths on the same "
                          "states (one JSON line)")
@@ -551,7 +553,8 @@ def main():
     ctx = tera.Context(wl.lo, wl.hi, wl.grid, wl.w, device=local, periodic=wl.periodic)
     fixed = tuple(int(v) for v in args.tune.split(",")) if args.tune else None
     ex = tera.AuraExchange(ctx, max_agents=nmax, max_records=max_records, path=args.path,
-                           tune=fixed, ref_interval=args.ref_interval)
+                           tune=fixed, ref_interval=args.ref_interval,
+                           id_columns=not args.no_id_columns)
     stream = torch.cuda.current_stream()
     use_graph = args.path == "batched" and not args.no_graph
     tune_info = {"tune": list(fixed), "candidates": 0} if fixed else None
@@ -650,6 +653,7 @@ def main():
         hs = cpu_sample_states(wl, states[args.warmup - 1:args.warmup + 1], ns)
     agents_cfg = int(states[args.warmup]["x"].shape[0])
     tune_e2e = ex.tune
+    ex_id_columns = ex.id_columns
     e2e_host = None
     if args.e2e_steps > 0:
         e2e_host = e2e_inputs(args, states)
@@ -688,6 +692,7 @@ def main():
                    "agents": agents_cfg,
                    "grid": list(wl.grid), "aura_width": wl.w, "path": args.path,
                    "cuda_graph": use_graph, "tune": tune_info, "ref_interval": args.ref_interval,
+                   "id_columns": bool(ex_id_columns),
                    "boundary": wl.boundary,
                    "l2": "inputs larger than L2 (64 B/agent state per step)",
                    "parallelism": f"replicas{world}"},
