@@ -100,6 +100,8 @@ def lib():
             L.or_mlp_loss_grad_f64.restype = C.c_double
             L.or_mlp_sgd_f64.argtypes = [P, P, C.c_double]
             L.or_mlp_sgd_f64.restype = None
+            L.or_mlp_sgd_clip_f64.argtypes = [P, P, C.c_double, C.c_double]
+            L.or_mlp_sgd_clip_f64.restype = None
             L.or_zigzag.argtypes = [u64]
             L.or_zigzag.restype = u64
             L.or_unzigzag.argtypes = [u64]
@@ -419,6 +421,14 @@ def mlp_loss_grad(params64, X, Y, with_grad=True):
     g = np.zeros(NPARAM, dtype=np.float64) if with_grad else None
     loss = lib().or_mlp_loss_grad_f64(_p(p), _p(X), _p(Y), X.shape[0], _p(g))
     return loss, g
+
+
+def mlp_sgd_clip(params64, grad64, lr, clip):
+    """One float64 SGD step with global-norm clipping (a new array)."""
+    p = np.ascontiguousarray(params64, dtype=np.float64).copy()
+    g = np.ascontiguousarray(grad64, dtype=np.float64)
+    lib().or_mlp_sgd_clip_f64(_p(p), _p(g), float(lr), float(clip))
+    return p
 
 
 def zigzag(d):

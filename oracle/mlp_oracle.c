@@ -122,6 +122,17 @@ void or_mlp_sgd_f64(double* p, const double* grad, double lr) {
   for (int i = 0; i < NPARAM; ++i) p[i] -= lr * grad[i];
 }
 
+/* One SGD step with global-norm clipping (the predictor's training rule, not
+ * in the paper): with |g| the Euclidean norm of the whole gradient,
+ * c = clip / |g| when clip > 0 and |g| > clip, else c = 1; p -= lr * c * g. */
+void or_mlp_sgd_clip_f64(double* p, const double* grad, double lr, double clip) {
+  double ss = 0.0;
+  for (int i = 0; i < NPARAM; ++i) ss += grad[i] * grad[i];
+  double norm = sqrt(ss);
+  double c = (clip > 0.0 && norm > clip) ? clip / norm : 1.0;
+  for (int i = 0; i < NPARAM; ++i) p[i] -= lr * c * grad[i];
+}
+
 /* ---------- features, history, residual ---------- */
 
 static uint64_t rd64(const uint8_t* b) {

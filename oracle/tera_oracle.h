@@ -153,6 +153,7 @@ void or_mlp_infer_f32(const float* params, const float* in, float* out);
 double or_mlp_loss_grad_f64(const double* params, const double* X, const double* Y, int64_t n,
                             double* grad);
 void or_mlp_sgd_f64(double* params, const double* grad, double lr);
+void or_mlp_sgd_clip_f64(double* params, const double* grad, double lr, double clip);
 uint64_t or_zigzag(uint64_t d);
 uint64_t or_unzigzag(uint64_t z);
 void or_cell_counts(const uint8_t* ref, uint64_t r, const double lo[3], double w,

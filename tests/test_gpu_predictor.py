@@ -50,6 +50,37 @@ def test_gradient_matches_oracle(tera):
     ctx.close()
 
 
+@pytest.mark.parametrize("clip", [0.0, 0.05, 1e9])
+def test_sgd_step_with_clipping_matches_oracle(tera, clip):
+    # one training step over every valid sample (tera_mlp_train, steps = 1,
+    # batch = all) against the float64 oracle: gradient, then the clipped step
+    rng = np.random.default_rng(6)
+    n = 900
+    X = rng.standard_normal((n, 8)).astype(np.float32)
+    Y = (rng.standard_normal((n, 3)) * 2.0).astype(np.float32)
+    flag = (rng.random(n) < 0.9).astype(np.float32)
+    samples = np.concatenate([X, Y, flag[:, None]], axis=1).astype(np.float32)
+    p0 = (rng.standard_normal(4931) * 0.2).astype(np.float32)
+    ctx = tera.Context((0, 0, 0), (10, 10, 10), (1, 1, 1), 1.0)
+    keep = flag != 0
+    pt = torch.from_numpy(p0.copy()).cuda()
+    lr = 0.05
+    nv = ctx.mlp_train(torch.from_numpy(samples).cuda(), pt, 1, int(keep.sum()), lr, clip)
+    assert nv == int(keep.sum())
+    _, g64 = oracle.mlp_loss_grad(p0.astype(np.float64), X[keep].astype(np.float64),
+                                  Y[keep].astype(np.float64))
+    want = oracle.mlp_sgd_clip(p0.astype(np.float64), g64, lr, clip)
+    got = pt.cpu().numpy().astype(np.float64)
+    norm = np.linalg.norm(g64)
+    c = clip / norm if 0.0 < clip < norm else 1.0
+    if clip == 0.05:
+        assert c < 0.5  # the limit is in force
+    # float32 gradient (1e-4 of each layer's largest entry) and float32 rounding of the parameters
+    tol = lr * c * 1e-3 * np.abs(g64).max() + 4e-7 * np.abs(p0).max()
+    assert np.abs(got - want).max() <= tol
+    ctx.close()
+
+
 def run_pred_chain(tera, wl, params, path, tune=None):
     gen = Generator(wl, device="cuda")
     states = list(gen.series(wl.iterations))

@@ -119,6 +119,28 @@ def test_sgd_step(oracle):
     assert np.array_equal(p, np.arange(oracle.NPARAM) - 0.5)
 
 
+def test_sgd_step_with_global_norm_clipping(oracle):
+    # a gradient of norm 5 (entries 3 and 4): clipped to norm 1 the step is
+    # lr * (3, 4) / 5; unclipped (clip 0, or clip above the norm) it is lr * g
+    p = np.linspace(-1.0, 1.0, oracle.NPARAM)
+    g = np.zeros(oracle.NPARAM)
+    g[7], g[4000] = 3.0, 4.0
+    q = oracle.mlp_sgd_clip(p, g, 0.5, 1.0)
+    d = p - q
+    assert d[7] == pytest.approx(0.5 * 0.6, rel=1e-15) and d[4000] == pytest.approx(0.5 * 0.8, rel=1e-15)
+    assert np.count_nonzero(d) == 2
+    for clip in (0.0, -1.0, 5.0, 100.0):
+        np.testing.assert_array_equal(oracle.mlp_sgd_clip(p, g, 0.5, clip), p - 0.5 * g)
+    # any gradient above the limit: the step's norm is lr * clip, along -g
+    rng = np.random.default_rng(4)
+    g = rng.standard_normal(oracle.NPARAM) * 3.0
+    q = oracle.mlp_sgd_clip(p, g, 0.25, 2.0)
+    step = p - q
+    assert np.linalg.norm(step) == pytest.approx(0.25 * 2.0, rel=1e-12)
+    cos = step @ g / (np.linalg.norm(step) * np.linalg.norm(g))
+    assert cos == pytest.approx(1.0, abs=1e-12)
+
+
 @pytest.mark.parametrize("d,z", [(0, 0), (-1, 1), (1, 2), (-2, 3), (2, 4),
                                  (2**63 - 1, 2**64 - 2), (-2**63, 2**64 - 1)])
 def test_zigzag_vectors(oracle, d, z):
