@@ -764,6 +764,8 @@ def run_predictor(args):
         ex.step(evals[t])
     ctx.status()
     ctx.stats(reset=True)
+    ctx.profile_table(reset=True)
+    ctx.profile(True)
     stream = torch.cuda.current_stream()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -774,6 +776,13 @@ def run_predictor(args):
         e1.record(stream)
         torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
+    ctx.profile(False)
+    prof = ctx.profile_table(reset=True)
+    if args.profile_table:
+        tot = sum(v[1] for v in prof.values())
+        for k, (n_, ms_) in sorted(prof.items(), key=lambda kv: -kv[1][1]):
+            print(f"{k:24s} {n_:6d} launches {ms_:9.3f} ms {100 * ms_ / tot:5.1f}%",
+                  file=sys.stderr)
     st = ctx.stats(reset=True)
     ctx.status()
     steps = len(evals) - skip

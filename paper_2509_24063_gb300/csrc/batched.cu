@@ -525,6 +525,34 @@ __device__ __forceinline__ u64 pred_slot(const EncArgs& A, u32 p, u64 j, u64 r, 
   u64* ps = A.pr.pscr + 4 * (A.ref_off[p] + j);
   bool ok = false;
   float f[kMlpIn];
+  if (A.pr.pre) {
+    // the prediction is the pre-pass's; a training sample needs the features
+    if (mode != TERA_MODE_XOR) return vres;
+    if (A.pr.samples) {
+      const Hist H = load_hist(A.pr.hist + kHistBytes * (A.ref_off[p] + j));
+      const u32 nc = cell_count(A.pr.cseg, seg_base(A.ref_off[p], p), seg_size(r),
+                                cell_key(R, A.pr));
+      if (features(R, H, nc, f)) {
+        float* smp = A.pr.samples + (u64)kSampleFloats * (A.ref_off[p] + j);
+#pragma unroll
+        for (int i = 0; i < kMlpIn; ++i) smp[i] = f[i];
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+          smp[kMlpIn + a] = __double2float_rn(
+              __dsub_rn(__longlong_as_double((long long)M.w[1 + a]),
+                        __longlong_as_double((long long)R.w[1 + a])));
+        smp[11] = 1.0f;
+      }
+    }
+    if (__ldcg(ps + 3)) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        vres += sig_bytes(zigzag(M.w[1 + a] - __ldcg(ps + a)));
+        vres -= sig_bytes(M.w[1 + a] ^ R.w[1 + a]);
+      }
+    }
+    return vres;
+  }
   if (A.pr.hist && mode == TERA_MODE_XOR) {
     const Hist H = load_hist(A.pr.hist + kHistBytes * (A.ref_off[p] + j));
     const u32 nc = cell_count(A.pr.cseg, seg_base(A.ref_off[p], p), seg_size(r), cell_key(R, A.pr));
@@ -649,7 +677,7 @@ __device__ __forceinline__ void bat_match(const EncArgs& A, const BatchArgs& B, 
         br = pred_slot<PR>(A, p, j, r, pi[PI_MODE], R, M, b, sW);
       }
     } else if constexpr (PR) {
-      A.pr.pscr[4 * (ro + j) + 3] = 0;
+      if (!A.pr.pre) A.pr.pscr[4 * (ro + j) + 3] = 0;
     }
     A.slot_src[ro + j] = g;
   }
@@ -1084,11 +1112,18 @@ __device__ __forceinline__ void bat_dec_tile(const DecArgs& A, const BatchArgs& 
         Hist H;
         if (A.pr.hist) H = load_hist(A.pr.hist + kHistBytes * (q.ro + e));
         if (A.pr.hist && h.mode == kModeResidual) {
-          const u64 r = A.ref_off[p + 1] - A.ref_off[p];
-          const u32 nc = cell_count(A.pr.cseg, seg_base(A.ref_off[p], p), seg_size(r),
-                                    cell_key(R, A.pr));
-          float f[kMlpIn];
-          if (features(R, H, nc, f)) pred_ok = predict_from(sW, R, f, pred);
+          if (A.pr.pre) {  // the receiver's own prediction, made by the pre-pass
+            const u64* ps = A.pr.pscr + 4 * (q.ro + e);
+            pred_ok = __ldcg(ps + 3) != 0;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) pred[a] = __ldcg(ps + a);
+          } else {
+            const u64 r = A.ref_off[p + 1] - A.ref_off[p];
+            const u32 nc = cell_count(A.pr.cseg, seg_base(A.ref_off[p], p), seg_size(r),
+                                      cell_key(R, A.pr));
+            float f[kMlpIn];
+            if (features(R, H, nc, f)) pred_ok = predict_from(sW, R, f, pred);
+          }
         }
         if (A.pr.hist_next)
           store_hist_next(A.pr.hist_next + kHistBytes * (q.rv + pos), &R,
@@ -1449,9 +1484,9 @@ __device__ __noinline__ void team_pair(const EncArgs& E, const DecArgs& D, const
   const u64 nst = ceil_div(r, T);
   for (u64 t = i; t < ceil_div(m, (u64)T * kIlp); t += g) bat_build<T>(E, p, t, epoch);
   if constexpr (PR) {
-    if (E.pr.hist)
+    if (E.pr.hist && !E.pr.pre)
       for (u64 t = i; t < nst; t += g) cells_unit(E.pr, E.ref, E.ref_off, p, t, r, T);
-    if (D.pr.hist) {
+    if (D.pr.hist && !D.pr.pre) {
       const u64 rr = D.ref_off[p + 1] - D.ref_off[p];
       for (u64 t = i; t < ceil_div(rr, T); t += g) cells_unit(D.pr, D.ref, D.ref_off, p, t, rr, T);
     }
@@ -1504,6 +1539,79 @@ __device__ __noinline__ void team_pair(const EncArgs& E, const DecArgs& D, const
     bat_dec_tile<T, PR>(D, B, p, dq, t, c, h, mr, bufs + 33 * (k & 1), stage, stash, run, sW);
   }
   __syncthreads();
+}
+
+// ---------------- the predictor's pre-pass ----------------
+//
+// A slot's prediction depends only on its reference record, its history and
+// the cell counts of its pair's reference, not on the message: each side makes
+// the predictions of its own reference before the codec runs, over every slot
+// of every pair at once (one thread per slot), in kernels built with room for
+// the network's hidden layer in registers.  The codec then reads them.
+
+// The pair of slot g of an arena laid out with off[0..P] (off[p] <= g < off[p+1]).
+__device__ __forceinline__ u32 pair_of_slot(const u64* __restrict__ off, u32 P, u64 g) {
+  u32 lo = 0, hi = P;
+  while (hi - lo > 1) {
+    const u32 mid = (lo + hi) >> 1;
+    if (__ldg(off + mid) <= g) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// Every reference record counted in its cell (segments zeroed before).
+__global__ void __launch_bounds__(256) pred_cells_kernel(PredArgs pr, const uint8_t* __restrict__ ref,
+                                                         const u64* __restrict__ off, u32 P) {
+  const u64 total = off[P];
+  for (u64 g = (u64)blockIdx.x * blockDim.x + threadIdx.x; g < total;
+       g += (u64)gridDim.x * blockDim.x) {
+    const u32 p = pair_of_slot(off, P, g);
+    const u64 r = off[p + 1] - off[p];
+    const Rec R = load_rec(ref + (g + p + 1) * kRecBytes);
+    cell_insert(pr.cseg, seg_base(off[p], p), seg_size(r), cell_key(R, pr));
+  }
+}
+
+// Every reference slot's prediction (bits of the three predicted positions)
+// and whether it is usable, into out[4 g .. 4 g + 3].
+__global__ void __launch_bounds__(256, 2) pred_slots_kernel(PredArgs pr,
+                                                            const uint8_t* __restrict__ ref,
+                                                            const u64* __restrict__ off, u32 P,
+                                                            u64* __restrict__ out) {
+  __shared__ float sW[kMlpParams];
+  load_mlp(sW, pr.params);
+  const u64 total = off[P];
+  for (u64 g = (u64)blockIdx.x * blockDim.x + threadIdx.x; g < total;
+       g += (u64)gridDim.x * blockDim.x) {
+    const u32 p = pair_of_slot(off, P, g);
+    const u64 r = off[p + 1] - off[p];
+    const Rec R = load_rec(ref + (g + p + 1) * kRecBytes);
+    const Hist H = load_hist(pr.hist + kHistBytes * g);
+    const u32 nc = cell_count(pr.cseg, seg_base(off[p], p), seg_size(r), cell_key(R, pr));
+    float f[kMlpIn];
+    u64 pred[3] = {0, 0, 0};
+    bool ok = features(R, H, nc, f);
+    if (ok) ok = predict_from(sW, R, f, pred);
+    u64* o = out + 4 * g;
+    o[0] = pred[0];
+    o[1] = pred[1];
+    o[2] = pred[2];
+    o[3] = ok ? 1ull : 0ull;
+  }
+}
+
+// The pre-pass of one side: cell counts, then predictions.
+static tera_status pred_prepass(tera_ctx* ctx, const PredArgs& pr, const uint8_t* ref,
+                                const u64* off, u64* out, cudaStream_t s) {
+  const unsigned grid = (unsigned)(ctx->num_sms * 2);
+  prof_begin(ctx, s);
+  pred_cells_kernel<<<grid, 256, 0, s>>>(pr, ref, off, (u32)ctx->n_pairs);
+  tera_status st = check_launch(ctx, "pred_cells_kernel", s);
+  if (st != TERA_OK) return st;
+  prof_begin(ctx, s);
+  pred_slots_kernel<<<grid, 256, 0, s>>>(pr, ref, off, (u32)ctx->n_pairs, out);
+  return check_launch(ctx, "pred_slots_kernel", s);
 }
 
 // ---------------- the persistent kernel ----------------
@@ -1595,7 +1703,7 @@ __global__ void __launch_bounds__(T, (1024 / T) > 0 ? (1024 / T) : 1)
       __syncthreads();
       if constexpr (PR) {
         const u64 nst = ceil_div(r, T);
-        if (E.pr.hist) {
+        if (E.pr.hist && !E.pr.pre) {
           for (u64 t = 0; t < nst; ++t) cells_unit(E.pr, E.ref, E.ref_off, p, t, r, T);
           __syncthreads();
         }
@@ -1637,7 +1745,7 @@ __global__ void __launch_bounds__(T, (1024 / T) > 0 ? (1024 / T) : 1)
     }
     __syncthreads();
     if constexpr (PR) {
-      if (D.pr.hist) {
+      if (D.pr.hist && !D.pr.pre) {
         const u64 rr = D.ref_off[p + 1] - D.ref_off[p];
         const u64 ntr = ceil_div(rr, T);
         for (u64 t = 0; t < ntr; ++t) cells_unit(D.pr, D.ref, D.ref_off, p, t, rr, T);
@@ -1808,6 +1916,17 @@ static tera_status batched_impl(
       if ((dec_pred->hist_prev != nullptr) != (recv_prev != nullptr)) return TERA_EINVAL;
       fill_pred(ctx, &D.pr, dec_pred, ctx->cseg_dec);
       if (D.pr.hist) cudaMemsetAsync(ctx->cseg_dec, 0, sizeof(u64) * cwords, s);
+    }
+    // each side's predictions of its own reference, before the codec
+    if (enc_pred && E.pr.hist && E.pr.params) {
+      if ((st = pred_prepass(ctx, E.pr, ref_prev, E.ref_off, ctx->pscr, s)) != TERA_OK) return st;
+      E.pr.pre = 1;
+    }
+    if (dec_pred && D.pr.hist && D.pr.params) {
+      D.pr.pscr = ctx->pscr_dec;
+      if ((st = pred_prepass(ctx, D.pr, recv_prev, D.ref_off, ctx->pscr_dec, s)) != TERA_OK)
+        return st;
+      D.pr.pre = 1;
     }
   }
   cudaMemsetAsync(ctx->b_ptot, 0, sizeof(u64) * P * PT_COUNT, s);

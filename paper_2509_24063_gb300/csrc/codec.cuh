@@ -78,6 +78,10 @@ struct PredArgs {
   double w;
   u64 ncell[3];
   int allow_residual;
+  // batched path: the cell counts and every reference slot's prediction were
+  // made by the pre-pass (pred_cells_kernel, pred_slots_kernel) into cseg and
+  // pscr before the codec kernel
+  int pre = 0;
 };
 
 struct EncArgs {

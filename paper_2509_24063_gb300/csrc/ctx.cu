@@ -358,6 +358,7 @@ tera_status ensure_pred(tera_ctx* ctx) {
   if ((st = alloc_dev(ctx->cseg_enc, 2 * (2 * cap + 2 * P))) != TERA_OK) return st;
   if ((st = alloc_dev(ctx->cseg_dec, 2 * (2 * cap + 2 * P))) != TERA_OK) return st;
   if ((st = alloc_dev(ctx->pscr, 4 * cap)) != TERA_OK) return st;
+  if ((st = alloc_dev(ctx->pscr_dec, 4 * cap)) != TERA_OK) return st;
   if ((st = alloc_dev(ctx->unit_res, ctx->cap_units)) != TERA_OK) return st;
   ctx->pred_cap = cap;
   ctx->unit_res_cap = ctx->cap_units;
@@ -507,6 +508,7 @@ tera_status tera_ctx_destroy(tera_ctx* c) {
   free_dev(c->b_scalars);
   free_dev(c->b_ptot);
   free_dev(c->b_items);
+  free_dev(c->pscr_dec);
   free_dev(c->b_team);
   free_dev(c->b_tsum);
   free_dev(c->b_tbase);

@@ -65,6 +65,7 @@ struct tera_ctx {
   tera::u64* cseg_enc;
   tera::u64* cseg_dec;
   tera::u64* pscr;
+  tera::u64* pscr_dec;      // the receiver's predictions (batched pre-pass)
   tera::u64* unit_res;
   uint64_t unit_res_cap;
   float* mlp_scratch;       // training: compacted samples + gradient partials
