@@ -785,6 +785,21 @@ def run_predictor(args):
                   file=sys.stderr)
     st = ctx.stats(reset=True)
     ctx.status()
+    del ex
+    # the same iterations on the plain batched path (XOR difference only), also eager
+    ex = tera.AuraExchange(ctx, nmax, max_records, path="batched")
+    for t in range(skip):
+        ex.step(evals[t])
+    ctx.status()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for t in range(skip, len(evals)):
+        ex.step(evals[t])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_xor = e0.elapsed_time(e1)
+    ctx.status()
+    del ex
     steps = len(evals) - skip
     agents = sum(int(evals[t]["x"].shape[0]) for t in range(skip, len(evals)))
     line = {
@@ -797,6 +812,10 @@ def run_predictor(args):
         "bytes_per_agent_xor": bx / max(1, rx),
         "bytes_per_agent_residual": st["wire_bytes"] / max(1, st["records"]),
         "residual_vs_xor": (st["wire_bytes"] / max(1, st["records"])) / (bx / max(1, rx)),
+        "records_per_step": st["records"] / max(1, steps),
+        "ref_slots_per_step": st["ref_slots"] / max(1, steps),
+        "xor_ms_per_step": ms_xor / steps,
+        "predictor_vs_xor_time": ms / max(ms_xor, 1e-9),
         "training": {"samples": nv, "steps": 4000, "batch": 8192, "lr": 0.02, "clip": 1.0,
                      "seconds": t2 - t1, "collect_seconds": t1 - t0},
         "clocks": clk.summary(),

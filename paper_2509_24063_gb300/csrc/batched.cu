@@ -516,34 +516,34 @@ __device__ __forceinline__ void bat_build(const EncArgs& A, u32 p, u64 tile, u32
   }
 }
 
-// Predictor work of a matched slot (as in the per-call encoder): training
-// sample, prediction and the slot's residual payload size.
+// Predictor work of a matched slot: the training sample, and the slot's
+// residual payload size from the prediction the pre-pass made (predictions
+// exist only with both a history and the network, and then the pre-pass has
+// run).
 template <bool PR>
 __device__ __forceinline__ u64 pred_slot(const EncArgs& A, u32 p, u64 j, u64 r, u64 mode,
-                                         const Rec& R, const Rec& M, u32 bxor, const float* sW) {
+                                         const Rec& R, const Rec& M, u32 bxor) {
   u64 vres = bxor;
-  u64* ps = A.pr.pscr + 4 * (A.ref_off[p] + j);
-  bool ok = false;
-  float f[kMlpIn];
-  if (A.pr.pre) {
-    // the prediction is the pre-pass's; a training sample needs the features
-    if (mode != TERA_MODE_XOR) return vres;
-    if (A.pr.samples) {
-      const Hist H = load_hist(A.pr.hist + kHistBytes * (A.ref_off[p] + j));
-      const u32 nc = cell_count(A.pr.cseg, seg_base(A.ref_off[p], p), seg_size(r),
-                                cell_key(R, A.pr));
-      if (features(R, H, nc, f)) {
-        float* smp = A.pr.samples + (u64)kSampleFloats * (A.ref_off[p] + j);
+  if (!A.pr.hist || mode != TERA_MODE_XOR) return vres;
+  if (A.pr.samples) {
+    const Hist H = load_hist(A.pr.hist + kHistBytes * (A.ref_off[p] + j));
+    const u32 nc = cell_count(A.pr.cseg, seg_base(A.ref_off[p], p), seg_size(r),
+                              cell_key(R, A.pr));
+    float f[kMlpIn];
+    if (features(R, H, nc, f)) {
+      float* smp = A.pr.samples + (u64)kSampleFloats * (A.ref_off[p] + j);
 #pragma unroll
-        for (int i = 0; i < kMlpIn; ++i) smp[i] = f[i];
+      for (int i = 0; i < kMlpIn; ++i) smp[i] = f[i];
 #pragma unroll
-        for (int a = 0; a < 3; ++a)
-          smp[kMlpIn + a] = __double2float_rn(
-              __dsub_rn(__longlong_as_double((long long)M.w[1 + a]),
-                        __longlong_as_double((long long)R.w[1 + a])));
-        smp[11] = 1.0f;
-      }
+      for (int a = 0; a < 3; ++a)
+        smp[kMlpIn + a] = __double2float_rn(
+            __dsub_rn(__longlong_as_double((long long)M.w[1 + a]),
+                      __longlong_as_double((long long)R.w[1 + a])));
+      smp[11] = 1.0f;
     }
+  }
+  if (A.pr.pre) {
+    const u64* ps = A.pr.pscr + 4 * (A.ref_off[p] + j);
     if (__ldcg(ps + 3)) {
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
@@ -551,37 +551,7 @@ __device__ __forceinline__ u64 pred_slot(const EncArgs& A, u32 p, u64 j, u64 r, 
         vres -= sig_bytes(M.w[1 + a] ^ R.w[1 + a]);
       }
     }
-    return vres;
   }
-  if (A.pr.hist && mode == TERA_MODE_XOR) {
-    const Hist H = load_hist(A.pr.hist + kHistBytes * (A.ref_off[p] + j));
-    const u32 nc = cell_count(A.pr.cseg, seg_base(A.ref_off[p], p), seg_size(r), cell_key(R, A.pr));
-    if (features(R, H, nc, f)) {
-      if (A.pr.samples) {
-        float* s = A.pr.samples + (u64)kSampleFloats * (A.ref_off[p] + j);
-#pragma unroll
-        for (int i = 0; i < kMlpIn; ++i) s[i] = f[i];
-#pragma unroll
-        for (int a = 0; a < 3; ++a)
-          s[kMlpIn + a] = __double2float_rn(__dsub_rn(__longlong_as_double((long long)M.w[1 + a]),
-                                                      __longlong_as_double((long long)R.w[1 + a])));
-        s[11] = 1.0f;
-      }
-      if (A.pr.params) {
-        u64 pred[3];
-        ok = predict_from(sW, R, f, pred);
-        if (ok) {
-#pragma unroll
-          for (int a = 0; a < 3; ++a) {
-            vres += sig_bytes(zigzag(M.w[1 + a] - pred[a]));
-            vres -= sig_bytes(M.w[1 + a] ^ R.w[1 + a]);
-            ps[a] = pred[a];
-          }
-        }
-      }
-    }
-  }
-  ps[3] = ok ? 1ull : 0ull;
   return vres;
 }
 
@@ -640,7 +610,7 @@ __device__ __forceinline__ void bat_match_ilp(const EncArgs& A, const BatchArgs&
 
 template <int T, bool PR>
 __device__ __forceinline__ void bat_match(const EncArgs& A, const BatchArgs& B, u32 p, u64 tile,
-                                          u32 epoch, U64x2* sm, const float* sW) {
+                                          u32 epoch, U64x2* sm) {
   const u64* pi = A.info + (u64)p * 8;
   const u64 r = pi[PI_R], m = pi[PI_M];
   const u64 j = tile * T + threadIdx.x;
@@ -674,10 +644,8 @@ __device__ __forceinline__ void bat_match(const EncArgs& A, const BatchArgs& B, 
 #pragma unroll
         for (int w = 0; w < 8; ++w) b += sig_bytes(M.w[w] ^ R.w[w]);
         bx = b;
-        br = pred_slot<PR>(A, p, j, r, pi[PI_MODE], R, M, b, sW);
+        br = pred_slot<PR>(A, p, j, r, pi[PI_MODE], R, M, b);
       }
-    } else if constexpr (PR) {
-      if (!A.pr.pre) A.pr.pscr[4 * (ro + j) + 3] = 0;
     }
     A.slot_src[ro + j] = g;
   }
@@ -1052,8 +1020,7 @@ template <int T, bool PR>
 __device__ __forceinline__ void bat_dec_tile(const DecArgs& A, const BatchArgs& B, u32 p,
                                              const DecPair& q, u64 tile, u32 code,
                                              const DecShared& h, u64 m, u64* buf,
-                                             uint8_t* stage, ulonglong2* stash, U64x2& run,
-                                             const float* sW) {
+                                             uint8_t* stage, ulonglong2* stash, U64x2& run) {
   const u64 ns = h.ns, n = h.ns + h.nn;
   const uint8_t* w8 = q.w8;
   const u64 e = tile * T + threadIdx.x;
@@ -1111,19 +1078,14 @@ __device__ __forceinline__ void bat_dec_tile(const DecArgs& A, const BatchArgs& 
       if constexpr (PR) {
         Hist H;
         if (A.pr.hist) H = load_hist(A.pr.hist + kHistBytes * (q.ro + e));
-        if (A.pr.hist && h.mode == kModeResidual) {
-          if (A.pr.pre) {  // the receiver's own prediction, made by the pre-pass
-            const u64* ps = A.pr.pscr + 4 * (q.ro + e);
-            pred_ok = __ldcg(ps + 3) != 0;
+        // the receiver's own prediction, made by the pre-pass (a residual
+        // message needs the network, so the header check has rejected one
+        // that arrives without it)
+        if (A.pr.pre && h.mode == kModeResidual) {
+          const u64* ps = A.pr.pscr + 4 * (q.ro + e);
+          pred_ok = __ldcg(ps + 3) != 0;
 #pragma unroll
-            for (int a = 0; a < 3; ++a) pred[a] = __ldcg(ps + a);
-          } else {
-            const u64 r = A.ref_off[p + 1] - A.ref_off[p];
-            const u32 nc = cell_count(A.pr.cseg, seg_base(A.ref_off[p], p), seg_size(r),
-                                      cell_key(R, A.pr));
-            float f[kMlpIn];
-            if (features(R, H, nc, f)) pred_ok = predict_from(sW, R, f, pred);
-          }
+          for (int a = 0; a < 3; ++a) pred[a] = __ldcg(ps + a);
         }
         if (A.pr.hist_next)
           store_hist_next(A.pr.hist_next + kHistBytes * (q.rv + pos), &R,
@@ -1274,7 +1236,7 @@ __device__ __forceinline__ void dec_tiles_pipelined(const DecArgs& A, u32 p, con
 template <int T, bool PR>
 __device__ __forceinline__ void bat_dec(const DecArgs& A, const BatchArgs& B, u32 p,
                                         DecShared* hs, u64* bufs, uint8_t* stage,
-                                        ulonglong2* stash, const float* sW) {
+                                        ulonglong2* stash) {
   const u64 m = A.recv_off[p + 1] - A.recv_off[p];
   const DecShared h = dec_header<PR>(A, p, m, hs, true);
   if (!h.ok) return;  // block-uniform
@@ -1293,7 +1255,7 @@ __device__ __forceinline__ void bat_dec(const DecArgs& A, const BatchArgs& B, u3
     const u32 c = c_next;
     const u64 en = (t + 1) * T + threadIdx.x;
     c_next = en < n ? __ldcg(codes + en) : 0u;
-    bat_dec_tile<T, PR>(A, B, p, q, t, c, h, m, bufs + 33 * (t & 1), stage, stash, run, sW);
+    bat_dec_tile<T, PR>(A, B, p, q, t, c, h, m, bufs + 33 * (t & 1), stage, stash, run);
   }
   __syncthreads();  // the scan buffers and the stage are reused next
 }
@@ -1473,8 +1435,7 @@ __device__ __forceinline__ void team_dec_sum(const DecArgs& A, u32 p, const DecS
 template <int T, bool PR>
 __device__ __noinline__ void team_pair(const EncArgs& E, const DecArgs& D, const BatchArgs& B,
                                           u32 p, u32 i, u32 g, u32 epoch, U64x2* sm, u64* red,
-                                          uint8_t* stage, ulonglong2* stash, DecShared* hs,
-                                          const float* sW) {
+                                          uint8_t* stage, ulonglong2* stash, DecShared* hs) {
   constexpr u32 kStageCap = (u32)T * kRecBytes + 48;
   const u64* pi = E.info + (u64)p * 8;
   const u64 r = pi[PI_R], m = pi[PI_M];
@@ -1484,16 +1445,13 @@ __device__ __noinline__ void team_pair(const EncArgs& E, const DecArgs& D, const
   const u64 nst = ceil_div(r, T);
   for (u64 t = i; t < ceil_div(m, (u64)T * kIlp); t += g) bat_build<T>(E, p, t, epoch);
   if constexpr (PR) {
-    if (E.pr.hist && !E.pr.pre)
+    // cell counts for the training samples when no pre-pass has made them
+    if (E.pr.hist && E.pr.samples && !E.pr.pre)
       for (u64 t = i; t < nst; t += g) cells_unit(E.pr, E.ref, E.ref_off, p, t, r, T);
-    if (D.pr.hist && !D.pr.pre) {
-      const u64 rr = D.ref_off[p + 1] - D.ref_off[p];
-      for (u64 t = i; t < ceil_div(rr, T); t += g) cells_unit(D.pr, D.ref, D.ref_off, p, t, rr, T);
-    }
   }
   if (!team_barrier(ctr + 0, g, E.st, B.wait_ns)) return;
   if constexpr (PR) {
-    for (u64 t = i; t < nst; t += g) bat_match<T, PR>(E, B, p, t, epoch, sm, sW);
+    for (u64 t = i; t < nst; t += g) bat_match<T, PR>(E, B, p, t, epoch, sm);
   } else {
     for (u64 t = i; t < ceil_div(r, (u64)T * kIlp); t += g) bat_match_ilp<T>(E, B, p, t, epoch);
   }
@@ -1536,7 +1494,7 @@ __device__ __noinline__ void team_pair(const EncArgs& E, const DecArgs& D, const
     U64x2 run = tiles_prefix<T>(ds, t, red);
     const u64 e = t * T + threadIdx.x;
     const u32 c = e < n ? __ldcg(codes + e) : 0u;
-    bat_dec_tile<T, PR>(D, B, p, dq, t, c, h, mr, bufs + 33 * (k & 1), stage, stash, run, sW);
+    bat_dec_tile<T, PR>(D, B, p, dq, t, c, h, mr, bufs + 33 * (k & 1), stage, stash, run);
   }
   __syncthreads();
 }
@@ -1573,13 +1531,56 @@ __global__ void __launch_bounds__(256) pred_cells_kernel(PredArgs pr, const uint
   }
 }
 
+// The network on one feature vector, as mlp_infer computes it (the same
+// fused multiply-adds in the same order, so the same bits), with its weights
+// in this block's shared memory read a row of four at a time.
+__device__ __forceinline__ void mlp_infer_rows(const float* __restrict__ sW, const float* f,
+                                               float* o) {
+  const float4* W4 = reinterpret_cast<const float4*>(sW);
+  float h1[kMlpH];
+#pragma unroll
+  for (int j = 0; j < kMlpH; ++j) {
+    float acc = sW[kMlpB1 + j];
+    const float4 a = W4[(kMlpW1 + j * kMlpIn) / 4], b = W4[(kMlpW1 + j * kMlpIn) / 4 + 1];
+    acc = __fmaf_rn(a.x, f[0], acc);
+    acc = __fmaf_rn(a.y, f[1], acc);
+    acc = __fmaf_rn(a.z, f[2], acc);
+    acc = __fmaf_rn(a.w, f[3], acc);
+    acc = __fmaf_rn(b.x, f[4], acc);
+    acc = __fmaf_rn(b.y, f[5], acc);
+    acc = __fmaf_rn(b.z, f[6], acc);
+    acc = __fmaf_rn(b.w, f[7], acc);
+    h1[j] = acc > 0.0f ? acc : 0.0f;
+  }
+  o[0] = sW[kMlpB3 + 0];
+  o[1] = sW[kMlpB3 + 1];
+  o[2] = sW[kMlpB3 + 2];
+  // two neurons' chains in flight at a time; each neuron's own order is unchanged
+#pragma unroll 2
+  for (int j = 0; j < kMlpH; ++j) {
+    float acc = sW[kMlpB2 + j];
+    const float4* row = W4 + (kMlpW2 + j * kMlpH) / 4;
+#pragma unroll
+    for (int k = 0; k < kMlpH / 4; ++k) {
+      const float4 w = row[k];
+      acc = __fmaf_rn(w.x, h1[4 * k + 0], acc);
+      acc = __fmaf_rn(w.y, h1[4 * k + 1], acc);
+      acc = __fmaf_rn(w.z, h1[4 * k + 2], acc);
+      acc = __fmaf_rn(w.w, h1[4 * k + 3], acc);
+    }
+    const float h2 = acc > 0.0f ? acc : 0.0f;
+#pragma unroll
+    for (int a = 0; a < kMlpOut; ++a) o[a] = __fmaf_rn(sW[kMlpW3 + a * kMlpH + j], h2, o[a]);
+  }
+}
+
 // Every reference slot's prediction (bits of the three predicted positions)
 // and whether it is usable, into out[4 g .. 4 g + 3].
 __global__ void __launch_bounds__(256, 2) pred_slots_kernel(PredArgs pr,
                                                             const uint8_t* __restrict__ ref,
                                                             const u64* __restrict__ off, u32 P,
                                                             u64* __restrict__ out) {
-  __shared__ float sW[kMlpParams];
+  __shared__ __align__(16) float sW[(kMlpParams + 3) & ~3];
   load_mlp(sW, pr.params);
   const u64 total = off[P];
   for (u64 g = (u64)blockIdx.x * blockDim.x + threadIdx.x; g < total;
@@ -1592,7 +1593,11 @@ __global__ void __launch_bounds__(256, 2) pred_slots_kernel(PredArgs pr,
     float f[kMlpIn];
     u64 pred[3] = {0, 0, 0};
     bool ok = features(R, H, nc, f);
-    if (ok) ok = predict_from(sW, R, f, pred);
+    if (ok) {
+      float y[kMlpOut];
+      mlp_infer_rows(sW, f, y);
+      ok = predict_out(R, y, pred);
+    }
     u64* o = out + 4 * g;
     o[0] = pred[0];
     o[1] = pred[1];
@@ -1602,6 +1607,28 @@ __global__ void __launch_bounds__(256, 2) pred_slots_kernel(PredArgs pr,
 }
 
 // The pre-pass of one side: cell counts, then predictions.
+// Zeroes the cell counts' segments of every pair of a reference laid out
+// with off[0..P] (seg_base(off[P], P) entries of 16 bytes; the segments are
+// contiguous), the part of the cell hash the codec and the pre-pass use, at
+// most the cap entries allocated.
+__global__ void __launch_bounds__(256) cells_clear_kernel(u64* __restrict__ cseg,
+                                                          const u64* __restrict__ off, u32 P,
+                                                          u64 cap) {
+  const u64 used = seg_base(off[P], P);
+  const u64 n = used < cap ? used : cap;
+  ulonglong2* c = reinterpret_cast<ulonglong2*>(cseg);
+  for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (u64)gridDim.x * blockDim.x)
+    c[i] = make_ulonglong2(0ull, 0ull);
+}
+
+static tera_status cells_clear(tera_ctx* ctx, u64* cseg, const u64* off, cudaStream_t s) {
+  prof_begin(ctx, s);
+  const u64 P = ctx->n_pairs;
+  cells_clear_kernel<<<(unsigned)(ctx->num_sms * 4), 256, 0, s>>>(cseg, off, (u32)P,
+                                                                  2 * ctx->pred_cap + 2 * P);
+  return check_launch(ctx, "cells_clear_kernel", s);
+}
+
 static tera_status pred_prepass(tera_ctx* ctx, const PredArgs& pr, const uint8_t* ref,
                                 const u64* off, u64* out, cudaStream_t s) {
   const unsigned grid = (unsigned)(ctx->num_sms * 2);
@@ -1647,17 +1674,12 @@ __global__ void __launch_bounds__(T, (1024 / T) > 0 ? (1024 / T) : 1)
   unsigned short* list = tbl;
   uint8_t* stage = dyn + stage_off(T, table_records);
   ulonglong2* stash = reinterpret_cast<ulonglong2*>(dyn);
-  float* sW = reinterpret_cast<float*>(dyn + region);
-  u32* bits = reinterpret_cast<u32*>(dyn + region + (PR ? sizeof(float) * kMlpParams : 0));
+  u32* bits = reinterpret_cast<u32*>(dyn + region);
   __shared__ U64x2 sm[33];
   __shared__ u64 red[66];
   __shared__ u64 s_item;
   __shared__ u32 s_cnt;
   __shared__ DecShared hs;
-  if (PR) {
-    const float* params = E.pr.params ? E.pr.params : D.pr.params;
-    if (params) load_mlp(sW, params);
-  }
   const u32 epoch = __ldcg(E.epoch);
   const u64 n_items = __ldcg(B.n_items);
   if (threadIdx.x == 0) s_cnt = 0;
@@ -1675,7 +1697,7 @@ __global__ void __launch_bounds__(T, (1024 / T) > 0 ? (1024 / T) : 1)
     const u32 g = (u32)it & 0xFFFFu;
     if (g > 1) {
       team_pair<T, PR>(E, D, B, p, (u32)(it >> 16) & 0xFFFFu, g, epoch, sm, red, stage, stash,
-                       &hs, sW);
+                       &hs);
       continue;
     }
     const u64* pi = E.info + (u64)p * 8;
@@ -1703,11 +1725,11 @@ __global__ void __launch_bounds__(T, (1024 / T) > 0 ? (1024 / T) : 1)
       __syncthreads();
       if constexpr (PR) {
         const u64 nst = ceil_div(r, T);
-        if (E.pr.hist && !E.pr.pre) {
+        if (E.pr.hist && E.pr.samples && !E.pr.pre) {
           for (u64 t = 0; t < nst; ++t) cells_unit(E.pr, E.ref, E.ref_off, p, t, r, T);
           __syncthreads();
         }
-        for (u64 t = 0; t < nst; ++t) bat_match<T, PR>(E, B, p, t, epoch, sm, sW);
+        for (u64 t = 0; t < nst; ++t) bat_match<T, PR>(E, B, p, t, epoch, sm);
       } else {
         const u64 ntm = ceil_div(r, (u64)T * kIlp);
         for (u64 t = 0; t < ntm; ++t) bat_match_ilp<T>(E, B, p, t, epoch);
@@ -1744,15 +1766,7 @@ __global__ void __launch_bounds__(T, (1024 / T) > 0 ? (1024 / T) : 1)
         bat_new<T, PR>(E, B, p, t, epoch, sm, stage, kStageCap, run, slot_tot, tb);
     }
     __syncthreads();
-    if constexpr (PR) {
-      if (D.pr.hist && !D.pr.pre) {
-        const u64 rr = D.ref_off[p + 1] - D.ref_off[p];
-        const u64 ntr = ceil_div(rr, T);
-        for (u64 t = 0; t < ntr; ++t) cells_unit(D.pr, D.ref, D.ref_off, p, t, rr, T);
-        __syncthreads();
-      }
-    }
-    bat_dec<T, PR>(D, B, p, &hs, reinterpret_cast<u64*>(sm), stage, stash, sW);
+    bat_dec<T, PR>(D, B, p, &hs, reinterpret_cast<u64*>(sm), stage, stash);
     __syncthreads();
   }
 }
@@ -1760,7 +1774,6 @@ __global__ void __launch_bounds__(T, (1024 / T) > 0 ? (1024 / T) : 1)
 // Shared memory of one block for tile size T: (bytes, table_records).
 inline void persistent_smem(u32 T, bool PR, int ctas_per_sm, u32 want_records, size_t* bytes,
                             u32* records) {
-  const size_t weights = PR ? sizeof(float) * kMlpParams : 0;
   // per-SM shared memory (228 KB) split over the blocks, minus the static
   // shared memory and the 1 KB the runtime reserves per block
   const size_t per_block = (size_t)228 * 1024 / (size_t)(ctas_per_sm > 0 ? ctas_per_sm : 1);
@@ -1774,7 +1787,7 @@ inline void persistent_smem(u32 T, bool PR, int ctas_per_sm, u32 want_records, s
   }
   *records = rec;
   // + 16 bytes: the decode's 8-byte reads may pass the end of the stage
-  *bytes = region_bytes(T, rec) + weights + rec / 8 + 16;
+  *bytes = region_bytes(T, rec) + rec / 8 + 16;
 }
 
 template <int T, bool PR>
@@ -1904,18 +1917,19 @@ static tera_status batched_impl(
 
   if (PR) {
     if ((st = ensure_pred(ctx)) != TERA_OK) return st;
-    const u64 cwords = 2 * (2 * ctx->cap_records + 2 * P);
     if (enc_pred) {
       if ((enc_pred->hist_prev != nullptr) != (ref_prev != nullptr)) return TERA_EINVAL;
       fill_pred(ctx, &E.pr, enc_pred, ctx->cseg_enc);
       E.pr.samples = enc_pred->samples;
       E.pr.allow_residual = enc_pred->allow_residual;
-      if (E.pr.hist) cudaMemsetAsync(ctx->cseg_enc, 0, sizeof(u64) * cwords, s);
+      if (E.pr.hist && (st = cells_clear(ctx, ctx->cseg_enc, E.ref_off, s)) != TERA_OK) return st;
     }
     if (dec_pred) {
       if ((dec_pred->hist_prev != nullptr) != (recv_prev != nullptr)) return TERA_EINVAL;
       fill_pred(ctx, &D.pr, dec_pred, ctx->cseg_dec);
-      if (D.pr.hist) cudaMemsetAsync(ctx->cseg_dec, 0, sizeof(u64) * cwords, s);
+      if (D.pr.hist && D.pr.params &&
+          (st = cells_clear(ctx, ctx->cseg_dec, D.ref_off, s)) != TERA_OK)
+        return st;
     }
     // each side's predictions of its own reference, before the codec
     if (enc_pred && E.pr.hist && E.pr.params) {

@@ -280,16 +280,23 @@ __device__ __forceinline__ bool features(const Rec& R, const Hist& H, u32 ncount
 }
 
 // Predicted position bits from features; false when an output is not finite.
-__device__ __forceinline__ bool predict_from(const float* W, const Rec& R, const float* f,
-                                             u64* pred) {
-  float o[kMlpOut];
-  mlp_infer(W, f, o);
+// The predicted positions from the network's output: each displacement added
+// to the reference position in double precision; false when an output is
+// not finite.
+__device__ __forceinline__ bool predict_out(const Rec& R, const float* o, u64* pred) {
   bool ok = isfinite(o[0]) && isfinite(o[1]) && isfinite(o[2]);
 #pragma unroll
   for (int a = 0; a < 3; ++a)
     pred[a] = (u64)__double_as_longlong(
         __dadd_rn(__longlong_as_double((long long)R.w[1 + a]), (double)o[a]));
   return ok;
+}
+
+__device__ __forceinline__ bool predict_from(const float* W, const Rec& R, const float* f,
+                                             u64* pred) {
+  float o[kMlpOut];
+  mlp_infer(W, f, o);
+  return predict_out(R, o, pred);
 }
 
 __device__ __forceinline__ u64 zigzag(u64 d) { return (d << 1) ^ (u64)((long long)d >> 63); }
