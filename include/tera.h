@@ -479,6 +479,21 @@ tera_status tera_migrate_recv(tera_ctx* ctx, const uint8_t* arena, uint64_t aren
 tera_status tera_ref_schedule(uint64_t t, uint32_t ref_interval, int32_t* out_buf,
                               int32_t* ref_buf, uint64_t* ref_iteration);
 
+/* Cell boundaries of one axis of the predictor's cell grid (the ncount
+ * feature above; cells of width w from lo, cell(x) = floor((x - lo) / w) in
+ * binary64).  Host-only arithmetic, no device work: the library builds these
+ * tables once per context (for axes of at most 65536 cells) so that the
+ * device finds a cell by integer comparisons instead of binary64 division.
+ * n must be floor((hi - lo) / w) + 1 (the context's cell count of the axis);
+ * T (caller-owned, n + 1 entries) receives T[0] = key(lo), T[n] = key(hi)
+ * and, for 1 <= k < n, T[k] = key of the smallest binary64 x with
+ * cell(x) >= k, where key(x) is the order-preserving map of x's bits
+ * (b ^ 0x8000000000000000 for a non-negative x, ~b for a negative one,
+ * -0.0 taken as +0.0).  A value x in [lo, hi) then lies in the largest cell
+ * k < n with key(x) >= T[k].  TERA_EINVAL when T is NULL, lo, hi or w is
+ * not finite, lo >= hi, w <= 0, or n is not that count. */
+tera_status tera_cell_thresholds(double lo, double hi, double w, uint64_t n, uint64_t* T);
+
 /* Read (and clear) the latched device status; synchronizes `stream`.
  * *required_capacity (optional) receives the largest capacity a call asked
  * for when the status is TERA_ECAPACITY. */

@@ -109,6 +109,7 @@ SIGNATURES = {
     "tera_version": (C.c_char_p, []),
     "tera_ref_schedule": (C.c_int, [u64, u32, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                                     C.POINTER(C.c_uint64)]),
+    "tera_cell_thresholds": (C.c_int, [C.c_double, C.c_double, C.c_double, u64, P]),
 }
 
 _lock = threading.Lock()

@@ -100,6 +100,19 @@ def ref_schedule(t: int, ref_interval: int):
     return int(ob.value), int(rb.value), int(ri.value)
 
 
+def cell_thresholds(lo: float, hi: float, w: float):
+    """tera_cell_thresholds: the n + 1 keys of one axis of the predictor's cell
+    grid (n = floor((hi - lo) / w) + 1), as a numpy uint64 array."""
+    import math
+    import numpy as np
+    n = int(math.floor((hi - lo) / w)) + 1
+    out = np.zeros(n + 1, dtype=np.uint64)
+    check(_lib.load().tera_cell_thresholds(float(lo), float(hi), float(w), n,
+                                           out.ctypes.data_as(C.c_void_p)),
+          "tera_cell_thresholds")
+    return out
+
+
 class Context:
     """One partitioning grid on one GPU (owns scratch, hash table, status word)."""
 

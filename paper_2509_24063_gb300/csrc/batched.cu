@@ -1518,59 +1518,104 @@ __device__ __forceinline__ u32 pair_of_slot(const u64* __restrict__ off, u32 P, 
   return lo;
 }
 
+// Slots the pre-pass covers: the reference's, or none when they exceed the
+// cap slots its scratch holds (the codec's setup then reports the capacity
+// error before any use of the predictions).
+__device__ __forceinline__ u64 prepass_slots(const u64* __restrict__ off, u32 P, u64 cap) {
+  const u64 n = off[P];
+  return n <= cap ? n : 0;
+}
+
+// The slots [*g0, *g1) of the calling warp: the arena's slots split into
+// equal runs of whole 32-slot steps, one run per warp of the grid, so that a
+// warp finds the pair of its first slot once and then walks the pairs.
+__device__ __forceinline__ void warp_run(u64 total, u64* g0, u64* g1) {
+  const u64 wpb = blockDim.x / 32;
+  const u64 nw = (u64)gridDim.x * wpb;
+  const u64 w = (u64)blockIdx.x * wpb + threadIdx.x / 32;
+  const u64 per = ceil_div(ceil_div(total, 32), nw) * 32;
+  const u64 a = w * per, b = a + per;
+  *g0 = a < total ? a : total;
+  *g1 = b < total ? b : total;
+}
+
 // Every reference record counted in its cell (segments zeroed before).
 __global__ void __launch_bounds__(256) pred_cells_kernel(PredArgs pr, const uint8_t* __restrict__ ref,
-                                                         const u64* __restrict__ off, u32 P) {
-  const u64 total = off[P];
-  for (u64 g = (u64)blockIdx.x * blockDim.x + threadIdx.x; g < total;
-       g += (u64)gridDim.x * blockDim.x) {
-    const u32 p = pair_of_slot(off, P, g);
-    const u64 r = off[p + 1] - off[p];
+                                                         const u64* __restrict__ off, u32 P,
+                                                         u64 cap) {
+  u64 g0, g1;
+  warp_run(prepass_slots(off, P, cap), &g0, &g1);
+  if (g0 >= g1) return;
+  u32 p = pair_of_slot(off, P, g0);
+  for (u64 g = g0 + (threadIdx.x & 31); g < g1; g += 32) {
+    while (__ldg(off + p + 1) <= g) ++p;
+    const u64 o = __ldg(off + p), r = __ldg(off + p + 1) - o;
     const Rec R = load_rec(ref + (g + p + 1) * kRecBytes);
-    cell_insert(pr.cseg, seg_base(off[p], p), seg_size(r), cell_key(R, pr));
+    cell_insert(pr.cseg, seg_base(o, p), seg_size(r), cell_key(R, pr));
   }
 }
 
-// The network on one feature vector, as mlp_infer computes it (the same
-// fused multiply-adds in the same order, so the same bits), with its weights
-// in this block's shared memory read a row of four at a time.
-__device__ __forceinline__ void mlp_infer_rows(const float* __restrict__ sW, const float* f,
+// The network's weights in shared memory with layer 2 stored by columns: the
+// weights of hidden input k for neurons 0 .. 63 at kMlpW2 + 64 k (the other
+// arrays as in the parameter vector).
+__device__ __forceinline__ void load_mlp_cols(float* sW, const float* __restrict__ params) {
+  for (int i = threadIdx.x; i < kMlpParams; i += blockDim.x) {
+    int d = i;
+    if (i >= kMlpW2 && i < kMlpW2 + kMlpH * kMlpH) {
+      const int j = (i - kMlpW2) / kMlpH, k = (i - kMlpW2) % kMlpH;
+      d = kMlpW2 + k * kMlpH + j;
+    }
+    sW[d] = __ldg(params + i);
+  }
+  __syncthreads();
+}
+
+// The network on one feature vector with the same fused multiply-adds, in
+// the same order per neuron, as mlp_infer (so the same bits): the first
+// hidden layer is made one neuron k at a time, and its output enters all 64
+// accumulators of the second layer at once, two neurons per paired
+// multiply-add (each component an fmaf of its own).  Each second-layer
+// neuron still adds its inputs k = 0 .. 63 in ascending order.
+__device__ __forceinline__ void mlp_infer_cols(const float* __restrict__ sW, const float* f,
                                                float* o) {
   const float4* W4 = reinterpret_cast<const float4*>(sW);
-  float h1[kMlpH];
+  const float2* B2 = reinterpret_cast<const float2*>(sW + kMlpB2);
+  float2 acc[kMlpH / 2];
 #pragma unroll
-  for (int j = 0; j < kMlpH; ++j) {
-    float acc = sW[kMlpB1 + j];
-    const float4 a = W4[(kMlpW1 + j * kMlpIn) / 4], b = W4[(kMlpW1 + j * kMlpIn) / 4 + 1];
-    acc = __fmaf_rn(a.x, f[0], acc);
-    acc = __fmaf_rn(a.y, f[1], acc);
-    acc = __fmaf_rn(a.z, f[2], acc);
-    acc = __fmaf_rn(a.w, f[3], acc);
-    acc = __fmaf_rn(b.x, f[4], acc);
-    acc = __fmaf_rn(b.y, f[5], acc);
-    acc = __fmaf_rn(b.z, f[6], acc);
-    acc = __fmaf_rn(b.w, f[7], acc);
-    h1[j] = acc > 0.0f ? acc : 0.0f;
+  for (int i = 0; i < kMlpH / 2; ++i) acc[i] = B2[i];
+#pragma unroll 1
+  for (int k = 0; k < kMlpH; ++k) {
+    const float4 a = W4[(kMlpW1 + k * kMlpIn) / 4], b = W4[(kMlpW1 + k * kMlpIn) / 4 + 1];
+    float h = sW[kMlpB1 + k];
+    h = __fmaf_rn(a.x, f[0], h);
+    h = __fmaf_rn(a.y, f[1], h);
+    h = __fmaf_rn(a.z, f[2], h);
+    h = __fmaf_rn(a.w, f[3], h);
+    h = __fmaf_rn(b.x, f[4], h);
+    h = __fmaf_rn(b.y, f[5], h);
+    h = __fmaf_rn(b.z, f[6], h);
+    h = __fmaf_rn(b.w, f[7], h);
+    h = h > 0.0f ? h : 0.0f;
+    const float2 hh = make_float2(h, h);
+    const float4* col = W4 + (kMlpW2 + k * kMlpH) / 4;
+#pragma unroll
+    for (int q = 0; q < kMlpH / 4; ++q) {
+      const float4 w = col[q];
+      acc[2 * q] = __ffma2_rn(make_float2(w.x, w.y), hh, acc[2 * q]);
+      acc[2 * q + 1] = __ffma2_rn(make_float2(w.z, w.w), hh, acc[2 * q + 1]);
+    }
   }
   o[0] = sW[kMlpB3 + 0];
   o[1] = sW[kMlpB3 + 1];
   o[2] = sW[kMlpB3 + 2];
-  // two neurons' chains in flight at a time; each neuron's own order is unchanged
-#pragma unroll 2
-  for (int j = 0; j < kMlpH; ++j) {
-    float acc = sW[kMlpB2 + j];
-    const float4* row = W4 + (kMlpW2 + j * kMlpH) / 4;
 #pragma unroll
-    for (int k = 0; k < kMlpH / 4; ++k) {
-      const float4 w = row[k];
-      acc = __fmaf_rn(w.x, h1[4 * k + 0], acc);
-      acc = __fmaf_rn(w.y, h1[4 * k + 1], acc);
-      acc = __fmaf_rn(w.z, h1[4 * k + 2], acc);
-      acc = __fmaf_rn(w.w, h1[4 * k + 3], acc);
-    }
-    const float h2 = acc > 0.0f ? acc : 0.0f;
+  for (int i = 0; i < kMlpH / 2; ++i) {
+    const float h0 = acc[i].x > 0.0f ? acc[i].x : 0.0f;
+    const float h1 = acc[i].y > 0.0f ? acc[i].y : 0.0f;
 #pragma unroll
-    for (int a = 0; a < kMlpOut; ++a) o[a] = __fmaf_rn(sW[kMlpW3 + a * kMlpH + j], h2, o[a]);
+    for (int a = 0; a < kMlpOut; ++a) o[a] = __fmaf_rn(sW[kMlpW3 + a * kMlpH + 2 * i], h0, o[a]);
+#pragma unroll
+    for (int a = 0; a < kMlpOut; ++a) o[a] = __fmaf_rn(sW[kMlpW3 + a * kMlpH + 2 * i + 1], h1, o[a]);
   }
 }
 
@@ -1579,23 +1624,25 @@ __device__ __forceinline__ void mlp_infer_rows(const float* __restrict__ sW, con
 __global__ void __launch_bounds__(256, 2) pred_slots_kernel(PredArgs pr,
                                                             const uint8_t* __restrict__ ref,
                                                             const u64* __restrict__ off, u32 P,
-                                                            u64* __restrict__ out) {
+                                                            u64 cap, u64* __restrict__ out) {
   __shared__ __align__(16) float sW[(kMlpParams + 3) & ~3];
-  load_mlp(sW, pr.params);
-  const u64 total = off[P];
-  for (u64 g = (u64)blockIdx.x * blockDim.x + threadIdx.x; g < total;
-       g += (u64)gridDim.x * blockDim.x) {
-    const u32 p = pair_of_slot(off, P, g);
-    const u64 r = off[p + 1] - off[p];
+  load_mlp_cols(sW, pr.params);
+  u64 g0, g1;
+  warp_run(prepass_slots(off, P, cap), &g0, &g1);
+  if (g0 >= g1) return;
+  u32 p = pair_of_slot(off, P, g0);
+  for (u64 g = g0 + (threadIdx.x & 31); g < g1; g += 32) {
+    while (__ldg(off + p + 1) <= g) ++p;
+    const u64 o0 = __ldg(off + p), r = __ldg(off + p + 1) - o0;
     const Rec R = load_rec(ref + (g + p + 1) * kRecBytes);
     const Hist H = load_hist(pr.hist + kHistBytes * g);
-    const u32 nc = cell_count(pr.cseg, seg_base(off[p], p), seg_size(r), cell_key(R, pr));
+    const u32 nc = cell_count(pr.cseg, seg_base(o0, p), seg_size(r), cell_key(R, pr));
     float f[kMlpIn];
     u64 pred[3] = {0, 0, 0};
     bool ok = features(R, H, nc, f);
     if (ok) {
       float y[kMlpOut];
-      mlp_infer_rows(sW, f, y);
+      mlp_infer_cols(sW, f, y);
       ok = predict_out(R, y, pred);
     }
     u64* o = out + 4 * g;
@@ -1606,7 +1653,6 @@ __global__ void __launch_bounds__(256, 2) pred_slots_kernel(PredArgs pr,
   }
 }
 
-// The pre-pass of one side: cell counts, then predictions.
 // Zeroes the cell counts' segments of every pair of a reference laid out
 // with off[0..P] (seg_base(off[P], P) entries of 16 bytes; the segments are
 // contiguous), the part of the cell hash the codec and the pre-pass use, at
@@ -1633,11 +1679,12 @@ static tera_status pred_prepass(tera_ctx* ctx, const PredArgs& pr, const uint8_t
                                 const u64* off, u64* out, cudaStream_t s) {
   const unsigned grid = (unsigned)(ctx->num_sms * 2);
   prof_begin(ctx, s);
-  pred_cells_kernel<<<grid, 256, 0, s>>>(pr, ref, off, (u32)ctx->n_pairs);
+  const u64 cap = ctx->pred_cap;
+  pred_cells_kernel<<<grid, 256, 0, s>>>(pr, ref, off, (u32)ctx->n_pairs, cap);
   tera_status st = check_launch(ctx, "pred_cells_kernel", s);
   if (st != TERA_OK) return st;
   prof_begin(ctx, s);
-  pred_slots_kernel<<<grid, 256, 0, s>>>(pr, ref, off, (u32)ctx->n_pairs, out);
+  pred_slots_kernel<<<grid, 256, 0, s>>>(pr, ref, off, (u32)ctx->n_pairs, cap, out);
   return check_launch(ctx, "pred_slots_kernel", s);
 }
 

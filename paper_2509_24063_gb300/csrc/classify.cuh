@@ -55,16 +55,6 @@ __device__ __forceinline__ void load_grid(SmemGrid& s, const GridTables* __restr
   __syncthreads();
 }
 
-// A float32 near a positive binary64 value from the high word of its bits,
-// by integer operations only (exponent re-biased, mantissa cut to 20 bits;
-// a binary64 conversion instruction runs at the GPU's low binary64 rate).
-// Values outside the normal float range give a meaningless estimate, which
-// the exact correction below still turns into the right index.
-__device__ __forceinline__ float approx_f32(u64 bits) {
-  const u32 hi = (u32)(bits >> 32);
-  return __uint_as_float((hi & 0x80000000u) | (((hi & 0x7FFFFFFFu) - 0x38000000u) << 3));
-}
-
 // Box index along one axis of a value inside [lo, hi) (k = key_of(bits)):
 // i = #{k in 1..n-1 : v >= e[k]}, and the keys of that box in *r.  A float32
 // estimate of i is corrected by exact comparisons of the 64-bit keys, so the

@@ -77,6 +77,10 @@ struct PredArgs {
   double lo[3];
   double w;
   u64 ncell[3];
+  // per axis, the cell thresholds (ncell + 1 keys: key(lo), the key of the
+  // first value of each cell 1 .. ncell - 1, key(hi)); null: no table
+  const u64* ck[3];
+  float cflo[3], cfs[3];  // float estimate of a cell index: (x - lo) * (1 / w)
   int allow_residual;
   // batched path: the cell counts and every reference slot's prediction were
   // made by the pre-pass (pred_cells_kernel, pred_slots_kernel) into cseg and
@@ -150,14 +154,32 @@ __device__ __forceinline__ u32 rec_code(const Rec& d, u32* bytes) {
 
 
 // Cell of a reference record: floor((v - lo) / w) per axis, in binary64.
+// Values in [lo, hi) take the axis's threshold table: the index is the
+// largest i < ncell with key(v) >= ck[i], found from a float estimate by
+// exact key comparisons (the table holds the binary64 formula's own
+// boundaries, so the result is the formula's, without binary64 division).
+__device__ __forceinline__ u64 cell_index(u64 bits, int a, const PredArgs& pr) {
+  const u64* T = pr.ck[a];
+  if (T) {
+    const u64 n = pr.ncell[a];
+    const u64 k = key_of(bits);
+    if (k >= __ldg(T) && k < __ldg(T + n)) {
+      const float f = (approx_f32(bits) - pr.cflo[a]) * pr.cfs[a];
+      u64 i = f > 0.0f ? (u64)f : 0;  // the conversion saturates
+      i = i < n - 1 ? i : n - 1;
+      while (i > 0 && k < __ldg(T + i)) --i;
+      while (i + 1 < n && k >= __ldg(T + i + 1)) ++i;
+      return i;
+    }
+  }
+  const double q = floor(__ddiv_rn(__dsub_rn(__longlong_as_double((long long)bits), pr.lo[a]), pr.w));
+  return (u64)(long long)q;
+}
+
 __device__ __forceinline__ u64 cell_key(const Rec& R, const PredArgs& pr) {
   u64 c[3];
 #pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    const double q = floor(__ddiv_rn(__dsub_rn(__longlong_as_double((long long)R.w[1 + a]), pr.lo[a]),
-                                     pr.w));
-    c[a] = (u64)(long long)q;
-  }
+  for (int a = 0; a < 3; ++a) c[a] = cell_index(R.w[1 + a], a, pr);
   return c[0] + pr.ncell[0] * (c[1] + pr.ncell[1] * c[2]);
 }
 
@@ -279,7 +301,6 @@ __device__ __forceinline__ bool features(const Rec& R, const Hist& H, u32 ncount
   return ok;
 }
 
-// Predicted position bits from features; false when an output is not finite.
 // The predicted positions from the network's output: each displacement added
 // to the reference position in double precision; false when an output is
 // not finite.
@@ -292,6 +313,7 @@ __device__ __forceinline__ bool predict_out(const Rec& R, const float* o, u64* p
   return ok;
 }
 
+// Predicted position bits from features; false when an output is not finite.
 __device__ __forceinline__ bool predict_from(const float* W, const Rec& R, const float* f,
                                              u64* pred) {
   float o[kMlpOut];
@@ -314,6 +336,9 @@ inline void fill_pred(const tera_ctx* ctx, PredArgs* pr, const tera_predictor* p
   for (int a = 0; a < 3; ++a) {
     pr->lo[a] = ctx->grid.lo[a];
     pr->ncell[a] = ctx->ncell[a];
+    pr->ck[a] = ctx->ck[a];
+    pr->cflo[a] = ctx->ck_flo[a];
+    pr->cfs[a] = ctx->ck_fs[a];
   }
   pr->w = ctx->grid.w;
   pr->allow_residual = 0;

@@ -349,12 +349,78 @@ tera_status ensure_migrate(tera_ctx* ctx, uint64_t n, uint64_t leavers) {
   return TERA_OK;
 }
 
+// Axes with more cells than this keep the binary64 formula on the device.
+constexpr uint64_t kCellTableMax = 1ull << 16;
+
+static double value_of_key(uint64_t k) {
+  const uint64_t b = k >= 0x8000000000000000ull ? k ^ 0x8000000000000000ull : ~k;
+  double d;
+  memcpy(&d, &b, 8);
+  return d;
+}
+
+static uint64_t key_of_value(double d) {
+  uint64_t b;
+  memcpy(&b, &d, 8);
+  return key_of(b);
+}
+
+// Cell thresholds of one axis of the predictor's cell grid: T[0] = key(lo),
+// T[n] = key(hi), and for 1 <= k < n, T[k] = the key of the smallest binary64
+// x with floor((x - lo) / w) >= k, the quotient evaluated in binary64 exactly
+// as the device's formula evaluates it (IEEE subtraction and division, round
+// to nearest).  The cell is monotone in x, so each T[k] is found by bisection
+// over the keys of [lo, hi], starting above T[k - 1].
+void cell_thresholds(double lo, double hi, double w, uint64_t n, uint64_t* T) {
+  auto cell = [&](uint64_t k) { return (int64_t)std::floor((value_of_key(k) - lo) / w); };
+  const uint64_t klo = key_of_value(lo), khi = key_of_value(hi);
+  T[0] = klo;
+  T[n] = khi;
+  uint64_t below = klo;  // cell(below) < k
+  for (uint64_t k = 1; k < n; ++k) {
+    uint64_t L = below, H = khi;  // cell(L) < k <= cell(H) = n - 1
+    while (H - L > 1) {
+      const uint64_t M = L + (H - L) / 2;
+      if (cell(M) >= (int64_t)k) H = M;
+      else L = M;
+    }
+    T[k] = H;
+    below = H - 1;
+  }
+}
+
+// The predictor's cell threshold tables (once per context).
+static tera_status ensure_cell_tables(tera_ctx* ctx) {
+  if (ctx->d_ckeys) return TERA_OK;
+  uint64_t total = 0, off[3] = {0, 0, 0};
+  for (int a = 0; a < 3; ++a) {
+    off[a] = total;
+    if (ctx->ncell[a] <= kCellTableMax) total += ctx->ncell[a] + 1;
+  }
+  if (total == 0) return TERA_OK;
+  std::vector<uint64_t> h(total);
+  for (int a = 0; a < 3; ++a)
+    if (ctx->ncell[a] <= kCellTableMax)
+      cell_thresholds(ctx->grid.lo[a], ctx->grid.hi[a], ctx->grid.w, ctx->ncell[a], h.data() + off[a]);
+  tera_status st = alloc_dev(ctx->d_ckeys, total);
+  if (st != TERA_OK) return st;
+  if (cudaMemcpy(ctx->d_ckeys, h.data(), 8 * total, cudaMemcpyHostToDevice) != cudaSuccess)
+    return TERA_ECUDA;
+  for (int a = 0; a < 3; ++a) {
+    ctx->ck[a] = ctx->ncell[a] <= kCellTableMax ? ctx->d_ckeys + off[a] : nullptr;
+    ctx->ck_flo[a] = (float)ctx->grid.lo[a];
+    ctx->ck_fs[a] = (float)(1.0 / ctx->grid.w);
+  }
+  return TERA_OK;
+}
+
 tera_status ensure_pred(tera_ctx* ctx) {
   const u64 cap = ctx->cap_records, P = ctx->n_pairs;
   if (ctx->cseg_enc && ctx->pred_cap >= cap && ctx->unit_res && ctx->unit_res_cap >= ctx->cap_units)
     return TERA_OK;
   cudaDeviceSynchronize();
   tera_status st;
+  if ((st = ensure_cell_tables(ctx)) != TERA_OK) return st;
   if ((st = alloc_dev(ctx->cseg_enc, 2 * (2 * cap + 2 * P))) != TERA_OK) return st;
   if ((st = alloc_dev(ctx->cseg_dec, 2 * (2 * cap + 2 * P))) != TERA_OK) return st;
   if ((st = alloc_dev(ctx->pscr, 4 * cap)) != TERA_OK) return st;
@@ -370,6 +436,16 @@ tera_status ensure_pred(tera_ctx* ctx) {
 extern "C" {
 
 const char* tera_version(void) { return "tera-gb300 1.0 (sm_103a)"; }
+
+tera_status tera_cell_thresholds(double lo, double hi, double w, uint64_t n, uint64_t* T) {
+  if (!T || !std::isfinite(lo) || !std::isfinite(hi) || !std::isfinite(w) || !(lo < hi) ||
+      !(w > 0.0))
+    return TERA_EINVAL;
+  const double c = std::floor((hi - lo) / w);
+  if (!(c >= 0.0 && c < 1.8e19) || n != (uint64_t)c + 1) return TERA_EINVAL;
+  tera::cell_thresholds(lo, hi, w, n, T);
+  return TERA_OK;
+}
 
 tera_status tera_ref_schedule(uint64_t t, uint32_t ref_interval, int32_t* out_buf,
                               int32_t* ref_buf, uint64_t* ref_iteration) {
@@ -530,6 +606,7 @@ tera_status tera_ctx_destroy(tera_ctx* c) {
   free_dev(c->m_hist);
   free_dev(c->cseg_enc);
   free_dev(c->cseg_dec);
+  free_dev(c->d_ckeys);
   free_dev(c->pscr);
   free_dev(c->unit_res);
   free_dev(c->mlp_scratch);

@@ -80,6 +80,16 @@ __host__ __device__ __forceinline__ u64 key_of(u64 b) {
   return b ^ (neg | 0x8000000000000000ull);
 }
 
+// A float32 near a binary64 value from the high word of its bits, by integer
+// operations only (exponent re-biased, mantissa cut to 20 bits; a binary64
+// conversion instruction runs at the GPU's low binary64 rate).  Values
+// outside the normal float range give a meaningless estimate: callers only
+// use it as the start of an exact search.
+__device__ __forceinline__ float approx_f32(u64 bits) {
+  const u32 hi = (u32)(bits >> 32);
+  return __uint_as_float((hi & 0x80000000u) | (((hi & 0x7FFFFFFFu) - 0x38000000u) << 3));
+}
+
 // Device-side totals (layout of tera_stats).
 struct DevStats {
   u64 iterations, agents, records, ref_slots, holes, new_records, payload_bytes, wire_bytes;

@@ -61,6 +61,9 @@ struct tera_ctx {
 
   // learned predictor (cell counts of both sides, per-slot predictions)
   uint64_t ncell[3];
+  tera::u64* d_ckeys;       // cell thresholds of the axes that have a table
+  const tera::u64* ck[3];   // axis a's table in d_ckeys (null: none)
+  float ck_flo[3], ck_fs[3];
   uint64_t pred_cap;
   tera::u64* cseg_enc;
   tera::u64* cseg_dec;

@@ -103,3 +103,73 @@ def test_reference_schedule_rejects_zero_interval(libpath):
     ob, rb, ri = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_uint64()
     assert lib.tera_ref_schedule(3, 0, ctypes.byref(ob), ctypes.byref(rb),
                                  ctypes.byref(ri)) == _lib.EINVAL
+
+
+def _key(x: float) -> int:
+    """Order-preserving key of a binary64 value (-0.0 taken as +0.0)."""
+    import struct
+    b = struct.unpack("<Q", struct.pack("<d", x + 0.0 if x == 0.0 else x))[0]
+    return b ^ 0x8000000000000000 if b < 0x8000000000000000 else b ^ 0xFFFFFFFFFFFFFFFF
+
+
+def _value(k: int) -> float:
+    import struct
+    b = k ^ 0x8000000000000000 if k >= 0x8000000000000000 else k ^ 0xFFFFFFFFFFFFFFFF
+    return struct.unpack("<d", struct.pack("<Q", b))[0]
+
+
+@pytest.mark.parametrize("lo,hi,w", [
+    (0.0, 600.0, 30.0),          # exact multiples
+    (-37.5, 41.3, 0.7),          # negative lo, a width with no exact binary64 value
+    (12.25, 13.0, 0.1),
+    (1.0e6, 1.0e6 + 3.0, 0.01),  # large coordinates: the cell edges fall between ulps
+    (-0.0, 5.0, 7.0),            # a single cell
+    (-1.0e-3, 1.0e-3, 1.0e-5),   # across zero
+])
+def test_cell_thresholds_match_the_binary64_rule(libpath, lo, hi, w):
+    """tera_cell_thresholds against the rule itself, evaluated with Python's
+    IEEE binary64 arithmetic: T[k] is the first value of cell k (the value
+    before it lies in a lower cell), and the lookup by keys gives
+    floor((x - lo) / w) for values spread over the axis and for every value
+    within two ulps of each boundary."""
+    import math
+    import numpy as np
+    from paper_2509_24063_gb300.api import cell_thresholds
+    cell = lambda x: math.floor((x - lo) / w)  # noqa: E731
+    n = math.floor((hi - lo) / w) + 1
+    T = cell_thresholds(lo, hi, w)
+    assert T.shape == (n + 1,)
+    assert int(T[0]) == _key(lo) and int(T[n]) == _key(hi)
+    assert np.all(T[1:] >= T[:-1])
+    for k in range(1, n):
+        x = _value(int(T[k]))
+        assert cell(x) >= k
+        assert cell(math.nextafter(x, -math.inf)) < k
+    rng = np.random.default_rng(4)
+    xs = list(rng.uniform(lo, hi, 2000)) + [lo, math.nextafter(hi, -math.inf)]
+    for k in range(1, n):
+        x = _value(int(T[k]))
+        for _ in range(2):
+            x = math.nextafter(x, -math.inf)
+        for _ in range(5):
+            xs.append(x)
+            x = math.nextafter(x, math.inf)
+    for x in xs:
+        if not (lo <= x < hi):
+            continue
+        i = int(np.searchsorted(T[:n], np.uint64(_key(x)), side="right")) - 1
+        assert i == cell(x), x
+
+
+def test_cell_thresholds_reject_bad_arguments(libpath):
+    import numpy as np
+    from paper_2509_24063_gb300 import _lib
+    lib = _lib.load()
+    T = np.zeros(64, dtype=np.uint64)
+    p = T.ctypes.data_as(ctypes.c_void_p)
+    assert lib.tera_cell_thresholds(0.0, 10.0, 1.0, 11, p) == _lib.OK
+    for args in ((0.0, 10.0, 1.0, 10), (0.0, 10.0, 1.0, 12), (0.0, 10.0, 0.0, 1),
+                 (0.0, 10.0, -1.0, 11), (10.0, 0.0, 1.0, 1), (float("nan"), 10.0, 1.0, 11),
+                 (0.0, float("inf"), 1.0, 11)):
+        assert lib.tera_cell_thresholds(*args, p) == _lib.EINVAL, args
+    assert lib.tera_cell_thresholds(0.0, 10.0, 1.0, 11, None) == _lib.EINVAL

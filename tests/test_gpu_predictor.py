@@ -2,6 +2,8 @@
 the residual codec against the oracle byte for byte (records and histories of
 both sides, per-call and batched paths), deterministic training, and the
 bytes a trained network saves over plain XOR differences."""
+import math
+
 import numpy as np
 import pytest
 import torch
@@ -84,15 +86,59 @@ def test_sgd_step_with_clipping_matches_oracle(tera, clip):
 def run_pred_chain(tera, wl, params, path, tune=None):
     gen = Generator(wl, device="cuda")
     states = list(gen.series(wl.iterations))
+    return run_pred_states(tera, states, wl.lo, wl.hi, wl.grid, wl.w, params, path, tune)
+
+
+def check_samples(samples, rec, off, ref, wire, wo, wl_, lo, w):
+    """The encoder's training samples of every slot of every XOR-mode message
+    against the oracle: the features (the cell count among them, as
+    ncount / 32) and targets of each matched slot with a full history, a zero
+    flag everywhere else.  Returns the number of valid samples."""
+    ra, ro, rh = ref
+    P = len(off) - 1
+    valid = 0
+    for p in range(P):
+        if not wl_[p] or int(wire[int(wo[p]) + 12]) != oracle.MODE_XOR:
+            continue
+        refp = oracle.arena_pair(ra, ro, p)
+        if not len(refp):
+            continue
+        msg = oracle.arena_pair(rec, off, p)
+        where = {int(i): k for k, i in enumerate(msg[:, 0])}
+        cnt = oracle.cell_counts(refp, lo, w)
+        for j in range(len(refp)):
+            row = samples[12 * (int(ro[p]) + j):12 * (int(ro[p]) + j + 1)]
+            h = rh[48 * (int(ro[p]) + j):48 * (int(ro[p]) + j + 1)]
+            ok, f = oracle.features(refp[j], h, int(cnt[j]))
+            m = where.get(int(refp[j, 0]))
+            if m is None or not ok:
+                assert row[11] == 0.0, (p, j)
+                continue
+            assert row[11] == 1.0, (p, j)
+            assert row[:8].tobytes() == f.tobytes(), (p, j, row[:8], f, int(cnt[j]))
+            tgt = (msg[m, 1:4].view(np.float64) - refp[j, 1:4].view(np.float64)).astype(np.float32)
+            assert row[8:11].tobytes() == tgt.tobytes(), (p, j)
+            valid += 1
+    return valid
+
+
+def run_pred_states(tera, states, lo, hi, grid, w, params, path, tune=None, samples=False):
+    """The predictor path over `states` against the oracle: every message, both
+    sides' references and histories byte for byte; with samples, the encoder's
+    training samples too (check_samples).  Returns the message modes."""
     nmax = max(int(s["x"].shape[0]) for s in states)
-    ctx = tera.Context(wl.lo, wl.hi, wl.grid, wl.w)
+    ctx = tera.Context(lo, hi, grid, w)
     pt = torch.from_numpy(params).cuda()
-    ex = tera.AuraExchange(ctx, max_agents=nmax, max_records=4 * nmax + 1024, path=path,
+    mr = 4 * nmax + 1024
+    ex = tera.AuraExchange(ctx, max_agents=nmax, max_records=mr, path=path,
                            params=pt, tune=tune)
-    g = oracle.make_grid(wl.lo, wl.hi, wl.grid, wl.w)
+    g = oracle.make_grid(lo, hi, grid, w)
     ref = recv = None
     modes = []
+    n_valid = 0
     for st in states:
+        if samples:
+            ex.samples = torch.zeros(12 * mr, dtype=torch.float32, device="cuda")
         ex.step(st)
         ctx.status()
         s = to_numpy(st)
@@ -100,12 +146,13 @@ def run_pred_chain(tera, wl, params, path, tune=None):
         _, cnt, off, idx = oracle.pair_lists(g, owner, mask)
         rec = oracle.pack(s, off, idx)
         ra, ro, rh = (None, None, None) if ref is None else ref
-        st_, wire, wo, wl_, nxt, hn = oracle.encode_all_pred(rec, off, ra, ro, rh, params, wl.lo,
-                                                             wl.w)
+        st_, wire, wo, wl_, nxt, hn = oracle.encode_all_pred(rec, off, ra, ro, rh, params, lo, w)
         assert st_ == oracle.OK
         va, vo, vh = (None, None, None) if recv is None else recv
-        st_, rcv, rvo, rhn = oracle.decode_all_pred(wire, wo, va, vo, vh, params, wl.lo, wl.w)
+        st_, rcv, rvo, rhn = oracle.decode_all_pred(wire, wo, va, vo, vh, params, lo, w)
         assert st_ == oracle.OK
+        if samples and ref is not None:
+            n_valid += check_samples(ex.samples.cpu().numpy(), rec, off, ref, wire, wo, wl_, lo, w)
         P = ctx.n_pairs
         E = int(off[-1])
         gwo = ex.wire_off.cpu().numpy().view(np.uint64)
@@ -126,7 +173,69 @@ def run_pred_chain(tera, wl, params, path, tune=None):
         assert ex.receiver_hist()[:E * 48].cpu().numpy().tobytes() == rhn.tobytes()
         ref, recv = (nxt, off, hn), (rcv, rvo, rhn)
     ctx.close()
+    if samples:
+        assert n_valid > 0
     return modes
+
+
+def cell_edges(lo, hi, w):
+    """The first binary64 value of each cell 1 .. n - 1 of one axis (cell(x) =
+    floor((x - lo) / w)), found by stepping from lo + k w one ulp at a time."""
+    n = math.floor((hi - lo) / w) + 1
+    out = []
+    for k in range(1, n):
+        x = lo + k * w
+        while math.floor((x - lo) / w) >= k:
+            x = math.nextafter(x, -math.inf)
+        while math.floor((x - lo) / w) < k:
+            x = math.nextafter(x, math.inf)
+        out.append(x)
+    return np.array(out)
+
+
+def boundary_states(lo, hi, w, near, n, iters, seed):
+    """Agents (same ids every iteration) placed on cell edges of each axis or
+    within two ulps of one, re-drawn every iteration: per axis, the edges
+    within 4 w of the `near` coordinates (the box faces, so that many agents
+    are in some aura), which gives dozens of agents per cell on both sides of
+    every edge."""
+    rng = np.random.default_rng(seed)
+    edges = []
+    for a in range(3):
+        e = cell_edges(lo[a], hi[a], w)
+        sel = np.zeros(len(e), dtype=bool)
+        for c in near[a]:
+            sel |= np.abs(e - c) <= 4 * w
+        edges.append(e[sel])
+    d = 8.0 + 4.0 * rng.random(n)
+    states = []
+    for _ in range(iters):
+        pos = []
+        for a in range(3):
+            x = edges[a][rng.integers(0, len(edges[a]), n)]
+            k = rng.integers(-2, 3, n)
+            for s in (1, 2):
+                x = np.where(k >= s, np.nextafter(x, np.inf), x)
+                x = np.where(k <= -s, np.nextafter(x, -np.inf), x)
+            pos.append(np.clip(x, lo[a], np.nextafter(hi[a], -np.inf)))
+        st = dict(id=np.arange(n, dtype=np.int64), x=pos[0], y=pos[1], z=pos[2], diameter=d,
+                  volume=(math.pi / 6.0) * d ** 3, adherence=np.full(n, 0.5),
+                  density=np.ones(n))
+        states.append({k: torch.from_numpy(np.ascontiguousarray(v)).cuda() for k, v in st.items()})
+    return states
+
+
+@pytest.mark.parametrize("path", ["batched", "all_pairs"])
+def test_cell_counts_on_binary64_cell_edges(tera, path):
+    """Every reference record on a cell edge or within two ulps of one (the
+    device finds cells by the context's threshold tables, the oracle by the
+    binary64 formula): the training samples' cell counts and features, the
+    messages and both sides' histories all equal the oracle's."""
+    lo, hi, w = (-37.5, 12.25, 0.0), (41.3, 70.0, 33.0), 0.7
+    grid = (2, 2, 1)
+    near = [[lo[0] + (hi[0] - lo[0]) / 2], [lo[1] + (hi[1] - lo[1]) / 2], [5.0, 20.0]]
+    states = boundary_states(lo, hi, w, near, 20000, 5, seed=12)
+    run_pred_states(tera, states, lo, hi, grid, w, velocity_network(), path, samples=True)
 
 
 @pytest.mark.parametrize("path", ["all_pairs", "batched", "per_subdomain"])
