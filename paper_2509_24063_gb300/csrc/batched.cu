@@ -1570,63 +1570,79 @@ __device__ __forceinline__ void load_mlp_cols(float* sW, const float* __restrict
   __syncthreads();
 }
 
-// The network on one feature vector with the same fused multiply-adds, in
-// the same order per neuron, as mlp_infer (so the same bits): the first
-// hidden layer is made one neuron k at a time, and its output enters all 64
-// accumulators of the second layer at once, two neurons per paired
-// multiply-add (each component an fmaf of its own).  Each second-layer
-// neuron still adds its inputs k = 0 .. 63 in ascending order.
-__device__ __forceinline__ void mlp_infer_cols(const float* __restrict__ sW, const float* f,
-                                               float* o) {
+// First-layer neuron k of one feature vector: its bias, then the inputs in
+// ascending order, then ReLU (as mlp_infer).
+__device__ __forceinline__ float hidden1(const float4 wa, const float4 wb, float bias,
+                                         const float* f) {
+  float h = bias;
+  h = __fmaf_rn(wa.x, f[0], h);
+  h = __fmaf_rn(wa.y, f[1], h);
+  h = __fmaf_rn(wa.z, f[2], h);
+  h = __fmaf_rn(wa.w, f[3], h);
+  h = __fmaf_rn(wb.x, f[4], h);
+  h = __fmaf_rn(wb.y, f[5], h);
+  h = __fmaf_rn(wb.z, f[6], h);
+  h = __fmaf_rn(wb.w, f[7], h);
+  return h > 0.0f ? h : 0.0f;
+}
+
+// The network on two feature vectors A and B with the same fused
+// multiply-adds, in the same order per neuron, as mlp_infer (so the same
+// bits), each weight read from shared memory once for both vectors.  The
+// second layer runs in two halves of 32 neurons (the first layer is made
+// again for each half, one neuron k at a time, and its output enters the
+// half's 32 accumulators of both vectors); each second-layer neuron adds its
+// inputs k = 0 .. 63 in ascending order, and each output adds j = 0 .. 63 in
+// ascending order across the halves.
+__device__ __forceinline__ void mlp_infer_pair(const float* __restrict__ sW, const float* fA,
+                                               const float* fB, float* oA, float* oB) {
   const float4* W4 = reinterpret_cast<const float4*>(sW);
-  const float2* B2 = reinterpret_cast<const float2*>(sW + kMlpB2);
-  float2 acc[kMlpH / 2];
 #pragma unroll
-  for (int i = 0; i < kMlpH / 2; ++i) acc[i] = B2[i];
+  for (int a = 0; a < kMlpOut; ++a) oA[a] = oB[a] = sW[kMlpB3 + a];
 #pragma unroll 1
-  for (int k = 0; k < kMlpH; ++k) {
-    const float4 a = W4[(kMlpW1 + k * kMlpIn) / 4], b = W4[(kMlpW1 + k * kMlpIn) / 4 + 1];
-    float h = sW[kMlpB1 + k];
-    h = __fmaf_rn(a.x, f[0], h);
-    h = __fmaf_rn(a.y, f[1], h);
-    h = __fmaf_rn(a.z, f[2], h);
-    h = __fmaf_rn(a.w, f[3], h);
-    h = __fmaf_rn(b.x, f[4], h);
-    h = __fmaf_rn(b.y, f[5], h);
-    h = __fmaf_rn(b.z, f[6], h);
-    h = __fmaf_rn(b.w, f[7], h);
-    h = h > 0.0f ? h : 0.0f;
-    const float2 hh = make_float2(h, h);
-    const float4* col = W4 + (kMlpW2 + k * kMlpH) / 4;
+  for (int hf = 0; hf < 2; ++hf) {
+    float accA[32], accB[32];
 #pragma unroll
-    for (int q = 0; q < kMlpH / 4; ++q) {
-      const float4 w = col[q];
-      acc[2 * q] = __ffma2_rn(make_float2(w.x, w.y), hh, acc[2 * q]);
-      acc[2 * q + 1] = __ffma2_rn(make_float2(w.z, w.w), hh, acc[2 * q + 1]);
+    for (int j = 0; j < 32; ++j) accA[j] = accB[j] = sW[kMlpB2 + 32 * hf + j];
+#pragma unroll 1
+    for (int k = 0; k < kMlpH; ++k) {
+      const float4 wa = W4[(kMlpW1 + k * kMlpIn) / 4], wb = W4[(kMlpW1 + k * kMlpIn) / 4 + 1];
+      const float bias = sW[kMlpB1 + k];
+      const float hA = hidden1(wa, wb, bias, fA), hB = hidden1(wa, wb, bias, fB);
+      const float4* col = W4 + (kMlpW2 + k * kMlpH + 32 * hf) / 4;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const float4 w = col[q];
+        accA[4 * q] = __fmaf_rn(w.x, hA, accA[4 * q]);
+        accB[4 * q] = __fmaf_rn(w.x, hB, accB[4 * q]);
+        accA[4 * q + 1] = __fmaf_rn(w.y, hA, accA[4 * q + 1]);
+        accB[4 * q + 1] = __fmaf_rn(w.y, hB, accB[4 * q + 1]);
+        accA[4 * q + 2] = __fmaf_rn(w.z, hA, accA[4 * q + 2]);
+        accB[4 * q + 2] = __fmaf_rn(w.z, hB, accB[4 * q + 2]);
+        accA[4 * q + 3] = __fmaf_rn(w.w, hA, accA[4 * q + 3]);
+        accB[4 * q + 3] = __fmaf_rn(w.w, hB, accB[4 * q + 3]);
+      }
     }
-  }
-  o[0] = sW[kMlpB3 + 0];
-  o[1] = sW[kMlpB3 + 1];
-  o[2] = sW[kMlpB3 + 2];
 #pragma unroll
-  for (int i = 0; i < kMlpH / 2; ++i) {
-    const float h0 = acc[i].x > 0.0f ? acc[i].x : 0.0f;
-    const float h1 = acc[i].y > 0.0f ? acc[i].y : 0.0f;
+    for (int j = 0; j < 32; ++j) {
+      const float h2A = accA[j] > 0.0f ? accA[j] : 0.0f, h2B = accB[j] > 0.0f ? accB[j] : 0.0f;
 #pragma unroll
-    for (int a = 0; a < kMlpOut; ++a) o[a] = __fmaf_rn(sW[kMlpW3 + a * kMlpH + 2 * i], h0, o[a]);
-#pragma unroll
-    for (int a = 0; a < kMlpOut; ++a) o[a] = __fmaf_rn(sW[kMlpW3 + a * kMlpH + 2 * i + 1], h1, o[a]);
+      for (int a = 0; a < kMlpOut; ++a) {
+        const float w = sW[kMlpW3 + a * kMlpH + 32 * hf + j];
+        oA[a] = __fmaf_rn(w, h2A, oA[a]);
+        oB[a] = __fmaf_rn(w, h2B, oB[a]);
+      }
+    }
   }
 }
 
-// Every reference slot's prediction (bits of the three predicted positions)
-// and whether it is usable, into out[4 g .. 4 g + 3].
-__global__ void __launch_bounds__(256, 2) pred_slots_kernel(PredArgs pr,
+// Every reference slot's features into out[4 g .. 4 g + 3] (8 floats), the
+// first one a NaN when the slot is not predictable (features() false; a
+// predictable slot's features are all finite).
+__global__ void __launch_bounds__(256) pred_features_kernel(PredArgs pr,
                                                             const uint8_t* __restrict__ ref,
                                                             const u64* __restrict__ off, u32 P,
                                                             u64 cap, u64* __restrict__ out) {
-  __shared__ __align__(16) float sW[(kMlpParams + 3) & ~3];
-  load_mlp_cols(sW, pr.params);
   u64 g0, g1;
   warp_run(prepass_slots(off, P, cap), &g0, &g1);
   if (g0 >= g1) return;
@@ -1638,18 +1654,79 @@ __global__ void __launch_bounds__(256, 2) pred_slots_kernel(PredArgs pr,
     const Hist H = load_hist(pr.hist + kHistBytes * g);
     const u32 nc = cell_count(pr.cseg, seg_base(o0, p), seg_size(r), cell_key(R, pr));
     float f[kMlpIn];
-    u64 pred[3] = {0, 0, 0};
-    bool ok = features(R, H, nc, f);
-    if (ok) {
-      float y[kMlpOut];
-      mlp_infer_cols(sW, f, y);
-      ok = predict_out(R, y, pred);
+    if (!features(R, H, nc, f)) f[0] = __int_as_float(0x7FC00000);
+    float4* o = reinterpret_cast<float4*>(out + 4 * g);
+    o[0] = make_float4(f[0], f[1], f[2], f[3]);
+    o[1] = make_float4(f[4], f[5], f[6], f[7]);
+  }
+}
+
+// One slot's features from out (read before its prediction replaces them);
+// false when the slot is not predictable.
+__device__ __forceinline__ bool load_features(const u64* out, u64 g, float* f) {
+  const float4* fi = reinterpret_cast<const float4*>(out + 4 * g);
+  const float4 a = __ldcs(fi), b = __ldcs(fi + 1);
+  const bool ok = !isnan(a.x);
+  f[0] = ok ? a.x : 0.0f;
+  f[1] = ok ? a.y : 0.0f;
+  f[2] = ok ? a.z : 0.0f;
+  f[3] = ok ? a.w : 0.0f;
+  f[4] = ok ? b.x : 0.0f;
+  f[5] = ok ? b.y : 0.0f;
+  f[6] = ok ? b.z : 0.0f;
+  f[7] = ok ? b.w : 0.0f;
+  return ok;
+}
+
+// The prediction of slot g (pair p) from the network's output, into
+// out[4 g .. 4 g + 3]: bits of the three predicted positions and whether it
+// is usable.
+__device__ __forceinline__ void store_pred(const uint8_t* __restrict__ ref, u32 p, u64* out,
+                                           u64 g, const float* y, bool ok) {
+  u64 pred[3] = {0, 0, 0};
+  if (ok) {
+    const u64* rp = reinterpret_cast<const u64*>(ref + (g + p + 1) * kRecBytes);
+    Rec R;
+    R.w[1] = __ldg(rp + 1);
+    R.w[2] = __ldg(rp + 2);
+    R.w[3] = __ldg(rp + 3);
+    ok = predict_out(R, y, pred);
+  }
+  ulonglong2* o = reinterpret_cast<ulonglong2*>(out + 4 * g);
+  o[0] = make_ulonglong2(pred[0], pred[1]);
+  o[1] = make_ulonglong2(pred[2], ok ? 1ull : 0ull);
+}
+
+// Every reference slot's prediction from its features (in out[4 g .. 4 g +
+// 3], replaced).  A thread takes two slots of its warp's run at a time (gA
+// and gA + 32) and runs the network on both at once.
+__global__ void __launch_bounds__(256, 2) pred_slots_kernel(PredArgs pr,
+                                                            const uint8_t* __restrict__ ref,
+                                                            const u64* __restrict__ off, u32 P,
+                                                            u64 cap, u64* __restrict__ out) {
+  __shared__ __align__(16) float sW[(kMlpParams + 3) & ~3];
+  load_mlp_cols(sW, pr.params);
+  u64 g0, g1;
+  warp_run(prepass_slots(off, P, cap), &g0, &g1);
+  if (g0 >= g1) return;
+  u32 pA = pair_of_slot(off, P, g0), pB = pA;
+  for (u64 gA = g0 + (threadIdx.x & 31); gA < g1; gA += 64) {
+    const bool liveB = gA + 32 < g1;
+    const u64 gB = liveB ? gA + 32 : gA;
+    float fA[kMlpIn], fB[kMlpIn];
+    const bool okA = load_features(out, gA, fA);
+    const bool okB = liveB && load_features(out, gB, fB);
+    if (!liveB)
+      for (int i = 0; i < kMlpIn; ++i) fB[i] = 0.0f;
+    float yA[kMlpOut] = {0.0f, 0.0f, 0.0f}, yB[kMlpOut] = {0.0f, 0.0f, 0.0f};
+    if (__any_sync(__activemask(), okA || okB)) mlp_infer_pair(sW, fA, fB, yA, yB);
+    while (__ldg(off + pA + 1) <= gA) ++pA;
+    store_pred(ref, pA, out, gA, yA, okA);
+    if (liveB) {
+      if (pB < pA) pB = pA;
+      while (__ldg(off + pB + 1) <= gB) ++pB;
+      store_pred(ref, pB, out, gB, yB, okB);
     }
-    u64* o = out + 4 * g;
-    o[0] = pred[0];
-    o[1] = pred[1];
-    o[2] = pred[2];
-    o[3] = ok ? 1ull : 0ull;
   }
 }
 
@@ -1683,6 +1760,10 @@ static tera_status pred_prepass(tera_ctx* ctx, const PredArgs& pr, const uint8_t
   pred_cells_kernel<<<grid, 256, 0, s>>>(pr, ref, off, (u32)ctx->n_pairs, cap);
   tera_status st = check_launch(ctx, "pred_cells_kernel", s);
   if (st != TERA_OK) return st;
+  prof_begin(ctx, s);
+  pred_features_kernel<<<(unsigned)(ctx->num_sms * 8), 256, 0, s>>>(pr, ref, off,
+                                                                   (u32)ctx->n_pairs, cap, out);
+  if ((st = check_launch(ctx, "pred_features_kernel", s)) != TERA_OK) return st;
   prof_begin(ctx, s);
   pred_slots_kernel<<<grid, 256, 0, s>>>(pr, ref, off, (u32)ctx->n_pairs, cap, out);
   return check_launch(ctx, "pred_slots_kernel", s);
