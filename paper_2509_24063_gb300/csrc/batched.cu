@@ -665,6 +665,40 @@ __device__ __forceinline__ void bat_match(const EncArgs& A, const BatchArgs& B, 
   }
 }
 
+// The predictor's match totals of one slot tile of pair p after a match in
+// shared memory (slot_src written by this block): the XOR and residual
+// payload bytes of the matched slots (and their training samples), as
+// bat_match makes them in the global path.
+template <int T, bool PR>
+__device__ __forceinline__ void bat_sizes(const EncArgs& A, const BatchArgs& B, u32 p, u64 tile,
+                                          U64x2* sm) {
+  const u64* pi = A.info + (u64)p * 8;
+  const u64 r = pi[PI_R];
+  const u64 j = tile * T + threadIdx.x;
+  u64 bx = 0, br = 0;
+  if (j < r) {
+    const u64 ro = A.ref_off[p];
+    if (A.pr.samples) A.pr.samples[(u64)kSampleFloats * (ro + j) + 11] = 0.0f;
+    const u32 g = A.slot_src[ro + j];
+    if (g != kNoMatch) {
+      const Rec R = load_rec(A.ref + (ro + p + 1 + j) * kRecBytes);
+      const Rec M = load_rec(A.rec + ((u64)g + p + 1) * kRecBytes);
+      u32 b = 0;
+#pragma unroll
+      for (int w = 0; w < 8; ++w) b += sig_bytes(M.w[w] ^ R.w[w]);
+      bx = b;
+      br = pred_slot<PR>(A, p, j, r, pi[PI_MODE], R, M, b);
+    }
+  }
+  U64x2 tot;
+  block_excl_scan2(U64x2{bx, br}, sm, &tot);
+  if (threadIdx.x == 0) {
+    u64* pt = B.ptot + (u64)p * PT_COUNT;
+    if (tot.a) atomicAdd(pt + PT_XOR, tot.a);
+    if (tot.b) atomicAdd(pt + PT_RES, tot.b);
+  }
+}
+
 // Message mode of pair p once MATCH is complete.
 template <bool PR>
 __device__ __forceinline__ u64 pair_mode(const EncArgs& A, const BatchArgs& B, u32 p) {
@@ -1831,7 +1865,7 @@ __global__ void __launch_bounds__(T, (1024 / T) > 0 ? (1024 / T) : 1)
     const u64* pi = E.info + (u64)p * 8;
     const u64 r = pi[PI_R], m = pi[PI_M];
     SmemTable tb{nullptr, 0u, bits};
-    if (!PR && table_records > 0 && m <= table_records && m <= kTableMax) {
+    if (table_records > 0 && m <= table_records && m <= kTableMax) {
       u32 size = 32;
       while (size < 2 * m) size <<= 1;
       tb.tbl = tbl;
@@ -1846,6 +1880,13 @@ __global__ void __launch_bounds__(T, (1024 / T) > 0 ? (1024 / T) : 1)
       if (threadIdx.x == 0) {
         B.ptot[(u64)p * PT_COUNT + PT_MATCHED] = s_cnt;
         s_cnt = 0;
+      }
+      if constexpr (PR) {
+        if (E.pr.hist && E.pr.samples && !E.pr.pre) {
+          for (u64 t = 0; t < ceil_div(r, T); ++t) cells_unit(E.pr, E.ref, E.ref_off, p, t, r, T);
+          __syncthreads();
+        }
+        for (u64 t = 0; t < ceil_div(r, T); ++t) bat_sizes<T, PR>(E, B, p, t, sm);
       }
     } else {
       const u64 ntb = ceil_div(m, (u64)T * kIlp);
@@ -1908,11 +1949,9 @@ inline void persistent_smem(u32 T, bool PR, int ctas_per_sm, u32 want_records, s
   size_t cap = per_block > 2048 ? per_block - 2048 : 0;
   if (cap > (size_t)227 * 1024) cap = (size_t)227 * 1024;
   u32 rec = 0;
-  if (!PR) {
-    for (u32 c = 32; c <= 8192; c <<= 1)
-      if (region_bytes(T, c) + c / 8 + 16 <= cap && (want_records == 0 || c <= want_records))
-        rec = c;
-  }
+  for (u32 c = 32; c <= 8192; c <<= 1)
+    if (region_bytes(T, c) + c / 8 + 16 <= cap && (want_records == 0 || c <= want_records))
+      rec = c;
   *records = rec;
   // + 16 bytes: the decode's 8-byte reads may pass the end of the stage
   *bytes = region_bytes(T, rec) + rec / 8 + 16;

@@ -254,6 +254,13 @@ def test_residual_codec_carried_by_teams(tera, tune):
     assert oracle.MODE_RESIDUAL in modes
 
 
+def test_residual_codec_with_global_hash_pairs(tera):
+    # shared-memory tables limited to 32 records: every larger pair below the
+    # team threshold is matched in the global hash segments by one block
+    modes = run_pred_chain(tera, drift(), velocity_network(), "batched", tune=(256, 4, 32, 0))
+    assert oracle.MODE_RESIDUAL in modes
+
+
 @pytest.mark.parametrize("path", ["all_pairs", "batched"])
 def test_residual_codec_matches_oracle_random_net(tera, path):
     rng = np.random.default_rng(9)
