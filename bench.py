@@ -508,6 +508,9 @@ def main():
     ap.add_argument("--compare-paths", action="store_true",
                     help="agents/s of the per-subdomain, all-pairs and batched paths on the same "
                          "states (one JSON line)")
+    ap.add_argument("--metrics-log", default="",
+                    help="after the timed run, re-run its iterations eagerly and write one JSON "
+                         "line per iteration to this file")
     ap.add_argument("--train-iters", type=int, default=200)
     ap.add_argument("--eval-iters", type=int, default=20)
     args = ap.parse_args()
@@ -643,6 +646,34 @@ def main():
                   file=sys.stderr)
         print(json.dumps(stats), file=sys.stderr)
 
+    # per-iteration metrics: the same iterations again, eager, untimed by the line above
+    metrics_rows = []
+    if args.metrics_log and rank == 0:
+        ex.reset()
+        ctx.stats(reset=True)
+        ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for t in range(total_steps):
+            ea.record(stream)
+            ex.step(states[t])
+            eb.record(stream)
+            torch.cuda.synchronize()
+            st = ctx.stats(reset=True)
+            ms = ea.elapsed_time(eb)
+            n = int(states[t]["x"].shape[0])
+            step_bytes = kernel_bytes("pack_kernel", st) + kernel_bytes("codec_persistent_kernel", st)
+            metrics_rows.append({
+                "workload": args.workload + (f"@{args.agents}" if args.agents else ""),
+                "path": args.path, "tune": list(ex.tune) if ex.tune else None,
+                "ref_interval": args.ref_interval, "iteration": t, "agents": n,
+                "pairs": ctx.n_pairs, "aura_records": st["records"], "ref_slots": st["ref_slots"],
+                "new_records": st["new_records"], "holes": st["holes"],
+                "raw_bytes": 64 * st["records"], "packed_bytes": st["wire_bytes"],
+                "payload_bytes": st["payload_bytes"], "ms_eager": ms,
+                "agents_per_s": n / (ms / 1e3),
+                "pack_codec_gbs": step_bytes / (ms / 1e3) / 1e9,
+                "pack_codec_hbm_frac": step_bytes / (ms / 1e3) / 1e9 / hbm})
+        ctx.status()
+
     # the CPU baseline's sample (host copies) and the end-to-end inputs are
     # taken from the device states; then every device buffer of the measured
     # run is released, so the end-to-end leg runs on a clean device
@@ -682,6 +713,14 @@ def main():
                          f"consecutive states of {args.workload}; C oracle with agents and pairs "
                          f"spread over {cores} host threads",
                "single_core": {"value": na / tms1[1], "unit": "agents/s", "cores": 1}}
+    if metrics_rows:
+        with open(args.metrics_log, "w") as f:
+            for row in metrics_rows:
+                row["host_cores"] = host_cores()
+                if cpu is not None:
+                    row["oracle_agents_per_s"] = cpu["value"]
+                    row["oracle_ms_per_iteration"] = row["agents"] / cpu["value"] * 1e3
+                f.write(json.dumps(row) + "\n")
     clk_sum = clk.summary()
     line = {
         "metric": METRIC, "value": value, "unit": "agents/s", "n_gpus": world,

@@ -2148,6 +2148,7 @@ extern "C" tera_status tera_codec_batched(
     uint64_t* wire_off, uint64_t* wire_len, const uint8_t* recv_prev,
     const uint64_t* recv_off_prev, uint8_t* recv, uint64_t recv_capacity_units,
     uint64_t* recv_off, int mode, const tera_tune* tune, void* stream) {
+  TERA_CALL_RANGE("tera_codec_batched");
   return batched_impl(ctx, rec_arena, pair_off, ref_prev, ref_off_prev, ref_next, wire,
                       wire_capacity, wire_off, wire_len, recv_prev, recv_off_prev, recv,
                       recv_capacity_units, recv_off, mode, tune, nullptr, nullptr, nullptr,
@@ -2160,6 +2161,7 @@ extern "C" tera_status tera_codec_batched_ids(
     uint64_t* wire_off, uint64_t* wire_len, const uint8_t* recv_prev,
     const uint64_t* recv_off_prev, uint8_t* recv, uint64_t recv_capacity_units,
     uint64_t* recv_off, int mode, const tera_tune* tune, const tera_ids* ids, void* stream) {
+  TERA_CALL_RANGE("tera_codec_batched_ids");
   if (!ids) return TERA_EINVAL;
   return batched_impl(ctx, rec_arena, pair_off, ref_prev, ref_off_prev, ref_next, wire,
                       wire_capacity, wire_off, wire_len, recv_prev, recv_off_prev, recv,
@@ -2173,6 +2175,7 @@ extern "C" tera_status tera_codec_batched_pred(
     const uint64_t* recv_off_prev, uint8_t* recv, uint64_t recv_capacity_units,
     uint64_t* recv_off, int mode, const tera_tune* tune, const tera_predictor* enc_pred,
     const tera_predictor* dec_pred, void* stream) {
+  TERA_CALL_RANGE("tera_codec_batched_pred");
   return batched_impl(ctx, rec_arena, pair_off, ref_prev, ref_off_prev, ref_next, wire,
                       wire_capacity, wire_off, wire_len, recv_prev, recv_off_prev, recv,
                       recv_capacity_units, recv_off, mode, tune, enc_pred, dec_pred, nullptr,

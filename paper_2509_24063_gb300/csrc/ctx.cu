@@ -758,6 +758,7 @@ tera_status tera_unpack_inplace(const uint8_t* buf, uint64_t len, uint32_t class
 
 tera_status tera_unpack_validate(tera_ctx* ctx, const uint8_t* arena, const uint64_t* off,
                                  void* stream) {
+  TERA_CALL_RANGE("tera_unpack_validate");
   if (!ctx || !arena || !off) return TERA_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
   int blocks = (int)((ctx->n_pairs + 255) / 256);
@@ -799,6 +800,7 @@ extern "C" tera_status tera_wire_to_host(tera_ctx* ctx, const uint8_t* wire,
                                          const uint64_t* wire_off, uint8_t* host_dst,
                                          uint64_t host_capacity, uint64_t* host_count,
                                          void* stream) {
+  TERA_CALL_RANGE("tera_wire_to_host");
   if (!ctx || !wire || !wire_off || !host_dst || !host_count) return TERA_EINVAL;
   if (((uintptr_t)wire | (uintptr_t)host_dst) & 15u) return TERA_EINVAL;
   if ((uintptr_t)host_count & 7u) return TERA_EINVAL;

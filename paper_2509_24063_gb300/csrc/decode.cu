@@ -217,6 +217,7 @@ extern "C" tera_status tera_delta_decode(tera_ctx* ctx, const uint8_t* wire,
                                          uint32_t pair_end, uint8_t* recv,
                                          uint64_t recv_capacity_units, uint64_t* recv_off,
                                          void* stream) {
+  TERA_CALL_RANGE("tera_delta_decode");
   return decode_impl(ctx, wire, wire_off, ref_prev, ref_off_prev, pair_begin, pair_end, recv,
                      recv_capacity_units, recv_off, nullptr, stream);
 }
@@ -227,6 +228,7 @@ extern "C" tera_status tera_delta_decode_pred(tera_ctx* ctx, const uint8_t* wire
                                               uint32_t pair_end, uint8_t* recv,
                                               uint64_t recv_capacity_units, uint64_t* recv_off,
                                               const tera_predictor* pred, void* stream) {
+  TERA_CALL_RANGE("tera_delta_decode_pred");
   if (!pred) return TERA_EINVAL;
   return decode_impl(ctx, wire, wire_off, ref_prev, ref_off_prev, pair_begin, pair_end, recv,
                      recv_capacity_units, recv_off, pred, stream);

@@ -282,6 +282,7 @@ extern "C" tera_status tera_delta_encode(tera_ctx* ctx, const uint8_t* rec_arena
                                          uint32_t pair_end, uint8_t* ref_next, uint8_t* wire,
                                          uint64_t wire_capacity, uint64_t* wire_off,
                                          uint64_t* wire_len, int mode, void* stream) {
+  TERA_CALL_RANGE("tera_delta_encode");
   return encode_impl(ctx, rec_arena, pair_off, ref_prev, ref_off_prev, pair_begin, pair_end,
                      ref_next, wire, wire_capacity, wire_off, wire_len, mode, nullptr, stream);
 }
@@ -293,6 +294,7 @@ extern "C" tera_status tera_delta_encode_pred(tera_ctx* ctx, const uint8_t* rec_
                                               uint8_t* wire, uint64_t wire_capacity,
                                               uint64_t* wire_off, uint64_t* wire_len, int mode,
                                               const tera_predictor* pred, void* stream) {
+  TERA_CALL_RANGE("tera_delta_encode_pred");
   if (!pred) return TERA_EINVAL;
   return encode_impl(ctx, rec_arena, pair_off, ref_prev, ref_off_prev, pair_begin, pair_end,
                      ref_next, wire, wire_capacity, wire_off, wire_len, mode, pred, stream);

@@ -515,6 +515,7 @@ extern "C" tera_status tera_migrate_send(tera_ctx* ctx, const tera_soa* prev,
                                          uint64_t arena_units, uint64_t* inbox_off,
                                          const tera_soa_mut* next, uint64_t* box_off_next,
                                          void* stream) {
+  TERA_CALL_RANGE("tera_migrate_send");
   if (!ctx || !prev || !next || !box_off_prev || !inbox_off || !box_off_next) return TERA_EINVAL;
   if (prev->n < 0 || prev->n > (int64_t)0xFFFFFFFFll || next->n != prev->n) return TERA_EINVAL;
   if (arena_units > 0 && (!arena || ((uintptr_t)arena & 15u))) return TERA_EINVAL;
@@ -574,6 +575,7 @@ extern "C" tera_status tera_migrate_send(tera_ctx* ctx, const tera_soa* prev,
 extern "C" tera_status tera_migrate_recv(tera_ctx* ctx, const uint8_t* arena, uint64_t arena_units,
                                          const uint64_t* inbox_off, const uint64_t* box_off_next,
                                          const tera_soa_mut* next, void* stream) {
+  TERA_CALL_RANGE("tera_migrate_recv");
   if (!ctx || !next || !inbox_off || !box_off_next) return TERA_EINVAL;
   if (!arena || ((uintptr_t)arena & 15u)) return TERA_EINVAL;
   if (next->n < 0 || next->n > (int64_t)0xFFFFFFFFll) return TERA_EINVAL;

@@ -254,12 +254,14 @@ static tera_status pack_impl(tera_ctx* ctx, const tera_soa* soa, const tera_part
 extern "C" tera_status tera_pack(tera_ctx* ctx, const tera_soa* soa, const tera_partition_out* part,
                                  uint32_t pair_begin, uint32_t pair_end, uint8_t* rec_arena,
                                  uint64_t arena_units, void* stream) {
+  TERA_CALL_RANGE("tera_pack");
   return pack_impl(ctx, soa, part, pair_begin, pair_end, rec_arena, arena_units, nullptr, stream);
 }
 
 extern "C" tera_status tera_pack_ids(tera_ctx* ctx, const tera_soa* soa,
                                      const tera_partition_out* part, uint8_t* rec_arena,
                                      uint64_t arena_units, uint64_t* rec_ids, void* stream) {
+  TERA_CALL_RANGE("tera_pack_ids");
   if (!ctx || !rec_ids || ((uintptr_t)rec_ids & 7u)) return TERA_EINVAL;
   return pack_impl(ctx, soa, part, 0, (uint32_t)ctx->n_pairs, rec_arena, arena_units, rec_ids,
                    stream);

@@ -369,6 +369,7 @@ tera_status radix_sort_entries(tera_ctx* ctx, const SortBufs& b, const u32* keys
 
 extern "C" tera_status tera_partition(tera_ctx* ctx, const tera_soa* soa, tera_partition_out* out,
                                       void* stream) {
+  TERA_CALL_RANGE("tera_partition");
   if (!ctx || !soa || !out) return TERA_EINVAL;
   if (soa->n < 0 || soa->n > (int64_t)0xFFFFFFFFll) return TERA_EINVAL;
   if (soa->n > 0 && (!soa->x || !soa->y || !soa->z)) return TERA_EINVAL;

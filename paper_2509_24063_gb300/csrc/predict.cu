@@ -232,6 +232,7 @@ tera_status grad_step(tera_ctx* ctx, const float* dense, u64 nv, u64 start, u32 
 extern "C" tera_status tera_mlp_grad(tera_ctx* ctx, const float* samples, uint64_t n,
                                      const float* params, float* grad, uint64_t* n_valid,
                                      void* stream) {
+  TERA_CALL_RANGE("tera_mlp_grad");
   if (!ctx || !samples || !params || !grad || n == 0 || n > 0xFFFFFFF0ull) return TERA_EINVAL;
   cudaSetDevice(ctx->device);
   cudaStream_t s = (cudaStream_t)stream;
@@ -250,6 +251,7 @@ extern "C" tera_status tera_mlp_grad(tera_ctx* ctx, const float* samples, uint64
 extern "C" tera_status tera_mlp_train(tera_ctx* ctx, const float* samples, uint64_t n,
                                       float* params, int steps, int batch, float lr, float clip,
                                       uint64_t* n_valid, void* stream) {
+  TERA_CALL_RANGE("tera_mlp_train");
   if (!ctx || !samples || !params || n == 0 || n > 0xFFFFFFF0ull || steps < 0 || batch < 1 ||
       batch > (1 << 24))
     return TERA_EINVAL;

@@ -2,7 +2,23 @@
 // device-side helpers (tera_device.cuh) and the host-side context.
 #pragma once
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "tera_device.cuh"
+
+namespace tera {
+// One NVTX range around a library call, named after the entry point (shown by
+// Nsight Systems on the calling thread; nothing happens when no tool is
+// attached).
+struct CallRange {
+  explicit CallRange(const char* name) { nvtxRangePushA(name); }
+  ~CallRange() { nvtxRangePop(); }
+  CallRange(const CallRange&) = delete;
+  CallRange& operator=(const CallRange&) = delete;
+};
+}  // namespace tera
+
+#define TERA_CALL_RANGE(name) ::tera::CallRange tera_call_range_(name)
 
 // The context (host side).
 struct tera_ctx {

@@ -185,6 +185,74 @@ class AuraExchange:
     def advance(self):
         self.t += 1
 
+    # --- checkpoint / resume ---
+    def _spec(self) -> dict:
+        g = self.ctx.grid
+        return {"lo": tuple(g.lo), "hi": tuple(g.hi), "n": tuple(g.n), "w": g.w,
+                "periodic": int(g.periodic), "class_id": self.ctx.class_id, "P": self.P,
+                "mode": self.mode, "K": self.K, "id_columns": self.id_columns,
+                "predictor": self.predictor}
+
+    def checkpoint(self) -> dict:
+        """The state the next iterations read, copied to host memory: the
+        iteration counter and, once an iteration has run, the reference buffer
+        the next iteration reads (tera_ref_schedule) on both sides: the sender
+        reference with its offsets (and id column), the receive buffer with its
+        offsets (and both sides' predictor histories).  Only the used bytes are
+        copied.  Pairs marked with reset_reference are not part of it.  A new
+        exchange on an equal grid resumes the chain with restore(); without a
+        checkpoint the chain can only restart from a raw iteration (reset())."""
+        torch.cuda.synchronize(self.ctx.device)
+        state = {"version": 1, "t": self.t, "spec": self._spec()}
+        if self.t == 0:
+            return state
+        _, prv, _ = self.schedule(self.t)
+        off = self.pair_off[prv].cpu()
+        roff = self.recv_off[prv].cpu()
+        E, R = int(off[-1]), int(roff[-1])
+        state["ref_off"] = off
+        state["ref"] = self.ref[prv][:(E + self.P) * 64].cpu()
+        state["recv_off"] = roff
+        state["recv"] = self.recv[prv][:(R + self.P) * 64].cpu()
+        if self.id_columns:
+            state["ref_ids"] = self.ref_ids[prv][:E].cpu()
+        if self.predictor:
+            state["hist"] = self.hist[prv][:E * 48].cpu()
+            state["rhist"] = self.rhist[prv][:R * 48].cpu()
+        return state
+
+    def restore(self, state: dict):
+        """Resume from checkpoint(): the next step() runs the checkpoint's next
+        iteration against its references, producing the bytes the original
+        chain would have produced.  The exchange must have the same grid,
+        class id, mode, reference interval, id columns and predictor setting,
+        and room for the references (ValueError otherwise)."""
+        if state.get("version") != 1:
+            raise ValueError("unknown checkpoint version")
+        spec = self._spec()
+        if state["spec"] != spec:
+            diff = sorted(k for k in spec if state["spec"].get(k) != spec[k])
+            raise ValueError(f"checkpoint taken with another configuration: {diff}")
+        t = int(state["t"])
+        if t > 0:
+            _, prv, _ = self.schedule(t)
+            units = self.max_records + self.P
+            ref, recv = state["ref"], state["recv"]
+            if ref.numel() > units * 64 or recv.numel() > units * 64:
+                raise ValueError("checkpoint references exceed this exchange's max_records")
+            self.pair_off[prv].copy_(state["ref_off"])
+            self.ref[prv][:ref.numel()].copy_(ref)
+            self.recv_off[prv].copy_(state["recv_off"])
+            self.recv[prv][:recv.numel()].copy_(recv)
+            if self.id_columns:
+                ids = state["ref_ids"]
+                self.ref_ids[prv][:ids.numel()].copy_(ids)
+            if self.predictor:
+                self.hist[prv][:state["hist"].numel()].copy_(state["hist"])
+                self.rhist[prv][:state["rhist"].numel()].copy_(state["rhist"])
+            torch.cuda.synchronize(self.ctx.device)
+        self.t = t
+
     # --- views of the last iteration's outputs ---
     @property
     def last(self) -> int:
