@@ -85,7 +85,9 @@ typedef enum {
   TERA_EDOMAIN = 5,      /* an agent lies outside [lo, hi) (or is NaN) */
   TERA_EREFMISMATCH = 6, /* message n_slots differs from the receiver's reference */
   TERA_ETIMEOUT = 7,     /* a bounded device-side wait gave up */
-  TERA_ECUDA = 8         /* a CUDA runtime call failed */
+  TERA_ECUDA = 8,        /* a CUDA runtime call failed */
+  TERA_EBOUNDS = 9       /* debug builds only (TERA_DEBUG_BOUNDS): a write fell outside the
+                            range its pair or buffer owns; the write was skipped */
 } tera_status;
 
 enum { TERA_MODE_RAW = 0, TERA_MODE_XOR = 1, TERA_MODE_RESIDUAL = 2 };

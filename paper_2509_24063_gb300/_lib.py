@@ -6,11 +6,15 @@ import os
 import threading
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libtera.so")
+# TERA_DEBUG_BOUNDS=1 in the environment selects the bounds-checking build
+# (libtera_debug.so, `build.build(debug_bounds=True)`): the same kernels with
+# every write checked against the range its pair or buffer owns
+DEBUG_BOUNDS = os.environ.get("TERA_DEBUG_BOUNDS", "") == "1"
+LIB_PATH = os.path.join(HERE, "libtera_debug.so" if DEBUG_BOUNDS else "libtera.so")
 
-OK, EINVAL, ENOMEM, ECAPACITY, ECORRUPT, EDOMAIN, EREFMISMATCH, ETIMEOUT, ECUDA = range(9)
+OK, EINVAL, ENOMEM, ECAPACITY, ECORRUPT, EDOMAIN, EREFMISMATCH, ETIMEOUT, ECUDA, EBOUNDS = range(10)
 STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECAPACITY", "ECORRUPT", "EDOMAIN", "EREFMISMATCH",
-                "ETIMEOUT", "ECUDA"]
+                "ETIMEOUT", "ECUDA", "EBOUNDS"]
 MODE_RAW, MODE_XOR, MODE_RESIDUAL = 0, 1, 2
 MLP_PARAMS = 4931
 HIST_BYTES = 48

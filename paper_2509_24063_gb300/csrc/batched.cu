@@ -777,7 +777,7 @@ __device__ __forceinline__ void bat_slot(const EncArgs& A, const BatchArgs& B, u
       vn = 1;
       stash_put<T>(stash, cur);  // the new reference's record, stored after the scan
     }
-    reinterpret_cast<u32*>(q.w8 + kHdrBytes)[j] = code;
+    if (in_bounds(A.st, j, 0, r + q.n_new)) reinterpret_cast<u32*>(q.w8 + kHdrBytes)[j] = code;
   }
   // this warp's payload bytes, staged from offset 0 of its stage
   const u32 wincl = warp_incl_scan<u32>(vb);
@@ -837,6 +837,8 @@ __device__ __forceinline__ void finish_pair(const EncArgs& A, const BatchArgs& B
   const u64 msg = round16(body);
   const u64 mode = pair_mode<PR>(A, B, p);
   uint8_t* w8 = A.wire + A.wire_off[p];
+  // the message fits the slab reserved for it (checked after the fact)
+  if (lane == 0) (void)in_bounds(A.st, msg, 0, A.wire_off[p + 1] - A.wire_off[p] + 1);
   if (lane == 0) {
     if (new_tot.b != n_new || slot_tot.b != matched) latch(A.st, TERA_EINVAL);
     ulonglong2* h = reinterpret_cast<ulonglong2*>(w8);
@@ -917,7 +919,7 @@ __device__ __forceinline__ void bat_new(const EncArgs& A, const BatchArgs& B, u3
         code |= L << (4 * w);
         put_word(dst, o, M.w[w], L);
       }
-      reinterpret_cast<u32*>(w8 + kHdrBytes)[r + rank] = code;
+      if (in_bounds(A.st, rank, 0, n_new)) reinterpret_cast<u32*>(w8 + kHdrBytes)[r + rank] = code;
       store_ref_next(A, p, g_lo + matched + rank, M);
       if constexpr (PR) {
         if (A.pr.hist_next)
@@ -986,7 +988,7 @@ __device__ __forceinline__ void bat_new_list(const EncArgs& A, u32 p, const Slot
       vb += L;
       code |= L << (4 * w);
     }
-    reinterpret_cast<u32*>(q.w8 + kHdrBytes)[r + i] = code;
+    if (in_bounds(A.st, i, 0, n_new)) reinterpret_cast<u32*>(q.w8 + kHdrBytes)[r + i] = code;
     store_ref_next(A, p, g_lo + matched + i, M);
     if constexpr (PR) {
       if (A.pr.hist_next)
@@ -1136,7 +1138,7 @@ __device__ __forceinline__ void bat_dec_tile(const DecArgs& A, const BatchArgs& 
           store_hist_next(A.pr.hist_next + kHistBytes * (q.rv + pos), nullptr, nullptr);
       }
     }
-    store_rec(A.recv + (q.rv + p + 1 + pos) * kRecBytes, rec);
+    if (in_bounds(A.st, pos, 0, m)) store_rec(A.recv + (q.rv + p + 1 + pos) * kRecBytes, rec);
   }
   __syncwarp();
   // the last tile: every byte and record the header announced was decoded
@@ -1258,7 +1260,8 @@ __device__ __forceinline__ void dec_tiles_pipelined(const DecArgs& A, u32 p, con
 #pragma unroll
         for (int w = 0; w < 8; ++w) rec.w[w] ^= R.w[w];
       }
-      store_rec(A.recv + (q.rv + p + 1 + pre.b + ex.b) * kRecBytes, rec);
+      if (in_bounds(A.st, pre.b + ex.b, 0, m))
+        store_rec(A.recv + (q.rv + p + 1 + pre.b + ex.b) * kRecBytes, rec);
     }
     __syncwarp();
     // the last tile: every byte and record the header announced was decoded

@@ -429,6 +429,7 @@ __device__ __forceinline__ u64 ref_id(const EncArgs& A, u32 p, u64 ro, u64 j) {
 // A record of the new sender reference at global index g (pair p), and its
 // id in the id column when there is one.
 __device__ __forceinline__ void store_ref_next(const EncArgs& A, u32 p, u64 g, const Rec& R) {
+  if (!in_bounds(A.st, g, A.pair_off[p], A.pair_off[p + 1])) return;
   store_rec(A.ref_next + (g + p + 1) * kRecBytes, R);
   if (A.ref_ids_next) A.ref_ids_next[g] = R.w[0];
 }
@@ -749,7 +750,8 @@ __device__ __forceinline__ void enc_emit_unit(const EncArgs& A, u32 p, u64 local
       reinterpret_cast<u32*>(w8 + kHdrBytes)[r + rank] = code;
       pos = ldx<CG>(pi + PI_MATCHED) + rank;
     }
-    store_rec(A.ref_next + (A.pair_off[p] + p + 1 + pos) * kRecBytes, cur);
+    if (in_bounds(A.st, pos, 0, A.pair_off[p + 1] - A.pair_off[p]))
+      store_rec(A.ref_next + (A.pair_off[p] + p + 1 + pos) * kRecBytes, cur);
     if constexpr (PR) {
       if (A.pr.hist_next) {
         uint8_t* hn = A.pr.hist_next + kHistBytes * (A.pair_off[p] + pos);
@@ -986,7 +988,8 @@ __device__ __forceinline__ void dec_emit_unit(const DecArgs& A, u32 p, u64 local
           store_hist_next(A.pr.hist_next + kHistBytes * (A.recv_off[p] + pos), nullptr, nullptr);
       }
     }
-    store_rec(A.recv + (A.recv_off[p] + p + 1 + pos) * kRecBytes, rec);
+    if (in_bounds(A.st, pos, 0, A.recv_off[p + 1] - A.recv_off[p]))
+      store_rec(A.recv + (A.recv_off[p] + p + 1 + pos) * kRecBytes, rec);
   }
   __syncthreads();
 }

@@ -101,6 +101,7 @@ __global__ void __launch_bounds__(256)
     Rec R;
 #pragma unroll
     for (int w = 0; w < 8; ++w) R.w[w] = soa.col[w][a];
+    if (!in_bounds(st, g, pair_off[p], pair_off[p + 1])) continue;
     store_rec(arena + (g + p + 1) * kRecBytes, R);
     if (rec_ids) rec_ids[g] = R.w[0];
   }
@@ -182,8 +183,10 @@ __global__ void __launch_bounds__(kClassifyThreads)
       for (u32 mm = m[q]; mm; mm &= mm - 1) {
         const u64 p = (u64)o[q] * 27u + (u64)(__ffs(mm) - 1);
         const u64 g = ent_dest[e];
-        store_rec(arena + (g + p + 1) * kRecBytes, R);
-        if (rec_ids) rec_ids[g] = R.w[0];
+        if (in_bounds(st, g, pair_off[p], pair_off[p + 1])) {
+          store_rec(arena + (g + p + 1) * kRecBytes, R);
+          if (rec_ids) rec_ids[g] = R.w[0];
+        }
         ++e;
       }
     }

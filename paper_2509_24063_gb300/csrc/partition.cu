@@ -93,6 +93,7 @@ __global__ void __launch_bounds__(kClassifyThreads)
                 const u64* __restrict__ run_base, u64 n_runs, u32* __restrict__ keys,
                 u32* __restrict__ vals, u64 cap, DevStatus* st) {
   const u64 total = run_base[n_runs];
+  const u64 n_entries = total;  // (a warp's own count below is also called total)
   if (total > cap) {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
       latch(st, TERA_ECAPACITY);
@@ -146,6 +147,7 @@ __global__ void __launch_bounds__(kClassifyThreads)
       k = second ? k - n0 : k;
       for (u32 t = 0; t < k; ++t) mm &= mm - 1;
       const u32 b = (u32)(__ffs(mm) - 1);
+      if (!in_bounds(st, base + idx, 0, n_entries)) continue;
       keys[base + idx] = (u32)(second ? s_o1 : s_o0) * 27u + b;
       vals[base + idx] = (u32)(first + 2u * src + (second ? 1u : 0u));  // the entry's agent
     }
@@ -198,7 +200,8 @@ __global__ void __launch_bounds__(kSortThreads)
                       const u32* __restrict__ agents_in, u32* __restrict__ keys_out,
                       u32* __restrict__ vals_out, u32* __restrict__ agents_out,
                       u32* __restrict__ dest, int last, const u64* __restrict__ total_ptr, u64 cap,
-                      u32 shift, u32 radix, const u32* __restrict__ hist_scan, u32 n_tiles) {
+                      u32 shift, u32 radix, const u32* __restrict__ hist_scan, u32 n_tiles,
+                      DevStatus* st) {
   constexpr int kWarps = kSortThreads / 32;
   constexpr int kRoundEntries = kSortThreads * kSortSub;
   extern __shared__ __align__(16) u32 sort_stage[];
@@ -274,6 +277,7 @@ __global__ void __launch_bounds__(kSortThreads)
     const u32 key = skey[li], v = sval[li], a = sagt[li];
     const u32 d = (key >> shift) & (radix - 1);
     const u32 pos = base[d] + (li - lstart[d]);
+    if (!in_bounds(st, pos, 0, E) || !in_bounds(st, v, 0, E)) continue;
     keys_out[pos] = key;
     if (last) {
       vals_out[pos] = a;
@@ -355,7 +359,7 @@ tera_status radix_sort_entries(tera_ctx* ctx, const SortBufs& b, const u32* keys
     prof_begin(ctx, s);
     rs_scatter_kernel<<<(unsigned)sort_tiles, kSortThreads, kSortSmem, s>>>(
         kin, vin, ain, kout, vout, aout, last ? dest : nullptr, last ? 1 : 0, total_ptr, cap,
-        shift, radix, b.hist, (u32)sort_tiles);
+        shift, radix, b.hist, (u32)sort_tiles, ctx->d_status);
     if ((st = check_launch(ctx, "rs_scatter_kernel", s)) != TERA_OK) return st;
     kin = kout;
     vin = vout;

@@ -99,6 +99,23 @@ struct DevStats {
 __device__ __forceinline__ void latch(DevStatus* s, u32 code) { atomicCAS(&s->code, 0u, code); }
 __device__ __forceinline__ void need(DevStatus* s, u64 req) { atomicMax(&s->required, req); }
 
+// Bounds check of the debug build (compiled with TERA_DEBUG_BOUNDS): true
+// when lo <= i < hi; otherwise TERA_EBOUNDS is latched and the caller skips
+// its write.  Other builds check nothing (always true, no code).
+__device__ __forceinline__ bool in_bounds(DevStatus* s, u64 i, u64 lo, u64 hi) {
+#ifdef TERA_DEBUG_BOUNDS
+  if (i >= lo && i < hi) return true;
+  latch(s, TERA_EBOUNDS);
+  return false;
+#else
+  (void)s;
+  (void)i;
+  (void)lo;
+  (void)hi;
+  return true;
+#endif
+}
+
 __device__ __forceinline__ u64 mix64(u64 z) {
   // splitmix64 finalizer (Steele, Lea, Flood 2014)
   z ^= z >> 30;

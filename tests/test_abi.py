@@ -31,6 +31,13 @@ def test_library_exports_every_declared_symbol(libpath):
         assert hasattr(lib, name), name
 
 
+def test_bounds_checking_library_exports_every_declared_symbol():
+    from paper_2509_24063_gb300 import build
+    lib = ctypes.CDLL(build.build(debug_bounds=True))
+    for name in declared_symbols():
+        assert hasattr(lib, name), name
+
+
 def test_binding_declares_every_symbol():
     from paper_2509_24063_gb300 import _lib
     assert sorted(_lib.SIGNATURES) == declared_symbols()

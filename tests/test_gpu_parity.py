@@ -76,7 +76,7 @@ def run_chain(tera, wl, iters, per_subdomain=False, max_records=None, device="cu
     for st in states:
         ex.step(st)
         code, _ = ctx.status(raise_on_error=False)
-        assert code == tera.OK
+        assert code == tera.OK, f"device status {code}"
         res = oracle.exchange_iteration(g, to_numpy(st), ref=ref, recv_ref=recv_ref)
         stats.append(compare_iteration(ctx, ex, st, res, ctx.n_pairs))
         ref = (res["ref_next"], res["pair_off"])
