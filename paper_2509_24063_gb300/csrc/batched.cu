@@ -51,6 +51,12 @@ struct BatchArgs {
   U64x2* tsum;        // per-tile totals of team pairs (slot tiles, then decode tiles)
   const u64* tbase;   // [P] first tile total of a team pair
   u64 wait_ns;        // time limit of one team barrier (global timer)
+  // the work list is split in two: items [0, *n_first) (teams, then the other
+  // pairs) and [*n_first, *n_items) (the small pairs, carried by a launch of
+  // one-warp blocks); part selects the range and its ticket
+  u64* n_first;
+  u64* ticket_small;
+  u32 part;
 };
 
 __device__ __forceinline__ u64 make_item(u64 p, u32 member, u32 g) {
@@ -235,6 +241,13 @@ struct PairFacts {
   bool raw;
 };
 
+// The work-list count word of a pair carried by one block: 1 (low half) for an
+// ordinary pair, 1 << 32 (high half) for a small one.
+__device__ __forceinline__ u64 single_word(const PairFacts& f, u64 small_max) {
+  const bool small = small_max > 0 && f.r <= small_max && f.m <= small_max && f.rr <= small_max;
+  return small ? (1ull << 32) : 1ull;
+}
+
 __device__ __forceinline__ PairFacts pair_facts(const EncArgs& E, const DecArgs& D, u64 p, int mode,
                                                 u64 thresh, u32 gmax, int pred, u32 forced) {
   PairFacts f;
@@ -252,14 +265,17 @@ __device__ __forceinline__ PairFacts pair_facts(const EncArgs& E, const DecArgs&
 // t, coalesced): a first pass writes the per-pair facts and sums the block's
 // totals; a second pass scans each chunk (carried from chunk to chunk) into
 // the wire slab offsets, the work list (team items first, so the large pairs
-// start early, then one item per other pair, each in pair order) and the
-// teams' first tile totals.
+// start early, then one item per other pair, then, when small_max > 0, one
+// item per small pair: at most small_max slots, records and receiver slots;
+// each group in pair order) and the teams' first tile totals.  The counts of
+// the other and the small pairs travel packed in one word (low and high 32
+// bits) through the scans.
 __global__ void __launch_bounds__(1024)
     bat_setup_kernel(EncArgs E, DecArgs D, BatchArgs B, u64 P, int mode,
                      u64* __restrict__ wire_off, u64 wire_cap, u64 rec_cap, u64 recv_cap,
                      u32* epoch, u32 T, u32 blocks, u32 gmax, u32 forced, u64 min_team, int pred,
                      u64* __restrict__ items, u64 items_cap, u64* __restrict__ tbase,
-                     u64 tsum_cap, u64* __restrict__ n_items) {
+                     u64 tsum_cap, u64* __restrict__ n_items, u64 small_max) {
   __shared__ U64x2 sm2[33];
   __shared__ u64 s_thresh;
   if (threadIdx.x == 0) {
@@ -284,21 +300,23 @@ __global__ void __launch_bounds__(1024)
     pi[PI_MODE] = f.raw ? TERA_MODE_RAW : TERA_MODE_XOR;
     D.recv_off[p] = E.pair_off[p];  // receive buffers sized by the record counts
     acc_a += U64x2{f.slab, f.g > 1 ? team_tiles(f.r, f.m, f.rr, T) : 0};
-    acc_b += U64x2{f.g > 1 ? f.g : 0u, f.g > 1 ? 0u : 1u};
+    acc_b += U64x2{f.g > 1 ? f.g : 0u, f.g > 1 ? 0u : single_word(f, small_max)};
   }
   U64x2 tot_a, tot_b;
   block_excl_scan2(acc_a, sm2, &tot_a);
   block_excl_scan2(acc_b, sm2, &tot_b);
-  const u64 tw = tot_a.a, ttiles = tot_a.b, tbig = tot_b.a, tsmall = tot_b.b;
+  const u64 tw = tot_a.a, ttiles = tot_a.b, tbig = tot_b.a;
+  const u64 n_other = tot_b.b & 0xFFFFFFFFull, n_small = tot_b.b >> 32;
+  const u64 tsmall = n_other + n_small;
   const bool fits = tbig + tsmall <= items_cap && ttiles <= tsum_cap;
-  U64x2 carry_a{0, 0}, carry_b{0, tbig};  // team items first
+  U64x2 carry_a{0, 0}, carry_b{0, 0};
   for (u64 c = 0; c < P; c += blockDim.x) {  // block-uniform
     const u64 p = c + threadIdx.x;
     PairFacts f{};
     if (p < P) f = pair_facts(E, D, p, mode, thresh, gmax, pred, forced);
     const bool team = p < P && f.g > 1;
     const U64x2 va{p < P ? f.slab : 0, team ? team_tiles(f.r, f.m, f.rr, T) : 0};
-    const U64x2 vb{team ? f.g : 0u, (p < P && !team) ? 1u : 0u};
+    const U64x2 vb{team ? f.g : 0u, (p < P && !team) ? single_word(f, small_max) : 0u};
     U64x2 ta, tb;
     const U64x2 ea = carry_a + block_excl_scan2(va, sm2, &ta);
     const U64x2 eb = carry_b + block_excl_scan2(vb, sm2, &tb);
@@ -310,8 +328,10 @@ __global__ void __launch_bounds__(1024)
     if (team) {
       for (u32 i = 0; i < f.g; ++i) items[eb.a + i] = make_item(p, i, f.g);
       tbase[p] = ea.b;
+    } else if (single_word(f, small_max) == 1u) {
+      items[tbig + (eb.b & 0xFFFFFFFFull)] = make_item(p, 0, 1);
     } else {
-      items[eb.b] = make_item(p, 0, 1);
+      items[tbig + n_other + (eb.b >> 32)] = make_item(p, 0, 1);
     }
   }
   if (threadIdx.x == 0) {
@@ -342,8 +362,10 @@ __global__ void __launch_bounds__(1024)
       abort = true;
     }
     *n_items = abort ? 0 : tbig + tsmall;
+    *B.n_first = abort ? 0 : tbig + n_other;
     *B.abort = abort ? 1u : 0u;
     *B.ticket = 0;
+    *B.ticket_small = 0;
   }
 }
 
@@ -1846,13 +1868,16 @@ __global__ void __launch_bounds__(T, (1024 / T) > 0 ? (1024 / T) : 1)
   __shared__ u32 s_cnt;
   __shared__ DecShared hs;
   const u32 epoch = __ldcg(E.epoch);
-  const u64 n_items = __ldcg(B.n_items);
+  // this launch's range of the work list (see BatchArgs)
+  const u64 first = B.part ? __ldcg(B.n_first) : 0;
+  const u64 n_items = B.part ? __ldcg(B.n_items) : __ldcg(B.n_first);
+  u64* ticket = B.part ? B.ticket_small : B.ticket;
   if (threadIdx.x == 0) s_cnt = 0;
   for (;;) {
     // claim the next item only when this block is free: a team member never
     // waits for an item that a busy block holds
     if (threadIdx.x == 0) {
-      const u64 t = atomicAdd(B.ticket, 1ull);
+      const u64 t = first + atomicAdd(ticket, 1ull);
       s_item = (t < n_items && !*(volatile u32*)B.abort) ? B.items[t] : ~0ull;
     }
     __syncthreads();
@@ -1959,6 +1984,14 @@ inline void persistent_smem(u32 T, bool PR, int ctas_per_sm, u32 want_records, s
   // + 16 bytes: the decode's 8-byte reads may pass the end of the stage
   *bytes = region_bytes(T, rec) + rec / 8 + 16;
 }
+
+// Small pairs (at most kSmallPair slots, records and receiver slots) of the
+// plain codec are carried by a launch of their own: one-warp blocks,
+// kSmallCtas per SM, so that thousands of them are in flight at once (each
+// small pair is a chain of latency-bound steps that a 256-thread block would
+// carry with most of its threads idle).
+constexpr u64 kSmallPair = 512;
+constexpr int kSmallCtas = 32;
 
 template <int T, bool PR>
 tera_status launch_persistent(tera_ctx* ctx, const EncArgs& E, const DecArgs& D,
@@ -2084,6 +2117,9 @@ static tera_status batched_impl(
   B.tsum = ctx->b_tsum;
   B.tbase = ctx->b_tbase;
   B.wait_ns = 1000ull * (u64)(tn.wait_limit_us ? tn.wait_limit_us : 1000000);
+  B.n_first = ctx->b_scalars + 3;
+  B.ticket_small = ctx->b_scalars + 4;
+  B.part = 0;
 
   if (PR) {
     if ((st = ensure_pred(ctx)) != TERA_OK) return st;
@@ -2131,8 +2167,15 @@ static tera_status batched_impl(
                                       ctx->d_epoch, T, blocks, gmax, (u32)tn.team_blocks,
                                       min_team, PR ? 1 : 0,
                                       ctx->b_items, ctx->b_items_cap, ctx->b_tbase,
-                                      ctx->b_tsum_cap, ctx->b_scalars + 0);
+                                      ctx->b_tsum_cap, ctx->b_scalars + 0,
+                                      PR ? 0 : kSmallPair);
   if ((st = check_launch(ctx, "bat_setup_kernel", s)) != TERA_OK) return st;
+  if (!PR) {
+    BatchArgs Bs = B;
+    Bs.part = 1;
+    if ((st = launch_persistent<32, false>(ctx, E, D, Bs, kSmallCtas, 0, s)) != TERA_OK)
+      return st;
+  }
   if (PR) {
     if (T == 128) return launch_persistent<128, true>(ctx, E, D, B, c, want, s);
     return launch_persistent<256, true>(ctx, E, D, B, c, want, s);

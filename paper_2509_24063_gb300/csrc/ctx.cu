@@ -299,10 +299,10 @@ tera_status ensure_batched(tera_ctx* ctx) {
   tera_status st;
   if (!ctx->b_ptot) {
     if ((st = alloc_dev(ctx->b_ptot, P * 4)) != TERA_OK) return st;
-    if ((st = alloc_dev(ctx->b_scalars, 4)) != TERA_OK) return st;
+    if ((st = alloc_dev(ctx->b_scalars, 6)) != TERA_OK) return st;
     if ((st = alloc_dev(ctx->b_team, P * 8)) != TERA_OK) return st;
     if ((st = alloc_dev(ctx->b_tbase, P)) != TERA_OK) return st;
-    cudaMemset(ctx->b_scalars, 0, 4 * sizeof(u64));
+    cudaMemset(ctx->b_scalars, 0, 6 * sizeof(u64));
   }
   if ((st = alloc_dev(ctx->b_items, items)) != TERA_OK) return st;
   if ((st = alloc_dev(ctx->b_tsum, tsum)) != TERA_OK) return st;
