@@ -967,10 +967,30 @@ def run_e2e(args, tera, wl, host, nmax, max_records, local, tune=None):
     agents = sum(int(hs["x"].shape[0]) for hs in host[1:])
     h2d = sum(int(hs[f].numel() * hs[f].element_size()) for hs in host[1:] for f in FIELDS)
     ctx.status()
+    # the host link's own rate for one step's input copies (pinned host to
+    # device, the same columns into the same device buffers, nothing else
+    # running): the bound the end-to-end number is read against
+    hs, buf = host[1], hx.inputs[0]
+    n1 = int(hs["x"].shape[0])
+    copy = torch.cuda.Stream(device=local)
+    l0, l1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(copy):
+        for f in FIELDS:
+            buf[f][:n1].copy_(hs[f], non_blocking=True)
+        l0.record(copy)
+        for _ in range(3):
+            for f in FIELDS:
+                buf[f][:n1].copy_(hs[f], non_blocking=True)
+        l1.record(copy)
+    l1.synchronize()
+    step_bytes = sum(int(hs[f].numel() * hs[f].element_size()) for f in FIELDS)
+    link_gbs = 3 * step_bytes / (l0.elapsed_time(l1) / 1e3) / 1e9
     ctx.close()
     return {"value": agents / dt, "unit": "agents/s", "h2d_bytes_per_step": h2d // k,
             "d2h_bytes_per_step": sum(nbytes) // k, "steps": k,
-            "overlap": "inputs of step t+1 copied while step t computes"}
+            "overlap": "inputs of step t+1 copied while step t computes",
+            "h2d_link_gbs": link_gbs,
+            "link_bound_agents_per_s": n1 / (step_bytes / (link_gbs * 1e9))}
 
 
 if __name__ == "__main__":
