@@ -301,6 +301,11 @@ tera_status ensure_batched(tera_ctx* ctx) {
     if ((st = alloc_dev(ctx->b_ptot, P * 4)) != TERA_OK) return st;
     if ((st = alloc_dev(ctx->b_scalars, 6)) != TERA_OK) return st;
     if ((st = alloc_dev(ctx->b_team, P * 8)) != TERA_OK) return st;
+    if (!ctx->b_side &&
+        (cudaStreamCreateWithFlags(&ctx->b_side, cudaStreamNonBlocking) != cudaSuccess ||
+         cudaEventCreateWithFlags(&ctx->b_fork, cudaEventDisableTiming) != cudaSuccess ||
+         cudaEventCreateWithFlags(&ctx->b_join, cudaEventDisableTiming) != cudaSuccess))
+      return TERA_ECUDA;
     if ((st = alloc_dev(ctx->b_tbase, P)) != TERA_OK) return st;
     cudaMemset(ctx->b_scalars, 0, 6 * sizeof(u64));
   }
@@ -582,6 +587,9 @@ tera_status tera_ctx_destroy(tera_ctx* c) {
   free_dev(c->d_units_total);
   free_dev(c->d_stats);
   free_dev(c->b_scalars);
+  if (c->b_side) cudaStreamDestroy(c->b_side);
+  if (c->b_fork) cudaEventDestroy(c->b_fork);
+  if (c->b_join) cudaEventDestroy(c->b_join);
   free_dev(c->b_ptot);
   free_dev(c->b_items);
   free_dev(c->pscr_dec);

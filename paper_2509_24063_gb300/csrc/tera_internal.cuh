@@ -90,6 +90,8 @@ struct tera_ctx {
   float* mlp_scratch;       // training: compacted samples + gradient partials
   uint64_t mlp_scratch_cap;
   // batched codec (batched.cu)
+  cudaStream_t b_side;     // the small-pair launch runs on it, forked from and joined to the
+  cudaEvent_t b_fork, b_join;  // caller's stream by these events
   tera::u64* b_scalars;  // [0] work items, [1] ticket, [2] abort flag, [3] first small-pair
                          // item, [4] ticket of the small-pair launch
   tera::u64* b_ptot;     // [P * 4] per-pair totals of the match step
