@@ -69,15 +69,42 @@ KERNEL_SOURCES = {"codec_persistent_kernel": ("batched.cu", "codec.cuh", "tera_d
                   "mig_move_kernel": ("migrate.cu", "classify.cuh", "tera_device.cuh")}
 
 
+def source_code_text(text: str) -> str:
+    """The code of a C++/CUDA source without its comments and whitespace, so
+    that the digest below changes with the code only (string literals kept)."""
+    out, i, n = [], 0, len(text)
+    while i < n:
+        c = text[i]
+        if c == '"':
+            j = i + 1
+            while j < n and text[j] != '"':
+                j += 2 if text[j] == "\\" else 1
+            out.append(text[i:j + 1])
+            i = j + 1
+        elif text.startswith("//", i):
+            j = text.find("\n", i)
+            i = n if j < 0 else j
+        elif text.startswith("/*", i):
+            j = text.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+        elif c.isspace():
+            i += 1
+        else:
+            out.append(c)
+            i += 1
+    return "".join(out)
+
+
 def kernel_digest(name):
+    """Digest of the code (not the comments) of the sources a kernel is built from."""
     import hashlib
     files = KERNEL_SOURCES.get(name)
     if not files:
         return None
     h = hashlib.sha256()
     for f in files:
-        with open(os.path.join(ROOT, "paper_2509_24063_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2509_24063_gb300", "csrc", f), encoding="utf-8") as fh:
+            h.update(source_code_text(fh.read()).encode())
     return h.hexdigest()[:16]
 
 

@@ -1563,8 +1563,10 @@ __device__ __noinline__ void team_pair(const EncArgs& E, const DecArgs& D, const
 // A slot's prediction depends only on its reference record, its history and
 // the cell counts of its pair's reference, not on the message: each side makes
 // the predictions of its own reference before the codec runs, over every slot
-// of every pair at once (one thread per slot), in kernels built with room for
-// the network's hidden layer in registers.  The codec then reads them.
+// of every pair at once: the cell counts, the features (one thread per slot,
+// few registers, so that many loads are in flight), then the network (two
+// slots per thread, in a kernel with room for both slots' accumulators).  The
+// codec then reads them.
 
 // The pair of slot g of an arena laid out with off[0..P] (off[p] <= g < off[p+1]).
 __device__ __forceinline__ u32 pair_of_slot(const u64* __restrict__ off, u32 P, u64 g) {
