@@ -348,7 +348,12 @@ typedef struct {
  * (NULL pairs = empty references).  rec_arena is any packed arena laid out
  * with pair_off (record ids are read from the records).  tune == NULL uses
  * {256, 4, 0, 0, 0, 0}.  Asynchronous, no host synchronization (graph-capturable once
- * scratch is reserved); device errors are latched in the status word. */
+ * scratch is reserved); device errors are latched in the status word.  Small
+ * pairs (at most 512 slots, records and receiver slots) are carried by a
+ * second launch on a stream the context owns, forked from `stream` after the
+ * call's first kernel and joined back into it before the call returns (CUDA
+ * events), so all of the call's work is ordered on `stream` like one launch;
+ * a context is not to be used from two streams at once. */
 tera_status tera_codec_batched(tera_ctx* ctx, const uint8_t* rec_arena, const uint64_t* pair_off,
                                const uint8_t* ref_prev, const uint64_t* ref_off_prev,
                                uint8_t* ref_next, uint8_t* wire, uint64_t wire_capacity,
