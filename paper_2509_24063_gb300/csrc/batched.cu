@@ -495,6 +495,118 @@ __device__ __forceinline__ u32 smem_match(const EncArgs& A, u32 p, u64 r, const 
   return found;
 }
 
+// ---------------- match of ascending id lists ----------------
+//
+// When the ids of a pair's message and of its reference are both strictly
+// ascending (agents kept in the order their ids were given, so that each list,
+// in agent order, is in id order), a slot's match is found without an index:
+// tile t of the reference loads the message ids from kWinSlack before to
+// kWinSlack after [j0 + d, j0 + d + T) into shared memory, d = (message index
+// - slot index) of the last match so far, and each slot searches that window
+// by bisection (a slot whose id lies outside it searches all message ids).
+// Ids that occur once on each side give exactly the matches of the index;
+// other pairs take the index.
+
+constexpr u32 kWinSlack = 64;
+
+// The message ids of pair p strictly ascending (the same answer in every
+// thread).  A reference slot whose id repeats finds a record already taken,
+// which the search treats as the index does (an invalid reference; the slot
+// is a hole).
+template <int T>
+__device__ __forceinline__ bool ids_ascending(const EncArgs& A, u32 p, u64 m) {
+  const u64 g_lo = A.pair_off[p];
+  int bad = 0;
+  for (u64 k = threadIdx.x; k + 1 < m; k += T)
+    bad |= !(msg_id(A, p, g_lo + k) < msg_id(A, p, g_lo + k + 1));
+  return __syncthreads_or(bad) == 0;
+}
+
+// Every slot of pair p looked up (ascending message ids): slot_src[slot] =
+// global record index or kNoMatch, and the taken bits; kIlp slots per thread
+// per round.  Returns this thread's match count.  win: shared memory for
+// kIlp T + 2 kWinSlack ids.
+template <int T>
+__device__ __forceinline__ u32 sorted_match(const EncArgs& A, u32 p, u64 m, u64 r,
+                                            const SmemTable& tb, u64* win) {
+  constexpr u64 kSpan = (u64)T * kIlp;
+  __shared__ long long s_d;
+  __shared__ unsigned long long s_jk;
+  const u64 ro = A.ref_off ? A.ref_off[p] : 0, g_lo = A.pair_off[p];
+  for (u32 i = threadIdx.x; i < (u32)((m + 31) / 32); i += T) tb.bits[i] = 0u;
+  if (threadIdx.x == 0) {
+    s_d = 0;
+    s_jk = 0;
+  }
+  __syncthreads();
+  u32 found = 0;
+  for (u64 j0 = 0; j0 < r; j0 += kSpan) {  // block-uniform
+    const long long ws = (long long)j0 + s_d - (long long)kWinSlack;
+    const u64 wlo = ws < 0 ? 0 : ((u64)ws < m ? (u64)ws : m);
+    const u64 whi = wlo + kSpan + 2 * kWinSlack < m ? wlo + kSpan + 2 * kWinSlack : m;
+    u64 x[kIlp];
+#pragma unroll
+    for (u32 i = 0; i < kIlp; ++i) {
+      const u64 j = j0 + (u64)i * T + threadIdx.x;
+      x[i] = j < r ? ref_id(A, p, ro, j) : 0;
+    }
+    for (u64 k = wlo + threadIdx.x; k < whi; k += T) win[k - wlo] = msg_id(A, p, g_lo + k);
+    __syncthreads();  // the window is loaded
+    const u64 n = whi - wlo;
+    u64 last = 0;  // (slot + 1) << 32 | record of this thread's last match
+#pragma unroll
+    for (u32 i = 0; i < kIlp; ++i) {
+      const u64 j = j0 + (u64)i * T + threadIdx.x;
+      if (j >= r) continue;
+      u32 k = kNoMatch;
+      if (n > 0 && x[i] >= win[0] && x[i] <= win[n - 1]) {
+        u64 lo = 0, hi = n;
+        while (lo < hi) {
+          const u64 mid = (lo + hi) >> 1;
+          if (win[mid] < x[i]) lo = mid + 1;
+          else hi = mid;
+        }
+        if (win[lo] == x[i]) k = (u32)(wlo + lo);
+      } else {
+        u64 lo = 0, hi = m;
+        while (lo < hi) {
+          const u64 mid = (lo + hi) >> 1;
+          if (msg_id(A, p, g_lo + mid) < x[i]) lo = mid + 1;
+          else hi = mid;
+        }
+        if (lo < m && msg_id(A, p, g_lo + lo) == x[i]) k = (u32)lo;
+      }
+      if (k != kNoMatch) {
+        const u32 bit = 1u << (k & 31u);
+        if (atomicOr(&tb.bits[k >> 5], bit) & bit) {
+          latch(A.st, TERA_EINVAL);  // a second slot with the same id: that slot is a hole
+          k = kNoMatch;
+        }
+      }
+      if (k != kNoMatch) {
+        ++found;
+        last = ((j + 1) << 32) | k;
+      }
+      A.slot_src[ro + j] = k != kNoMatch ? (u32)(g_lo + k) : kNoMatch;
+    }
+    // the round's last match: its offset carries to the next round
+    u64 wl = last;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const u64 t = __shfl_xor_sync(0xFFFFFFFFu, wl, o);
+      wl = t > wl ? t : wl;
+    }
+    if ((threadIdx.x & 31) == 0 && wl) atomicMax(&s_jk, wl);
+    __syncthreads();  // the window is read, s_jk is final
+    if (threadIdx.x == 0 && s_jk) {
+      s_d = (long long)(s_jk & 0xFFFFFFFFull) - (long long)((s_jk >> 32) - 1);
+      s_jk = 0;
+    }
+    __syncthreads();
+  }
+  return found;
+}
+
 // ---------------- match in the global hash segments ----------------
 
 template <int T>
@@ -1900,9 +2012,14 @@ __global__ void __launch_bounds__(T, (1024 / T) > 0 ? (1024 / T) : 1)
       while (size < 2 * m) size <<= 1;
       tb.tbl = tbl;
       tb.mask = size - 1;
-      smem_build<T>(E, p, m, tb);
-      __syncthreads();
-      u32 c = smem_match<T>(E, p, r, tb);
+      u32 c;
+      if (ids_ascending<T>(E, p, m)) {
+        c = sorted_match<T>(E, p, m, r, tb, reinterpret_cast<u64*>(dyn));
+      } else {
+        smem_build<T>(E, p, m, tb);
+        __syncthreads();
+        c = smem_match<T>(E, p, r, tb);
+      }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xFFFFFFFFu, c, o);
       if ((threadIdx.x & 31) == 0 && c) atomicAdd(&s_cnt, c);

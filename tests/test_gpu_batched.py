@@ -200,3 +200,45 @@ def test_autotuner_picks_a_valid_schedule(tera, tmp_path, monkeypatch):
     res = oracle.exchange_iteration(g, to_numpy(states[2]), ref=ref, recv_ref=recv_ref)
     compare_iteration(ctx, ex, states[2], res, ctx.n_pairs)
     ctx.close()
+
+
+@pytest.mark.parametrize("order", ["shuffled", "few_swaps", "reversed"])
+@pytest.mark.parametrize("id_columns", [True, False])
+def test_batched_agent_orders(tera, order, id_columns):
+    """Pairs whose id lists are both strictly ascending (agents in id order)
+    are matched by a windowed search, the others by the hash index: a chain
+    whose agents are re-ordered every iteration (all pairs unsorted, a few
+    agents swapped so that some pairs are unsorted, and the order reversed)
+    gives the oracle's bytes on every output, through both matches."""
+    wl = Workload("t", 50000, (0.0,) * 3, (300.0, 200.0, 200.0), (3, 2, 2), 25.0, 4,
+                  p_grow=0.1, p_divide=0.02, p_die=0.02, seed=17)
+    rng = np.random.default_rng(23)
+    states = []
+    for st in Generator(wl, device="cuda").series(4):
+        n = int(st["x"].shape[0])
+        if order == "shuffled":
+            perm = rng.permutation(n)
+        elif order == "reversed":
+            perm = np.arange(n)[::-1].copy()
+        else:
+            perm = np.arange(n)
+            a = rng.choice(n, 40, replace=False)
+            perm[a] = perm[np.roll(a, 1)]
+        idx = torch.from_numpy(perm).cuda()
+        states.append({f: st[f][idx].contiguous() for f in
+                       ("id", "x", "y", "z", "diameter", "volume", "adherence", "density")})
+    nmax = max(int(s["x"].shape[0]) for s in states)
+    ctx = tera.Context(wl.lo, wl.hi, wl.grid, wl.w)
+    ex = tera.AuraExchange(ctx, max_agents=nmax, max_records=4 * nmax + 1024, path="batched",
+                           id_columns=id_columns)
+    g = oracle.make_grid(wl.lo, wl.hi, wl.grid, wl.w)
+    ref = recv_ref = None
+    for st in states:
+        ex.step(st)
+        code, _ = ctx.status(raise_on_error=False)
+        assert code == tera.OK, f"device status {code}"
+        res = oracle.exchange_iteration(g, to_numpy(st), ref=ref, recv_ref=recv_ref)
+        compare_iteration(ctx, ex, st, res, ctx.n_pairs)
+        ref = (res["ref_next"], res["pair_off"])
+        recv_ref = (res["recv"], res["recv_off"])
+    ctx.close()
