@@ -517,19 +517,29 @@ template <int T>
 __device__ __forceinline__ bool ids_ascending(const EncArgs& A, u32 p, u64 m) {
   const u64 g_lo = A.pair_off[p];
   int bad = 0;
-  for (u64 k = threadIdx.x; k + 1 < m; k += T)
-    bad |= !(msg_id(A, p, g_lo + k) < msg_id(A, p, g_lo + k + 1));
+  for (u64 k0 = threadIdx.x; k0 + 1 < m; k0 += 4 * (u64)T) {
+    u64 a[4], b[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const u64 k = k0 + (u64)i * T;
+      a[i] = k + 1 < m ? msg_id(A, p, g_lo + k) : 0;
+      b[i] = k + 1 < m ? msg_id(A, p, g_lo + k + 1) : 1;
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) bad |= !(a[i] < b[i]);
+  }
   return __syncthreads_or(bad) == 0;
 }
 
 // Every slot of pair p looked up (ascending message ids): slot_src[slot] =
-// global record index or kNoMatch, and the taken bits; kIlp slots per thread
-// per round.  Returns this thread's match count.  win: shared memory for
-// kIlp T + 2 kWinSlack ids.
+// global record index or kNoMatch, and the taken bits; 2 kIlp slots per
+// thread per round.  Returns this thread's match count.  win: shared memory
+// for 2 kIlp T + 2 kWinSlack ids.
 template <int T>
 __device__ __forceinline__ u32 sorted_match(const EncArgs& A, u32 p, u64 m, u64 r,
                                             const SmemTable& tb, u64* win) {
-  constexpr u64 kSpan = (u64)T * kIlp;
+  constexpr u32 kW = 2 * kIlp;  // slots per thread per round
+  constexpr u64 kSpan = (u64)T * kW;
   __shared__ long long s_d;
   __shared__ unsigned long long s_jk;
   const u64 ro = A.ref_off ? A.ref_off[p] : 0, g_lo = A.pair_off[p];
@@ -544,9 +554,9 @@ __device__ __forceinline__ u32 sorted_match(const EncArgs& A, u32 p, u64 m, u64 
     const long long ws = (long long)j0 + s_d - (long long)kWinSlack;
     const u64 wlo = ws < 0 ? 0 : ((u64)ws < m ? (u64)ws : m);
     const u64 whi = wlo + kSpan + 2 * kWinSlack < m ? wlo + kSpan + 2 * kWinSlack : m;
-    u64 x[kIlp];
+    u64 x[kW];
 #pragma unroll
-    for (u32 i = 0; i < kIlp; ++i) {
+    for (u32 i = 0; i < kW; ++i) {
       const u64 j = j0 + (u64)i * T + threadIdx.x;
       x[i] = j < r ? ref_id(A, p, ro, j) : 0;
     }
@@ -555,7 +565,7 @@ __device__ __forceinline__ u32 sorted_match(const EncArgs& A, u32 p, u64 m, u64 
     const u64 n = whi - wlo;
     u64 last = 0;  // (slot + 1) << 32 | record of this thread's last match
 #pragma unroll
-    for (u32 i = 0; i < kIlp; ++i) {
+    for (u32 i = 0; i < kW; ++i) {
       const u64 j = j0 + (u64)i * T + threadIdx.x;
       if (j >= r) continue;
       u32 k = kNoMatch;
