@@ -179,22 +179,37 @@ __global__ void __launch_bounds__(kSortThreads)
   for (u32 d = threadIdx.x; d < radix; d += blockDim.x) hist[(u64)d * n_tiles + blockIdx.x] = cnt[d];
 }
 
-// Stable scatter of one sort tile of kSortTile entries, staged in shared
-// memory.  The tile is ranked in kSortPerThread / 4 rounds: in a round warp w
-// takes 128 consecutive entries (4 sub-steps of 32, lane order), ranks equal
+// Stable scatter of one sort tile of kSortTile entries.  The tile's input
+// (keys, entry indices when given, agents) is first copied into shared memory
+// in input order by cp.async in 16-byte pieces (a ragged end, or unaligned
+// arrays, by plain loads), so the tile pays the latency of its global loads
+// once.  The tile is then ranked in kSortPerThread / 4 rounds: in a round warp
+// w takes 128 consecutive entries (4 sub-steps of 32, lane order), ranks equal
 // digits with match_any against warp-private counters, and one prefix over the
-// warps places them; every entry goes to its tile-local sorted position
-// (digit start + rank) in shared memory.  The tile is then written out in
-// sorted order, so consecutive threads write consecutive addresses of a
-// digit's run.  Each entry carries its index (vals_in == nullptr on the first
-// pass: entry i is at position i) and its agent (agents_in, read in input
-// order: the entry list's agents on the first pass, the previous pass's
-// output after it).  Every pass but the last writes both; the last writes the
-// agent as the value (vals_out[pos] = agent) and, when dest is given, the
-// entry's record index (dest[e] = pos).
+// warps places them; the tile-local sorted position of every entry (digit
+// start + rank) records the entry's place in the tile (inv).  The tile is
+// written out in sorted order, so consecutive threads write consecutive
+// addresses of a digit's run.  Each entry carries its index (vals_in ==
+// nullptr on the first pass: entry i is at position i) and its agent
+// (agents_in, read in input order: the entry list's agents on the first pass,
+// the previous pass's output after it).  Every pass but the last writes both;
+// the last writes the agent as the value (vals_out[pos] = agent) and, when
+// dest is given, the entry's record index (dest[e] = pos).  kR bounds the
+// radix (digit arrays in shared memory).
 constexpr int kSortSub = 4;  // sub-steps of 32 entries per warp and round
-constexpr size_t kSortSmem = 3 * sizeof(u32) * kSortTile;  // staged keys, entries, agents
 
+// Dynamic shared memory of a scatter: raw keys and agents, the sorted-position
+// index, and the raw entry indices when the pass reads them.
+__host__ __device__ constexpr size_t sort_smem_bytes(bool with_vals) {
+  return (with_vals ? 3 : 2) * sizeof(u32) * kSortTile + sizeof(unsigned short) * kSortTile;
+}
+
+__device__ __forceinline__ void cp_async16(u32* smem_dst, const u32* gmem_src) {
+  const unsigned dst = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" : : "r"(dst), "l"(gmem_src) : "memory");
+}
+
+template <u32 kR>
 __global__ void __launch_bounds__(kSortThreads)
     rs_scatter_kernel(const u32* __restrict__ keys_in, const u32* __restrict__ vals_in,
                       const u32* __restrict__ agents_in, u32* __restrict__ keys_out,
@@ -205,13 +220,14 @@ __global__ void __launch_bounds__(kSortThreads)
   constexpr int kWarps = kSortThreads / 32;
   constexpr int kRoundEntries = kSortThreads * kSortSub;
   extern __shared__ __align__(16) u32 sort_stage[];
-  u32* skey = sort_stage;
-  u32* sval = sort_stage + kSortTile;
-  u32* sagt = sort_stage + 2 * kSortTile;
-  __shared__ u32 base[kRadix];    // global start of each digit for this tile
-  __shared__ u32 lstart[kRadix];  // tile-local start of each digit
-  __shared__ u32 run[kRadix];     // entries of each digit placed in earlier rounds
-  __shared__ u32 wcnt[kWarps][kRadix];
+  u32* rkey = sort_stage;
+  u32* ragt = sort_stage + kSortTile;
+  unsigned short* inv = reinterpret_cast<unsigned short*>(sort_stage + 2 * kSortTile);
+  u32* rval = sort_stage + 2 * kSortTile + kSortTile / 2;  // only when vals_in != nullptr
+  __shared__ u32 base[kR];    // global start of each digit for this tile
+  __shared__ u32 lstart[kR];  // tile-local start of each digit
+  __shared__ u32 run[kR];     // entries of each digit placed in earlier rounds
+  __shared__ u32 wcnt[kWarps][kR];
   __shared__ u32 sm[33];
   const u64 E = live_entries(total_ptr, cap);
   const u64 t0 = (u64)blockIdx.x * kSortTile;
@@ -219,6 +235,23 @@ __global__ void __launch_bounds__(kSortThreads)
   const u32 tile_n = (u32)(E - t0 < (u64)kSortTile ? E - t0 : (u64)kSortTile);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const u32 lt = (1u << lane) - 1u;
+  {
+    const uintptr_t al = reinterpret_cast<uintptr_t>(keys_in) |
+                         reinterpret_cast<uintptr_t>(agents_in) |
+                         reinterpret_cast<uintptr_t>(vals_in);
+    const u32 n4 = (al & 15u) == 0 ? tile_n / 4 : 0;  // t0 is a multiple of 4096 entries
+    for (u32 c = threadIdx.x; c < n4; c += blockDim.x) {
+      cp_async16(rkey + 4 * c, keys_in + t0 + 4 * c);
+      cp_async16(ragt + 4 * c, agents_in + t0 + 4 * c);
+      if (vals_in) cp_async16(rval + 4 * c, vals_in + t0 + 4 * c);
+    }
+    asm volatile("cp.async.commit_group;" : : : "memory");
+    for (u32 li = 4 * n4 + threadIdx.x; li < tile_n; li += blockDim.x) {
+      rkey[li] = keys_in[t0 + li];
+      ragt[li] = agents_in[t0 + li];
+      if (vals_in) rval[li] = vals_in[t0 + li];
+    }
+  }
   {
     const u32 d = threadIdx.x;
     u32 c = 0;
@@ -232,19 +265,17 @@ __global__ void __launch_bounds__(kSortThreads)
     const u32 ex = block_excl_scan<u32>(c, sm, &tot);
     if (d < radix) lstart[d] = ex;
   }
+  asm volatile("cp.async.wait_all;" : : : "memory");
+  __syncthreads();
   for (u32 r0 = 0; r0 < tile_n; r0 += kRoundEntries) {  // block-uniform
     for (u32 d = lane; d < radix; d += 32) wcnt[warp][d] = 0;
     __syncwarp();
-    u32 key[kSortSub], val[kSortSub], agt[kSortSub], dig[kSortSub], rank[kSortSub];
+    u32 dig[kSortSub], rank[kSortSub];
 #pragma unroll
     for (int q = 0; q < kSortSub; ++q) {
       const u32 li = r0 + (u32)warp * (32 * kSortSub) + (u32)q * 32 + (u32)lane;
       const bool live = li < tile_n;
-      const u64 i = t0 + li;
-      key[q] = live ? keys_in[i] : 0u;
-      val[q] = live ? (vals_in ? vals_in[i] : (u32)i) : 0u;
-      agt[q] = live ? agents_in[i] : 0u;
-      dig[q] = live ? ((key[q] >> shift) & (radix - 1)) : radix;  // sentinel for padding
+      dig[q] = live ? ((rkey[li] >> shift) & (radix - 1)) : kR;  // sentinel for padding
       const u32 peers = __match_any_sync(0xFFFFFFFFu, dig[q]);
       rank[q] = (live ? wcnt[warp][dig[q]] : 0u) + __popc(peers & lt);
       __syncwarp();
@@ -264,19 +295,19 @@ __global__ void __launch_bounds__(kSortThreads)
     __syncthreads();
 #pragma unroll
     for (int q = 0; q < kSortSub; ++q) {
-      if (dig[q] < radix) {
-        const u32 lp = lstart[dig[q]] + wcnt[warp][dig[q]] + rank[q];
-        skey[lp] = key[q];
-        sval[lp] = val[q];
-        sagt[lp] = agt[q];
+      if (dig[q] < kR) {
+        const u32 li = r0 + (u32)warp * (32 * kSortSub) + (u32)q * 32 + (u32)lane;
+        inv[lstart[dig[q]] + wcnt[warp][dig[q]] + rank[q]] = (unsigned short)li;
       }
     }
     __syncthreads();
   }
-  for (u32 li = threadIdx.x; li < tile_n; li += blockDim.x) {
-    const u32 key = skey[li], v = sval[li], a = sagt[li];
+  for (u32 lp = threadIdx.x; lp < tile_n; lp += blockDim.x) {
+    const u32 src = inv[lp];
+    const u32 key = rkey[src], a = ragt[src];
+    const u32 v = vals_in ? rval[src] : (u32)(t0 + src);
     const u32 d = (key >> shift) & (radix - 1);
-    const u32 pos = base[d] + (li - lstart[d]);
+    const u32 pos = base[d] + (lp - lstart[d]);
     if (!in_bounds(st, pos, 0, E) || !in_bounds(st, v, 0, E)) continue;
     keys_out[pos] = key;
     if (last) {
@@ -340,8 +371,10 @@ tera_status radix_sort_entries(tera_ctx* ctx, const SortBufs& b, const u32* keys
   tera_status st;
   static bool smem_set = false;
   if (!smem_set) {
-    cudaFuncSetAttribute(rs_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)kSortSmem);
+    cudaFuncSetAttribute(rs_scatter_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sort_smem_bytes(true));
+    cudaFuncSetAttribute(rs_scatter_kernel<kRadix>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sort_smem_bytes(true));
     smem_set = true;
   }
   for (int pass = 0; pass < passes && cap > 0; ++pass) {
@@ -357,9 +390,15 @@ tera_status radix_sort_entries(tera_ctx* ctx, const SortBufs& b, const u32* keys
     if ((st = scan_u32(ctx, b.hist, nullptr, b.hist, (u64)radix * sort_tiles, s)) != TERA_OK)
       return st;
     prof_begin(ctx, s);
-    rs_scatter_kernel<<<(unsigned)sort_tiles, kSortThreads, kSortSmem, s>>>(
-        kin, vin, ain, kout, vout, aout, last ? dest : nullptr, last ? 1 : 0, total_ptr, cap,
-        shift, radix, b.hist, (u32)sort_tiles, ctx->d_status);
+    const size_t smem = sort_smem_bytes(vin != nullptr);
+    if (radix <= 128)
+      rs_scatter_kernel<128><<<(unsigned)sort_tiles, kSortThreads, smem, s>>>(
+          kin, vin, ain, kout, vout, aout, last ? dest : nullptr, last ? 1 : 0, total_ptr, cap,
+          shift, radix, b.hist, (u32)sort_tiles, ctx->d_status);
+    else
+      rs_scatter_kernel<kRadix><<<(unsigned)sort_tiles, kSortThreads, smem, s>>>(
+          kin, vin, ain, kout, vout, aout, last ? dest : nullptr, last ? 1 : 0, total_ptr, cap,
+          shift, radix, b.hist, (u32)sort_tiles, ctx->d_status);
     if ((st = check_launch(ctx, "rs_scatter_kernel", s)) != TERA_OK) return st;
     kin = kout;
     vin = vout;
