@@ -261,80 +261,121 @@ __device__ __forceinline__ PairFacts pair_facts(const EncArgs& E, const DecArgs&
   return f;
 }
 
-// One block, pairs in chunks of blockDim.x (pair c * blockDim.x + t to thread
-// t, coalesced): a first pass writes the per-pair facts and sums the block's
-// totals; a second pass scans each chunk (carried from chunk to chunk) into
-// the wire slab offsets, the work list (team items first, so the large pairs
-// start early, then one item per other pair, then, when small_max > 0, one
-// item per small pair: at most small_max slots, records and receiver slots;
-// each group in pair order) and the teams' first tile totals.  The counts of
-// the other and the small pairs travel packed in one word (low and high 32
-// bits) through the scans.
-__global__ void __launch_bounds__(1024)
-    bat_setup_kernel(EncArgs E, DecArgs D, BatchArgs B, u64 P, int mode,
-                     u64* __restrict__ wire_off, u64 wire_cap, u64 rec_cap, u64 recv_cap,
-                     u32* epoch, u32 T, u32 blocks, u32 gmax, u32 forced, u64 min_team, int pred,
-                     u64* __restrict__ items, u64 items_cap, u64* __restrict__ tbase,
-                     u64 tsum_cap, u64* __restrict__ n_items, u64 small_max) {
+// A pair becomes a team when its entries exceed the average per block of the
+// launch (and min_team).
+__device__ __forceinline__ u64 setup_thresh(const EncArgs& E, const DecArgs& D, u64 P, u32 blocks,
+                                            u64 min_team) {
+  const u64 total = E.pair_off[P] + (E.ref_off ? E.ref_off[P] : 0) + (D.ref_off ? D.ref_off[P] : 0);
+  const u64 avg = ceil_div(total, blocks);
+  return avg > min_team ? avg : min_team;
+}
+
+// The setup's two scanned values of a pair: (slab bytes, team tiles) and
+// (team items, work-list count word).
+__device__ __forceinline__ void setup_values(const PairFacts& f, u32 T, u64 small_max, U64x2* va,
+                                             U64x2* vb) {
+  const bool team = f.g > 1;
+  *va = U64x2{f.slab, team ? team_tiles(f.r, f.m, f.rr, T) : 0};
+  *vb = U64x2{team ? f.g : 0u, team ? 0u : single_word(f, small_max)};
+}
+
+constexpr int kSetupThreads = 1024;
+
+// Setup, first launch: one pair per thread, kSetupThreads pairs per block.
+// Writes the per-pair facts (slots, records, mode, receive offsets) and the
+// block's sums of the two scanned values (part[2b], part[2b + 1]).
+__global__ void __launch_bounds__(kSetupThreads)
+    bat_setup_sums_kernel(EncArgs E, DecArgs D, u64 P, int mode, u32 T, u32 blocks, u32 gmax,
+                          u32 forced, u64 min_team, int pred, u64 small_max,
+                          U64x2* __restrict__ part) {
   __shared__ U64x2 sm2[33];
   __shared__ u64 s_thresh;
-  if (threadIdx.x == 0) {
-    const u32 ep = *epoch + 1u;
-    *epoch = ep == 0u ? 1u : ep;
-    // a pair becomes a team when its entries exceed the average per block
-    const u64 total = E.pair_off[P] + (E.ref_off ? E.ref_off[P] : 0) +
-                      (D.ref_off ? D.ref_off[P] : 0);
-    const u64 avg = ceil_div(total, blocks);
-    s_thresh = avg > min_team ? avg : min_team;
-  }
+  if (threadIdx.x == 0) s_thresh = setup_thresh(E, D, P, blocks, min_team);
   __syncthreads();
-  const u64 thresh = s_thresh;
-  U64x2 acc_a{0, 0}, acc_b{0, 0};  // (slab bytes, team tiles), (team items, other items)
-  for (u64 c = 0; c < P; c += blockDim.x) {
-    const u64 p = c + threadIdx.x;
-    if (p >= P) continue;
-    const PairFacts f = pair_facts(E, D, p, mode, thresh, gmax, pred, forced);
+  const u64 p = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+  U64x2 va{0, 0}, vb{0, 0};
+  if (p < P) {
+    const PairFacts f = pair_facts(E, D, p, mode, s_thresh, gmax, pred, forced);
     u64* pi = E.info + p * 8;
     pi[PI_R] = f.r;
     pi[PI_M] = f.m;
     pi[PI_MODE] = f.raw ? TERA_MODE_RAW : TERA_MODE_XOR;
     D.recv_off[p] = E.pair_off[p];  // receive buffers sized by the record counts
-    acc_a += U64x2{f.slab, f.g > 1 ? team_tiles(f.r, f.m, f.rr, T) : 0};
-    acc_b += U64x2{f.g > 1 ? f.g : 0u, f.g > 1 ? 0u : single_word(f, small_max)};
+    setup_values(f, T, small_max, &va, &vb);
   }
-  U64x2 tot_a, tot_b;
-  block_excl_scan2(acc_a, sm2, &tot_a);
-  block_excl_scan2(acc_b, sm2, &tot_b);
+  U64x2 ta, tb;
+  block_excl_scan2(va, sm2, &ta);
+  block_excl_scan2(vb, sm2, &tb);
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = ta;
+    part[2 * blockIdx.x + 1] = tb;
+  }
+}
+
+// Setup, second launch (the same blocks): each block adds up the first
+// launch's block sums before it (its carry) and over all blocks (the totals),
+// then scans its pairs into the wire slab offsets, the work list (team items
+// first, so the large pairs start early, then one item per other pair, then,
+// when small_max > 0, one item per small pair: at most small_max slots,
+// records and receiver slots; each group in pair order) and the teams' first
+// tile totals.  The counts of the other and the small pairs travel packed in
+// one word (low and high 32 bits) through the scans.  The last block's thread
+// 0 writes the totals, checks the capacities and resets the claim tickets.
+__global__ void __launch_bounds__(kSetupThreads)
+    bat_setup_place_kernel(EncArgs E, DecArgs D, BatchArgs B, u64 P, int mode,
+                           u64* __restrict__ wire_off, u64 wire_cap, u64 rec_cap, u64 recv_cap,
+                           u32* epoch, u32 T, u32 blocks, u32 gmax, u32 forced, u64 min_team,
+                           int pred, u64* __restrict__ items, u64 items_cap,
+                           u64* __restrict__ tbase, u64 tsum_cap, u64* __restrict__ n_items,
+                           u64 small_max, const U64x2* __restrict__ part) {
+  __shared__ U64x2 sm2[33];
+  __shared__ u64 s_thresh;
+  if (threadIdx.x == 0) s_thresh = setup_thresh(E, D, P, blocks, min_team);
+  U64x2 ca{0, 0}, cb{0, 0}, qa{0, 0}, qb{0, 0};  // (before this block), (all blocks)
+  for (u32 i = threadIdx.x; i < gridDim.x; i += blockDim.x) {
+    const U64x2 a = part[2 * i], b = part[2 * i + 1];
+    if (i < blockIdx.x) {
+      ca += a;
+      cb += b;
+    }
+    qa += a;
+    qb += b;
+  }
+  U64x2 carry_a, carry_b, tot_a, tot_b;
+  block_excl_scan2(ca, sm2, &carry_a);
+  block_excl_scan2(cb, sm2, &carry_b);
+  block_excl_scan2(qa, sm2, &tot_a);
+  block_excl_scan2(qb, sm2, &tot_b);
   const u64 tw = tot_a.a, ttiles = tot_a.b, tbig = tot_b.a;
   const u64 n_other = tot_b.b & 0xFFFFFFFFull, n_small = tot_b.b >> 32;
   const u64 tsmall = n_other + n_small;
   const bool fits = tbig + tsmall <= items_cap && ttiles <= tsum_cap;
-  U64x2 carry_a{0, 0}, carry_b{0, 0};
-  for (u64 c = 0; c < P; c += blockDim.x) {  // block-uniform
-    const u64 p = c + threadIdx.x;
-    PairFacts f{};
-    if (p < P) f = pair_facts(E, D, p, mode, thresh, gmax, pred, forced);
-    const bool team = p < P && f.g > 1;
-    const U64x2 va{p < P ? f.slab : 0, team ? team_tiles(f.r, f.m, f.rr, T) : 0};
-    const U64x2 vb{team ? f.g : 0u, (p < P && !team) ? single_word(f, small_max) : 0u};
-    U64x2 ta, tb;
-    const U64x2 ea = carry_a + block_excl_scan2(va, sm2, &ta);
-    const U64x2 eb = carry_b + block_excl_scan2(vb, sm2, &tb);
-    carry_a += ta;
-    carry_b += tb;
-    if (p >= P) continue;
+  const u64 p = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+  PairFacts f{};
+  U64x2 va{0, 0}, vb{0, 0};
+  if (p < P) {
+    f = pair_facts(E, D, p, mode, s_thresh, gmax, pred, forced);
+    setup_values(f, T, small_max, &va, &vb);
+  }
+  U64x2 ta, tb;
+  const U64x2 ea = carry_a + block_excl_scan2(va, sm2, &ta);
+  const U64x2 eb = carry_b + block_excl_scan2(vb, sm2, &tb);
+  if (p < P) {
     wire_off[p] = ea.a;
-    if (!fits) continue;
-    if (team) {
-      for (u32 i = 0; i < f.g; ++i) items[eb.a + i] = make_item(p, i, f.g);
-      tbase[p] = ea.b;
-    } else if (single_word(f, small_max) == 1u) {
-      items[tbig + (eb.b & 0xFFFFFFFFull)] = make_item(p, 0, 1);
-    } else {
-      items[tbig + n_other + (eb.b >> 32)] = make_item(p, 0, 1);
+    if (fits) {
+      if (f.g > 1) {
+        for (u32 i = 0; i < f.g; ++i) items[eb.a + i] = make_item(p, i, f.g);
+        tbase[p] = ea.b;
+      } else if (vb.b == 1u) {
+        items[tbig + (eb.b & 0xFFFFFFFFull)] = make_item(p, 0, 1);
+      } else {
+        items[tbig + n_other + (eb.b >> 32)] = make_item(p, 0, 1);
+      }
     }
   }
-  if (threadIdx.x == 0) {
+  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) {
+    const u32 ep = *epoch + 1u;
+    *epoch = ep == 0u ? 1u : ep;
     wire_off[P] = tw;
     D.recv_off[P] = E.pair_off[P];
     bool abort = false;
@@ -2320,15 +2361,20 @@ static tera_status batched_impl(
   const u32 gmax = blocks / 2 < 64 ? (blocks / 2 > 1 ? blocks / 2 : 1) : 64;
   // pairs smaller than this stay on one block (and in shared memory if they fit)
   const u64 min_team = (u64)16 * T > 2 * (u64)table_records ? (u64)16 * T : 2 * (u64)table_records;
+  const u64 small_max = PR ? 0 : kSmallPair;
+  const unsigned setup_blocks = (unsigned)(P == 0 ? 1 : (P + kSetupThreads - 1) / kSetupThreads);
+  U64x2* part = reinterpret_cast<U64x2*>(ctx->b_part);
   prof_begin(ctx, s);
-  bat_setup_kernel<<<1, 1024, 0, s>>>(E, D, B, P, mode, reinterpret_cast<u64*>(wire_off),
-                                      wire_capacity, ctx->cap_records, recv_capacity_units,
-                                      ctx->d_epoch, T, blocks, gmax, (u32)tn.team_blocks,
-                                      min_team, PR ? 1 : 0,
-                                      ctx->b_items, ctx->b_items_cap, ctx->b_tbase,
-                                      ctx->b_tsum_cap, ctx->b_scalars + 0,
-                                      PR ? 0 : kSmallPair);
-  if ((st = check_launch(ctx, "bat_setup_kernel", s)) != TERA_OK) return st;
+  bat_setup_sums_kernel<<<setup_blocks, kSetupThreads, 0, s>>>(
+      E, D, P, mode, T, blocks, gmax, (u32)tn.team_blocks, min_team, PR ? 1 : 0, small_max, part);
+  if ((st = check_launch(ctx, "bat_setup_sums_kernel", s)) != TERA_OK) return st;
+  prof_begin(ctx, s);
+  bat_setup_place_kernel<<<setup_blocks, kSetupThreads, 0, s>>>(
+      E, D, B, P, mode, reinterpret_cast<u64*>(wire_off), wire_capacity, ctx->cap_records,
+      recv_capacity_units, ctx->d_epoch, T, blocks, gmax, (u32)tn.team_blocks, min_team,
+      PR ? 1 : 0, ctx->b_items, ctx->b_items_cap, ctx->b_tbase, ctx->b_tsum_cap,
+      ctx->b_scalars + 0, small_max, part);
+  if ((st = check_launch(ctx, "bat_setup_place_kernel", s)) != TERA_OK) return st;
   if (PR) {
     if (T == 128) return launch_persistent<128, true>(ctx, E, D, B, c, want, s);
     return launch_persistent<256, true>(ctx, E, D, B, c, want, s);

@@ -307,6 +307,8 @@ tera_status ensure_batched(tera_ctx* ctx) {
          cudaEventCreateWithFlags(&ctx->b_join, cudaEventDisableTiming) != cudaSuccess))
       return TERA_ECUDA;
     if ((st = alloc_dev(ctx->b_tbase, P)) != TERA_OK) return st;
+    // block sums of the setup's first launch: 4 words per block of 1024 pairs
+    if ((st = alloc_dev(ctx->b_part, 4 * (P / 1024 + 1))) != TERA_OK) return st;
     cudaMemset(ctx->b_scalars, 0, 6 * sizeof(u64));
   }
   if ((st = alloc_dev(ctx->b_items, items)) != TERA_OK) return st;
@@ -596,6 +598,7 @@ tera_status tera_ctx_destroy(tera_ctx* c) {
   free_dev(c->b_team);
   free_dev(c->b_tsum);
   free_dev(c->b_tbase);
+  free_dev(c->b_part);
   free_dev(c->m_tile_cnt);
   free_dev(c->m_tile_base);
   free_dev(c->m_from);

@@ -101,6 +101,7 @@ struct tera_ctx {
   tera::U64x2* b_tsum;   // per-tile totals of the team pairs
   uint64_t b_tsum_cap;
   tera::u64* b_tbase;    // [P] first tile total of each team pair
+  tera::u64* b_part;     // [4 * (P / 1024 + 1)] block sums of the setup's first launch
   // agent migration (migrate.cu)
   uint64_t m_cap_agents;   // agents the tile arrays cover
   uint64_t m_cap_leavers;  // leavers the list and sort buffers hold
