@@ -239,7 +239,7 @@ __global__ void __launch_bounds__(kSortThreads)
     const uintptr_t al = reinterpret_cast<uintptr_t>(keys_in) |
                          reinterpret_cast<uintptr_t>(agents_in) |
                          reinterpret_cast<uintptr_t>(vals_in);
-    const u32 n4 = (al & 15u) == 0 ? tile_n / 4 : 0;  // t0 is a multiple of 4096 entries
+    const u32 n4 = (al & 15u) == 0 ? tile_n / 4 : 0;  // t0 is a multiple of 4 entries
     for (u32 c = threadIdx.x; c < n4; c += blockDim.x) {
       cp_async16(rkey + 4 * c, keys_in + t0 + 4 * c);
       cp_async16(ragt + 4 * c, agents_in + t0 + 4 * c);

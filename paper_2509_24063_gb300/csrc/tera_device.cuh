@@ -40,8 +40,8 @@ constexpr int kRunAgents = 64;
 
 // Radix sort of (pair, agent) entries.
 constexpr int kSortThreads = 256;
-constexpr int kSortPerThread = 16;
-constexpr int kSortTile = kSortThreads * kSortPerThread;  // 4096
+constexpr int kSortPerThread = 12;
+constexpr int kSortTile = kSortThreads * kSortPerThread;  // 3072
 constexpr int kRadixBits = 8;
 constexpr int kRadix = 1 << kRadixBits;
 
