@@ -538,15 +538,16 @@ __device__ __forceinline__ u32 smem_match(const EncArgs& A, u32 p, u64 r, const 
 
 // ---------------- match of ascending id lists ----------------
 //
-// When the ids of a pair's message and of its reference are both strictly
-// ascending (agents kept in the order their ids were given, so that each list,
-// in agent order, is in id order), a slot's match is found without an index:
-// tile t of the reference loads the message ids from kWinSlack before to
-// kWinSlack after [j0 + d, j0 + d + T) into shared memory, d = (message index
-// - slot index) of the last match so far, and each slot searches that window
-// by bisection (a slot whose id lies outside it searches all message ids).
-// Ids that occur once on each side give exactly the matches of the index;
-// other pairs take the index.
+// When the ids of a pair's message strictly ascend (agents kept in the order
+// their ids were given, so that each list, in agent order, is in id order), a
+// slot's match is found without an index: the round of reference slots from
+// j0 (2 kIlp per thread) loads the message ids from kWinSlack before to
+// kWinSlack after [j0 + d, j0 + d + 2 kIlp T) into shared memory, d = (message
+// index - slot index) of the last match so far, and each slot searches that
+// window by bisection (a slot whose id lies outside it searches all message
+// ids).  Every slot is looked up by bisection, so the matches are the index's
+// whatever the reference order; an ascending reference keeps the searches in
+// the window.  Pairs whose message ids do not ascend take the index.
 
 constexpr u32 kWinSlack = 64;
 
