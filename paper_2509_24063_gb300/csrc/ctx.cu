@@ -1,5 +1,6 @@
 // Context, scratch memory, status word, generic scan and the in-place
 // deserialization check of libtera.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -440,6 +441,70 @@ tera_status ensure_pred(tera_ctx* ctx) {
 
 }  // namespace tera
 
+namespace tera {
+
+// The classification table of the grid (see AxisBuckets); false when the grid
+// gets none.  The device's bucket position of v differs from the true one,
+// (v - lo) * kAxisBuckets / (hi - lo), by at most: the estimate's mantissa cut
+// to 20 bits (2^-20 of |v|; only |v| <= 2 max(|lo|, |hi|) can land inside the
+// table at all), lo and the scale rounded to float (2^-24 each) and the
+// subtraction and product rounded (2^-24 of a position below kAxisBuckets);
+// twice that sum is the margin kept around every threshold.
+static bool build_axis_buckets(const tera_grid& g, const GridTables& t, AxisBuckets* b) {
+  memset(b, 0, sizeof(*b));
+  const double eps20 = std::ldexp(1.0, -20), eps24 = std::ldexp(1.0, -24);
+  for (int a = 0; a < 3; ++a) {
+    const int n = t.n[a];
+    const double lo = g.lo[a], hi = g.hi[a];
+    const double mag = std::fmax(std::fabs(lo), std::fabs(hi));
+    if (n > 32 || !(mag < 1e37)) return false;
+    const double s = (double)kAxisBuckets / (hi - lo);
+    b->flo[a] = (float)lo;
+    b->fs[a] = (float)s;
+    if (!std::isfinite(s) || !std::isfinite(b->fs[a]) || !(b->fs[a] > 0.0f)) return false;
+    const double err = 2.0 * (2.0 * mag * eps20 * s + std::fabs(lo) * eps24 * s +
+                              4.0 * kAxisBuckets * eps24) + 1e-9;
+    if (!(err < 0.25)) return false;
+    // the values where the classification can change, ascending
+    std::vector<double> th;
+    th.push_back(lo);
+    th.push_back(hi);
+    for (int k = 0; k < n; ++k) {
+      const double e0 = lo + ((hi - lo) * (double)k) / (double)n;
+      const double e1 = k + 1 == n ? hi : lo + ((hi - lo) * (double)(k + 1)) / (double)n;
+      if (k > 0) th.push_back(e0);
+      th.push_back(e0 + g.w);
+      th.push_back(e1 - g.w);
+    }
+    std::sort(th.begin(), th.end());
+    const bool wrap = (t.periodic >> a) & 1;
+    for (int j = 0; j < kAxisBuckets; ++j) {
+      const double A = lo + ((double)j - err) / s, B = lo + ((double)j + 1.0 + err) / s;
+      bool exact = !(A > lo) || !(B < hi);
+      const auto it = std::lower_bound(th.begin(), th.end(), A);
+      if (it != th.end() && *it <= B) exact = true;
+      if (exact) {
+        b->tab[a][j] = kBucketExact;
+        continue;
+      }
+      // every value of [A, B] classifies as its midpoint: the rule on the keys
+      const double v = 0.5 * (A + B);
+      uint64_t bits;
+      memcpy(&bits, &v, 8);
+      const u64 k = key_of(bits);
+      int i = 0;
+      while (i < n - 1 && k >= t.ke[a][i + 1]) ++i;
+      const u32 lowq = (i > 0 || wrap) && k < t.ktl[a][i];
+      const u32 highq = (i < n - 1 || wrap) && k >= t.kth[a][i];
+      b->tab[a][j] = (uint8_t)((u32)i << 2 | lowq | highq << 1);
+    }
+  }
+  b->on = 1;
+  return true;
+}
+
+}  // namespace tera
+
 extern "C" {
 
 const char* tera_version(void) { return "tera-gb300 1.0 (sm_103a)"; }
@@ -540,6 +605,21 @@ tera_status tera_ctx_create(tera_ctx** out, const tera_grid* grid, int device, u
     goto fail;
   }
   cudaMemcpy(c->d_grid, &t, sizeof(t), cudaMemcpyHostToDevice);
+  {
+    AxisBuckets* hb = new (std::nothrow) AxisBuckets;
+    if (!hb) {
+      st = TERA_ENOMEM;
+      goto fail;
+    }
+    if (build_axis_buckets(*grid, t, hb)) {
+      if ((st = alloc_dev(c->d_buckets, 1)) != TERA_OK) {
+        delete hb;
+        goto fail;
+      }
+      cudaMemcpy(c->d_buckets, hb, sizeof(*hb), cudaMemcpyHostToDevice);
+    }
+    delete hb;
+  }
   cudaMemset(c->d_status, 0, sizeof(DevStatus));
   cudaMemset(c->d_epoch, 0, sizeof(uint32_t));
   cudaMemset(c->d_reset, 0, c->n_pairs);
@@ -561,6 +641,7 @@ tera_status tera_ctx_destroy(tera_ctx* c) {
   cudaSetDevice(c->device);
   cudaDeviceSynchronize();
   free_dev(c->d_grid);
+  free_dev(c->d_buckets);
   free_dev(c->d_status);
   free_dev(c->d_epoch);
   free_dev(c->d_reset);

@@ -21,66 +21,131 @@ using namespace tera;
 
 namespace {
 
-// Each block classifies one tile of kClassifyTile agents.  In round k thread t
-// holds agents 512k + 2t and 512k + 2t + 1 of the tile (one 16-byte load per
-// coordinate), so every warp load is fully coalesced, and each warp covers a
-// run of kRunAgents consecutive agents per round; the number of (agent, pair)
-// entries of every run is written (runs are in agent order).
+// One axis by the bucket table when the coordinate's bucket holds an answer,
+// else by the exact key comparisons.  The estimate is taken only for
+// magnitudes in the float normal range (2^-126 <= |v| < 2^128, which also
+// sends NaN and infinities to the exact path).
+__device__ __forceinline__ u32 classify_axis_table(u64 bits, int a, const SmemGrid& s,
+                                                   const uint8_t* tab, float flo, float fs,
+                                                   int* idx) {
+  const u32 hi = (u32)(bits >> 32);
+  const u32 ha = hi & 0x7FFFFFFFu;
+  if (ha - 0x38100000u < 0x0FE00000u) {
+    const float af = __uint_as_float((hi & 0x80000000u) | ((ha - 0x38000000u) << 3));
+    const int j = __float2int_rz((af - flo) * fs);
+    if ((u32)j < (u32)kAxisBuckets) {
+      const u32 e = tab[j];
+      if (!(e & kBucketExact)) {
+        *idx = (int)(e >> 2);
+        return 2u | (e & 1u) | ((e & 2u) << 1);
+      }
+    }
+  }
+  return classify_axis(bits, a, s, idx);
+}
+
+// classify_agent with the bucket tables in shared memory (tab: three axes of
+// kAxisBuckets entries).
+__device__ __forceinline__ void classify_agent_table(u64 bx, u64 by, u64 bz, const SmemGrid& s,
+                                                     const uint8_t* tab, const float* flo,
+                                                     const float* fs, int* owner, u32* mask,
+                                                     bool* ok) {
+  int ix, iy, iz;
+  const u32 ox = classify_axis_table(bx, 0, s, tab, flo[0], fs[0], &ix);
+  const u32 oy = classify_axis_table(by, 1, s, tab + kAxisBuckets, flo[1], fs[1], &iy);
+  const u32 oz = classify_axis_table(bz, 2, s, tab + 2 * kAxisBuckets, flo[2], fs[2], &iz);
+  *ok = ox && oy && oz;
+  if (!*ok) {
+    *owner = -1;
+    *mask = 0;
+    return;
+  }
+  *owner = ix + s.n[0] * (iy + s.n[1] * iz);
+  const u32 m = ox * spread3(oy, 3) * spread3(oz, 9);
+  *mask = m & ~(1u << 13);
+}
+
+// Each block classifies tiles of kClassifyTile agents (tile blockIdx.x, then
+// every gridDim.x-th: the grid holds the blocks resident at once, so the grid
+// rows and the bucket tables are copied into shared memory once per block).
+// In round k of a tile, thread t holds agents 512k + 2t and 512k + 2t + 1 (one
+// 16-byte load per coordinate), so every warp load is fully coalesced, and
+// each warp covers a run of kRunAgents consecutive agents per round; the
+// number of (agent, pair) entries of every run is written (runs are in agent
+// order).  bk == nullptr: every agent takes the exact key comparisons.
 __global__ void __launch_bounds__(kClassifyThreads, 6)
     classify_kernel(const u64* __restrict__ x, const u64* __restrict__ y,
                     const u64* __restrict__ z, u64 n, const GridTables* __restrict__ g,
-                    int* __restrict__ owner, u32* __restrict__ mask, u32* __restrict__ run_cnt,
-                    u64 n_runs, DevStatus* st, DevStats* stats) {
+                    const AxisBuckets* __restrict__ bk, u64 n_tiles, int* __restrict__ owner,
+                    u32* __restrict__ mask, u32* __restrict__ run_cnt, u64 n_runs, DevStatus* st,
+                    DevStats* stats) {
   __shared__ SmemGrid sg;
+  __shared__ float s_flo[3], s_fs[3];
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     stats->iterations += 1;
     stats->agents += n;
   }
-  load_grid(sg, g);
+  // the tables follow the grid rows (a multiple of 32 bytes) in dynamic shared memory
+  uint8_t* tab = reinterpret_cast<uint8_t*>(grid_rows() + (g->n[0] + g->n[1] + g->n[2]));
+  if (bk) {
+    const uint4* src = reinterpret_cast<const uint4*>(bk->tab);
+    uint4* dst = reinterpret_cast<uint4*>(tab);
+    for (int i = threadIdx.x; i < 3 * kAxisBuckets / 16; i += blockDim.x) dst[i] = src[i];
+    if (threadIdx.x < 3) {
+      s_flo[threadIdx.x] = bk->flo[threadIdx.x];
+      s_fs[threadIdx.x] = bk->fs[threadIdx.x];
+    }
+  }
+  load_grid(sg, g);  // ends with a block barrier
   const int lane = threadIdx.x & 31;
-  const u64 tile0 = (u64)blockIdx.x * kClassifyTile;
   bool bad = false;
+  for (u64 tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    const u64 tile0 = tile * kClassifyTile;
 #pragma unroll
-  for (int k = 0; k < kClassifyPerThread / 2; ++k) {
-    const u64 a0 = tile0 + (u64)k * (2 * kClassifyThreads) + 2u * threadIdx.x;
-    u64 vx[2], vy[2], vz[2];
-    if (a0 + 1 < n) {
-      ulonglong2 tx = *reinterpret_cast<const ulonglong2*>(x + a0);
-      ulonglong2 ty = *reinterpret_cast<const ulonglong2*>(y + a0);
-      ulonglong2 tz = *reinterpret_cast<const ulonglong2*>(z + a0);
-      vx[0] = tx.x; vx[1] = tx.y; vy[0] = ty.x; vy[1] = ty.y; vz[0] = tz.x; vz[1] = tz.y;
-    } else {
+    for (int k = 0; k < kClassifyPerThread / 2; ++k) {
+      const u64 a0 = tile0 + (u64)k * (2 * kClassifyThreads) + 2u * threadIdx.x;
+      u64 vx[2], vy[2], vz[2];
+      if (a0 + 1 < n) {
+        ulonglong2 tx = *reinterpret_cast<const ulonglong2*>(x + a0);
+        ulonglong2 ty = *reinterpret_cast<const ulonglong2*>(y + a0);
+        ulonglong2 tz = *reinterpret_cast<const ulonglong2*>(z + a0);
+        vx[0] = tx.x; vx[1] = tx.y; vy[0] = ty.x; vy[1] = ty.y; vz[0] = tz.x; vz[1] = tz.y;
+      } else {
 #pragma unroll
-      for (int q = 0; q < 2; ++q) {
-        if (a0 + q < n) {
-          vx[q] = x[a0 + q]; vy[q] = y[a0 + q]; vz[q] = z[a0 + q];
-        } else {
-          vx[q] = vy[q] = vz[q] = 0ull;
+        for (int q = 0; q < 2; ++q) {
+          if (a0 + q < n) {
+            vx[q] = x[a0 + q]; vy[q] = y[a0 + q]; vz[q] = z[a0 + q];
+          } else {
+            vx[q] = vy[q] = vz[q] = 0ull;
+          }
         }
       }
-    }
-    int o[2];
-    u32 m[2];
-    u32 cnt = 0;
+      int o[2];
+      u32 m[2];
+      u32 cnt = 0;
 #pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      bool ok;
-      classify_agent(vx[q], vy[q], vz[q], sg, &o[q], &m[q], &ok);
-      if (a0 + q < n) {
-        bad |= !ok;
-        cnt += __popc(m[q]);
+      for (int q = 0; q < 2; ++q) {
+        bool ok;
+        if (bk)
+          classify_agent_table(vx[q], vy[q], vz[q], sg, tab, s_flo, s_fs, &o[q], &m[q], &ok);
+        else
+          classify_agent(vx[q], vy[q], vz[q], sg, &o[q], &m[q], &ok);
+        if (a0 + q < n) {
+          bad |= !ok;
+          cnt += __popc(m[q]);
+        }
       }
+      if (a0 + 1 < n) {
+        *reinterpret_cast<int2*>(owner + a0) = make_int2(o[0], o[1]);
+        *reinterpret_cast<uint2*>(mask + a0) = make_uint2(m[0], m[1]);
+      } else if (a0 < n) {
+        owner[a0] = o[0];
+        mask[a0] = m[0];
+      }
+      cnt = warp_sum(cnt);
+      const u64 run = (a0 - 2u * lane) / kRunAgents;
+      if (lane == 0 && run < n_runs) run_cnt[run] = cnt;
     }
-    if (a0 + 1 < n) {
-      *reinterpret_cast<int2*>(owner + a0) = make_int2(o[0], o[1]);
-      *reinterpret_cast<uint2*>(mask + a0) = make_uint2(m[0], m[1]);
-    } else if (a0 < n) {
-      owner[a0] = o[0];
-      mask[a0] = m[0];
-    }
-    cnt = warp_sum(cnt);
-    const u64 run = (a0 - 2u * lane) / kRunAgents;
-    if (lane == 0 && run < n_runs) run_cnt[run] = cnt;
   }
   if (bad) latch(st, TERA_EDOMAIN);
 }
@@ -435,11 +500,21 @@ extern "C" tera_status tera_partition(tera_ctx* ctx, const tera_soa* soa, tera_p
   const u64 blocks = n == 0 ? 1 : (n + kClassifyTile - 1) / kClassifyTile;
   const u64 runs = n == 0 ? 1 : (n + kRunAgents - 1) / kRunAgents;
   if (n == 0) cudaMemsetAsync(ctx->tile_cnt, 0, sizeof(u32), s);
+  // resident blocks only (6 per SM): each copies the tables into shared memory once
+  const size_t csmem =
+      grid_smem_bytes(ctx->grid) + (ctx->d_buckets ? 3 * (size_t)kAxisBuckets : 0);
+  static bool csmem_set = false;
+  if (!csmem_set) {
+    cudaFuncSetAttribute(classify_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(sizeof(BoxKeys) * 3 * kMaxAxis + 3 * (size_t)kAxisBuckets));
+    csmem_set = true;
+  }
+  const u64 cgrid = blocks < (u64)ctx->num_sms * 6 ? blocks : (u64)ctx->num_sms * 6;
   prof_begin(ctx, s);
-  classify_kernel<<<(unsigned)blocks, kClassifyThreads, grid_smem_bytes(ctx->grid), s>>>(
+  classify_kernel<<<(unsigned)cgrid, kClassifyThreads, csmem, s>>>(
       reinterpret_cast<const u64*>(soa->x), reinterpret_cast<const u64*>(soa->y),
-      reinterpret_cast<const u64*>(soa->z), n, ctx->d_grid, out->owner, out->mask, ctx->tile_cnt,
-      runs, ctx->d_status, ctx->d_stats);
+      reinterpret_cast<const u64*>(soa->z), n, ctx->d_grid, ctx->d_buckets, blocks, out->owner,
+      out->mask, ctx->tile_cnt, runs, ctx->d_status, ctx->d_stats);
   if ((st = check_launch(ctx, "classify_kernel", s)) != TERA_OK) return st;
   if ((st = scan_u32(ctx, ctx->tile_cnt, ctx->tile_base, nullptr, runs, s)) != TERA_OK)
     return st;

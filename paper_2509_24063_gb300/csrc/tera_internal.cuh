@@ -2,6 +2,8 @@
 // device-side helpers (tera_device.cuh) and the host-side context.
 #pragma once
 
+#include <cstddef>
+
 #include <nvtx3/nvToolsExt.h>
 
 #include "tera_device.cuh"
@@ -20,6 +22,27 @@ struct CallRange {
 
 #define TERA_CALL_RANGE(name) ::tera::CallRange tera_call_range_(name)
 
+namespace tera {
+// Classification by table (the partition's classify_kernel).  Each axis's
+// domain [lo, hi) is cut into kAxisBuckets equal buckets.  The device places
+// a coordinate v in bucket j = trunc((approx_f32(v) - flo) * fs); the host
+// bounds how far that estimate can stray from v's true place and stores, for
+// every bucket that no threshold value (lo, hi, a box edge, e[k] + w,
+// e[k+1] - w) can reach within that bound, what every v placed there gets:
+// the box index (bits 2..6) and the aura offsets -1 (bit 0) and +1 (bit 1).
+// Other buckets hold kBucketExact, and those agents take the exact key
+// comparisons.  The table exists when every axis has at most 32 boxes and the
+// estimate's error stays under a quarter bucket (on == 0 otherwise).
+constexpr int kAxisBuckets = 8192;
+constexpr uint8_t kBucketExact = 0x80;
+struct AxisBuckets {
+  int on;
+  float flo[3], fs[3];
+  alignas(16) uint8_t tab[3][kAxisBuckets];  // copied to shared memory in 16-byte pieces
+};
+static_assert(offsetof(AxisBuckets, tab) % 16 == 0, "bucket tables are read as 16-byte vectors");
+}  // namespace tera
+
 // The context (host side).
 struct tera_ctx {
   int device;
@@ -32,6 +55,7 @@ struct tera_ctx {
   uint64_t iterations;
 
   tera::GridTables* d_grid;
+  tera::AxisBuckets* d_buckets;  // null when classification has no table
   tera::DevStatus* d_status;
   tera::DevStatus* h_status;  // pinned
   uint32_t* d_epoch;
