@@ -486,6 +486,27 @@ tera_status tera_migrate_recv(tera_ctx* ctx, const uint8_t* arena, uint64_t aren
 tera_status tera_ref_schedule(uint64_t t, uint32_t ref_interval, int32_t* out_buf,
                               int32_t* ref_buf, uint64_t* ref_iteration);
 
+/* Buckets per axis of the classification tables (tera_axis_buckets). */
+#define TERA_AXIS_BUCKETS 8192
+
+/* The classification tables a context of this grid uses in tera_partition
+ * (Sec. 2.1, "Aura Update": an agent's owner box and the neighbours whose
+ * aura holds it, per axis; Sec. 2.4.1: the partitioning grid).  Host-only
+ * arithmetic, no device work; the result of the classification never depends
+ * on them.  Axis a's domain [lo, hi) is cut into TERA_AXIS_BUCKETS buckets.
+ * The device places a coordinate v (only when 2^-126 <= |v| < 2^128) in bucket
+ * j = trunc((f - flo[a]) * fs[a]), in float32 arithmetic, f being v's binary64
+ * value with its mantissa cut to 20 bits.  tab[a * TERA_AXIS_BUCKETS + j] is
+ * 0x80 when the exact comparisons decide for the values placed in bucket j,
+ * else (i << 2) | q for every value placed there: i the box index along the
+ * axis, q bit 0 when the aura of the neighbour at offset -1 holds v, bit 1 for
+ * offset +1.  *on = 0 (tab, flo, fs untouched) when the grid gets no tables:
+ * an axis of more than 32 boxes, or a domain whose float estimate is too
+ * coarse for its bucket width.  tab (3 * TERA_AXIS_BUCKETS bytes), flo and fs
+ * (3 floats each) and on are caller-owned.  TERA_EINVAL when a pointer is
+ * NULL or tera_ctx_create would reject the grid. */
+tera_status tera_axis_buckets(const tera_grid* grid, uint8_t* tab, float* flo, float* fs, int* on);
+
 /* Cell boundaries of one axis of the predictor's cell grid (the ncount
  * feature above; cells of width w from lo, cell(x) = floor((x - lo) / w) in
  * binary64).  Host-only arithmetic, no device work: the library builds these

@@ -114,6 +114,7 @@ SIGNATURES = {
     "tera_ref_schedule": (C.c_int, [u64, u32, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                                     C.POINTER(C.c_uint64)]),
     "tera_cell_thresholds": (C.c_int, [C.c_double, C.c_double, C.c_double, u64, P]),
+    "tera_axis_buckets": (C.c_int, [C.POINTER(Grid), P, P, P, C.POINTER(C.c_int)]),
 }
 
 _lock = threading.Lock()

@@ -113,6 +113,30 @@ def cell_thresholds(lo: float, hi: float, w: float):
     return out
 
 
+AXIS_BUCKETS = 8192  # TERA_AXIS_BUCKETS
+
+
+def axis_buckets(lo, hi, n, w, periodic: int = 0):
+    """tera_axis_buckets: (tab, flo, fs) of the grid's classification tables
+    (tab: uint8 array of shape (3, AXIS_BUCKETS); flo, fs: float32 arrays of 3),
+    or None when the grid gets no tables."""
+    import numpy as np
+    g = Grid()
+    for a in range(3):
+        g.lo[a], g.hi[a], g.n[a] = float(lo[a]), float(hi[a]), int(n[a])
+    g.w = float(w)
+    g.periodic = int(periodic)
+    tab = np.zeros((3, AXIS_BUCKETS), dtype=np.uint8)
+    flo = np.zeros(3, dtype=np.float32)
+    fs = np.zeros(3, dtype=np.float32)
+    on = C.c_int(0)
+    check(_lib.load().tera_axis_buckets(C.byref(g), tab.ctypes.data_as(C.c_void_p),
+                                        flo.ctypes.data_as(C.c_void_p),
+                                        fs.ctypes.data_as(C.c_void_p), C.byref(on)),
+          "tera_axis_buckets")
+    return (tab, flo, fs) if on.value else None
+
+
 class Context:
     """One partitioning grid on one GPU (owns scratch, hash table, status word)."""
 

@@ -443,6 +443,46 @@ tera_status ensure_pred(tera_ctx* ctx) {
 
 namespace tera {
 
+// The key tables of a grid (and its cell counts per axis); TERA_EINVAL for a
+// grid tera_ctx_create rejects.
+static tera_status grid_tables(const tera_grid* grid, GridTables* tp, uint64_t ncell[3]) {
+  GridTables& t = *tp;
+  if (grid->reserved != 0 || (grid->periodic & ~7u) != 0) return TERA_EINVAL;
+  memset(&t, 0, sizeof(t));
+  auto key = [](double d) {
+    uint64_t b;
+    memcpy(&b, &d, 8);
+    return key_of(b);
+  };
+  for (int a = 0; a < 3; ++a) {
+    int n = grid->n[a];
+    if (n < 1 || n > kMaxAxis) return TERA_EINVAL;
+    if ((grid->periodic >> a & 1u) && n < 3) return TERA_EINVAL;
+    if (!(grid->lo[a] < grid->hi[a])) return TERA_EINVAL;
+    if (!std::isfinite(grid->lo[a]) || !std::isfinite(grid->hi[a])) return TERA_EINVAL;
+    double lo = grid->lo[a], hi = grid->hi[a];
+    std::vector<double> e((size_t)n + 1);
+    for (int k = 0; k < n; ++k) e[k] = lo + ((hi - lo) * (double)k) / (double)n;
+    e[n] = hi;
+    if (!(grid->w > 0.0)) return TERA_EINVAL;
+    for (int k = 0; k <= n; ++k) t.ke[a][k] = key(e[k]);
+    for (int k = 0; k < n; ++k) {
+      if (!(grid->w < e[k + 1] - e[k])) return TERA_EINVAL;
+      t.ktl[a][k] = key(e[k] + grid->w);
+      t.kth[a][k] = key(e[k + 1] - grid->w);
+    }
+    t.klo[a] = key(lo);
+    t.khi[a] = key(hi);
+    t.n[a] = n;
+    t.periodic = (int)grid->periodic;
+    // only a starting guess: the index is fixed by exact key comparisons
+    t.flo[a] = (float)lo;
+    t.fscale[a] = (float)((double)n / (hi - lo));
+    ncell[a] = (uint64_t)std::floor((hi - lo) / grid->w) + 1;
+  }
+  return TERA_OK;
+}
+
 // The classification table of the grid (see AxisBuckets); false when the grid
 // gets none.  The device's bucket position of v differs from the true one,
 // (v - lo) * kAxisBuckets / (hi - lo), by at most: the estimate's mantissa cut
@@ -519,6 +559,29 @@ tera_status tera_cell_thresholds(double lo, double hi, double w, uint64_t n, uin
   return TERA_OK;
 }
 
+tera_status tera_axis_buckets(const tera_grid* grid, uint8_t* tab, float* flo, float* fs,
+                              int* on) {
+  if (!grid || !tab || !flo || !fs || !on) return TERA_EINVAL;
+  GridTables* t = new (std::nothrow) GridTables;
+  AxisBuckets* b = new (std::nothrow) AxisBuckets;
+  tera_status st = (t && b) ? TERA_OK : TERA_ENOMEM;
+  uint64_t ncell[3];
+  if (st == TERA_OK) st = grid_tables(grid, t, ncell);
+  if (st == TERA_OK) {
+    *on = build_axis_buckets(*grid, *t, b) ? 1 : 0;
+    if (*on) {
+      memcpy(tab, b->tab, sizeof(b->tab));
+      for (int a = 0; a < 3; ++a) {
+        flo[a] = b->flo[a];
+        fs[a] = b->fs[a];
+      }
+    }
+  }
+  delete t;
+  delete b;
+  return st;
+}
+
 tera_status tera_ref_schedule(uint64_t t, uint32_t ref_interval, int32_t* out_buf,
                               int32_t* ref_buf, uint64_t* ref_iteration) {
   if (ref_interval < 1 || !out_buf) return TERA_EINVAL;
@@ -542,41 +605,10 @@ uint64_t tera_ctx_launches(const tera_ctx* ctx) { return ctx ? ctx->launches : 0
 tera_status tera_ctx_create(tera_ctx** out, const tera_grid* grid, int device, uint32_t class_id) {
   if (!out || !grid) return TERA_EINVAL;
   *out = nullptr;
-  if (grid->reserved != 0 || (grid->periodic & ~7u) != 0) return TERA_EINVAL;
   GridTables t;
-  memset(&t, 0, sizeof(t));
   uint64_t ncell_tmp[3] = {1, 1, 1};
-  auto key = [](double d) {
-    uint64_t b;
-    memcpy(&b, &d, 8);
-    return key_of(b);
-  };
-  for (int a = 0; a < 3; ++a) {
-    int n = grid->n[a];
-    if (n < 1 || n > kMaxAxis) return TERA_EINVAL;
-    if ((grid->periodic >> a & 1u) && n < 3) return TERA_EINVAL;
-    if (!(grid->lo[a] < grid->hi[a])) return TERA_EINVAL;
-    if (!std::isfinite(grid->lo[a]) || !std::isfinite(grid->hi[a])) return TERA_EINVAL;
-    double lo = grid->lo[a], hi = grid->hi[a];
-    std::vector<double> e((size_t)n + 1);
-    for (int k = 0; k < n; ++k) e[k] = lo + ((hi - lo) * (double)k) / (double)n;
-    e[n] = hi;
-    if (!(grid->w > 0.0)) return TERA_EINVAL;
-    for (int k = 0; k <= n; ++k) t.ke[a][k] = key(e[k]);
-    for (int k = 0; k < n; ++k) {
-      if (!(grid->w < e[k + 1] - e[k])) return TERA_EINVAL;
-      t.ktl[a][k] = key(e[k] + grid->w);
-      t.kth[a][k] = key(e[k + 1] - grid->w);
-    }
-    t.klo[a] = key(lo);
-    t.khi[a] = key(hi);
-    t.n[a] = n;
-    t.periodic = (int)grid->periodic;
-    // only a starting guess: the index is fixed by exact key comparisons
-    t.flo[a] = (float)lo;
-    t.fscale[a] = (float)((double)n / (hi - lo));
-    ncell_tmp[a] = (uint64_t)std::floor((hi - lo) / grid->w) + 1;
-  }
+  const tera_status gst = grid_tables(grid, &t, ncell_tmp);
+  if (gst != TERA_OK) return gst;
   if (cudaSetDevice(device) != cudaSuccess) return TERA_ECUDA;
   tera_ctx* c = new (std::nothrow) tera_ctx();
   if (!c) return TERA_ENOMEM;

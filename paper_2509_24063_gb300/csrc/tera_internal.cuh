@@ -33,7 +33,7 @@ namespace tera {
 // Other buckets hold kBucketExact, and those agents take the exact key
 // comparisons.  The table exists when every axis has at most 32 boxes and the
 // estimate's error stays under a quarter bucket (on == 0 otherwise).
-constexpr int kAxisBuckets = 8192;
+constexpr int kAxisBuckets = TERA_AXIS_BUCKETS;
 constexpr uint8_t kBucketExact = 0x80;
 struct AxisBuckets {
   int on;
