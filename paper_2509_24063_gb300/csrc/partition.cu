@@ -5,14 +5,17 @@
 // Kernels:
 //   classify_kernel  one pass over x,y,z (coalesced 16-byte loads): owner box,
 //                    26-bit aura mask, count of (agent, pair) entries of every
-//                    run of 64 consecutive agents
+//                    run of 64 consecutive agents; per axis a bucket table in
+//                    shared memory answers most coordinates, the exact key
+//                    comparisons the rest
 //   emit_kernel      stable compaction of the entries in agent order (warp
 //                    scans inside a run, run bases from a scan)
 //   rs_hist_kernel / rs_scatter_kernel
 //                    stable LSD radix sort of the entry indices by pair
-//                    index, so each pair's list keeps ascending agent order;
-//                    the last pass writes the agent of every record and the
-//                    record index of every entry (pack reads in agent order)
+//                    index, so each pair's list keeps ascending agent order
+//                    (tiles staged into shared memory by cp.async); the last
+//                    pass writes the agent of every record and the record
+//                    index of every entry (pack reads in agent order)
 //   pair_off_kernel  per-pair counts and offsets from the sorted keys
 #include "classify.cuh"
 #include "tera_internal.cuh"
