@@ -1,5 +1,7 @@
 // Batched codec: steps a3-a5 (paper Sec. 2.3, steps B, C and D) for every
-// pair of one iteration in ONE persistent launch.
+// pair of one iteration in ONE persistent launch (on the plain path the small
+// pairs run in a second launch of one-warp blocks beside it), after a setup
+// of two short launches that lays out the wire slabs and the work list.
 //
 // Each block takes whole pairs (an atomic ticket over the work list, claimed
 // whenever the block is free) and carries a pair through every step on its
@@ -10,8 +12,9 @@
 //           the message records the slots take.  A pair with at most
 //           table_records (<= 8191) records does this in a shared-memory hash
 //           table (u16 entries: (record + 1) << 3 | 3-bit fingerprint, ids
-//           compared against word 0 of the message's records); larger pairs
-//           (and the predictor path) use the pair's global hash segment.
+//           compared against word 0 of the message's records), or, when the
+//           message's ids ascend, by a windowed bisection over them with no
+//           table; larger pairs use the pair's global hash segment.
 //   slots   difference, code, payload and new-reference record of every slot
 //           (tiles of T slots; payload positions from a running prefix kept
 //           on chip; the wire puts the slot payload after all r + n_new codes,
